@@ -1,0 +1,364 @@
+"""Benchmark of the EconoJax hot path on GB300.
+
+Workload (the env_step throughput configuration): E = 1024 environments x
+A = 100 population agents + 1 government, 2 resources, 1000-step episodes,
+tax period 100, uniform random seeded actions.  One benchmark step = one
+whole episode: env_step with n_steps = 1000 in one launch, inputs (actions,
+gather draws, tie-break keys, rate levels; 1.2 GB) resident in HBM, every
+output written (rewards, done flags, observations, government observations,
+masks; 11 GB).  Inputs and outputs are far larger than L2, so no flush.
+
+Metric: population agent-steps per second (E * A * 1000 per benchmark step).
+
+--impl reference times the CPU oracle (the plain C statement of the rules,
+test infrastructure) on the host cores on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "agent-steps/sec (env_step and full rollout) on 1 GB300; PPO updates/sec BF16 vs FP32"
+UNIT = "agent-steps/s"
+E, A, T_EP, T_TAX = 1024, 100, 1000, 100
+CONFIG = {"workload": "env_step E=1024 x A=100 (+1 government), R=2, P=5, 1000-step episode, "
+                      "tax period 100, uniform random seeded actions; one benchmark step = one episode "
+                      "in one launch",
+          "E": E, "A": A, "episode": T_EP, "tax_period": T_TAX,
+          "l2": "inputs (1.2 GB) and outputs (11 GB) per step far larger than L2; no flush"}
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes_per_launch(sizes, n_steps, state_bytes):
+    """Bytes env_step must move per launch: streamed inputs and outputs per
+    agent-step and per environment-step, plus one load and one store of the
+    state per launch."""
+    D, G, W = sizes.obs_dim, sizes.gobs_dim, sizes.mask_words
+    per_agent_step = 4 + 4 + 4 + 4 + 4 * D + 4 * W           # act, gather u, tie-break key, reward, obs, mask
+    per_env_step = 4 + 1 + 4 * G                              # government reward, done, government obs
+    gov_in = (n_steps // T_TAX) * 3 * 4                       # rate levels read at period starts
+    return n_steps * E * (A * per_agent_step + per_env_step) + E * gov_in + 2 * state_bytes
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2410_22165_gb300 import VecEnv
+    from paper_2410_22165_gb300 import build as cuda_build
+
+    rank, world, local = _dist()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        cuda_build.build()
+    if world > 1:
+        dist.barrier()
+
+    seed = 1000 + rank                     # replicas: each rank runs its own environments
+    env = VecEnv(E, A, device=dev, T_ep=T_EP, T_tax=T_TAX)
+    env.reset(seed=seed)
+    d = env.fill_draws(seed=seed, g0=0, n_steps=T_EP)
+    out = env.alloc_outputs(T_EP)
+    stream = torch.cuda.current_stream(dev)
+
+    def one_step():
+        env.step(T_EP, act=d["act"], gov_act=d["gov_act"], gather_u=d["gather_u"], tb=d["tb"], out=out)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        time.sleep(0.4)
+        torch.cuda.synchronize(dev)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(args.steps):
+            starts[k].record(stream)
+            one_step()
+            ends[k].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+    total_ms = t0.elapsed_time(t1)
+    launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        dist.barrier()
+
+    agent_steps = E * A * T_EP * args.steps * world
+    value = agent_steps / (total_ms / 1e3)
+
+    # end to end through the public API: pinned host inputs -> device, episode, outputs -> host
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(env, d, out, args, dev, world)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return None
+    peak, peak_kind = _peaks()
+    bytes_launch = algorithmic_bytes_per_launch(env.sizes, T_EP, env.sizes.state_bytes)
+    avg_launch_s = statistics.mean(launch_ms) / 1e3
+    achieved = bytes_launch / avg_launch_s / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+i32",
+        "data": "synthetic (Philox-4x32-10 seeded draws)", "config": dict(CONFIG, replicas=world),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
+                     "traffic": None, "algorithmic_bytes_per_launch": bytes_launch,
+                     "kernel": "env_kernel<128>", "launch_ms": statistics.mean(launch_ms)},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if world > 1:
+        dist.destroy_process_group()
+    return line
+
+
+def run_e2e(env, d, out, args, dev, world):
+    """Same metric, through VecEnv.step with host buffers: each step copies its
+    inputs from pinned host memory and all its outputs back, in 100-step chunks."""
+    import torch
+
+    chunk = 100
+    host_in = {k: v.cpu().pin_memory() for k, v in d.items()}
+    host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
+    dev_in = {k: torch.empty((chunk,) + tuple(v.shape[1:]), dtype=v.dtype, device=dev) for k, v in d.items()}
+    dev_out = env.alloc_outputs(chunk)
+    h2d = sum(v.numel() * v.element_size() for v in host_in.values())
+    d2h = sum(v.numel() * v.element_size() for v in host_out.values())
+
+    def one():
+        for s in range(0, T_EP, chunk):
+            for k, v in dev_in.items():
+                v.copy_(host_in[k][s:s + chunk], non_blocking=True)
+            env.step(chunk, act=dev_in["act"], gov_act=dev_in["gov_act"], gather_u=dev_in["gather_u"],
+                     tb=dev_in["tb"], out=dev_out)
+            for k, v in dev_out.items():
+                host_out[k][s:s + chunk].copy_(v, non_blocking=True)
+
+    steps = max(1, min(args.steps, 3))
+    one()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    return {"value": E * A * T_EP * steps * world / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": steps,
+            "how": "VecEnv.step on 100-step chunks: pinned host inputs copied in, all outputs copied out"}
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def _oracle_episode(e, seed, n_steps):
+    import synth
+    from oracle.env import OracleEnv, default_params
+
+    p = default_params(T_ep=T_EP, T_tax=T_TAX)
+    o = OracleEnv(p, A)
+    inp = synth.episode_inputs(seed, [e], A, p["R"], p["nb"], o.nA, p["tax_levels"], n_steps, p["T_ep"])
+    o.reset(inp["sg0"][0], inp["sc0"][0])
+    t0 = time.perf_counter()
+    o.run(inp["act"][:, 0], inp["gov_act"][:, 0], inp["gather_u"][:, 0], inp["tb"][:, 0],
+          inp["later_sg"][:, 0], inp["later_sc"][:, 0], outputs=True)
+    return time.perf_counter() - t0
+
+
+def oracle_throughput(target_s: float):
+    """Runs whole oracle episodes (A = 100, 1000 steps) on all host cores in
+    threads (the C oracle releases the GIL) for about target_s seconds."""
+    import concurrent.futures as cf
+
+    from oracle import build as oracle_build
+
+    oracle_build.build()
+    cores = os.cpu_count() or 1
+    probe = _oracle_episode(0, 0, 100)             # seconds per 100 steps of one environment
+    per_env = probe * (T_EP / 100)
+    n_env = max(cores, int(round(target_s * cores / max(per_env, 1e-3) / cores)) * cores)
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(lambda e: _oracle_episode(e, 0, T_EP), range(n_env)))
+    wall = time.perf_counter() - t0
+    value = n_env * A * T_EP / wall
+    sample = f"{n_env} environments x A={A} x {T_EP} steps (whole episodes, all outputs), {wall:.1f} s wall"
+    return value, cores, sample
+
+
+def cpu_baseline(target_s):
+    value, cores, sample = oracle_throughput(target_s)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return None
+    per_step = []
+    for _ in range(args.warmup):
+        oracle_throughput(args.ref_seconds)
+    for _ in range(args.steps):
+        v, cores, sample = oracle_throughput(args.ref_seconds)
+        per_step.append(v)
+    value = statistics.mean(per_step)
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 mirror",
+        "data": "synthetic (Philox-4x32-10 seeded draws)", "config": CONFIG,
+        "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": value, "unit": UNIT},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def run_profile_case(args):
+    """Small case for profilers: E = 1024 x A = 100, 100-step launches (inputs
+    123 MB, outputs 1.1 GB: larger than L2, a few GB on the device)."""
+    import torch
+
+    from paper_2410_22165_gb300 import VecEnv
+
+    n = 100
+    env = VecEnv(E, A, device="cuda", T_ep=T_EP, T_tax=T_TAX)
+    env.reset(seed=7)
+    d = env.fill_draws(seed=7, g0=0, n_steps=n)
+    out = env.alloc_outputs(n)
+    ms = []
+    for k in range(args.warmup + args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        env.step(n, act=d["act"], gov_act=d["gov_act"], gather_u=d["gather_u"], tb=d["tb"], out=out)
+        b.record()
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            ms.append(a.elapsed_time(b))
+    bytes_launch = algorithmic_bytes_per_launch(env.sizes, n, env.sizes.state_bytes)
+    print(json.dumps({"profile_case": "E=1024 A=100 n_steps=100", "launch_ms": ms,
+                      "algorithmic_bytes_per_launch": bytes_launch,
+                      "achieved_GBps": bytes_launch / (statistics.mean(ms) / 1e3) / 1e9}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--profile-case", action="store_true")
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=8.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.profile_case:
+        run_profile_case(args)
+        return
+    line = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * econojax.h - C ABI of the GB300 (sm_103a) EconoJax hot path.
+ *
+ * EconoJax (arxiv 2410.22165) is a vectorised economy: in each of E
+ * environments, A population agents gather resources, craft them into coin
+ * and trade them on a marketplace whose orders hold coin or units in escrow,
+ * while a government agent sets bracketed tax rates each period and pays the
+ * collected tax back in equal shares (Section 3).
+ *
+ * Conventions for every entry point:
+ *  - Pointers marked (device) are CUDA device pointers; (host) are host
+ *    pointers.  The caller allocates and owns all memory; no call allocates
+ *    device memory.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *    NULL = the legacy default stream).  They return after enqueueing.
+ *  - Return value: EJ_OK, or an error code for invalid arguments (checked on
+ *    the host before anything is enqueued; nothing runs) or a failed launch.
+ *    ej_last_error() describes the most recent error of the calling thread.
+ *  - Multi-dimensional arrays are dense, row-major, in the order written.
+ *    E = environments, A = population agents per environment (the maximum
+ *    when populations differ), n = steps.
+ *
+ * Environment rules (readings where the paper is silent are listed in the
+ * repository's design notes):
+ *  0. at a period start (t mod T_tax == 0) the government's rate levels take
+ *     effect: rate_b = level_b / (tax_levels - 1)      (Sec. 3, "Setting tax rates")
+ *  1. each agent's action is applied to its own state; an action the mask
+ *     forbids does nothing                              (Sec. 3, "Population Agents",
+ *                                                        "Action masking")
+ *  2. per resource, the k-th best bid meets the k-th best ask while bid >= ask;
+ *     priority: price, then age, then a random key; the trade is at the
+ *     price of the order placed last (the ask's when placed together)
+ *                                                       (Sec. 3 "Trading"; App. A)
+ *  3. an order leaves after `expire` matching rounds; escrow goes back
+ *  4. at a period end ((t+1) mod T_tax == 0) each agent pays the bracket tax
+ *     on the period's earnings (at most its liquid coin); the total is paid
+ *     back in equal shares                              (Sec. 3, "Setting tax rates")
+ *  5. reward = change of isoelastic utility (Eq. 1-2) of coin incl. escrow;
+ *     the government's = change of (omega(1-gini) + 1 - omega) * sum of coin (Eq. 3-5)
+ *  6. after T_ep steps the environment restarts with new skills
+ *  7. observation + action mask of the new state
+ *
+ * Action ids (nA = 2 + R + 2 R P):
+ *   0 NO-OP | 1..R gather resource a-1 | R+1 craft |
+ *   R+2 + r P + p   buy one unit of r at price level p |
+ *   R+2 + R P + r P + p   sell one unit of r at price level p.
+ * Mask: bit (a mod 32) of word a/32 is set when action a is allowed.
+ *
+ * Population observation (D = 8 + 7R + nb floats): coin, coin in escrow,
+ * labor, inv[R], inv in escrow[R], gather skill[R], craft skill,
+ * orders/max_orders, per resource {best bid, best ask (0 if none),
+ * #bids/A_e, #asks/A_e}, rates[nb], period earnings, fraction of the tax
+ * period left, t/T_ep.
+ * Government observation (G = 3(3+R) + nb + 2): {mean, std, median} of
+ * {coin incl. escrow, period earnings, labor, inv[r] for each r}, rates[nb],
+ * fraction of the tax period left, t/T_ep.
+ *
+ * Random draws (Philox-4x32-10, key = 64-bit seed, low word first; Salmon et
+ * al., SC'11).  Counter (c0, c1, c2, c3):
+ *   population agent i of env e at global step g:  (i, e, g, 0) ->
+ *       x0 uniform action floor(x0 nA / 2^32), x1 gather u, x2 tie-break key,
+ *       x3 policy-sampling u
+ *   government of env e at global step g:          (0, e, g, 1) ->
+ *       x_b rate level floor(x_b tax_levels / 2^32) / policy u of bracket b
+ *   skills of agent i, env e, episode k:           (i, e, k, 2 | c << 8) ->
+ *       uniforms of chunks c = 0, 1, ... in order: SG[0..R-1], SC
+ *   u = (x >> 8) * 2^-24.  g counts steps since env_reset across restarts.
+ */
+#ifndef ECONOJAX_H
+#define ECONOJAX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EJ_MAX_A 1024        /* population agents per environment */
+#define EJ_MAX_R 16          /* resource types */
+#define EJ_MAX_P 32          /* price levels */
+#define EJ_MAX_NB 4          /* tax brackets */
+#define EJ_MAX_ORDERS 16     /* active orders per agent */
+#define EJ_MAX_ACTIONS 256   /* 2 + R + 2 R P */
+#define EJ_MAX_LEVELS 512    /* 2 R P order-book levels */
+
+typedef enum {
+    EJ_OK = 0,
+    EJ_ERR_ARG = 1,          /* invalid argument; nothing was enqueued */
+    EJ_ERR_CUDA = 2,         /* a CUDA call or launch failed */
+    EJ_ERR_UNSUPPORTED = 3   /* valid but outside the compiled limits */
+} ej_status;
+
+/* Environment parameters.  Defaults (ej_params_default) are Table 2 of the
+ * paper; craft_coin, thresholds and tax_levels are readings of values the
+ * paper does not print. */
+typedef struct {
+    int32_t E;               /* environments */
+    int32_t A;               /* population agents per environment (maximum) */
+    int32_t R;               /* resource types (Table 2: 2) */
+    int32_t P;               /* price levels (Table 2: 5) */
+    int32_t nb;              /* tax brackets (3) */
+    int32_t T_ep;            /* episode length (1000) */
+    int32_t T_tax;           /* tax period (100) */
+    int32_t expire;          /* matching rounds an order takes part in (30) */
+    int32_t max_orders;      /* active orders per agent (15) */
+    int32_t Rk;              /* craft: units needed per resource (2) */
+    int32_t Rd;              /* craft: distinct resources needed (2) */
+    int32_t allow_noop;      /* 1: NO-OP allowed (True) */
+    int32_t gov_enabled;     /* 0: free market, no taxes */
+    int32_t tax_levels;      /* rate levels per bracket (21: 0, 5, ..., 100 %) */
+    float start_coin;        /* 15 */
+    float eta;               /* isoelastic utility (0.27) */
+    float omega;             /* equality weight (1) */
+    float labor_gather;      /* 1 */
+    float labor_craft;       /* 1 */
+    float labor_trade;       /* 0.05 */
+    float craft_coin;        /* coin per unit of craft skill (10) */
+    float gather_rho;        /* gather draw range [0, gather_rho) (1.1) */
+    float price_tick;        /* prices are whole multiples of this (2) */
+    int32_t price_ticks[EJ_MAX_P];      /* level p costs price_tick*price_ticks[p]; ascending ({1..5}) */
+    float thresholds[EJ_MAX_NB - 1];    /* bracket edges, ascending ({50, 100}) */
+} EjParams;
+
+/* Sizes implied by a parameter set. */
+typedef struct {
+    int32_t n_actions;       /* nA */
+    int32_t obs_dim;         /* D */
+    int32_t gobs_dim;        /* G */
+    int32_t mask_words;      /* W = ceil(nA / 32) */
+    int32_t levels;          /* 2 R P */
+    int32_t book_cap;        /* order slots per environment = A * max_orders */
+    int32_t threads;         /* threads of the CTA that runs one environment */
+    int32_t smem_bytes;      /* dynamic shared memory of that CTA */
+    uint64_t state_bytes;    /* size of the state buffer */
+} EjSizes;
+
+/* Fields of the state buffer, for inspection (ej_state_field). */
+typedef enum {
+    EJ_F_COIN = 0,       /* float   [E][A_s]    liquid coin */
+    EJ_F_ESC,            /* int32   [E][A_s]    coin in escrow, price ticks */
+    EJ_F_INCOME,         /* float   [E][A_s]    earnings this tax period */
+    EJ_F_UPREV,          /* float   [E][A_s]    utility after the previous step */
+    EJ_F_NORD,           /* int32   [E][A_s]    active orders */
+    EJ_F_COUNTS,         /* int32   [E][3][A_s] gathers, crafts, orders this episode */
+    EJ_F_SC,             /* float   [E][A_s]    craft skill */
+    EJ_F_INV,            /* int32   [E][R][A_s] liquid units */
+    EJ_F_INVE,           /* int32   [E][R][A_s] units in escrow */
+    EJ_F_SG,             /* float   [E][R][A_s] gather skill */
+    EJ_F_T,              /* int32   [E]         step within the episode */
+    EJ_F_GSTEP,          /* uint32  [E]         steps since env_reset */
+    EJ_F_EPISODE,        /* uint32  [E]         episodes started since env_reset */
+    EJ_F_POP,            /* int32   [E]         population A_e */
+    EJ_F_RATES,          /* float   [E][4]      tax rates in effect */
+    EJ_F_UGPREV,         /* float   [E]         social welfare after the previous step */
+    EJ_F_LEVEL_COUNT,    /* int32   [E][L]      resting orders per book level */
+    EJ_F_BOOK,           /* uint32  [E][cap]    orders: (placed step << 16) | agent,
+                                                level after level, oldest first */
+    EJ_F_KEY,            /* uint32  [2]         Philox key */
+    EJ_F_COUNT_
+} ej_field;
+
+/* Writes the defaults of Table 2 (and the readings above) into *p, with E = 1
+ * and A = 100. */
+ej_status ej_params_default(EjParams* p);
+
+/* Validates *p and fills *s.  EJ_ERR_ARG / EJ_ERR_UNSUPPORTED on bad values. */
+ej_status ej_sizes(const EjParams* p, EjSizes* s);
+
+/* Byte offset, element count and element size of a field of the state buffer.
+ * A_s = A rounded up to a multiple of 4; book levels are ordered
+ * l = (r * 2 + side) * P + p with side 0 = bids, 1 = asks. */
+ej_status ej_state_field(const EjParams* p, int32_t field, uint64_t* offset,
+                         uint64_t* count, int32_t* elem_bytes);
+
+/* env_reset (Sec. 3 "Overall design": functional reset(key, params)).
+ * state     (device) ej_sizes().state_bytes bytes, 256-byte aligned; written.
+ * pop_sizes (device) int32[E] populations A_e in [1, A], or NULL for all A.
+ * seed      Philox key for in-kernel draws (skills now and at restarts, and
+ *           any draws env_step makes itself).
+ * obs (device) float[E][A][D], gobs float[E][G], mask uint32[E][A][W]: the
+ *           first observation; each may be NULL.  Rows of agents >= A_e are 0. */
+ej_status env_reset(const EjParams* p, void* state, const int32_t* pop_sizes,
+                    uint64_t seed, float* obs, float* gobs, uint32_t* mask,
+                    void* stream);
+
+/* env_step (Sec. 3 "Overall design": step(key, state, action, params)),
+ * n_steps steps in one launch, state kept on chip between steps.
+ * act      (device) int32[n][E][A] population actions (ids above), or NULL to
+ *          draw uniform random actions, gather draws and tie-break keys in
+ *          the kernel with the counter mapping above (then gather_u and tb
+ *          must be NULL too).
+ * gov_act  (device) int32[n][E][nb] rate levels (read at period starts only),
+ *          or NULL to draw uniform levels in the kernel.
+ * gather_u (device) float[n][E][A] gather draws u in [0,1); rho = gather_rho*u.
+ * tb       (device) uint32[n][E][A] tie-break keys of orders placed that step.
+ * rew      (device) float[n][E][A] population rewards      (may be NULL)
+ * grew     (device) float[n][E]    government rewards      (may be NULL)
+ * done     (device) uint8[n][E]    1 when the step ended the episode (may be NULL)
+ * obs, gobs, mask (device) as in env_reset, one per step [n][...] (may be NULL).
+ * Out-of-range action ids act as forbidden actions; out-of-range rate levels
+ * are clamped.  Integer state is exact; coin and utility are float32. */
+ej_status env_step(const EjParams* p, void* state, int32_t n_steps,
+                   const int32_t* act, const int32_t* gov_act,
+                   const float* gather_u, const uint32_t* tb,
+                   float* rew, float* grew, uint8_t* done,
+                   float* obs, float* gobs, uint32_t* mask, void* stream);
+
+/* ej_fill_draws: the draws env_step would make itself, written out (device),
+ * for global steps g0 .. g0+n-1: act int32[n][E][A], gather_u float[n][E][A],
+ * tb uint32[n][E][A], policy_u float[n][E][A], gov_act int32[n][E][nb];
+ * each may be NULL.  Uses p->E, p->A and the counter mapping above. */
+ej_status ej_fill_draws(const EjParams* p, uint64_t seed, uint32_t g0, int32_t n_steps,
+                        int32_t* act, float* gather_u, uint32_t* tb, float* policy_u,
+                        int32_t* gov_act, void* stream);
+
+/* Description of the last error returned to the calling thread. */
+const char* ej_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ECONOJAX_H */

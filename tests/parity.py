@@ -1,0 +1,98 @@
+"""Comparison of the CUDA environment with the CPU oracle.
+
+Tolerances (float outputs; integer state and masks are compared exactly):
+  * coin-like quantities, observations, statistics: |gpu - oracle| <=
+    1e-5 * max(|scale|, 1), where the scale is the value itself (observation
+    features; for the coin-valued ones - coin, coin in escrow, period
+    earnings - at least the environment's mean total coin at that step, since
+    a float coin that falls to a small value after passing through large ones
+    keeps the absolute error of the large ones), the largest of mean / std /
+    median of the same metric
+    (government statistics), or the utility magnitude of the agent at this or
+    the previous step (rewards: the difference of two utilities loses the
+    relative precision of each);
+  * government reward: 1e-5 * max(total coin, 1).
+The float "decision mirror" of the oracle must equal the GPU's liquid coin
+bit for bit.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import synth
+from oracle.env import OracleEnv
+
+REL = 1e-5
+
+
+def oracle_run(params, A_e, e, seed, T, g0=0):
+    o = OracleEnv(params, A_e)
+    inp = synth.episode_inputs(seed, [e], A_e, params["R"], params["nb"], o.nA,
+                               params["tax_levels"], T, params["T_ep"], g0=g0)
+    o.reset(inp["sg0"][0], inp["sc0"][0])
+    out = o.run(inp["act"][:, 0], inp["gov_act"][:, 0], inp["gather_u"][:, 0], inp["tb"][:, 0],
+                inp["later_sg"][:, 0], inp["later_sc"][:, 0])
+    return o, out
+
+
+def _close(g, o, scale, what):
+    g = np.asarray(g, np.float64)
+    bound = REL * np.maximum(np.abs(scale), 1.0)
+    err = np.abs(g - o)
+    bad = err > bound
+    if bad.any():
+        idx = np.argwhere(bad)[:5]
+        raise AssertionError(f"{what}: {bad.sum()} values out of tolerance, first at {idx.tolist()}: "
+                             f"gpu={g[tuple(idx[0])]} oracle={o[tuple(idx[0])]} bound={bound[tuple(idx[0])]}")
+    return float((err / np.maximum(np.abs(scale), 1.0)).max()) if err.size else 0.0
+
+
+def compare_env(g, ref, params, A_e, obs0_ref=None):
+    """g: GPU outputs of one env as numpy (rew [n,A], grew [n], done [n], obs [n,A,D],
+    gobs [n,G], mask [n,A,W]); ref: oracle outputs (A_e agents).  Returns max rel errors."""
+    R, eta = params["R"], params["eta"]
+    errs = {}
+    if "done" in g:
+        assert np.array_equal(g["done"].astype(np.int32), ref["done"]), "done differs"
+    if "mask" in g:
+        m = g["mask"].view(np.uint32)
+        assert np.array_equal(m[:, :A_e], ref["mask"]), "mask differs"
+        assert not m[:, A_e:].any(), "mask of absent agents not zero"
+    if "obs" in g:
+        go, ro = g["obs"], ref["obs"]
+        ints = list(range(3, 3 + 2 * R))
+        assert np.array_equal(go[:, :A_e, ints].astype(np.int64), ro[:, :, ints].astype(np.int64)), \
+            "integer observation features (inventories) differ"
+        scale = np.abs(ro).copy()
+        mean_coin = ref["gobs"][:, 0][:, None]
+        D = ro.shape[2]
+        for f in (0, 1, D - 3):        # coin, coin in escrow, period earnings
+            scale[:, :, f] = np.maximum(scale[:, :, f], mean_coin)
+        errs["obs"] = _close(go[:, :A_e], ro, scale, "obs")
+        assert not go[:, A_e:].any(), "obs of absent agents not zero"
+    if "rew" in g:
+        ro = ref["obs"]
+        C = ro[:, :, 0] + ro[:, :, 1]
+        u = np.abs(np.power(C, 1 - eta) / (1 - eta)) + ro[:, :, 2] + 1.0
+        prev = np.concatenate([u[:1] if obs0_ref is None else
+                               (np.abs(np.power(obs0_ref[:, 0] + obs0_ref[:, 1], 1 - eta) / (1 - eta))
+                                + obs0_ref[:, 2] + 1.0)[None], u[:-1]])
+        scale = np.maximum(u, prev)
+        # a reward is the difference of two utilities: its error is bounded by the
+        # sum of their magnitudes (at an episode end the earlier one stands for both)
+        errs["rew"] = _close(g["rew"][:, :A_e], ref["rew"], scale * 2, "rew")
+        assert not g["rew"][:, A_e:].any()
+    if "gobs" in g:
+        M = 3 + R
+        ro = ref["gobs"]
+        scale = np.zeros_like(ro)
+        for m in range(M):
+            s = np.max(np.abs(ro[:, 3 * m:3 * m + 3]), axis=1, keepdims=True)
+            scale[:, 3 * m:3 * m + 3] = s
+        scale[:, 3 * M:] = np.abs(ro[:, 3 * M:])
+        errs["gobs"] = _close(g["gobs"], ro, scale, "gobs")
+    if "grew" in g:
+        prod = ref["gobs"][:, 0] * A_e
+        scale = np.maximum(prod, np.concatenate([prod[:1], prod[:-1]])) * 2
+        errs["grew"] = _close(g["grew"], ref["grew"], scale, "grew")
+    return errs

@@ -1,0 +1,98 @@
+"""The C ABI library loads without a GPU, exports every symbol the header
+declares, and validates parameters on the host."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from oracle.env import default_params
+from paper_2410_22165_gb300 import _native as N
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+           if f.endswith(".h")]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2410_22165_gb300 import build
+    build.build()
+    return N.load()
+
+
+def declared_functions():
+    names = []
+    for h in HEADERS:
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(\w+)\s*\([^;]*\)\s*;", src, flags=re.M)
+    return sorted(set(n for n in names if not n.startswith("_")))
+
+
+def test_header_symbols_exported(lib):
+    names = declared_functions()
+    assert {"env_reset", "env_step", "ej_sizes", "ej_params_default"} <= set(names)
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+    assert set(N.exported_symbols()) <= set(names)
+
+
+def test_defaults_match_table2_transcriptions(lib):
+    """The library's defaults and the oracle's are two independent
+    transcriptions of Table 2; they must agree."""
+    p = N.params_dict(N.make_params())
+    o = default_params()
+    for k, v in o.items():
+        if isinstance(v, float):
+            assert p[k] == pytest.approx(v, rel=1e-7), k
+        else:
+            assert p[k] == v, k
+
+
+def test_sizes(lib):
+    s = N.sizes(N.make_params(E=1024, A=100))
+    assert (s.n_actions, s.obs_dim, s.gobs_dim, s.mask_words) == (24, 25, 20, 1)
+    assert s.threads == 128 and s.book_cap == 1500
+    assert s.smem_bytes * 7 <= 227 * 1024 - 7 * 1024          # 7 CTAs per SM
+    s = N.sizes(N.make_params(R=12, P=3, price_ticks=[1, 2, 3]))
+    assert s.n_actions == 86
+
+
+@pytest.mark.parametrize("bad", [dict(A=0), dict(A=2000), dict(R=0), dict(P=33), dict(nb=5),
+                                 dict(T_ep=70000), dict(max_orders=17), dict(Rd=3),
+                                 dict(price_ticks=[1, 1, 2, 3, 4]), dict(tax_levels=1),
+                                 dict(eta=1.0), dict(price_tick=0.0)])
+def test_invalid_params_rejected(lib, bad):
+    p = N.make_params(**bad)
+    s = N.EjSizes()
+    st = lib.ej_sizes(C.byref(p), C.byref(s))
+    assert st in (1, 3)
+    assert lib.ej_last_error().decode()
+
+
+def test_step_argument_checks(lib):
+    p = N.make_params(E=2, A=10)
+    # NULL state, and act without tb: rejected on the host before any launch
+    assert lib.env_step(C.byref(p), None, 1, None, None, None, None, None, None, None, None,
+                        None, None, None) == 1
+    fake = C.c_void_p(256)
+    assert lib.env_step(C.byref(p), fake, 1, fake, None, None, None, None, None, None, None,
+                        None, None, None) == 1
+    assert lib.env_step(C.byref(p), fake, -1, None, None, None, None, None, None, None, None,
+                        None, None, None) == 1
+    assert lib.env_step(C.byref(p), C.c_void_p(300), 1, None, None, None, None, None, None, None,
+                        None, None, None, None) == 1                   # misaligned state
+    assert lib.env_step(C.byref(p), fake, 0, None, None, None, None, None, None, None, None,
+                        None, None, None) == 0                         # nothing to do
+
+
+def test_state_layout(lib):
+    p = N.make_params(E=3, A=10)
+    s = N.sizes(p)
+    prev_end = 0
+    for f in N.FIELDS:
+        off, cnt, esz = N.state_field(p, f)
+        assert off % 256 == 0 and off >= prev_end and esz == 4
+        prev_end = off + cnt * esz
+    assert prev_end <= s.state_bytes
