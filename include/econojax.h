@@ -51,9 +51,9 @@
  * orders/max_orders, per resource {best bid, best ask (0 if none),
  * #bids/A_e, #asks/A_e}, rates[nb], period earnings, fraction of the tax
  * period left, t/T_ep.
- * Government observation (G = 3(3+R) + nb + 2): {mean, std, median} of
- * {coin incl. escrow, period earnings, labor, inv[r] for each r}, rates[nb],
- * fraction of the tax period left, t/T_ep.
+ * Government observation (G = 9 + nb + 2): {mean, population std, median} of
+ * {coin incl. escrow, period earnings, labor}, rates[nb], fraction of the tax
+ * period left, t/T_ep.
  *
  * Random draws (Philox-4x32-10, key = 64-bit seed, low word first; Salmon et
  * al., SC'11).  Counter (c0, c1, c2, c3):

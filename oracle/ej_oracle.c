@@ -94,10 +94,10 @@ int orc_num_actions(const orc_params* p) { return 2 + p->R + 2 * p->R * p->P; }
  * rates[nb], period earnings, fraction of the tax period left, t/T_ep.      */
 int orc_obs_dim(const orc_params* p) { return 8 + 7 * p->R + p->nb; }
 
-/* Government observation: mean, std, median of {total coin, period
- * earnings, labor, inv[R]} (App. A: statistics, not individual states),
- * then rates[nb], fraction of the tax period left, t/T_ep.                */
-int orc_gobs_dim(const orc_params* p) { return 3 * (3 + p->R) + p->nb + 2; }
+/* Government observation (READING of Fig. 1 / App. A: statistics, not
+ * individual states): mean, std, median of {total coin, period earnings,
+ * labor}, then rates[nb], fraction of the tax period left, t/T_ep.         */
+int orc_gobs_dim(const orc_params* p) { return 3 * 3 + p->nb + 2; }
 
 int orc_mask_words(const orc_params* p) { return (orc_num_actions(p) + 31) / 32; }
 
@@ -441,14 +441,13 @@ void orc_env_observe(const orc_env* env, double* obs, double* gobs, uint32_t* ma
         }
     }
     if (gobs) {
-        int M = 3 + R;
+        int M = 3;
         double* x = (double*)malloc(sizeof(double) * (A > 0 ? A : 1));
         for (int m = 0; m < M; ++m) {
             for (int i = 0; i < A; ++i) {
                 if (m == 0) x[i] = total_coin64(env, i);
                 else if (m == 1) x[i] = env->income64[i];
-                else if (m == 2) x[i] = labor_of(env, i);
-                else x[i] = env->inv[i * R + (m - 3)];
+                else x[i] = labor_of(env, i);
             }
             stats3(x, A, gobs + 3 * m);
         }

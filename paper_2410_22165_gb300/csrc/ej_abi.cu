@@ -52,9 +52,9 @@ ej_status derive(const EjParams* p, Layout* lay, KParams* kp) {
 
     const int A_s = (p->A + 3) & ~3;
     const int D = 8 + 7 * p->R + p->nb;
-    const int G = 3 * (3 + p->R) + p->nb + 2;
+    const int G = 3 * 3 + p->nb + 2;
     const int W = (nA + 31) / 32;
-    const int M = 3 + p->R;
+    const int M = 3;          // statistics metrics: total coin, period earnings, labor
     const int cap = p->A * (p->max_orders > 0 ? p->max_orders : 1);
     const int NT = env_threads(p->A);
     const SmemLayout sl = smem_layout(NT, p->R, p->P, L, cap, M, D);

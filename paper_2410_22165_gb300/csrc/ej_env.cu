@@ -124,16 +124,6 @@ __device__ __forceinline__ void warp_excl_scan(const int* in, int* out, int n, i
     if (lane == 0) out[n] = carry;
 }
 
-// Largest l in [0, n) with start[l] <= j, for a non-decreasing start[].
-__device__ __forceinline__ int find_level(const int* start, int n, int j) {
-    int lo = 0, hi = n;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (start[mid] <= j) lo = mid; else hi = mid;
-    }
-    return lo;
-}
-
 // k-th order of level l this step: resting orders first, then this step's.
 __device__ __forceinline__ uint32_t seq_get(const Sm& s, int l, int k) {
     const int old = s.lvl_old[l];
@@ -239,9 +229,107 @@ __device__ void start_agent(const KParams& p, const Sm& s, Agent& g, int i, int 
     }
 }
 
-// Block-wide bitonic sort of M arrays of NT floats (ascending).
+// Each agent's values of the government's statistics metrics (total coin,
+// period earnings, labor) into s.stat[m][i]; absent agents get +FLT_MAX so
+// that they sort last.
 template <int NT>
-__device__ void bitonic_sort(float* a, int M) {
+__device__ __forceinline__ void fill_stats(const KParams& p, const Sm& s, const Agent& g, int i, int Ae) {
+    if (i < Ae) {
+        s.stat[0 * NT + i] = __fadd_rn(g.coin, __fmul_rn(p.tick, (float)g.esc));
+        s.stat[1 * NT + i] = g.income;
+        s.stat[2 * NT + i] = labor_of(p, g.ng, g.nc, g.nt);
+    } else {
+        s.stat[0 * NT + i] = FLT_MAX;
+        s.stat[1 * NT + i] = FLT_MAX;
+        s.stat[2 * NT + i] = FLT_MAX;
+    }
+}
+
+// Bitonic sort (ascending) of 32*V values held V per lane; element index
+// (v << 5) | lane.  Stages whose partner distance is below 32 exchange
+// through shuffles, the others between a lane's own registers.
+template <int V>
+__device__ __forceinline__ void warp_bitonic(float (&x)[V], int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32 * V; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int jr = j >> 5;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    if ((v & jr) == 0) {
+                        const int w = v | jr;
+                        const bool asc = ((v << 5) & k) == 0;
+                        const float lo = fminf(x[v], x[w]), hi = fmaxf(x[v], x[w]);
+                        x[v] = asc ? lo : hi;
+                        x[w] = asc ? hi : lo;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const float y = __shfl_xor_sync(FULL, x[v], j);
+                    const bool asc = ((((v << 5) | lane) & k) == 0);
+                    const bool lower = (lane & j) == 0;
+                    x[v] = (lower == asc) ? fminf(x[v], y) : fmaxf(x[v], y);
+                }
+            }
+        }
+    }
+}
+
+template <int V>
+__device__ __forceinline__ float sorted_at(const float (&x)[V], int k) {
+    float v = x[0];
+#pragma unroll
+    for (int r = 1; r < V; ++r) if ((k >> 5) == r) v = x[r];
+    return __shfl_sync(FULL, v, k & 31);
+}
+
+// Statistics of one metric by one warp (mean, population std, median; and
+// for total coin the gini index and the total, Eq. 5-6), from s.stat[m].
+template <int V>
+__device__ void warp_metric_stats(const Sm& s, int m, int lane, int Ae, int NT) {
+    float x[V];
+    float sum = 0.0f;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const int idx = (v << 5) | lane;
+        x[v] = s.stat[m * NT + idx];
+        if (idx < Ae) sum += x[v];
+    }
+    sum = warp_sum(sum);
+    warp_bitonic<V>(x, lane);
+    const float mean = sum / (float)Ae;
+    float ss = 0.0f, gnum = 0.0f;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const int idx = (v << 5) | lane;
+        if (idx < Ae) {
+            const float d = x[v] - mean;
+            ss += d * d;
+            gnum += (float)(2 * idx - Ae + 1) * x[v];
+        }
+    }
+    ss = warp_sum(ss);
+    const float lo = sorted_at<V>(x, (Ae - 1) >> 1), hi = sorted_at<V>(x, Ae >> 1);
+    if (m == 0) gnum = warp_sum(gnum);
+    if (lane == 0) {
+        s.gstat[3 * m + 0] = mean;
+        s.gstat[3 * m + 1] = sqrtf(ss / (float)Ae);
+        s.gstat[3 * m + 2] = (Ae & 1) ? hi : 0.5f * (lo + hi);
+        if (m == 0) {
+            s.misc[MISC_PROD] = sum;
+            s.misc[MISC_GINI] = sum > 0.0f ? gnum / ((float)Ae * sum) : 0.0f;
+        }
+    }
+}
+
+// Block-wide bitonic sort of M arrays of NT floats (ascending), for CTAs
+// too wide for the register sort.
+template <int NT>
+__device__ void block_bitonic(float* a, int M) {
     const int i = threadIdx.x;
 #pragma unroll 1
     for (int k = 2; k <= NT; k <<= 1) {
@@ -260,63 +348,47 @@ __device__ void bitonic_sort(float* a, int M) {
     }
 }
 
-// Population statistics of the current state (Sec. 3; App. A: the government
-// sees mean, std and median): sorts the metrics, computes the gini index and
-// total coin (Eq. 5-6).  Ends with the results in s.gstat / s.misc.
+// Population statistics (Sec. 3; App. A: the government sees mean, std and
+// median) from s.stat, which fill_stats wrote before a barrier.  Ends with
+// a barrier; results in s.gstat and s.misc.
 template <int NT>
-__device__ void population_stats(const KParams& p, const Sm& s, const Agent& g, int i, int Ae) {
-    const int M = p.M;
-    const bool live = i < Ae;
-    const int lane = i & 31, warp = i >> 5;
+__device__ void population_stats(const KParams& p, const Sm& s, int i, int Ae) {
     constexpr int NW = NT / 32;
-    if (live) {
-        s.stat[0 * NT + i] = __fadd_rn(g.coin, __fmul_rn(p.tick, (float)g.esc));
-        s.stat[1 * NT + i] = g.income;
-        s.stat[2 * NT + i] = labor_of(p, g.ng, g.nc, g.nt);
-        for (int r = 0; r < p.R; ++r) s.stat[(3 + r) * NT + i] = (float)s.inv[r * NT + i];
+    const int lane = i & 31, warp = i >> 5;
+    const int M = p.M;
+    if constexpr (NT <= 128) {
+        constexpr int V = NT / 32;
+        for (int m = warp; m < M; m += NW) warp_metric_stats<V>(s, m, lane, Ae, NT);
     } else {
-        for (int m = 0; m < M; ++m) s.stat[m * NT + i] = FLT_MAX;
-    }
-    __syncthreads();
-    bitonic_sort<NT>(s.stat, M);
-    // pass 1: sums and the gini numerator sum_k (2k - n + 1) x_(k)
-    for (int m = 0; m < M; ++m) {
-        const float v = warp_sum(live ? s.stat[m * NT + i] : 0.0f);
-        if (lane == 0) s.red[warp * (M + 1) + m] = v;
-    }
-    {
-        const float v = warp_sum(live ? (float)(2 * i - Ae + 1) * s.stat[i] : 0.0f);
-        if (lane == 0) s.red[warp * (M + 1) + M] = v;
-    }
-    __syncthreads();
-    if (i <= M) {
-        float acc = 0.0f;
-        for (int w = 0; w < NW; ++w) acc += s.red[w * (M + 1) + i];
-        s.fin[i] = acc;
-    }
-    __syncthreads();
-    // pass 2: squared deviations
-    for (int m = 0; m < M; ++m) {
-        const float mean = s.fin[m] / (float)Ae;
-        const float d = live ? s.stat[m * NT + i] - mean : 0.0f;
-        const float v = warp_sum(d * d);
-        if (lane == 0) s.red[warp * (M + 1) + m] = v;
-    }
-    __syncthreads();
-    if (i < M) {
-        float acc = 0.0f;
-        for (int w = 0; w < NW; ++w) acc += s.red[w * (M + 1) + i];
-        const float mean = s.fin[i] / (float)Ae;
-        const float med = (Ae & 1) ? s.stat[i * NT + Ae / 2]
-                                   : 0.5f * (s.stat[i * NT + Ae / 2 - 1] + s.stat[i * NT + Ae / 2]);
-        s.gstat[3 * i + 0] = mean;
-        s.gstat[3 * i + 1] = sqrtf(acc / (float)Ae);
-        s.gstat[3 * i + 2] = med;
-    }
-    if (i == 0) {
-        const float prod = s.fin[0];
-        s.misc[MISC_PROD] = prod;
-        s.misc[MISC_GINI] = prod > 0.0f ? s.fin[M] / ((float)Ae * prod) : 0.0f;
+        block_bitonic<NT>(s.stat, M);
+        for (int m = warp; m < M; m += NW) {
+            // sums over the sorted array by one warp
+            float sum = 0.0f, gnum = 0.0f;
+            for (int idx = lane; idx < Ae; idx += 32) {
+                const float v = s.stat[m * NT + idx];
+                sum += v;
+                gnum += (float)(2 * idx - Ae + 1) * v;
+            }
+            sum = warp_sum(sum);
+            gnum = warp_sum(gnum);
+            const float mean = sum / (float)Ae;
+            float ss = 0.0f;
+            for (int idx = lane; idx < Ae; idx += 32) {
+                const float d = s.stat[m * NT + idx] - mean;
+                ss += d * d;
+            }
+            ss = warp_sum(ss);
+            if (lane == 0) {
+                const float lo = s.stat[m * NT + ((Ae - 1) >> 1)], hi = s.stat[m * NT + (Ae >> 1)];
+                s.gstat[3 * m + 0] = mean;
+                s.gstat[3 * m + 1] = sqrtf(ss / (float)Ae);
+                s.gstat[3 * m + 2] = (Ae & 1) ? hi : 0.5f * (lo + hi);
+                if (m == 0) {
+                    s.misc[MISC_PROD] = sum;
+                    s.misc[MISC_GINI] = sum > 0.0f ? gnum / ((float)Ae * sum) : 0.0f;
+                }
+            }
+        }
     }
     __syncthreads();
 }
@@ -326,17 +398,15 @@ __device__ __forceinline__ float social_welfare(const KParams& p, const Sm& s) {
     return (p.omega * (1.0f - s.misc[MISC_GINI]) + (1.0f - p.omega)) * s.misc[MISC_PROD];
 }
 
-// Observation, government observation and action mask of the current state
-// (Sec. 3; App. A), written for output row `row`.
-template <int NT>
-__device__ void observe(const KParams& p, const Sm& s, const Agent& g, const DevIO& io,
-                        size_t row, int i, int Ae, int t) {
-    const int R = p.R, P = p.P, D = p.D;
-    if (i < R) {
+// Market statistics of the resting book for the observation (App. A:
+// highest bid, lowest ask, number of orders), from per-level counts.
+__device__ __forceinline__ void market_stats(const KParams& p, const Sm& s, const int* counts, int i, int Ae) {
+    const int P = p.P;
+    if (i < p.R) {
         const int lb = (i * 2) * P, la = (i * 2 + 1) * P;
         int hi = -1, lo = P, nbids = 0, nasks = 0;
         for (int q = 0; q < P; ++q) {
-            const int cb = s.lvl_old[lb + q], ca = s.lvl_old[la + q];
+            const int cb = counts[lb + q], ca = counts[la + q];
             nbids += cb;
             nasks += ca;
             if (cb > 0) hi = q;
@@ -347,9 +417,19 @@ __device__ void observe(const KParams& p, const Sm& s, const Agent& g, const Dev
         s.mkt[4 * i + 2] = __fdiv_rn((float)nbids, (float)Ae);
         s.mkt[4 * i + 3] = __fdiv_rn((float)nasks, (float)Ae);
     }
+}
+
+// Observation, government observation and action mask of the current state
+// (Sec. 3; App. A), written for output row `row`.  Needs s.mkt, s.gstat and
+// s.rates; each warp stages the observations of its own 32 agents and writes
+// them as one contiguous block.  Ends with a barrier.
+template <int NT>
+__device__ void observe(const KParams& p, const Sm& s, const Agent& g, const DevIO& io,
+                        size_t row, int i, int Ae, int t) {
+    const int R = p.R, P = p.P, D = p.D;
+    const int lane = i & 31, warp = i >> 5;
     const float period_left = __fdiv_rn((float)(p.T_tax - t % p.T_tax), (float)p.T_tax);
     const float time_frac = __fdiv_rn((float)t, (float)p.T_ep);
-    __syncthreads();
     if (io.gobs && i < p.G) {
         const int nst = 3 * p.M;
         float v;
@@ -365,7 +445,7 @@ __device__ void observe(const KParams& p, const Sm& s, const Agent& g, const Dev
         uint64_t buy_bits = 0;
         if (room)
             for (int q = 0; q < P; ++q) buy_bits |= (uint64_t)(g.coin >= p.price[q]) << q;
-        const uint64_t all_p = (P >= 64) ? ~0ull : ((1ull << P) - 1);
+        const uint64_t all_p = (1ull << P) - 1;
         const bool craft = craftable<NT>(p, s, i);
         for (int w = 0; w < p.W; ++w) {
             uint32_t word = 0;
@@ -382,41 +462,46 @@ __device__ void observe(const KParams& p, const Sm& s, const Agent& g, const Dev
         }
     }
     if (io.obs) {
-        if (i < p.A) {
-            float* o = s.obs + (size_t)i * D;
-            if (i < Ae) {
-                int k = 0;
-                o[k++] = g.coin;
-                o[k++] = __fmul_rn(p.tick, (float)g.esc);
-                o[k++] = labor_of(p, g.ng, g.nc, g.nt);
-                for (int r = 0; r < R; ++r) o[k++] = (float)s.inv[r * NT + i];
-                for (int r = 0; r < R; ++r) o[k++] = (float)s.inve[r * NT + i];
-                for (int r = 0; r < R; ++r) o[k++] = s.sg[r * NT + i];
-                o[k++] = g.sc;
-                o[k++] = __fdiv_rn((float)g.nord, (float)(p.max_orders > 0 ? p.max_orders : 1));
-                for (int r = 0; r < R; ++r) {
-                    o[k++] = s.mkt[4 * r + 0];
-                    o[k++] = s.mkt[4 * r + 1];
-                    o[k++] = s.mkt[4 * r + 2];
-                    o[k++] = s.mkt[4 * r + 3];
+        const int first = warp * 32;
+        if (first < p.A) {
+            if (i < p.A) {
+                float* o = s.obs + (size_t)i * D;
+                if (i < Ae) {
+                    int k = 0;
+                    o[k++] = g.coin;
+                    o[k++] = __fmul_rn(p.tick, (float)g.esc);
+                    o[k++] = labor_of(p, g.ng, g.nc, g.nt);
+                    for (int r = 0; r < R; ++r) o[k++] = (float)s.inv[r * NT + i];
+                    for (int r = 0; r < R; ++r) o[k++] = (float)s.inve[r * NT + i];
+                    for (int r = 0; r < R; ++r) o[k++] = s.sg[r * NT + i];
+                    o[k++] = g.sc;
+                    o[k++] = __fdiv_rn((float)g.nord, (float)(p.max_orders > 0 ? p.max_orders : 1));
+                    for (int r = 0; r < R; ++r) {
+                        o[k++] = s.mkt[4 * r + 0];
+                        o[k++] = s.mkt[4 * r + 1];
+                        o[k++] = s.mkt[4 * r + 2];
+                        o[k++] = s.mkt[4 * r + 3];
+                    }
+                    for (int b = 0; b < p.nb; ++b) o[k++] = s.rates[b];
+                    o[k++] = g.income;
+                    o[k++] = period_left;
+                    o[k++] = time_frac;
+                } else {
+                    for (int k = 0; k < D; ++k) o[k] = 0.0f;
                 }
-                for (int b = 0; b < p.nb; ++b) o[k++] = s.rates[b];
-                o[k++] = g.income;
-                o[k++] = period_left;
-                o[k++] = time_frac;
-            } else {
-                for (int k = 0; k < D; ++k) o[k] = 0.0f;
             }
-        }
-        __syncthreads();
-        const int n = p.A * D;
-        float* dst = io.obs + row * (size_t)n;
-        if ((n & 3) == 0 && (((uintptr_t)dst) & 15) == 0) {
-            const float4* src4 = (const float4*)s.obs;
-            float4* dst4 = (float4*)dst;
-            for (int j = i; j < (n >> 2); j += NT) dst4[j] = src4[j];
-        } else {
-            for (int j = i; j < n; j += NT) dst[j] = s.obs[j];
+            __syncwarp();
+            const int rows = min(32, p.A - first);
+            const int n = rows * D;
+            const float* src = s.obs + (size_t)first * D;
+            float* dst = io.obs + (row * p.A + first) * (size_t)D;
+            if ((n & 3) == 0 && (((uintptr_t)dst) & 15) == 0) {
+                const float4* src4 = (const float4*)src;
+                float4* dst4 = (float4*)dst;
+                for (int j = lane; j < (n >> 2); j += 32) dst4[j] = src4[j];
+            } else {
+                for (int j = lane; j < n; j += 32) dst[j] = src[j];
+            }
         }
     }
     __syncthreads();
@@ -429,7 +514,7 @@ template <int NT> struct MinCtas { static constexpr int value = NT <= 32 ? 16 : 
 
 template <int NT>
 __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, DevState st, DevIO io, int n_steps,
-                                                 int mode, uint32_t seed_lo, uint32_t seed_hi) {
+                                                                     int mode, uint32_t seed_lo, uint32_t seed_hi) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Sm s = carve<NT>(smem_raw, p);
     const int e = blockIdx.x;
@@ -438,6 +523,7 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
     constexpr int NW = NT / 32;
     const int R = p.R, P = p.P, L = p.L;
     const size_t ea = (size_t)e * p.A_s;
+    const int owner = NT - 1 - i;          // levels l = owner, owner + NT, ... belong to this thread
 
     Agent g;
     int t;
@@ -454,8 +540,10 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
         for (int l = i; l <= L; l += NT) s.lvl_start[l] = 0;
         if (i < EJ_MAX_NB) s.rates[i] = 0.0f;
         if (e == 0 && i == 0) { st.key[0] = k0; st.key[1] = k1; }
+        fill_stats<NT>(p, s, g, i, Ae);
         __syncthreads();
-        population_stats<NT>(p, s, g, i, Ae);
+        market_stats(p, s, s.lvl_old, i, Ae);
+        population_stats<NT>(p, s, i, Ae);
         if (i == 0) s.misc[MISC_UGPREV] = social_welfare(p, s);
         observe<NT>(p, s, g, io, (size_t)e, i, Ae, t);
     } else {
@@ -463,7 +551,6 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
         k0 = st.key[0];
         k1 = st.key[1];
         t = st.t[e]; gs = st.gstep[e]; ep = st.episode[e];
-        const bool live = i < Ae;
         if (i < p.A_s) {
             g.coin = st.coin[ea + i]; g.esc = st.esc[ea + i]; g.income = st.income[ea + i];
             g.uprev = st.uprev[ea + i]; g.nord = st.nord[ea + i]; g.sc = st.sc[ea + i];
@@ -478,7 +565,6 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
             g.esc = g.nord = g.ng = g.nc = g.nt = 0;
             for (int r = 0; r < R; ++r) { s.inv[r * NT + i] = 0; s.inve[r * NT + i] = 0; s.sg[r * NT + i] = 0.0f; }
         }
-        (void)live;
         for (int l = i; l < L; l += NT) s.lvl_old[l] = st.lvl[(size_t)e * L + l];
         if (i < EJ_MAX_NB) s.rates[i] = st.rates[(size_t)e * EJ_MAX_NB + i];
         if (i == 0) s.misc[MISC_UGPREV] = st.ugprev[e];
@@ -515,8 +601,7 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
             int lev;
             if (mode & MODE_GOV_DRAW) {
                 const uint4 x = philox4x32_10(make_uint4(0u, (uint32_t)e, gs, 1u), k0, k1);
-                const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
-                lev = below(xs[i], p.tax_levels);
+                lev = below(i == 0 ? x.x : i == 1 ? x.y : i == 2 ? x.z : x.w, p.tax_levels);
             } else {
                 lev = io.gov_act[row * p.nb + i];
             }
@@ -572,16 +657,13 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
         }
         __syncthreads();
 
-        for (int l = i; l < L; l += NT) s.lvl_n[l] = s.lvl_old[l] + s.lvl_new[l];
+        // where this step's orders go; trades per resource K = max_q min(#bids >= q, #asks <= q)
         if (warp == 0) warp_excl_scan(s.lvl_new, s.lvl_nstart, L, lane);
-        __syncthreads();
-
-        if (my_l >= 0) s.newkey[s.lvl_nstart[my_l] + my_slot] = ((unsigned long long)tbk << 32) | (uint32_t)i;
-        // trades per resource: K = max_q min(#bids >= q, #asks <= q)
         for (int r = warp; r < R; r += NW) {
             const int q = lane;
-            const int bc = q < P ? s.lvl_n[(r * 2) * P + q] : 0;
-            const int ac = q < P ? s.lvl_n[(r * 2 + 1) * P + q] : 0;
+            const int lb = (r * 2) * P + q, la = (r * 2 + 1) * P + q;
+            const int bc = q < P ? s.lvl_old[lb] + s.lvl_new[lb] : 0;
+            const int ac = q < P ? s.lvl_old[la] + s.lvl_new[la] : 0;
             int B = bc, S = ac;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -593,11 +675,17 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
             int m = q < P ? min(B, S) : 0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(FULL, m, o));
-            if (q < P) { s.bid_before[r * P + q] = B - bc; s.ask_before[r * P + q] = S - ac; }
+            if (q < P) {
+                s.bid_before[r * P + q] = B - bc;
+                s.ask_before[r * P + q] = S - ac;
+                s.lvl_n[lb] = bc;
+                s.lvl_n[la] = ac;
+            }
             if (lane == 0) s.kmatch[r] = m;
         }
         __syncthreads();
-
+        if (my_l >= 0) s.newkey[s.lvl_nstart[my_l] + my_slot] = ((unsigned long long)tbk << 32) | (uint32_t)i;
+        __syncthreads();
         // this step's orders in priority order within their level (random key, then agent)
         if (my_l >= 0) {
             const unsigned long long mk = ((unsigned long long)tbk << 32) | (uint32_t)i;
@@ -631,36 +719,19 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
                 atomicAdd(&s.d_nord[seller], 1);
             }
         }
-        for (int l = i; l < L; l += NT) {
-            const int r = l / (2 * P), side = (l / P) & 1, q = l % P;
-            const int before = side ? s.ask_before[r * P + q] : s.bid_before[r * P + q];
-            const int m = s.kmatch[r] - before;
-            s.lvl_rm[l] = m < 0 ? 0 : (m > s.lvl_n[l] ? s.lvl_n[l] : m);
-        }
-        __syncthreads();
-
-        // 3. expiry: orders that have now taken part in `expire` rounds
+        // 3. expiry (level owners): after the matched prefix, the orders that have
+        //    now taken part in `expire` rounds leave; escrow goes back
         const int thr = t + 1 - p.expire;
-        for (int l = i; l < L; l += NT) {
-            int lo = s.lvl_rm[l], hi = s.lvl_n[l];
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if ((int)(seq_get(s, l, mid) >> 16) <= thr) lo = mid + 1; else hi = mid;
-            }
-            s.lvl_exp[l] = lo - s.lvl_rm[l];
-            s.lvl_new[l] = s.lvl_n[l] - lo;          // survivors
-        }
-        __syncthreads();
-        if (warp == 0) warp_excl_scan(s.lvl_exp, s.lvl_xstart, L, lane);
-        if (warp == (NW > 1 ? 1 : 0)) warp_excl_scan(s.lvl_new, s.lvl_cstart, L, lane);
-        __syncthreads();
-        {
-            const int X = s.lvl_xstart[L];
-            for (int j = i; j < X; j += NT) {
-                const int l = find_level(s.lvl_xstart, L, j);
-                const uint32_t o = seq_get(s, l, s.lvl_rm[l] + j - s.lvl_xstart[l]);
+        for (int l = owner; l < L; l += NT) {
+            const int r = l / (2 * P), side = (l / P) & 1, q = l % P;
+            const int n = s.lvl_n[l];
+            const int before = side ? s.ask_before[r * P + q] : s.bid_before[r * P + q];
+            int idx = s.kmatch[r] - before;
+            idx = idx < 0 ? 0 : (idx > n ? n : idx);
+            while (idx < n) {
+                const uint32_t o = seq_get(s, l, idx);
+                if ((int)(o >> 16) > thr) break;
                 const int who = o & 0xFFFF;
-                const int r = l / (2 * P), side = (l / P) & 1, q = l % P;
                 if (side == 0) {
                     atomicAdd(&s.d_coin[who], p.ticks[q]);
                     atomicAdd(&s.d_esc[who], p.ticks[q]);
@@ -669,18 +740,20 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
                     atomicAdd(&s.d_inve[r * NT + who], 1);
                 }
                 atomicAdd(&s.d_nord[who], 1);
+                ++idx;
             }
-        }
-        // compaction of the survivors into the other book buffer
-        const int Ctot = s.lvl_cstart[L];
-        for (int j = i; j < Ctot; j += NT) {
-            const int l = find_level(s.lvl_cstart, L, j);
-            s.book_alt[j] = seq_get(s, l, s.lvl_rm[l] + s.lvl_exp[l] + j - s.lvl_cstart[l]);
+            s.lvl_rm[l] = idx;                  // removed by matching or expiry
+            s.lvl_exp[l] = n - idx;             // survivors
         }
         __syncthreads();
-        { uint32_t* tmp = s.book; s.book = s.book_alt; s.book_alt = tmp; }
-        for (int l = i; l < L; l += NT) { s.lvl_old[l] = s.lvl_new[l]; s.lvl_start[l] = s.lvl_cstart[l]; }
-        if (i == 0) s.lvl_start[L] = Ctot;
+        if (warp == 0) warp_excl_scan(s.lvl_exp, s.lvl_cstart, L, lane);
+        __syncthreads();
+        // survivors into the other book buffer, one warp per level
+        for (int l = warp; l < L; l += NW) {
+            const int c = s.lvl_exp[l], src0 = s.lvl_rm[l], dst0 = s.lvl_cstart[l];
+            for (int j = lane; j < c; j += 32) s.book_alt[dst0 + j] = seq_get(s, l, src0 + j);
+        }
+        market_stats(p, s, s.lvl_exp, i, Ae);
         if (live) {
             g.coin = __fadd_rn(g.coin, __fmul_rn(p.tick, (float)s.d_coin[i]));
             g.income = __fadd_rn(g.income, __fmul_rn(p.tick, (float)s.d_inc[i]));
@@ -692,6 +765,9 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
             }
         }
         __syncthreads();
+        { uint32_t* tmp = s.book; s.book = s.book_alt; s.book_alt = tmp; }
+        for (int l = owner; l < L; l += NT) { s.lvl_old[l] = s.lvl_exp[l]; s.lvl_start[l] = s.lvl_cstart[l]; }
+        if (owner == 0) s.lvl_start[L] = s.lvl_cstart[L];
 
         // 4. period end: bracket tax, equal redistribution, new period of earnings
         if ((t + 1) % p.T_tax == 0) {
@@ -723,7 +799,9 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
         } else if (io.rew && i < p.A) {
             io.rew[row * p.A + i] = 0.0f;
         }
-        population_stats<NT>(p, s, g, i, Ae);
+        fill_stats<NT>(p, s, g, i, Ae);
+        __syncthreads();
+        population_stats<NT>(p, s, i, Ae);
         if (i == 0) {
             const float ug = social_welfare(p, s);
             if (io.grew) io.grew[row] = __fsub_rn(ug, s.misc[MISC_UGPREV]);
@@ -738,13 +816,17 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
         if (ended) {
             t = 0;
             ep += 1;
+            __syncthreads();
             start_agent<NT>(p, s, g, i, e, ep, k0, k1, live);
             for (int l = i; l < L; l += NT) s.lvl_old[l] = 0;
             for (int l = i; l <= L; l += NT) s.lvl_start[l] = 0;
             if (i < EJ_MAX_NB) s.rates[i] = 0.0f;
+            fill_stats<NT>(p, s, g, i, Ae);
             __syncthreads();
-            population_stats<NT>(p, s, g, i, Ae);
+            market_stats(p, s, s.lvl_old, i, Ae);
+            population_stats<NT>(p, s, i, Ae);
             if (i == 0) s.misc[MISC_UGPREV] = social_welfare(p, s);
+            __syncthreads();
         }
         // 7. observation of the new state
         observe<NT>(p, s, g, io, row, i, Ae, t);

@@ -83,7 +83,7 @@ def compare_env(g, ref, params, A_e, obs0_ref=None):
         errs["rew"] = _close(g["rew"][:, :A_e], ref["rew"], scale * 2, "rew")
         assert not g["rew"][:, A_e:].any()
     if "gobs" in g:
-        M = 3 + R
+        M = 3
         ro = ref["gobs"]
         scale = np.zeros_like(ro)
         for m in range(M):

@@ -52,7 +52,7 @@ def test_defaults_match_table2_transcriptions(lib):
 
 def test_sizes(lib):
     s = N.sizes(N.make_params(E=1024, A=100))
-    assert (s.n_actions, s.obs_dim, s.gobs_dim, s.mask_words) == (24, 25, 20, 1)
+    assert (s.n_actions, s.obs_dim, s.gobs_dim, s.mask_words) == (24, 25, 14, 1)
     assert s.threads == 128 and s.book_cap == 1500
     assert s.smem_bytes * 7 <= 227 * 1024 - 7 * 1024          # 7 CTAs per SM
     s = N.sizes(N.make_params(R=12, P=3, price_ticks=[1, 2, 3]))

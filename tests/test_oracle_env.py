@@ -48,7 +48,7 @@ def test_action_counts(R, P, n):
 
 def test_sizes_default():
     p = default_params()
-    assert oenv.obs_dim(p) == 25 and oenv.gobs_dim(p) == 20 and oenv.mask_words(p) == 1
+    assert oenv.obs_dim(p) == 25 and oenv.gobs_dim(p) == 14 and oenv.mask_words(p) == 1
 
 
 # ------------------------------------------------------------- closed forms
