@@ -187,13 +187,13 @@ ej_status env_reset(const EjParams* p, void* state, const int32_t* pop_sizes,
 /* env_step (Sec. 3 "Overall design": step(key, state, action, params)),
  * n_steps steps in one launch, state kept on chip between steps.
  * act      (device) int32[n][E][A] population actions (ids above), or NULL to
- *          draw uniform random actions, gather draws and tie-break keys in
- *          the kernel with the counter mapping above (then gather_u and tb
- *          must be NULL too).
+ *          draw uniform random actions in the kernel with the counter mapping
+ *          above (then gather_u and tb must be NULL too).
  * gov_act  (device) int32[n][E][nb] rate levels (read at period starts only),
  *          or NULL to draw uniform levels in the kernel.
  * gather_u (device) float[n][E][A] gather draws u in [0,1); rho = gather_rho*u.
  * tb       (device) uint32[n][E][A] tie-break keys of orders placed that step.
+ *          gather_u and tb are both given or both NULL (drawn in the kernel).
  * rew      (device) float[n][E][A] population rewards      (may be NULL)
  * grew     (device) float[n][E]    government rewards      (may be NULL)
  * done     (device) uint8[n][E]    1 when the step ended the episode (may be NULL)
@@ -213,6 +213,142 @@ ej_status env_step(const EjParams* p, void* state, int32_t n_steps,
 ej_status ej_fill_draws(const EjParams* p, uint64_t seed, uint32_t g0, int32_t n_steps,
                         int32_t* act, float* gather_u, uint32_t* tb, float* policy_u,
                         int32_t* gov_act, void* stream);
+
+/* ------------------------------------------------------------------ policy
+ * Actor and critic of Section 4: two hidden layers of `hidden` units with
+ * ReLU, weights shared by all population agents (EJ_NET_POP: input D, one
+ * head of nA logits, masked) and a separate pair for the government
+ * (EJ_NET_GOV: input G, nb heads of tax_levels logits).  Parameter vector
+ * (float32, row-major, y = x W + b, 16-byte aligned), in this order:
+ *   W1 [in][H], b1 [H], W2 [H][H], b2 [H], W3 [H][O], b3 [O]      (actor)
+ *   V1 [in][H], c1 [H], V2 [H][H], c2 [H], V3 [H], c3 [1]          (critic)
+ * with O = nA (population) or nb * tax_levels (government); each tensor
+ * starts at a multiple of 4 floats (the gaps are padding, ignored).
+ * Sampling (Section 3 "Action masking": forbidden actions have probability 0)
+ * is by inverse CDF on the masked softmax, computed in float32 with the
+ * library's own exp (Cody-Waite reduction + degree-7 Taylor polynomial),
+ * weights summed in action order; uniforms are x3 of the population counter
+ * (i, e, g, 0) and x_b of the government counter (0, e, g, 1) at the state's
+ * global step g, unless given. */
+typedef enum { EJ_NET_POP = 0, EJ_NET_GOV = 1 } ej_net;
+typedef enum { EJ_FP32 = 0, EJ_BF16 = 1 } ej_precision;
+
+/* Floats of one network's parameter vector. hidden: multiple of 32 in [32, 256]. */
+ej_status ej_net_floats(const EjParams* p, int32_t net, int32_t hidden, uint64_t* n_floats);
+
+/* policy_forward: actor + critic over every row of the current state, and a
+ * sampled action per row.
+ * state   (device) the environment state (read: global step, Philox key).
+ * weights (device) float[ej_net_floats].
+ * obs     (device) float[E][A][D] (population) or float[E][G] (government).
+ * mask    (device) uint32[E][A][W] (population; NULL: all allowed), ignored for the government.
+ * u       (device) float[rows][heads] sampling uniforms, or NULL (Philox, above).
+ * act     (device) int32[E][A] or int32[E][nb]; NULL: no sampling (values only).
+ * logp, entropy (device) float[rows] (sum over heads); value float[rows];
+ * logits  (device) float[rows][O] (may be NULL).  Rows with no allowed action
+ * get action 0, logp 0, entropy 0. */
+ej_status policy_forward(const EjParams* p, const void* state, int32_t net, int32_t hidden,
+                         int32_t precision, const float* weights, const float* obs,
+                         const uint32_t* mask, const float* u, int32_t* act, float* logp,
+                         float* value, float* entropy, float* logits, void* stream);
+
+/* Rollout buffer (device pointers, caller-owned).  Slot 0 of obs, gobs and
+ * mask must hold the current observation (from env_reset or the previous
+ * rollout's slot T). */
+typedef struct {
+    float* obs;          /* [T+1][E][A][D] */
+    float* gobs;         /* [T+1][E][G] */
+    uint32_t* mask;      /* [T+1][E][A][W] */
+    int32_t* act;        /* [T][E][A] */
+    int32_t* gact;       /* [T][E][nb] */
+    float* logp;         /* [T][E][A] */
+    float* glogp;        /* [T][E] */
+    float* value;        /* [T+1][E][A]  (slot T: bootstrap value) */
+    float* gvalue;       /* [T+1][E] */
+    float* rew;          /* [T][E][A] */
+    float* grew;         /* [T][E] */
+    uint8_t* done;       /* [T][E] */
+} EjRollout;
+
+/* rollout: T steps of {population policy, government policy, env_step},
+ * then the critics on slot T.  3T + 2 launches on `stream` (capture them in
+ * a CUDA graph to replay).  Gather draws and tie-break keys come from the
+ * kernel's Philox streams. */
+ej_status rollout(const EjParams* p, void* state, int32_t T, int32_t hidden, int32_t precision,
+                  const float* pop_weights, const float* gov_weights, const EjRollout* buf,
+                  void* stream);
+
+/* --------------------------------------------------------------------- PPO
+ * Clipped PPO (Section 4; Table 2) for the population and the government
+ * networks at once (simultaneous training, Section 4): GAE, then `epochs`
+ * passes over `minibatches` shuffled minibatches, each an Adam step of both
+ * networks.  Loss per minibatch (advantages normalised over the minibatch):
+ *   -mean(min(r A, clip(r, 1-clip, 1+clip) A))
+ *   + vf_coef * mean(0.5 max((v - R)^2, (v_old + clip(v - v_old, +-vclip) - R)^2))
+ *   - ent_coef * mean(entropy),       r = exp(logp - logp_old), R = A + v_old.
+ * Minibatch m of an epoch holds the rollout rows pi(p), p in
+ * [floor(m N / M), floor((m+1) N / M)), N = T * rows per step, where pi is
+ * the Feistel permutation of [0, N) (4 rounds on 2h bits, Philox word x0 of
+ * counter (R, round, shuffle_ctr, 4) as round function, cycle walking into
+ * [0, N)) keyed by `seed`.  ppo_update uses shuffle_ctr = update_index *
+ * epochs + epoch for the population, with bit 31 set for the government. */
+typedef struct {
+    float gamma;         /* discount (0.99) */
+    float lam;           /* GAE lambda (0.95) */
+    float clip;          /* ratio clip (0.2) */
+    float vf_coef;       /* value-loss coefficient (0.25) */
+    float vclip;         /* value clip (10) */
+    float ent_coef;      /* entropy coefficient (0.1; the caller anneals it) */
+    float lr;            /* Adam learning rate (5e-4; the caller anneals it) */
+    float beta1, beta2, eps;   /* Adam (0.9, 0.999, 1e-5) */
+    int32_t epochs;      /* 4 */
+    int32_t minibatches; /* 8 */
+    uint64_t seed;       /* key of the minibatch shuffles */
+} EjPpoParams;
+
+ej_status ej_ppo_params_default(EjPpoParams* pp);
+
+/* Bytes of the workspace the PPO calls need (caller-allocated, 256-byte
+ * aligned, contents need no initialisation).  hidden in {32, 64, 96, 128}. */
+ej_status ej_ppo_workspace_bytes(const EjParams* p, const EjPpoParams* pp, int32_t T,
+                                 int32_t hidden, uint64_t* bytes);
+
+/* Byte offsets in the workspace of the advantages and returns (float
+ * [T][rows]) of the population and the government: offsets[4] = {adv_pop,
+ * ret_pop, adv_gov, ret_gov} (for inspection). */
+ej_status ej_ppo_workspace_offsets(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_t hidden,
+                                   uint64_t* offsets);
+
+/* GAE of both networks from a filled rollout buffer into the workspace:
+ * A_t = d_t + gamma lam (1 - done_t) A_{t+1}, d_t = r_t + gamma (1 - done_t) V_{t+1} - V_t. */
+ej_status ppo_advantages(const EjParams* p, const EjPpoParams* pp, int32_t T, const EjRollout* buf,
+                         void* workspace, void* stream);
+
+/* Gradient of one minibatch's loss for one network (net: EJ_NET_POP or
+ * EJ_NET_GOV) into grad (device float[ej_net_floats], padding zeroed), after
+ * ppo_advantages.  stats_out (device double[8], may be NULL): sums over the
+ * minibatch of {advantage, advantage^2, policy loss, value loss, entropy,
+ * clipped indicator, logp_old - logp}. */
+ej_status ppo_minibatch_grad(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_t hidden,
+                             int32_t precision, int32_t net, const float* weights,
+                             const EjRollout* buf, void* workspace, uint32_t shuffle_ctr,
+                             int32_t minibatch, float* grad, double* stats_out, void* stream);
+
+/* One Adam step (Kingma and Ba, 2015) over n parameters; step counts from 1. */
+ej_status adam_step(uint64_t n, float* params, const float* grad, float* m, float* v, int32_t step,
+                    float lr, float beta1, float beta2, float eps, void* stream);
+
+/* The whole update: ppo_advantages, then epochs x minibatches x {population,
+ * government} gradient + Adam step.  Adam moments m, v (device, zero before
+ * the first update) as long as the parameter vectors; adam_steps_done = Adam
+ * steps taken before this call.  stats_out (device float[2][8], may be NULL):
+ * per network mean policy loss, value loss, entropy, clip fraction,
+ * logp_old - logp over all minibatch rows of the update. */
+ej_status ppo_update(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_t hidden,
+                     int32_t precision, float* pop_weights, float* gov_weights, float* pop_m,
+                     float* pop_v, float* gov_m, float* gov_v, int32_t adam_steps_done,
+                     uint32_t update_index, const EjRollout* buf, void* workspace,
+                     float* stats_out, void* stream);
 
 /* Description of the last error returned to the calling thread. */
 const char* ej_last_error(void);

@@ -42,6 +42,22 @@ class EjSizes(C.Structure):
     ]
 
 
+class EjRollout(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("obs", "gobs", "mask", "act", "gact", "logp", "glogp",
+                                           "value", "gvalue", "rew", "grew", "done")]
+
+
+class EjPpoParams(C.Structure):
+    _fields_ = [("gamma", C.c_float), ("lam", C.c_float), ("clip", C.c_float), ("vf_coef", C.c_float),
+                ("vclip", C.c_float), ("ent_coef", C.c_float), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("epochs", C.c_int32),
+                ("minibatches", C.c_int32), ("seed", C.c_uint64)]
+
+
+NET_POP, NET_GOV = 0, 1
+FP32, BF16 = 0, 1
+
+
 class EjError(RuntimeError):
     pass
 
@@ -60,6 +76,24 @@ _PROTOS = {
                            _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "ej_fill_draws": (C.c_int, [C.POINTER(EjParams), C.c_uint64, C.c_uint32, C.c_int32,
                                 _VP, _VP, _VP, _VP, _VP, _VP]),
+    "ej_net_floats": (C.c_int, [C.POINTER(EjParams), C.c_int32, C.c_int32, C.POINTER(C.c_uint64)]),
+    "policy_forward": (C.c_int, [C.POINTER(EjParams), _VP, C.c_int32, C.c_int32, C.c_int32, _VP, _VP,
+                                 _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "rollout": (C.c_int, [C.POINTER(EjParams), _VP, C.c_int32, C.c_int32, C.c_int32, _VP, _VP,
+                          C.c_void_p, _VP]),
+    "ej_ppo_params_default": (C.c_int, [C.POINTER(EjPpoParams)]),
+    "ej_ppo_workspace_bytes": (C.c_int, [C.POINTER(EjParams), C.POINTER(EjPpoParams), C.c_int32, C.c_int32,
+                                         C.POINTER(C.c_uint64)]),
+    "ej_ppo_workspace_offsets": (C.c_int, [C.POINTER(EjParams), C.POINTER(EjPpoParams), C.c_int32, C.c_int32,
+                                           C.POINTER(C.c_uint64)]),
+    "ppo_advantages": (C.c_int, [C.POINTER(EjParams), C.POINTER(EjPpoParams), C.c_int32, C.c_void_p, _VP, _VP]),
+    "ppo_minibatch_grad": (C.c_int, [C.POINTER(EjParams), C.POINTER(EjPpoParams), C.c_int32, C.c_int32,
+                                     C.c_int32, C.c_int32, _VP, C.c_void_p, _VP, C.c_uint32, C.c_int32,
+                                     _VP, _VP, _VP]),
+    "adam_step": (C.c_int, [C.c_uint64, _VP, _VP, _VP, _VP, C.c_int32, C.c_float, C.c_float, C.c_float,
+                            C.c_float, _VP]),
+    "ppo_update": (C.c_int, [C.POINTER(EjParams), C.POINTER(EjPpoParams), C.c_int32, C.c_int32, C.c_int32,
+                             _VP, _VP, _VP, _VP, _VP, _VP, C.c_int32, C.c_uint32, C.c_void_p, _VP, _VP, _VP]),
     "ej_last_error": (C.c_char_p, []),
 }
 

@@ -203,15 +203,15 @@ ej_status env_step(const EjParams* p, void* state, int32_t n_steps, const int32_
     if (!state) return fail(EJ_ERR_ARG, "state is NULL");
     if ((uintptr_t)state % 256) return fail(EJ_ERR_ARG, "state must be 256-byte aligned");
     if (n_steps < 0) return fail(EJ_ERR_ARG, "n_steps must be >= 0");
-    const bool any = act || gather_u || tb;
-    if (any && !(act && gather_u && tb))
-        return fail(EJ_ERR_ARG, "act, gather_u and tb must be all given or all NULL");
+    if ((gather_u == nullptr) != (tb == nullptr))
+        return fail(EJ_ERR_ARG, "gather_u and tb must be both given or both NULL");
+    if (!act && gather_u) return fail(EJ_ERR_ARG, "gather_u and tb need act");
     if (n_steps == 0) return EJ_OK;
     DevIO io;
     memset(&io, 0, sizeof io);
     io.act = act; io.gov_act = gov_act; io.gather_u = gather_u; io.tb = tb;
     io.rew = rew; io.grew = grew; io.done = done; io.obs = obs; io.gobs = gobs; io.mask = mask;
-    int mode = (act ? 0 : MODE_POP_DRAW) | (gov_act ? 0 : MODE_GOV_DRAW);
+    int mode = (act ? 0 : MODE_POP_DRAW) | (gather_u ? 0 : MODE_AUX_DRAW) | (gov_act ? 0 : MODE_GOV_DRAW);
     return launch_env(kp, lay, state_pointers(lay, state), io, n_steps, mode, 0, (cudaStream_t)stream);
 }
 

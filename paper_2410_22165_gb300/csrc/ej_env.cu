@@ -584,14 +584,15 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
         float gu = 0.0f;
         uint32_t tbk = 0;
         if (live) {
-            if (mode & MODE_POP_DRAW) {
+            if (mode & (MODE_POP_DRAW | MODE_AUX_DRAW)) {
                 const uint4 x = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)e, gs, 0u), k0, k1);
                 a = below(x.x, p.nA);
                 gu = u01(x.y);
                 tbk = x.z;
-            } else {
+            }
+            if (!(mode & MODE_POP_DRAW)) a = io.act[row * p.A + i];
+            if (!(mode & MODE_AUX_DRAW)) {
                 const size_t k = row * p.A + i;
-                a = io.act[k];
                 gu = io.gather_u[k];
                 tbk = io.tb[k];
             }

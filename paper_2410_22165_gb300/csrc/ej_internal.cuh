@@ -49,7 +49,7 @@ DevState state_pointers(const Layout& lay, void* base);
 ej_status fail(ej_status s, const char* fmt, ...);
 
 // Launchers (ej_env.cu).
-enum : int { MODE_RESET = 1, MODE_POP_DRAW = 2, MODE_GOV_DRAW = 4 };
+enum : int { MODE_RESET = 1, MODE_POP_DRAW = 2, MODE_GOV_DRAW = 4, MODE_AUX_DRAW = 8 };
 ej_status launch_env(const KParams& kp, const Layout& lay, const DevState& st, const DevIO& io,
                      int n_steps, int mode, uint64_t seed, cudaStream_t stream);
 ej_status launch_fill_draws(const KParams& kp, uint64_t seed, uint32_t g0, int n_steps,

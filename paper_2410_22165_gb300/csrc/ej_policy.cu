@@ -1,0 +1,86 @@
+// Policy forward and masked action sampling, float32 on the CUDA cores.
+//
+// Actor and critic are the 2 x H MLPs of Section 4 (ReLU hidden layers), one
+// set of weights shared by all population agents and one for the government.
+// A CTA takes tiles of 64 rows (agents); the activations of a tile stay in
+// shared memory from the observation to the sampled action; weights are read
+// through the L1 cache.  The sampler draws from the masked softmax (Section 3
+// "Action masking": forbidden actions have probability zero) by inverse CDF.
+#include <cfloat>
+#include <cmath>
+
+#include "ej_internal.cuh"
+#include "ej_policy.cuh"
+
+namespace ej {
+
+namespace {
+
+__global__ void __launch_bounds__(NTH, 2) policy_fp32_kernel(PolicyArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    const int H = a.H, O = a.O, in_dim = a.in_dim;
+    const int ldx = a.in_pad, ldh = H + 4, ldo = O + 1;
+    float* xs = sm;                                  // [TILE][ldx]
+    float* hA = xs + TILE * ldx;                     // [TILE][ldh]
+    float* hB = hA + TILE * ldh;                     // [TILE][ldh]
+    float* lg = hB + TILE * ldh;                     // [TILE][ldo]
+    float* val = lg + TILE * ldo;                    // [TILE]
+    const NetOffsets off = net_offsets(in_dim, H, O);
+    const float* w = a.weights;
+    const int n_tiles = (a.rows + TILE - 1) / TILE;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int row0 = tile * TILE;
+        // observations of the tile (zero rows past the end, zero padding columns)
+        for (int idx = threadIdx.x; idx < TILE * ldx; idx += NTH) {
+            const int r = idx / ldx, k = idx % ldx;
+            const int row = row0 + r;
+            xs[idx] = (row < a.rows && k < in_dim) ? a.x[(size_t)row * in_dim + k] : 0.0f;
+        }
+        __syncthreads();
+        // actor: two hidden layers and the logits
+        dense_tile(xs, ldx, in_dim, w + off.W1, w + off.b1, H, hA, ldh, true);
+        __syncthreads();
+        dense_tile(hA, ldh, H, w + off.W2, w + off.b2, H, hB, ldh, true);
+        __syncthreads();
+        head_tile(hB, ldh, H, w + off.W3, w + off.b3, O, lg, ldo);
+        __syncthreads();
+        // critic
+        dense_tile(xs, ldx, in_dim, w + off.V1, w + off.c1, H, hA, ldh, true);
+        __syncthreads();
+        dense_tile(hA, ldh, H, w + off.V2, w + off.c2, H, hB, ldh, true);
+        __syncthreads();
+        value_tile(hB, ldh, H, w + off.V3, w[off.c3], val);
+        __syncthreads();
+        // sampling, one thread per row
+        if (threadIdx.x < TILE) {
+            const int r = threadIdx.x, row = row0 + r;
+            if (row < a.rows) sample_row(a, row, lg + r * ldo, val[r]);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+size_t policy_fp32_smem(int in_pad, int H, int O) {
+    return sizeof(float) * ((size_t)TILE * in_pad + 2 * (size_t)TILE * (H + 4) + (size_t)TILE * (O + 1) + TILE);
+}
+
+ej_status launch_policy_fp32(const PolicyArgs& a, cudaStream_t stream) {
+    const size_t smem = policy_fp32_smem(a.in_pad, a.H, a.O);
+    static size_t configured = 0;
+    if (configured < smem) {
+        cudaError_t err = cudaFuncSetAttribute(policy_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
+        configured = 227 * 1024;
+    }
+    const int n_tiles = (a.rows + TILE - 1) / TILE;
+    int grid = n_tiles < 2 * 152 ? n_tiles : 2 * 152;
+    if (grid < 1) grid = 1;
+    policy_fp32_kernel<<<grid, NTH, smem, stream>>>(a);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "policy kernel launch: %s", cudaGetErrorString(err));
+    return EJ_OK;
+}
+
+}  // namespace ej

@@ -1,0 +1,216 @@
+// Policy forward / sampling: shared declarations of the float32 and bf16 paths.
+#pragma once
+
+#include <cfloat>
+
+#include "ej_internal.cuh"
+
+namespace ej {
+
+// Offsets of the parameter vector of one network (actor then critic):
+// W1 [in][H], b1 [H], W2 [H][H], b2 [H], W3 [H][O], b3 [O],
+// V1 [in][H], c1 [H], V2 [H][H], c2 [H], V3 [H], c3 [1]; every tensor starts
+// at a multiple of 4 floats (16 bytes), the gaps are padding.
+struct NetOffsets {
+    size_t W1, b1, W2, b2, W3, b3, V1, c1, V2, c2, V3, c3, total;
+};
+
+__host__ __device__ inline size_t pad4(size_t x) { return (x + 3) & ~size_t(3); }
+
+__host__ __device__ inline NetOffsets net_offsets(int in, int H, int O) {
+    NetOffsets o;
+    size_t p = 0;
+    o.W1 = p; p = pad4(p + (size_t)in * H);
+    o.b1 = p; p = pad4(p + H);
+    o.W2 = p; p = pad4(p + (size_t)H * H);
+    o.b2 = p; p = pad4(p + H);
+    o.W3 = p; p = pad4(p + (size_t)H * O);
+    o.b3 = p; p = pad4(p + O);
+    o.V1 = p; p = pad4(p + (size_t)in * H);
+    o.c1 = p; p = pad4(p + H);
+    o.V2 = p; p = pad4(p + (size_t)H * H);
+    o.c2 = p; p = pad4(p + H);
+    o.V3 = p; p = pad4(p + H);
+    o.c3 = p; p = pad4(p + 1);
+    o.total = p;
+    return o;
+}
+
+struct PolicyArgs {
+    int rows;            // rows of x (E*A for the population, E for the government)
+    int per_env;         // rows per environment (A or 1)
+    int in_dim, in_pad;  // observation width and its padding to a multiple of 4
+    int H, O;            // hidden units, logits per row (n_heads * head)
+    int n_heads, head;   // population: 1 head of nA (masked); government: nb heads of tax_levels
+    int W;               // mask words per row (0: every action allowed)
+    int stream_id;       // Philox stream of the sampling uniforms (0 population, 1 government)
+    const float* weights;
+    const float* x;
+    const uint32_t* mask;
+    const float* u;               // [rows][n_heads] or NULL: Philox at the state's global step
+    const uint32_t* gstep;        // state: global step per environment
+    const uint32_t* key;          // state: Philox key
+    int32_t* act;                 // [rows][n_heads] or NULL (no sampling)
+    float* logp;                  // [rows] sum over heads
+    float* value;                 // [rows]
+    float* entropy;               // [rows] sum over heads (may be NULL)
+    float* logits;                // [rows][O] (may be NULL)
+};
+
+// exp on float32 by Cody-Waite reduction (Cody and Waite, "Software Manual for
+// the Elementary Functions", 1980) and the degree-7 Taylor polynomial of e^r
+// on |r| <= ln2/2, Horner's rule, each operation rounded once; 0 below -80.
+__device__ __forceinline__ float exp32(float x) {
+    if (x < -80.0f) return 0.0f;
+    const float n = rintf(__fmul_rn(x, 0x1.715476p+0f));
+    float r = __fsub_rn(x, __fmul_rn(n, 0x1.62e4p-1f));
+    r = __fsub_rn(r, __fmul_rn(n, 0x1.7f7d1cp-20f));
+    float p = 0x1.a01a02p-13f;
+    p = __fadd_rn(__fmul_rn(p, r), 0x1.6c16c2p-10f);
+    p = __fadd_rn(__fmul_rn(p, r), 0x1.111112p-7f);
+    p = __fadd_rn(__fmul_rn(p, r), 0x1.555556p-5f);
+    p = __fadd_rn(__fmul_rn(p, r), 0x1.555556p-3f);
+    p = __fadd_rn(__fmul_rn(p, r), 0.5f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f);
+    const int ni = (int)n;
+    return __fmul_rn(p, __int_as_float((ni + 127) << 23));
+}
+
+// Inverse-CDF draw of one head from its logits l[0..K) under `valid` bits.
+// Returns the action (-1 if nothing is allowed) and adds the head's log
+// probability and entropy.
+__device__ __forceinline__ int sample_head(const float* l, int K, const uint32_t* valid_words,
+                                           int bit0, float u, float& logp, float& ent) {
+    float m = -FLT_MAX;
+    bool any = false;
+    for (int j = 0; j < K; ++j) {
+        const bool ok = !valid_words || ((valid_words[(bit0 + j) >> 5] >> ((bit0 + j) & 31)) & 1u);
+        if (ok) { any = true; m = fmaxf(m, l[j]); }
+    }
+    if (!any) return -1;
+    float S = 0.0f, dot = 0.0f;
+    for (int j = 0; j < K; ++j) {
+        const bool ok = !valid_words || ((valid_words[(bit0 + j) >> 5] >> ((bit0 + j) & 31)) & 1u);
+        if (ok) {
+            const float d = __fsub_rn(l[j], m);
+            const float w = exp32(d);
+            S = __fadd_rn(S, w);
+            dot = fmaf(w, d, dot);
+        }
+    }
+    const float thr = __fmul_rn(u, S);
+    float c = 0.0f;
+    int act = -1, last = -1;
+    for (int j = 0; j < K; ++j) {
+        const bool ok = !valid_words || ((valid_words[(bit0 + j) >> 5] >> ((bit0 + j) & 31)) & 1u);
+        if (ok) {
+            last = j;
+            c = __fadd_rn(c, exp32(__fsub_rn(l[j], m)));
+            if (act < 0 && c > thr) act = j;
+        }
+    }
+    if (act < 0) act = last;
+    const float logS = logf(S);
+    logp += (l[act] - m) - logS;
+    ent += logS - dot / S;
+    return act;
+}
+
+__device__ __forceinline__ void sample_row(const PolicyArgs& a, int row, const float* l, float value) {
+    a.value[row] = value;
+    if (a.logits)
+        for (int j = 0; j < a.O; ++j) a.logits[(size_t)row * a.O + j] = l[j];
+    if (!a.act) return;
+    const int e = row / a.per_env, i = row % a.per_env;
+    float us[EJ_MAX_NB];
+    if (a.u) {
+        for (int h = 0; h < a.n_heads; ++h) us[h] = a.u[(size_t)row * a.n_heads + h];
+    } else {
+        const uint32_t g = a.gstep[e];
+        const uint4 x = philox4x32_10(make_uint4(a.stream_id == 0 ? (uint32_t)i : 0u, (uint32_t)e, g,
+                                                 (uint32_t)a.stream_id), a.key[0], a.key[1]);
+        if (a.stream_id == 0) us[0] = u01(x.w);
+        else { us[0] = u01(x.x); us[1] = u01(x.y); us[2] = u01(x.z); us[3] = u01(x.w); }
+    }
+    float logp = 0.0f, ent = 0.0f;
+    const uint32_t* mw = a.W ? a.mask + (size_t)row * a.W : nullptr;
+    bool none = false;
+    for (int h = 0; h < a.n_heads; ++h) {
+        int act = sample_head(l + h * a.head, a.head, mw, h * a.head, us[h < EJ_MAX_NB ? h : 0], logp, ent);
+        if (act < 0) { act = 0; none = true; }
+        a.act[(size_t)row * a.n_heads + h] = act;
+    }
+    if (none) { logp = 0.0f; ent = 0.0f; }
+    a.logp[row] = logp;
+    if (a.entropy) a.entropy[row] = ent;
+}
+
+// Row tiles of the SIMT (float32) network kernels.
+constexpr int TILE = 64;       // rows per tile
+constexpr int NTH = 256;       // threads per CTA
+
+// out[r][c] = act(b[c] + sum_k in[r][k] W[k][c]) for a TILE x N block, N a
+// multiple of 4 (here H = 128); b may be NULL (no bias).  Thread tile: 8 rows x 4 columns.
+__device__ inline void dense_tile(const float* in, int ldi, int K, const float* __restrict__ W,
+                           const float* __restrict__ b, int N, float* out, int ldo, bool relu) {
+    const int t = threadIdx.x;
+    const int groups = N >> 2;                 // column groups of 4
+    for (int base = t; base < groups * (TILE / 8); base += NTH) {
+        const int cg = base % groups, rg = base / groups;
+        const int c0 = cg * 4, r0 = rg * 8;
+        float acc[8][4];
+        const float4 bb = b ? *reinterpret_cast<const float4*>(b + c0) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) { acc[r][0] = bb.x; acc[r][1] = bb.y; acc[r][2] = bb.z; acc[r][3] = bb.w; }
+#pragma unroll 4
+        for (int k = 0; k < K; ++k) {
+            const float4 w = __ldg(reinterpret_cast<const float4*>(W + (size_t)k * N + c0));
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const float x = in[(r0 + r) * ldi + k];
+                acc[r][0] = fmaf(x, w.x, acc[r][0]);
+                acc[r][1] = fmaf(x, w.y, acc[r][1]);
+                acc[r][2] = fmaf(x, w.z, acc[r][2]);
+                acc[r][3] = fmaf(x, w.w, acc[r][3]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            float4 v = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+            if (relu) { v.x = fmaxf(v.x, 0.0f); v.y = fmaxf(v.y, 0.0f); v.z = fmaxf(v.z, 0.0f); v.w = fmaxf(v.w, 0.0f); }
+            *reinterpret_cast<float4*>(out + (r0 + r) * ldo + c0) = v;
+        }
+    }
+}
+
+// Output head of width O (any): one thread per (row, column).
+__device__ inline void head_tile(const float* in, int ldi, int K, const float* __restrict__ W,
+                          const float* __restrict__ b, int O, float* out, int ldo) {
+    for (int idx = threadIdx.x; idx < TILE * O; idx += NTH) {
+        const int r = idx / O, c = idx % O;
+        float acc = b[c];
+        const float* x = in + r * ldi;
+#pragma unroll 8
+        for (int k = 0; k < K; ++k) acc = fmaf(x[k], __ldg(W + (size_t)k * O + c), acc);
+        out[r * ldo + c] = acc;
+    }
+}
+
+// Critic output: one warp per row, lanes split the hidden units.
+__device__ inline void value_tile(const float* in, int ldi, int K, const float* __restrict__ v,
+                           float c, float* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = warp; r < TILE; r += NTH / 32) {
+        float acc = 0.0f;
+        for (int k = lane; k < K; k += 32) acc = fmaf(in[r * ldi + k], __ldg(v + k), acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+        if (lane == 0) out[r] = acc + c;
+    }
+}
+
+size_t policy_fp32_smem(int in_pad, int H, int O);
+ej_status launch_policy_fp32(const PolicyArgs& a, cudaStream_t stream);
+
+}  // namespace ej

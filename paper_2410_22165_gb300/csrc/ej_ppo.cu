@@ -1,0 +1,409 @@
+// PPO update of Section 4 (Table 2: clip 0.2, value coefficient 0.25, value
+// clip 10, entropy coefficient 0.1, GAE lambda 0.95), float32 on the CUDA
+// cores: GAE, per-minibatch advantage normalisation, a fused tile kernel
+// (forward, loss gradient, backward through the activations), a split-K
+// weight-gradient kernel with its reduction, and Adam.
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+
+#include "ej_internal.cuh"
+#include "ej_policy.cuh"
+#include "ej_ppo.cuh"
+
+namespace ej {
+
+namespace {
+
+// ---------------------------------------------------------------- GAE
+__global__ void gae_kernel(const float* __restrict__ rew, const float* __restrict__ value,
+                           const uint8_t* __restrict__ done, int T, int rows, int per_env, float gamma,
+                           float lam, float* __restrict__ adv, float* __restrict__ ret) {
+    const int E = rows / per_env;
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < rows; row += gridDim.x * blockDim.x) {
+        const int e = row / per_env;
+        float next = 0.0f;
+        for (int t = T - 1; t >= 0; --t) {
+            const float nd = done[(size_t)t * E + e] ? 0.0f : 1.0f;
+            const float v = value[(size_t)t * rows + row];
+            const float vn = value[(size_t)(t + 1) * rows + row];
+            const float delta = rew[(size_t)t * rows + row] + gamma * nd * vn - v;
+            next = delta + gamma * lam * nd * next;
+            adv[(size_t)t * rows + row] = next;
+            ret[(size_t)t * rows + row] = next + v;
+        }
+    }
+}
+
+// ------------------------------------------------ minibatch shuffle
+// Feistel permutation of [0, 4^half) restricted to [0, N) by cycle walking
+// (Luby-Rackoff; Black-Rogaway), round function = Philox word x0.
+__device__ __forceinline__ uint32_t feistel(uint32_t x, int half, uint32_t k0, uint32_t k1, uint32_t ctr) {
+    const uint32_t mask = (1u << half) - 1u;
+    uint32_t L = (x >> half) & mask, R = x & mask;
+#pragma unroll
+    for (uint32_t rnd = 0; rnd < 4; ++rnd) {
+        const uint32_t F = philox4x32_10(make_uint4(R, rnd, ctr, 4u), k0, k1).x & mask;
+        const uint32_t nL = R;
+        R = (L ^ F) & mask;
+        L = nL;
+    }
+    return (L << half) | R;
+}
+
+__device__ __forceinline__ uint32_t mb_row(const MbDesc& d, int j) {
+    uint32_t x = feistel((uint32_t)(d.lo + j), d.half, d.k0, d.k1, d.ctr);
+    while (x >= d.N) x = feistel(x, d.half, d.k0, d.k1, d.ctr);
+    return x;
+}
+
+// ------------------------------------- minibatch advantage statistics
+__global__ void adv_stats_kernel(MbDesc d, const float* __restrict__ adv, double* stats) {
+    double s = 0.0, q = 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.count; j += gridDim.x * blockDim.x) {
+        const double a = adv[mb_row(d, j)];
+        s += a;
+        q += a * a;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+        q += __shfl_xor_sync(0xFFFFFFFFu, q, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&stats[ST_ADV_SUM], s);
+        atomicAdd(&stats[ST_ADV_SQ], q);
+    }
+}
+
+__global__ void zero_kernel(double* p, int n) {
+    for (int k = threadIdx.x; k < n; k += blockDim.x) p[k] = 0.0;
+}
+
+// --------------------------------------------------- transposes
+__global__ void transpose_kernel(const float* __restrict__ src, int rows, int cols, float* __restrict__ dst) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < rows * cols; k += gridDim.x * blockDim.x) {
+        const int r = k / cols, c = k % cols;
+        dst[(size_t)c * rows + r] = src[k];
+    }
+}
+
+// ---------------------------------- fused forward + loss + backward-data
+// Per tile of 64 minibatch rows: gather the rollout rows, run actor and
+// critic, form the gradient of the clipped PPO loss with respect to the
+// logits and the value, and back-propagate it through the hidden layers.
+// Every activation and activation gradient the weight gradients need is
+// written to the workspace.
+__global__ void __launch_bounds__(NTH, 1) fwd_bwd_kernel(FbArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    const int H = a.H, O = a.O, I = a.in_dim;
+    const int ldx = a.in_pad, ldh = H + 4, ldo = ((O + 3) & ~3) + 4;
+    float* xs = sm;                      // [TILE][ldx]
+    float* B0 = xs + TILE * ldx;         // [TILE][ldh]
+    float* B1 = B0 + TILE * ldh;
+    float* B2 = B1 + TILE * ldh;
+    float* LG = B2 + TILE * ldh;         // [TILE][ldo]
+    float* VAL = LG + TILE * ldo;        // [TILE]
+    float* DV = VAL + TILE;              // [TILE]
+    __shared__ float red[8][NTH / 32];
+    const NetOffsets off = net_offsets(I, H, O);
+    const float* w = a.weights;
+    const double n = (double)a.mb.count;
+    const float mean = (float)(a.stats[ST_ADV_SUM] / n);
+    const float var = (float)fmax(a.stats[ST_ADV_SQ] / n - (a.stats[ST_ADV_SUM] / n) * (a.stats[ST_ADV_SUM] / n), 0.0);
+    const float inv_std = 1.0f / (sqrtf(var) + 1e-8f);
+    const float inv_n = 1.0f / (float)a.mb.count;
+    const int n_tiles = (a.mb.count + TILE - 1) / TILE;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int j0 = tile * TILE;
+        // gather
+        __shared__ uint32_t src_row[TILE];
+        if (threadIdx.x < TILE) {
+            const int j = j0 + threadIdx.x;
+            src_row[threadIdx.x] = j < a.mb.count ? mb_row(a.mb, j) : 0u;
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < TILE * ldx; idx += NTH) {
+            const int r = idx / ldx, k = idx % ldx;
+            const bool in = j0 + r < a.mb.count && k < I;
+            xs[idx] = in ? a.x[(size_t)src_row[r] * I + k] : 0.0f;
+        }
+        __syncthreads();
+        // actor forward
+        dense_tile(xs, ldx, I, w + off.W1, w + off.b1, H, B0, ldh, true);
+        __syncthreads();
+        dense_tile(B0, ldh, H, w + off.W2, w + off.b2, H, B1, ldh, true);
+        __syncthreads();
+        head_tile(B1, ldh, H, w + off.W3, w + off.b3, O, LG, ldo);
+        __syncthreads();
+        store_tile(a, xs, ldx, I, a.ws_x, j0);
+        store_tile(a, B0, ldh, H, a.ws_h1, j0);
+        store_tile(a, B1, ldh, H, a.ws_h2, j0);
+        // loss gradient with respect to the logits, one thread per row
+        float pg = 0.0f, ent_sum = 0.0f, clipc = 0.0f, kl = 0.0f;
+        if (threadIdx.x < TILE && j0 + (int)threadIdx.x < a.mb.count) {
+            const int r = threadIdx.x;
+            const uint32_t row = src_row[r];
+            float* l = LG + r * ldo;
+            const uint32_t* mw = a.W ? a.mask + (size_t)row * a.W : nullptr;
+            float logp = 0.0f;
+            // per head: masked log-softmax, p
+            for (int h = 0; h < a.n_heads; ++h) {
+                float* lh = l + h * a.head;
+                float m = -FLT_MAX;
+                for (int k = 0; k < a.head; ++k) {
+                    const int bit = h * a.head + k;
+                    if (!mw || ((mw[bit >> 5] >> (bit & 31)) & 1u)) m = fmaxf(m, lh[k]);
+                }
+                float S = 0.0f;
+                for (int k = 0; k < a.head; ++k) {
+                    const int bit = h * a.head + k;
+                    if (!mw || ((mw[bit >> 5] >> (bit & 31)) & 1u)) S += expf(lh[k] - m);
+                }
+                const float logS = logf(S);
+                const int act = a.act[(size_t)row * a.n_heads + h];
+                logp += lh[act] - m - logS;
+                // keep log p in place (masked entries: +inf marker)
+                float Hh = 0.0f;
+                for (int k = 0; k < a.head; ++k) {
+                    const int bit = h * a.head + k;
+                    const bool ok = !mw || ((mw[bit >> 5] >> (bit & 31)) & 1u);
+                    const float lp = lh[k] - m - logS;
+                    if (ok) Hh -= expf(lp) * lp;
+                    lh[k] = ok ? lp : FLT_MAX;
+                }
+                ent_sum += Hh;
+                LG[r * ldo + O + (h & 3)] = Hh;   // per-head entropy (O is padded by at least 4)
+            }
+            const float lpo = a.logp_old[row];
+            const float ratio = expf(logp - lpo);
+            const float an = (a.adv[row] - mean) * inv_std;
+            const float cr = fminf(fmaxf(ratio, 1.0f - a.clip), 1.0f + a.clip);
+            const float s1 = ratio * an, s2 = cr * an;
+            pg = -fminf(s1, s2);
+            const bool inside = ratio > 1.0f - a.clip && ratio < 1.0f + a.clip;
+            const float dratio = (s1 <= s2 || inside) ? -an : 0.0f;
+            const float dlogp = dratio * ratio * inv_n;
+            clipc = fabsf(ratio - 1.0f) > a.clip ? 1.0f : 0.0f;
+            kl = lpo - logp;
+            for (int h = 0; h < a.n_heads; ++h) {
+                float* lh = l + h * a.head;
+                const int act = a.act[(size_t)row * a.n_heads + h];
+                const float Hh = LG[r * ldo + O + (h & 3)];
+                for (int k = 0; k < a.head; ++k) {
+                    const float lp = lh[k];
+                    float g = 0.0f;
+                    if (lp != FLT_MAX) {
+                        const float p = expf(lp);
+                        g = dlogp * ((k == act ? 1.0f : 0.0f) - p) + a.ent_coef * inv_n * p * (lp + Hh);
+                    }
+                    lh[k] = g;
+                }
+            }
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < TILE * O; idx += NTH) {
+            const int r = idx / O, c = idx % O;
+            if (j0 + r < a.mb.count) a.ws_dl[(size_t)(j0 + r) * O + c] = LG[r * ldo + c];
+        }
+        // dZ2 = (dL W3^T) * [h2 > 0]
+        dense_tile(LG, ldo, O, a.w3t, nullptr, H, B2, ldh, false);
+        __syncthreads();
+        mask_tile(B2, ldh, B1, H);
+        __syncthreads();
+        store_tile(a, B2, ldh, H, a.ws_dz2, j0);
+        // dZ1 = (dZ2 W2^T) * [h1 > 0]
+        dense_tile(B2, ldh, H, a.w2t, nullptr, H, B1, ldh, false);
+        __syncthreads();
+        mask_tile(B1, ldh, B0, H);
+        __syncthreads();
+        store_tile(a, B1, ldh, H, a.ws_dz1, j0);
+        // critic forward
+        dense_tile(xs, ldx, I, w + off.V1, w + off.c1, H, B0, ldh, true);
+        __syncthreads();
+        dense_tile(B0, ldh, H, w + off.V2, w + off.c2, H, B1, ldh, true);
+        __syncthreads();
+        value_tile(B1, ldh, H, w + off.V3, w[off.c3], VAL);
+        store_tile(a, B0, ldh, H, a.ws_g1, j0);
+        store_tile(a, B1, ldh, H, a.ws_g2, j0);
+        __syncthreads();
+        // value-loss gradient (clipped value loss), one thread per row
+        float vf = 0.0f;
+        if (threadIdx.x < TILE) {
+            const int r = threadIdx.x;
+            float dv = 0.0f;
+            if (j0 + r < a.mb.count) {
+                const uint32_t row = src_row[r];
+                const float v = VAL[r], vo = a.v_old[row], R = a.ret[row];
+                const float dvv = v - vo;
+                const float vc = vo + fminf(fmaxf(dvv, -a.vclip), a.vclip);
+                const float la = (v - R) * (v - R), lb = (vc - R) * (vc - R);
+                vf = 0.5f * fmaxf(la, lb);
+                dv = (la >= lb ? (v - R) : ((vc - R) * (fabsf(dvv) < a.vclip ? 1.0f : 0.0f))) * a.vf_coef * inv_n;
+                a.ws_dv[j0 + r] = dv;
+            }
+            DV[r] = dv;
+        }
+        __syncthreads();
+        // dY2 = dv V3^T * [g2 > 0]
+        for (int idx = threadIdx.x; idx < TILE * H; idx += NTH) {
+            const int r = idx / H, c = idx % H;
+            B2[r * ldh + c] = B1[r * ldh + c] > 0.0f ? DV[r] * __ldg(w + off.V3 + c) : 0.0f;
+        }
+        __syncthreads();
+        store_tile(a, B2, ldh, H, a.ws_dy2, j0);
+        dense_tile(B2, ldh, H, a.v2t, nullptr, H, B1, ldh, false);
+        __syncthreads();
+        mask_tile(B1, ldh, B0, H);
+        __syncthreads();
+        store_tile(a, B1, ldh, H, a.ws_dy1, j0);
+        // loss statistics
+        float vals[5] = {pg, vf, ent_sum, clipc, kl};
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            float v = vals[q];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+            if (lane == 0) red[q][warp] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 5) {
+            double s = 0.0;
+            for (int k = 0; k < NTH / 32; ++k) s += red[threadIdx.x][k];
+            atomicAdd(&a.stats[ST_PG + threadIdx.x], s);
+        }
+        __syncthreads();
+    }
+}
+
+// --------------------------------------- split-K weight gradients
+// Job q: G[m][n] = sum over minibatch rows of A[row][i] B[row][j], and the
+// bias gradient sum of B[row][j]; rows split in chunks over blockIdx.x.
+constexpr int WG_ROWS = 32;
+
+__global__ void __launch_bounds__(NTH) wgrad_kernel(WgJobs jobs, int rows, int chunks, float* __restrict__ partial) {
+    const WgJob jb = jobs.job[blockIdx.y];
+    __shared__ __align__(16) float As[WG_ROWS][128 + 4];
+    __shared__ __align__(16) float Bs[WG_ROWS][128 + 4];
+    const int c = blockIdx.x;
+    const int r0 = (int)(((long long)rows * c) / chunks), r1 = (int)(((long long)rows * (c + 1)) / chunks);
+    const int ib = threadIdx.x / 16, jbk = threadIdx.x % 16;    // 16 x 16 blocks of 8 x 8
+    const int i0 = ib * 8, j0 = jbk * 8;
+    const bool active = i0 < jb.m && j0 < jb.n;
+    float acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
+    float bsum = 0.0f;
+    for (int base = r0; base < r1; base += WG_ROWS) {
+        const int nr = min(WG_ROWS, r1 - base);
+        for (int k = threadIdx.x; k < WG_ROWS * 128; k += NTH) {
+            const int r = k / 128, col = k % 128;
+            As[r][col] = (r < nr && col < jb.m) ? jb.A[(size_t)(base + r) * jb.lda + col] : 0.0f;
+            Bs[r][col] = (r < nr && col < jb.n) ? jb.B[(size_t)(base + r) * jb.ldb + col] : 0.0f;
+        }
+        __syncthreads();
+        if (active) {
+            for (int r = 0; r < nr; ++r) {
+                float av[8], bv[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) { av[q] = As[r][i0 + q]; bv[q] = Bs[r][j0 + q]; }
+#pragma unroll
+                for (int x = 0; x < 8; ++x)
+#pragma unroll
+                    for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
+            }
+        }
+        if (threadIdx.x < jb.n)
+            for (int r = 0; r < nr; ++r) bsum += Bs[r][threadIdx.x];
+        __syncthreads();
+    }
+    float* out = partial + ((size_t)blockIdx.y * chunks + c) * WG_STRIDE;
+    if (active) {
+#pragma unroll
+        for (int x = 0; x < 8; ++x)
+#pragma unroll
+            for (int y = 0; y < 8; ++y)
+                if (i0 + x < jb.m && j0 + y < jb.n) out[(i0 + x) * jb.n + (j0 + y)] = acc[x][y];
+    }
+    if (threadIdx.x < jb.n) out[jb.m * jb.n + threadIdx.x] = bsum;
+}
+
+__global__ void wgrad_reduce_kernel(WgJobs jobs, int n_jobs, int chunks, const float* __restrict__ partial,
+                                    float* __restrict__ grad) {
+    for (int q = 0; q < n_jobs; ++q) {
+        const WgJob jb = jobs.job[q];
+        const int total = jb.m * jb.n + jb.n;
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+            float s = 0.0f;
+            for (int c = 0; c < chunks; ++c) s += partial[((size_t)q * chunks + c) * WG_STRIDE + k];
+            if (k < jb.m * jb.n) grad[jb.w_off + k] = s;
+            else if (jb.b_off >= 0) grad[jb.b_off + (k - jb.m * jb.n)] = s;
+        }
+    }
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, size_t n, float lr, float b1, float b2, float eps,
+                            float c1, float c2) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const float gk = g[k];
+        const float mk = b1 * m[k] + (1.0f - b1) * gk;
+        const float vk = b2 * v[k] + (1.0f - b2) * gk * gk;
+        m[k] = mk;
+        v[k] = vk;
+        p[k] -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
+    }
+}
+
+}  // namespace
+
+size_t fwd_bwd_smem(int in_pad, int H, int O) {
+    const int ldo = ((O + 3) & ~3) + 4;
+    return sizeof(float) * ((size_t)TILE * in_pad + 3 * (size_t)TILE * (H + 4) + (size_t)TILE * ldo + 2 * TILE);
+}
+
+ej_status launch_gae(const float* rew, const float* value, const uint8_t* done, int T, int rows,
+                     int per_env, float gamma, float lam, float* adv, float* ret, cudaStream_t s) {
+    int grid = (rows + 255) / 256;
+    if (grid > 152 * 8) grid = 152 * 8;
+    gae_kernel<<<grid, 256, 0, s>>>(rew, value, done, T, rows, per_env, gamma, lam, adv, ret);
+    return cudaGetLastError() == cudaSuccess ? EJ_OK : fail(EJ_ERR_CUDA, "gae launch failed");
+}
+
+ej_status launch_minibatch_grad(const FbArgs& fa, const WgJobs& jobs, int n_jobs, float* partial,
+                                int chunks, const float* w2, const float* w3, const float* v2,
+                                float* grad, cudaStream_t s) {
+    // transposed copies of the weights the backward pass multiplies by
+    transpose_kernel<<<64, 256, 0, s>>>(w3, fa.H, fa.O, fa.w3t);
+    transpose_kernel<<<64, 256, 0, s>>>(w2, fa.H, fa.H, fa.w2t);
+    transpose_kernel<<<64, 256, 0, s>>>(v2, fa.H, fa.H, fa.v2t);
+    zero_kernel<<<1, 32, 0, s>>>(fa.stats, ST_COUNT_);
+    int grid = (fa.mb.count + 255) / 256;
+    if (grid > 152 * 4) grid = 152 * 4;
+    adv_stats_kernel<<<grid, 256, 0, s>>>(fa.mb, fa.adv, fa.stats);
+    const size_t smem = fwd_bwd_smem(fa.in_pad, fa.H, fa.O);
+    static size_t configured = 0;
+    if (configured < smem) {
+        if (cudaFuncSetAttribute(fwd_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
+            return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute failed");
+        configured = 227 * 1024;
+    }
+    const int n_tiles = (fa.mb.count + TILE - 1) / TILE;
+    int g2 = n_tiles < 152 ? n_tiles : 152;
+    fwd_bwd_kernel<<<g2, NTH, smem, s>>>(fa);
+    wgrad_kernel<<<dim3(chunks, n_jobs), NTH, 0, s>>>(jobs, fa.mb.count, chunks, partial);
+    wgrad_reduce_kernel<<<152, 256, 0, s>>>(jobs, n_jobs, chunks, partial, grad);
+    return cudaGetLastError() == cudaSuccess ? EJ_OK : fail(EJ_ERR_CUDA, "minibatch gradient launch failed");
+}
+
+ej_status launch_adam(float* p, const float* g, float* m, float* v, size_t n, float lr, float b1, float b2,
+                      float eps, int step, cudaStream_t s) {
+    const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+    int grid = (int)((n + 255) / 256);
+    if (grid > 152 * 4) grid = 152 * 4;
+    adam_kernel<<<grid, 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError() == cudaSuccess ? EJ_OK : fail(EJ_ERR_CUDA, "adam launch failed");
+}
+
+}  // namespace ej

@@ -1,0 +1,70 @@
+// PPO update: shared declarations.
+#pragma once
+
+#include "ej_policy.cuh"
+
+namespace ej {
+
+// Statistics accumulated per minibatch (doubles).
+enum { ST_ADV_SUM = 0, ST_ADV_SQ = 1, ST_PG = 2, ST_VF = 3, ST_ENT = 4, ST_CLIP = 5, ST_KL = 6, ST_COUNT_ = 8 };
+
+// Minibatch m of an epoch: positions [lo, lo + count) of the Feistel
+// permutation of [0, N) keyed by (k0, k1, ctr).
+struct MbDesc {
+    int lo, count;
+    uint32_t N;
+    int half;
+    uint32_t k0, k1, ctr;
+};
+
+struct FbArgs {
+    MbDesc mb;
+    int in_dim, in_pad, H, O, n_heads, head, W;
+    float clip, vf_coef, vclip, ent_coef;
+    const float* weights;
+    const float* x;             // [N][in] rollout inputs (flat rows)
+    const uint32_t* mask;       // [N][W] or NULL
+    const int32_t* act;         // [N][n_heads]
+    const float* logp_old;      // [N]
+    const float* v_old;         // [N]
+    const float* adv;           // [N]
+    const float* ret;           // [N]
+    float* w3t; float* w2t; float* v2t;       // transposed weights (workspace)
+    double* stats;              // [ST_COUNT_]
+    float* ws_x; float* ws_h1; float* ws_h2; float* ws_g1; float* ws_g2;
+    float* ws_dl; float* ws_dz2; float* ws_dz1; float* ws_dy2; float* ws_dy1; float* ws_dv;
+};
+
+__device__ inline void store_tile(const FbArgs& a, const float* buf, int ld, int ncols, float* dst, int j0) {
+    for (int idx = threadIdx.x; idx < TILE * ncols; idx += NTH) {
+        const int r = idx / ncols, c = idx % ncols;
+        if (j0 + r < a.mb.count) dst[(size_t)(j0 + r) * ncols + c] = buf[r * ld + c];
+    }
+}
+
+// out[r][c] = ref[r][c] > 0 ? out[r][c] : 0  (ReLU derivative)
+__device__ inline void mask_tile(float* out, int ld, const float* ref, int ncols) {
+    for (int idx = threadIdx.x; idx < TILE * ncols; idx += NTH) {
+        const int r = idx / ncols, c = idx % ncols;
+        if (!(ref[r * ld + c] > 0.0f)) out[r * ld + c] = 0.0f;
+    }
+}
+
+constexpr int WG_STRIDE = 128 * 128 + 128;   // floats of one job's partial
+struct WgJob {
+    const float* A; const float* B;
+    int lda, ldb, m, n;
+    long long w_off, b_off;      // where the weight and bias gradients go in the gradient vector
+};
+struct WgJobs { WgJob job[6]; };
+
+size_t fwd_bwd_smem(int in_pad, int H, int O);
+ej_status launch_gae(const float* rew, const float* value, const uint8_t* done, int T, int rows,
+                     int per_env, float gamma, float lam, float* adv, float* ret, cudaStream_t s);
+ej_status launch_minibatch_grad(const FbArgs& fa, const WgJobs& jobs, int n_jobs, float* partial,
+                                int chunks, const float* w2, const float* w3, const float* v2,
+                                float* grad, cudaStream_t s);
+ej_status launch_adam(float* p, const float* g, float* m, float* v, size_t n, float lr, float b1, float b2,
+                      float eps, int step, cudaStream_t s);
+
+}  // namespace ej

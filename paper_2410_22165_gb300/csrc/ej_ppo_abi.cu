@@ -1,0 +1,304 @@
+// C ABI of the PPO update: parameters, workspace sizing, advantages,
+// minibatch gradients, Adam, and the whole update.
+#include <cmath>
+#include <cstring>
+
+#include "ej_internal.cuh"
+#include "ej_ppo.cuh"
+
+namespace ej {
+
+namespace {
+
+constexpr int WG_CHUNKS = 96;   // row chunks of the split-K weight-gradient kernel
+
+struct NetDims { int in, O, heads, head, rows_per_step; };
+
+NetDims dims(const KParams& kp, int net) {
+    NetDims d;
+    if (net == EJ_NET_POP) { d.in = kp.D; d.heads = 1; d.head = kp.nA; d.rows_per_step = kp.E * kp.A; }
+    else { d.in = kp.G; d.heads = kp.nb; d.head = kp.tax_levels; d.rows_per_step = kp.E; }
+    d.O = d.heads * d.head;
+    return d;
+}
+
+uint64_t a256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+
+// Workspace regions (byte offsets).
+struct Ws {
+    uint64_t adv[2], ret[2], stats[2], totals, wt3, wt2, wv2, rows, partial, grad[2], total;
+    uint64_t row_floats;   // floats of the per-row buffers (largest minibatch of either network)
+    uint64_t max_mb;       // rows of the largest minibatch
+};
+
+Ws ws_layout(const KParams& kp, const EjPpoParams* pp, int T, int H) {
+    Ws w;
+    uint64_t o = 0;
+    const NetDims dp = dims(kp, EJ_NET_POP), dg = dims(kp, EJ_NET_GOV);
+    const NetDims dd[2] = {dp, dg};
+    for (int n = 0; n < 2; ++n) {
+        const uint64_t N = (uint64_t)T * dd[n].rows_per_step;
+        w.adv[n] = o; o = a256(o + 4 * N);
+        w.ret[n] = o; o = a256(o + 4 * N);
+    }
+    w.stats[0] = o; o = a256(o + 8 * ST_COUNT_);
+    w.stats[1] = o; o = a256(o + 8 * ST_COUNT_);
+    w.totals = o; o = a256(o + 8 * 2 * ST_COUNT_);
+    const int Omax = dp.O > dg.O ? dp.O : dg.O;
+    w.wt3 = o; o = a256(o + 4ull * Omax * H);
+    w.wt2 = o; o = a256(o + 4ull * H * H);
+    w.wv2 = o; o = a256(o + 4ull * H * H);
+    uint64_t region = 0, mb = 0;
+    for (int n = 0; n < 2; ++n) {
+        const uint64_t f = dd[n].in + 8ull * H + dd[n].O + 1;   // x, h1, h2, g1, g2, dl, dz2, dz1, dy2, dy1, dv
+        const uint64_t N = (uint64_t)T * dd[n].rows_per_step;
+        const uint64_t m = (N + pp->minibatches - 1) / pp->minibatches;
+        if (f * m > region) region = f * m;
+        if (m > mb) mb = m;
+    }
+    w.row_floats = region;
+    w.max_mb = mb;
+    w.rows = o; o = a256(o + 4ull * region);
+    w.partial = o; o = a256(o + 4ull * 6 * WG_CHUNKS * WG_STRIDE);
+    for (int n = 0; n < 2; ++n) {
+        w.grad[n] = o;
+        o = a256(o + 4ull * net_offsets(dd[n].in, H, dd[n].O).total);
+    }
+    w.total = o;
+    return w;
+}
+
+int half_bits(uint64_t N) {
+    int b = 2;
+    while ((1ull << b) < N) ++b;
+    b += b & 1;
+    return b / 2;
+}
+
+ej_status check_common(const EjParams* p, const EjPpoParams* pp, int T, int H, Layout* lay, KParams* kp) {
+    ej_status st = derive(p, lay, kp);
+    if (st != EJ_OK) return st;
+    if (!pp) return fail(EJ_ERR_ARG, "ppo params is NULL");
+    if (T < 1) return fail(EJ_ERR_ARG, "T must be >= 1");
+    if (pp->minibatches < 1 || pp->epochs < 1) return fail(EJ_ERR_ARG, "epochs and minibatches must be >= 1");
+    if (H < 32 || H > 128 || H % 32) return fail(EJ_ERR_UNSUPPORTED, "PPO update supports hidden in {32, 64, 96, 128}");
+    if (kp->nb * p->tax_levels > 128 || kp->nA > 128 || kp->D > 128 || kp->G > 128)
+        return fail(EJ_ERR_UNSUPPORTED, "PPO update needs inputs and logits <= 128");
+    if ((uint64_t)T * kp->E * kp->A >= (1ull << 31)) return fail(EJ_ERR_UNSUPPORTED, "too many rows");
+    return EJ_OK;
+}
+
+ej_status minibatch_grad(const KParams& kp, const EjPpoParams* pp, int T, int H, int net,
+                         const float* weights, const EjRollout* b, char* ws, const Ws& W, uint32_t ctr,
+                         int m, float* grad, double* stats, cudaStream_t s) {
+    const NetDims d = dims(kp, net);
+    const NetOffsets off = net_offsets(d.in, H, d.O);
+    const uint64_t N = (uint64_t)T * d.rows_per_step;
+    FbArgs fa;
+    memset(&fa, 0, sizeof fa);
+    fa.mb.lo = (int)((N * m) / pp->minibatches);
+    fa.mb.count = (int)((N * (m + 1)) / pp->minibatches) - fa.mb.lo;
+    fa.mb.N = (uint32_t)N;
+    fa.mb.half = half_bits(N);
+    fa.mb.k0 = (uint32_t)pp->seed;
+    fa.mb.k1 = (uint32_t)(pp->seed >> 32);
+    fa.mb.ctr = ctr;
+    fa.in_dim = d.in; fa.in_pad = (d.in + 3) & ~3; fa.H = H; fa.O = d.O;
+    fa.n_heads = d.heads; fa.head = d.head; fa.W = net == EJ_NET_POP ? kp.W : 0;
+    fa.clip = pp->clip; fa.vf_coef = pp->vf_coef; fa.vclip = pp->vclip; fa.ent_coef = pp->ent_coef;
+    fa.weights = weights;
+    if (net == EJ_NET_POP) {
+        fa.x = b->obs; fa.mask = b->mask; fa.act = b->act; fa.logp_old = b->logp; fa.v_old = b->value;
+    } else {
+        fa.x = b->gobs; fa.mask = nullptr; fa.act = b->gact; fa.logp_old = b->glogp; fa.v_old = b->gvalue;
+    }
+    fa.adv = (const float*)(ws + W.adv[net]);
+    fa.ret = (const float*)(ws + W.ret[net]);
+    fa.w3t = (float*)(ws + W.wt3); fa.w2t = (float*)(ws + W.wt2); fa.v2t = (float*)(ws + W.wv2);
+    fa.stats = stats;
+    const uint64_t R = (uint64_t)fa.mb.count;
+    float* rb = (float*)(ws + W.rows);
+    fa.ws_x = rb; rb += R * d.in;
+    fa.ws_h1 = rb; rb += R * H;
+    fa.ws_h2 = rb; rb += R * H;
+    fa.ws_g1 = rb; rb += R * H;
+    fa.ws_g2 = rb; rb += R * H;
+    fa.ws_dl = rb; rb += R * d.O;
+    fa.ws_dz2 = rb; rb += R * H;
+    fa.ws_dz1 = rb; rb += R * H;
+    fa.ws_dy2 = rb; rb += R * H;
+    fa.ws_dy1 = rb; rb += R * H;
+    fa.ws_dv = rb;
+    WgJobs jobs;
+    memset(&jobs, 0, sizeof jobs);
+    auto job = [&](int q, const float* A, int m_, const float* B, int n_, size_t wo, size_t bo) {
+        jobs.job[q].A = A; jobs.job[q].B = B; jobs.job[q].lda = m_; jobs.job[q].ldb = n_;
+        jobs.job[q].m = m_; jobs.job[q].n = n_; jobs.job[q].w_off = (long long)wo; jobs.job[q].b_off = (long long)bo;
+    };
+    job(0, fa.ws_x, d.in, fa.ws_dz1, H, off.W1, off.b1);
+    job(1, fa.ws_h1, H, fa.ws_dz2, H, off.W2, off.b2);
+    job(2, fa.ws_h2, H, fa.ws_dl, d.O, off.W3, off.b3);
+    job(3, fa.ws_x, d.in, fa.ws_dy1, H, off.V1, off.c1);
+    job(4, fa.ws_g1, H, fa.ws_dy2, H, off.V2, off.c2);
+    job(5, fa.ws_g2, H, fa.ws_dv, 1, off.V3, off.c3);
+    if (cudaMemsetAsync(grad, 0, sizeof(float) * off.total, s) != cudaSuccess)
+        return fail(EJ_ERR_CUDA, "memset of the gradient failed");
+    return launch_minibatch_grad(fa, jobs, 6, (float*)(ws + W.partial), WG_CHUNKS, weights + off.W2,
+                                 weights + off.W3, weights + off.V2, grad, s);
+}
+
+__global__ void accumulate_stats_kernel(const double* st, double* totals) {
+    const int k = threadIdx.x;
+    if (k < ST_COUNT_) totals[k] += st[k];
+}
+
+__global__ void finalize_stats_kernel(const double* totals, double rows_pop, double rows_gov, float* out) {
+    const int k = threadIdx.x;
+    if (k < 2 * 5) {
+        const int net = k / 5, q = k % 5;
+        const double n = net == 0 ? rows_pop : rows_gov;
+        out[net * 8 + q] = (float)(totals[net * ST_COUNT_ + ST_PG + q] / n);
+    }
+}
+
+}  // namespace
+
+}  // namespace ej
+
+using namespace ej;
+
+extern "C" {
+
+ej_status ej_ppo_params_default(EjPpoParams* pp) {
+    if (!pp) return fail(EJ_ERR_ARG, "NULL");
+    memset(pp, 0, sizeof *pp);
+    pp->gamma = 0.99f; pp->lam = 0.95f; pp->clip = 0.2f; pp->vf_coef = 0.25f; pp->vclip = 10.0f;
+    pp->ent_coef = 0.1f; pp->lr = 5e-4f; pp->beta1 = 0.9f; pp->beta2 = 0.999f; pp->eps = 1e-5f;
+    pp->epochs = 4; pp->minibatches = 8; pp->seed = 0;
+    return EJ_OK;
+}
+
+ej_status ej_ppo_workspace_bytes(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_t hidden,
+                                 uint64_t* bytes) {
+    Layout lay;
+    KParams kp;
+    ej_status st = check_common(p, pp, T, hidden, &lay, &kp);
+    if (st != EJ_OK) return st;
+    if (bytes) *bytes = ws_layout(kp, pp, T, hidden).total;
+    return EJ_OK;
+}
+
+ej_status ej_ppo_workspace_offsets(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_t hidden,
+                                   uint64_t* offsets) {
+    Layout lay;
+    KParams kp;
+    ej_status st = check_common(p, pp, T, hidden, &lay, &kp);
+    if (st != EJ_OK) return st;
+    if (!offsets) return fail(EJ_ERR_ARG, "NULL");
+    const Ws W = ws_layout(kp, pp, T, hidden);
+    offsets[0] = W.adv[0]; offsets[1] = W.ret[0]; offsets[2] = W.adv[1]; offsets[3] = W.ret[1];
+    return EJ_OK;
+}
+
+ej_status ppo_advantages(const EjParams* p, const EjPpoParams* pp, int32_t T, const EjRollout* b,
+                         void* workspace, void* stream) {
+    Layout lay;
+    KParams kp;
+    ej_status st = check_common(p, pp, T, 128, &lay, &kp);
+    if (st != EJ_OK) return st;
+    if (!b || !workspace) return fail(EJ_ERR_ARG, "NULL rollout or workspace");
+    if ((uintptr_t)workspace % 256) return fail(EJ_ERR_ARG, "workspace must be 256-byte aligned");
+    const Ws W = ws_layout(kp, pp, T, 128);
+    char* ws = (char*)workspace;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = launch_gae(b->rew, b->value, b->done, T, kp.E * kp.A, kp.A, pp->gamma, pp->lam,
+                    (float*)(ws + W.adv[0]), (float*)(ws + W.ret[0]), s);
+    if (st != EJ_OK) return st;
+    return launch_gae(b->grew, b->gvalue, b->done, T, kp.E, 1, pp->gamma, pp->lam,
+                      (float*)(ws + W.adv[1]), (float*)(ws + W.ret[1]), s);
+}
+
+ej_status ppo_minibatch_grad(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_t hidden,
+                             int32_t precision, int32_t net, const float* weights, const EjRollout* b,
+                             void* workspace, uint32_t shuffle_ctr, int32_t minibatch, float* grad,
+                             double* stats_out, void* stream) {
+    Layout lay;
+    KParams kp;
+    ej_status st = check_common(p, pp, T, hidden, &lay, &kp);
+    if (st != EJ_OK) return st;
+    if (precision != EJ_FP32) return fail(EJ_ERR_UNSUPPORTED, "PPO gradients: precision %d not available", precision);
+    if (net != EJ_NET_POP && net != EJ_NET_GOV) return fail(EJ_ERR_ARG, "unknown network %d", net);
+    if (!b || !workspace || !weights || !grad) return fail(EJ_ERR_ARG, "NULL argument");
+    if ((uintptr_t)workspace % 256 || (uintptr_t)weights % 16) return fail(EJ_ERR_ARG, "misaligned buffer");
+    if (minibatch < 0 || minibatch >= pp->minibatches) return fail(EJ_ERR_ARG, "minibatch out of range");
+    const Ws W = ws_layout(kp, pp, T, hidden);
+    char* ws = (char*)workspace;
+    cudaStream_t s = (cudaStream_t)stream;
+    double* stats = (double*)(ws + W.stats[net]);
+    st = minibatch_grad(kp, pp, T, hidden, net, weights, b, ws, W, shuffle_ctr, minibatch, grad, stats, s);
+    if (st != EJ_OK) return st;
+    if (stats_out) {
+        if (cudaMemcpyAsync(stats_out, stats, sizeof(double) * ST_COUNT_, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return fail(EJ_ERR_CUDA, "stats copy failed");
+    }
+    return EJ_OK;
+}
+
+ej_status adam_step(uint64_t n, float* params, const float* grad, float* m, float* v, int32_t step,
+                    float lr, float beta1, float beta2, float eps, void* stream) {
+    if (!params || !grad || !m || !v) return fail(EJ_ERR_ARG, "NULL argument");
+    if (step < 1) return fail(EJ_ERR_ARG, "step counts from 1");
+    return launch_adam(params, grad, m, v, n, lr, beta1, beta2, eps, step, (cudaStream_t)stream);
+}
+
+ej_status ppo_update(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_t hidden,
+                     int32_t precision, float* pop_w, float* gov_w, float* pop_m, float* pop_v,
+                     float* gov_m, float* gov_v, int32_t adam_steps_done, uint32_t update_index,
+                     const EjRollout* b, void* workspace, float* stats_out, void* stream) {
+    Layout lay;
+    KParams kp;
+    ej_status st = check_common(p, pp, T, hidden, &lay, &kp);
+    if (st != EJ_OK) return st;
+    if (precision != EJ_FP32) return fail(EJ_ERR_UNSUPPORTED, "PPO update: precision %d not available", precision);
+    if (!pop_w || !gov_w || !pop_m || !pop_v || !gov_m || !gov_v || !b || !workspace)
+        return fail(EJ_ERR_ARG, "NULL argument");
+    if ((uintptr_t)workspace % 256 || (uintptr_t)pop_w % 16 || (uintptr_t)gov_w % 16)
+        return fail(EJ_ERR_ARG, "misaligned buffer");
+    const Ws W = ws_layout(kp, pp, T, hidden);
+    char* ws = (char*)workspace;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = ppo_advantages(p, pp, T, b, workspace, stream)) != EJ_OK) return st;
+    double* totals = (double*)(ws + W.totals);
+    if (cudaMemsetAsync(totals, 0, sizeof(double) * 2 * ST_COUNT_, s) != cudaSuccess)
+        return fail(EJ_ERR_CUDA, "memset failed");
+    float* w[2] = {pop_w, gov_w};
+    float* mm[2] = {pop_m, gov_m};
+    float* vv[2] = {pop_v, gov_v};
+    int step = adam_steps_done;
+    for (int ep = 0; ep < pp->epochs; ++ep) {
+        const uint32_t ctr = update_index * (uint32_t)pp->epochs + (uint32_t)ep;
+        for (int mb = 0; mb < pp->minibatches; ++mb) {
+            ++step;
+            for (int net = 0; net < 2; ++net) {
+                const NetDims d = dims(kp, net);
+                const size_t n = net_offsets(d.in, hidden, d.O).total;
+                float* grad = (float*)(ws + W.grad[net]);
+                double* stats = (double*)(ws + W.stats[net]);
+                st = minibatch_grad(kp, pp, T, hidden, net, w[net], b, ws, W, ctr ^ (net ? 0x80000000u : 0u),
+                                    mb, grad, stats, s);
+                if (st != EJ_OK) return st;
+                accumulate_stats_kernel<<<1, 32, 0, s>>>(stats, totals + net * ST_COUNT_);
+                if ((st = launch_adam(w[net], grad, mm[net], vv[net], n, pp->lr, pp->beta1, pp->beta2, pp->eps,
+                                      step, s)) != EJ_OK)
+                    return st;
+            }
+        }
+    }
+    if (stats_out) {
+        const double rp = (double)T * kp.E * kp.A * pp->epochs, rg = (double)T * kp.E * pp->epochs;
+        finalize_stats_kernel<<<1, 32, 0, s>>>(totals, rp, rg, stats_out);
+    }
+    return cudaGetLastError() == cudaSuccess ? EJ_OK : fail(EJ_ERR_CUDA, "ppo_update launch failed");
+}
+
+}  // extern "C"

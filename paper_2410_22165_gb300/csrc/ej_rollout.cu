@@ -1,0 +1,139 @@
+// C ABI of the policy side: network sizes, policy_forward and rollout.
+#include <cstring>
+
+#include "ej_internal.cuh"
+#include "ej_policy.cuh"
+
+namespace ej {
+
+static ej_status net_shape(const EjParams* p, const KParams& kp, int net, int hidden, int* in,
+                           int* O, int* heads, int* head) {
+    if (hidden < 32 || hidden > 256 || hidden % 32) return fail(EJ_ERR_UNSUPPORTED, "hidden must be a multiple of 32 in [32, 256]");
+    if (net == EJ_NET_POP) { *in = kp.D; *heads = 1; *head = kp.nA; }
+    else if (net == EJ_NET_GOV) { *in = kp.G; *heads = kp.nb; *head = p->tax_levels; }
+    else return fail(EJ_ERR_ARG, "unknown network %d", net);
+    *O = *heads * *head;
+    return EJ_OK;
+}
+
+static ej_status make_args(const EjParams* p, const KParams& kp, const Layout& lay, const void* state,
+                           int net, int hidden, const float* weights, const float* obs,
+                           const uint32_t* mask, const float* u, int32_t* act, float* logp,
+                           float* value, float* entropy, float* logits, PolicyArgs* a) {
+    int in, O, heads, head;
+    ej_status st = net_shape(p, kp, net, hidden, &in, &O, &heads, &head);
+    if (st != EJ_OK) return st;
+    if (!state || !weights || !obs || !value) return fail(EJ_ERR_ARG, "state, weights, obs and value are required");
+    if (act && !logp) return fail(EJ_ERR_ARG, "sampling needs logp");
+    if ((uintptr_t)weights % 16) return fail(EJ_ERR_ARG, "weights must be 16-byte aligned");
+    memset(a, 0, sizeof *a);
+    a->rows = net == EJ_NET_POP ? kp.E * kp.A : kp.E;
+    a->per_env = net == EJ_NET_POP ? kp.A : 1;
+    a->in_dim = in;
+    a->in_pad = (in + 3) & ~3;
+    a->H = hidden;
+    a->O = O;
+    a->n_heads = heads;
+    a->head = head;
+    a->W = (net == EJ_NET_POP && mask) ? kp.W : 0;
+    a->stream_id = net == EJ_NET_POP ? 0 : 1;
+    a->weights = weights;
+    a->x = obs;
+    a->mask = a->W ? mask : nullptr;
+    a->u = u;
+    const DevState s = state_pointers(lay, const_cast<void*>(state));
+    a->gstep = s.gstep;
+    a->key = s.key;
+    a->act = act;
+    a->logp = logp;
+    a->value = value;
+    a->entropy = entropy;
+    a->logits = logits;
+    return EJ_OK;
+}
+
+static ej_status launch_policy(const PolicyArgs& a, int precision, cudaStream_t stream) {
+    if (precision == EJ_FP32) return launch_policy_fp32(a, stream);
+    return fail(EJ_ERR_UNSUPPORTED, "precision %d is not available", precision);
+}
+
+}  // namespace ej
+
+using namespace ej;
+
+extern "C" {
+
+ej_status ej_net_floats(const EjParams* p, int32_t net, int32_t hidden, uint64_t* n_floats) {
+    Layout lay;
+    KParams kp;
+    ej_status st = derive(p, &lay, &kp);
+    if (st != EJ_OK) return st;
+    int in, O, heads, head;
+    st = net_shape(p, kp, net, hidden, &in, &O, &heads, &head);
+    if (st != EJ_OK) return st;
+    if (n_floats) *n_floats = net_offsets(in, hidden, O).total;
+    return EJ_OK;
+}
+
+ej_status policy_forward(const EjParams* p, const void* state, int32_t net, int32_t hidden,
+                         int32_t precision, const float* weights, const float* obs,
+                         const uint32_t* mask, const float* u, int32_t* act, float* logp,
+                         float* value, float* entropy, float* logits, void* stream) {
+    Layout lay;
+    KParams kp;
+    ej_status st = derive(p, &lay, &kp);
+    if (st != EJ_OK) return st;
+    PolicyArgs a;
+    st = make_args(p, kp, lay, state, net, hidden, weights, obs, mask, u, act, logp, value, entropy,
+                   logits, &a);
+    if (st != EJ_OK) return st;
+    return launch_policy(a, precision, (cudaStream_t)stream);
+}
+
+ej_status rollout(const EjParams* p, void* state, int32_t T, int32_t hidden, int32_t precision,
+                  const float* pop_weights, const float* gov_weights, const EjRollout* b,
+                  void* stream) {
+    Layout lay;
+    KParams kp;
+    ej_status st = derive(p, &lay, &kp);
+    if (st != EJ_OK) return st;
+    if (!b || !state || !pop_weights || !gov_weights) return fail(EJ_ERR_ARG, "rollout: NULL argument");
+    if (T < 1) return fail(EJ_ERR_ARG, "rollout: T must be >= 1");
+    if (!b->obs || !b->gobs || !b->mask || !b->act || !b->gact || !b->logp || !b->glogp ||
+        !b->value || !b->gvalue || !b->rew || !b->grew || !b->done)
+        return fail(EJ_ERR_ARG, "rollout: every buffer is required");
+    if ((uintptr_t)state % 256) return fail(EJ_ERR_ARG, "state must be 256-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t EA = (size_t)kp.E * kp.A;
+    const DevState ds = state_pointers(lay, state);
+    for (int t = 0; t <= T; ++t) {
+        const bool last = t == T;
+        PolicyArgs pa, ga;
+        st = make_args(p, kp, lay, state, EJ_NET_POP, hidden, pop_weights, b->obs + t * EA * kp.D,
+                       b->mask + t * EA * kp.W, nullptr, last ? nullptr : b->act + t * EA,
+                       last ? nullptr : b->logp + t * EA, b->value + t * EA, nullptr, nullptr, &pa);
+        if (st != EJ_OK) return st;
+        if ((st = launch_policy(pa, precision, s)) != EJ_OK) return st;
+        st = make_args(p, kp, lay, state, EJ_NET_GOV, hidden, gov_weights, b->gobs + (size_t)t * kp.E * kp.G,
+                       nullptr, nullptr, last ? nullptr : b->gact + (size_t)t * kp.E * kp.nb,
+                       last ? nullptr : b->glogp + (size_t)t * kp.E, b->gvalue + (size_t)t * kp.E,
+                       nullptr, nullptr, &ga);
+        if (st != EJ_OK) return st;
+        if ((st = launch_policy(ga, precision, s)) != EJ_OK) return st;
+        if (last) break;
+        DevIO io;
+        memset(&io, 0, sizeof io);
+        io.act = b->act + t * EA;
+        io.gov_act = b->gact + (size_t)t * kp.E * kp.nb;
+        io.rew = b->rew + t * EA;
+        io.grew = b->grew + (size_t)t * kp.E;
+        io.done = b->done + (size_t)t * kp.E;
+        io.obs = b->obs + (t + 1) * EA * kp.D;
+        io.gobs = b->gobs + (size_t)(t + 1) * kp.E * kp.G;
+        io.mask = b->mask + (t + 1) * EA * kp.W;
+        if ((st = launch_env(kp, lay, ds, io, 1, MODE_AUX_DRAW, 0, s)) != EJ_OK) return st;
+    }
+    return EJ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,71 @@
+"""PPO update on the GPU (thin wrapper of the C ABI)."""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _native as N
+from .env import _ptr, _stream
+from .policy import Policy, Rollout
+
+
+class PPO:
+    """Adam state, workspace and the update calls for a Policy and its rollouts."""
+
+    def __init__(self, policy: Policy, T: int, **overrides):
+        self.policy, self.env, self.T = policy, policy.env, T
+        self.pp = N.EjPpoParams()
+        N.check(N.load().ej_ppo_params_default(C.byref(self.pp)), "ej_ppo_params_default")
+        for k, v in overrides.items():
+            if not hasattr(self.pp, k):
+                raise KeyError(k)
+            setattr(self.pp, k, v)
+        nbytes = C.c_uint64()
+        N.check(N.load().ej_ppo_workspace_bytes(C.byref(self.env.p), C.byref(self.pp), T, policy.hidden,
+                                                C.byref(nbytes)), "ej_ppo_workspace_bytes")
+        dev = self.env.device
+        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=dev)
+        self.m = [torch.zeros_like(policy.pop_w), torch.zeros_like(policy.gov_w)]
+        self.v = [torch.zeros_like(policy.pop_w), torch.zeros_like(policy.gov_w)]
+        self.adam_steps = 0
+        self.updates = 0
+
+    def offsets(self):
+        off = (C.c_uint64 * 4)()
+        N.check(N.load().ej_ppo_workspace_offsets(C.byref(self.env.p), C.byref(self.pp), self.T,
+                                                  self.policy.hidden, off), "ej_ppo_workspace_offsets")
+        return list(off)
+
+    def advantages(self, rollout: Rollout, stream=None):
+        N.check(N.load().ppo_advantages(C.byref(self.env.p), C.byref(self.pp), self.T, C.byref(rollout._c),
+                                        _ptr(self.workspace), _stream(stream)), "ppo_advantages")
+        E, A, T = self.env.E, self.env.A, self.T
+        o = self.offsets()
+        ws = self.workspace
+        view = lambda off, n: ws[off: off + 4 * n].view(torch.float32)
+        return dict(adv=view(o[0], T * E * A).view(T, E, A), ret=view(o[1], T * E * A).view(T, E, A),
+                    gadv=view(o[2], T * E).view(T, E), gret=view(o[3], T * E).view(T, E))
+
+    def minibatch_grad(self, rollout: Rollout, net: int, shuffle_ctr: int, minibatch: int, stream=None):
+        pol = self.policy
+        w = pol.pop_w if net == N.NET_POP else pol.gov_w
+        grad = torch.empty_like(w)
+        stats = torch.empty(8, dtype=torch.float64, device=w.device)
+        N.check(N.load().ppo_minibatch_grad(C.byref(self.env.p), C.byref(self.pp), self.T, pol.hidden,
+                                            pol.precision, net, _ptr(w), C.byref(rollout._c),
+                                            _ptr(self.workspace), shuffle_ctr, minibatch, _ptr(grad),
+                                            _ptr(stats), _stream(stream)), "ppo_minibatch_grad")
+        return grad, stats
+
+    def update(self, rollout: Rollout, stream=None):
+        pol = self.policy
+        stats = torch.empty((2, 8), dtype=torch.float32, device=pol.pop_w.device)
+        N.check(N.load().ppo_update(C.byref(self.env.p), C.byref(self.pp), self.T, pol.hidden, pol.precision,
+                                    _ptr(pol.pop_w), _ptr(pol.gov_w), _ptr(self.m[0]), _ptr(self.v[0]),
+                                    _ptr(self.m[1]), _ptr(self.v[1]), self.adam_steps, self.updates,
+                                    C.byref(rollout._c), _ptr(self.workspace), _ptr(stats), _stream(stream)),
+                "ppo_update")
+        self.adam_steps += self.pp.epochs * self.pp.minibatches
+        self.updates += 1
+        return stats

@@ -12,3 +12,4 @@ from .draws import (  # noqa: F401
     STREAM_POP, STREAM_GOV, STREAM_SKILL,
     pop_draws, gov_draws, skill_draws, episode_inputs,
 )
+from .weights import STREAM_WEIGHTS, net_layout, net_offsets, net_weights, pack, unpack  # noqa: F401

@@ -77,7 +77,10 @@ def test_step_argument_checks(lib):
     assert lib.env_step(C.byref(p), None, 1, None, None, None, None, None, None, None, None,
                         None, None, None) == 1
     fake = C.c_void_p(256)
-    assert lib.env_step(C.byref(p), fake, 1, fake, None, None, None, None, None, None, None,
+    # gather draws without tie-break keys, and draws without actions: rejected
+    assert lib.env_step(C.byref(p), fake, 1, fake, None, fake, None, None, None, None, None,
+                        None, None, None) == 1
+    assert lib.env_step(C.byref(p), fake, 1, None, None, fake, fake, None, None, None, None,
                         None, None, None) == 1
     assert lib.env_step(C.byref(p), fake, -1, None, None, None, None, None, None, None, None,
                         None, None, None) == 1
@@ -96,3 +99,31 @@ def test_state_layout(lib):
         assert off % 256 == 0 and off >= prev_end and esz == 4
         prev_end = off + cnt * esz
     assert prev_end <= s.state_bytes
+
+
+def test_net_layout_matches_generator(lib):
+    import synth
+    p = N.make_params(E=4, A=10)
+    s = N.sizes(p)
+    for net, (i, o) in ((N.NET_POP, (s.obs_dim, s.n_actions)), (N.NET_GOV, (s.gobs_dim, 3 * 21))):
+        for H in (32, 128, 256):
+            n = C.c_uint64()
+            assert lib.ej_net_floats(C.byref(p), net, H, C.byref(n)) == 0
+            layout, total = synth.net_offsets(i, H, o)
+            assert n.value == total and all(off % 4 == 0 for *_, off in layout)
+    n = C.c_uint64()
+    assert lib.ej_net_floats(C.byref(p), 0, 100, C.byref(n)) == 3      # not a multiple of 32
+
+
+def test_policy_argument_checks(lib):
+    p = N.make_params(E=2, A=10)
+    fake = C.c_void_p(4096)
+    # misaligned weights and missing outputs are rejected on the host
+    assert lib.policy_forward(C.byref(p), fake, 0, 128, 0, C.c_void_p(4100), fake, None, None,
+                              None, None, fake, None, None, None) == 1
+    assert lib.policy_forward(C.byref(p), fake, 0, 128, 0, fake, fake, None, None,
+                              None, None, None, None, None, None) == 1
+    assert lib.policy_forward(C.byref(p), fake, 0, 128, 0, fake, fake, None, None,
+                              fake, None, fake, None, None, None) == 1   # act without logp
+    assert lib.policy_forward(C.byref(p), fake, 7, 128, 0, fake, fake, None, None,
+                              None, None, fake, None, None, None) == 1   # unknown network

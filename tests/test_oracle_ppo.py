@@ -1,0 +1,87 @@
+"""Pins of the GAE / PPO / Adam oracle (no GPU)."""
+import numpy as np
+import pytest
+
+from oracle import ppo
+
+
+def test_gae_constant_rewards_closed_form():
+    """Constant r and V, no episode end: delta = r + (gamma - 1) V and
+    A_t = delta (1 - (gamma lambda)^(T - t)) / (1 - gamma lambda)."""
+    T, N, r, V, g, lam = 50, 3, 0.7, 2.0, 0.99, 0.95
+    adv, ret = ppo.gae64(np.full((T, N), r), np.full((T + 1, N), V), np.zeros((T, N)), g, lam)
+    delta = r + (g - 1) * V
+    k = T - np.arange(T)
+    expect = delta * (1 - (g * lam) ** k) / (1 - g * lam)
+    assert np.allclose(adv[:, 0], expect, rtol=1e-12)
+    assert np.allclose(ret, adv + V)
+
+
+def test_gae_limits_and_episode_end():
+    rng = np.random.default_rng(1)
+    T, N, g = 20, 4, 0.9
+    rew = rng.normal(size=(T, N)); val = rng.normal(size=(T + 1, N))
+    done = np.zeros((T, N)); done[7, 1] = 1
+    # lambda = 0: one-step TD error
+    adv0, _ = ppo.gae64(rew, val, done, g, 0.0)
+    nd = 1 - done
+    assert np.allclose(adv0, rew + g * nd * val[1:] - val[:-1])
+    # lambda = 1: discounted return (bootstrapped at T, cut at the episode end) minus V
+    adv1, ret1 = ppo.gae64(rew, val, done, g, 1.0)
+    G = val[T].copy()
+    for t in range(T - 1, -1, -1):
+        G = rew[t] + g * nd[t] * G
+        assert np.allclose(ret1[t], G)
+
+
+def _rand_problem(seed, heads=1, head=6, in_dim=5, H=8, N=16):
+    rng = np.random.default_rng(seed)
+    O = heads * head
+    w = dict(W1=rng.normal(size=(in_dim, H)) * 0.5, b1=rng.normal(size=H) * 0.1,
+             W2=rng.normal(size=(H, H)) * 0.4, b2=rng.normal(size=H) * 0.1,
+             W3=rng.normal(size=(H, O)) * 0.4, b3=rng.normal(size=O) * 0.1,
+             V1=rng.normal(size=(in_dim, H)) * 0.5, c1=rng.normal(size=H) * 0.1,
+             V2=rng.normal(size=(H, H)) * 0.4, c2=rng.normal(size=H) * 0.1,
+             V3=rng.normal(size=(H, 1)) * 0.4, c3=rng.normal(size=1) * 0.1)
+    x = rng.normal(size=(N, in_dim))
+    valid = rng.random((N, O)) < 0.7
+    act = np.zeros((N, heads), int)
+    for h in range(heads):
+        valid[:, h * head] = True
+        for i in range(N):
+            act[i, h] = rng.choice(np.nonzero(valid[i, h * head:(h + 1) * head])[0])
+    logp_old = rng.normal(size=N) * 0.3 - 1.5
+    v_old = rng.normal(size=N)
+    adv = rng.normal(size=N)
+    ret = rng.normal(size=N) * 2
+    return w, x, act, valid, logp_old, v_old, adv, ret
+
+
+@pytest.mark.parametrize("heads,coef", [(1, dict(clip=0.2, vf_coef=0.25, vclip=10.0, ent_coef=0.1)),
+                                        (1, dict(clip=0.05, vf_coef=1.0, vclip=0.1, ent_coef=0.0)),
+                                        (3, dict(clip=0.2, vf_coef=0.25, vclip=10.0, ent_coef=0.1))])
+def test_ppo_gradient_matches_finite_differences(heads, coef):
+    """Hand-written backpropagation against central differences of the loss
+    (float64), for every parameter tensor, including clipped ratios and a
+    clipped value loss."""
+    w, x, act, valid, lo, vo, adv, ret = _rand_problem(3 + heads, heads=heads)
+    head = valid.shape[1] // heads
+    f = lambda ww: ppo.ppo_loss_grad64(ww, x, act, valid, lo, vo, adv, ret, heads=heads, head=head, **coef)
+    loss, g, st = f(w)
+    rng = np.random.default_rng(9)
+    h = 1e-6
+    for k in w:
+        flat = w[k].reshape(-1)
+        for idx in rng.choice(flat.size, size=min(6, flat.size), replace=False):
+            wp = {kk: vv.copy() for kk, vv in w.items()}
+            wm = {kk: vv.copy() for kk, vv in w.items()}
+            wp[k].reshape(-1)[idx] += h
+            wm[k].reshape(-1)[idx] -= h
+            fd = (f(wp)[0] - f(wm)[0]) / (2 * h)
+            assert g[k].reshape(-1)[idx] == pytest.approx(fd, rel=1e-5, abs=1e-8), (k, idx)
+
+
+def test_adam_first_step_is_signed_lr():
+    p = np.array([1.0, -2.0, 3.0]); gr = np.array([0.5, -4.0, 1e-3])
+    q, m, v = ppo.adam64(p, gr, np.zeros(3), np.zeros(3), 1, lr=1e-2, eps=1e-12)
+    assert np.allclose(q, p - 1e-2 * np.sign(gr))

@@ -1,0 +1,184 @@
+"""Parity of the policy forward, the sampler and the rollout with the oracle.
+
+Float32 forward tolerance, derived from the arithmetic: every output is a
+chain of three dot products of lengths K1 = in, K2 = K3 = H; with float32
+rounding u = 2^-24 its error is at most (K1 + K2 + K3) u times the magnitude
+obtained by running the network on |x| with |W| and |b| (float64).
+Sampled actions are integers decided by float32 arithmetic: the oracle
+takes the same decision in float32 (same exp, same summation order) from
+the GPU's logits and must agree exactly.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import policy as op
+from oracle.env import default_params
+from tests.parity import compare_env, oracle_run
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+H = 128
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_22165_gb300 import build
+    build.build()
+
+
+def _mods():
+    import paper_2410_22165_gb300 as P
+    from paper_2410_22165_gb300 import _native as N
+    return P, N
+
+
+def magnitude(w, x):
+    """Network outputs with every term replaced by its absolute value (float64)."""
+    a = {k: np.abs(v) for k, v in w.items()}
+    x = np.abs(np.asarray(x, np.float64))
+    h = x @ a["W1"] + a["b1"]
+    h = h @ a["W2"] + a["b2"]
+    lg = h @ a["W3"] + a["b3"]
+    g = x @ a["V1"] + a["c1"]
+    g = g @ a["V2"] + a["c2"]
+    v = (g @ a["V3"] + a["c3"])[:, 0]
+    return lg, v
+
+
+def _setup(E, A, seed=0, steps=37, **kw):
+    P, N = _mods()
+    env = P.VecEnv(E, A, **kw)
+    env.reset(seed=seed)
+    out = env.step(steps)                       # in-kernel random play to reach varied states
+    obs = out["obs"][-1].contiguous()
+    gobs = out["gobs"][-1].contiguous()
+    mask = out["mask"][-1].contiguous()
+    D, G = env.D, env.G
+    O_pop, O_gov = env.nA, env.p.nb * env.p.tax_levels
+    pw = synth.net_weights(seed, 0, D, H, O_pop)
+    gw = synth.net_weights(seed, 1, G, H, O_gov)
+    pol = P.Policy(env, torch.from_numpy(pw), torch.from_numpy(gw), hidden=H)
+    return env, pol, obs, gobs, mask, pw, gw
+
+
+def _check_forward(logits, value, w, x, in_dim):
+    lg64, v64 = op.mlp64(w, x)
+    mlg, mv = magnitude(w, x)
+    bound = (in_dim + 2 * H) * 2.0 ** -24
+    assert np.all(np.abs(logits - lg64) <= bound * mlg + 1e-30), np.max(np.abs(logits - lg64) / mlg)
+    assert np.all(np.abs(value - v64) <= bound * mv + 1e-30)
+
+
+def test_population_forward_and_sampling():
+    E, A = 3, 37
+    env, pol, obs, gobs, mask, pw, gw = _setup(E, A)
+    P, N = _mods()
+    out = pol.forward(N.NET_POP, obs, mask, logits=True, entropy=True)
+    lg = out["logits"].cpu().numpy()
+    val = out["value"].cpu().numpy()
+    x = obs.cpu().numpy().reshape(E * A, env.D)
+    w = synth.unpack(pw, env.D, H, env.nA)
+    _check_forward(lg, val, w, x, env.D)
+    valid = op.mask_bits(mask.cpu().numpy().view(np.uint32).reshape(E * A, env.W), env.nA)
+    g = int(env.field("gstep")[0].item())
+    u = synth.pop_draws(0, np.arange(E), A, g, 1, env.nA)[3][0].reshape(E * A)
+    act = op.sample32(lg, valid, u)
+    got = out["act"].cpu().numpy()[:, 0]
+    assert np.array_equal(got, act)
+    lp, ent = op.logp_entropy64(lg, valid, got)
+    assert np.allclose(out["logp"].cpu().numpy(), lp, rtol=0, atol=1e-5 * (1 + np.abs(lp)).max())
+    assert np.allclose(out["entropy"].cpu().numpy(), ent, rtol=0, atol=1e-5 * (1 + np.abs(ent)).max())
+
+
+def test_given_uniforms_and_values_only():
+    E, A = 2, 64
+    env, pol, obs, gobs, mask, pw, gw = _setup(E, A, seed=4)
+    P, N = _mods()
+    u = torch.rand(E * A, 1, device="cuda")
+    out = pol.forward(N.NET_POP, obs, mask, u=u, logits=True)
+    valid = op.mask_bits(mask.cpu().numpy().view(np.uint32).reshape(E * A, env.W), env.nA)
+    act = op.sample32(out["logits"].cpu().numpy(), valid, u.cpu().numpy()[:, 0])
+    assert np.array_equal(out["act"].cpu().numpy()[:, 0], act)
+    v_only = pol.forward(N.NET_POP, obs, mask, sample=False)
+    assert torch.equal(v_only["value"], out["value"])
+
+
+def test_government_forward_and_sampling():
+    E, A = 70, 10                     # 70 government rows: one full tile and a ragged one
+    env, pol, obs, gobs, mask, pw, gw = _setup(E, A, seed=2, T_ep=50, T_tax=10)
+    P, N = _mods()
+    out = pol.forward(N.NET_GOV, gobs, logits=True, entropy=True)
+    lg = out["logits"].cpu().numpy()
+    L = env.p.tax_levels
+    w = synth.unpack(gw, env.G, H, env.p.nb * L)
+    _check_forward(lg, out["value"].cpu().numpy(), w, gobs.cpu().numpy(), env.G)
+    g = int(env.field("gstep")[0].item())
+    _, gu = synth.gov_draws(2, np.arange(E), g, 1, env.p.nb, L)
+    got = out["act"].cpu().numpy()
+    lp_tot = np.zeros(E)
+    for b in range(env.p.nb):
+        head = lg[:, b * L:(b + 1) * L]
+        valid = np.ones_like(head, bool)
+        a = op.sample32(head, valid, gu[0, :, b])
+        assert np.array_equal(got[:, b], a)
+        lp, _ = op.logp_entropy64(head, valid, a)
+        lp_tot += lp
+    assert np.allclose(out["logp"].cpu().numpy(), lp_tot, atol=1e-5 * (1 + np.abs(lp_tot)).max())
+
+
+def test_rollout_fp32_matches_oracle_step_by_step():
+    """T = 25 steps across an episode end: every sampled action is the oracle's
+    decision on the GPU's logits; the environment transitions equal the oracle
+    run with the GPU's actions; stored values and log-probabilities are the
+    policy's."""
+    E, A, T = 3, 20, 25
+    kw = dict(T_ep=20, T_tax=5)
+    P, N = _mods()
+    env = P.VecEnv(E, A, **kw)
+    pw = synth.net_weights(9, 0, env.D, H, env.nA)
+    gw = synth.net_weights(9, 1, env.G, H, env.p.nb * env.p.tax_levels)
+    pol = P.Policy(env, torch.from_numpy(pw), torch.from_numpy(gw), hidden=H)
+    ro = P.Rollout(env, pol, T)
+    ro.reset(seed=9)
+    b = {k: v.cpu().numpy() for k, v in ro.run().items()}
+    torch.cuda.synchronize()
+    # a second environment replays the observations through policy_forward
+    probe = P.VecEnv(E, A, **kw)
+    probe.reset(seed=9)
+    pprobe = P.Policy(probe, torch.from_numpy(pw), torch.from_numpy(gw), hidden=H)
+    wp = synth.unpack(pw, env.D, H, env.nA)
+    L = env.p.tax_levels
+    for t in range(T + 1):
+        obs = torch.from_numpy(b["obs"][t]).cuda()
+        mask = torch.from_numpy(b["mask"][t]).cuda()
+        u = torch.from_numpy(synth.pop_draws(9, np.arange(E), A, t, 1, env.nA)[3][0].reshape(E * A, 1)).cuda()
+        o = pprobe.forward(N.NET_POP, obs, mask, u=u, logits=True)
+        assert np.array_equal(o["value"].cpu().numpy(), b["value"][t].reshape(-1))
+        if t == T:
+            break
+        lg = o["logits"].cpu().numpy()
+        valid = op.mask_bits(b["mask"][t].view(np.uint32).reshape(E * A, env.W), env.nA)
+        assert np.array_equal(b["act"][t].reshape(-1), op.sample32(lg, valid, u.cpu().numpy()[:, 0]))
+        assert np.array_equal(o["act"].cpu().numpy()[:, 0], b["act"][t].reshape(-1))
+        assert np.array_equal(o["logp"].cpu().numpy(), b["logp"][t].reshape(-1))
+        _check_forward(lg, o["value"].cpu().numpy(), wp, b["obs"][t].reshape(E * A, env.D), env.D)
+        _, gu = synth.gov_draws(9, np.arange(E), t, 1, env.p.nb, L)
+        og = pprobe.forward(N.NET_GOV, torch.from_numpy(b["gobs"][t]).cuda(),
+                            u=torch.from_numpy(gu[0]).cuda(), logits=True)
+        assert np.array_equal(og["act"].cpu().numpy(), b["gact"][t])
+    # environment transitions: the oracle stepped with the GPU's actions
+    p = default_params(**kw)
+    from oracle.env import OracleEnv
+    for e in range(E):
+        o = OracleEnv(p, A)
+        inp = synth.episode_inputs(9, [e], A, p["R"], p["nb"], o.nA, p["tax_levels"], T, p["T_ep"])
+        o.reset(inp["sg0"][0], inp["sc0"][0])
+        ref = o.run(b["act"][:, e], b["gact"][:, e], inp["gather_u"][:, 0], inp["tb"][:, 0],
+                    inp["later_sg"][:, 0], inp["later_sc"][:, 0])
+        g = dict(rew=b["rew"][:, e], grew=b["grew"][:, e], done=b["done"][:, e],
+                 obs=b["obs"][1:, e], gobs=b["gobs"][1:, e], mask=b["mask"][1:, e])
+        compare_env(g, ref, env.params, A)
