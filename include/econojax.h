@@ -224,6 +224,9 @@ ej_status ej_fill_draws(const EjParams* p, uint64_t seed, uint32_t g0, int32_t n
  *   V1 [in][H], c1 [H], V2 [H][H], c2 [H], V3 [H], c3 [1]          (critic)
  * with O = nA (population) or nb * tax_levels (government); each tensor
  * starts at a multiple of 4 floats (the gaps are padding, ignored).
+ * precision EJ_BF16: the five GEMMs on the tensor cores (tcgen05.mma, BF16
+ * operands, FP32 accumulation in tensor memory), hidden in {64, 128};
+ * EJ_FP32: float32 on the CUDA cores.
  * Sampling (Section 3 "Action masking": forbidden actions have probability 0)
  * is by inverse CDF on the masked softmax, computed in float32 with the
  * library's own exp (Cody-Waite reduction + degree-7 Taylor polynomial),
@@ -349,6 +352,11 @@ ej_status ppo_update(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_
                      float* pop_v, float* gov_m, float* gov_v, int32_t adam_steps_done,
                      uint32_t update_index, const EjRollout* buf, void* workspace,
                      float* stats_out, void* stream);
+
+/* Synchronous read of the device fault word: *fault != 0 when a bounded
+ * wait of a tensor-core kernel gave up (the kernel then freed its tensor
+ * memory and returned without finishing).  clear != 0 resets it. */
+ej_status ej_device_status(int32_t* fault, int32_t clear);
 
 /* Description of the last error returned to the calling thread. */
 const char* ej_last_error(void);

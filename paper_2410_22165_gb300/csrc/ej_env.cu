@@ -888,9 +888,9 @@ ej_status launch_nt(const KParams& kp, const Layout& lay, const DevState& st, co
     const int smem = lay.sizes.smem_bytes;
     static int configured = 0;   // max dynamic smem set once per instantiation
     if (configured < smem) {
-        cudaError_t err = cudaFuncSetAttribute(env_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaError_t err = cudaFuncSetAttribute(env_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
-        configured = 227 * 1024;
+        configured = smem;
     }
     env_kernel<NT><<<kp.E, NT, smem, stream>>>(kp, st, io, n_steps, mode, (uint32_t)seed,
                                                 (uint32_t)(seed >> 32));

@@ -70,9 +70,9 @@ ej_status launch_policy_fp32(const PolicyArgs& a, cudaStream_t stream) {
     const size_t smem = policy_fp32_smem(a.in_pad, a.H, a.O);
     static size_t configured = 0;
     if (configured < smem) {
-        cudaError_t err = cudaFuncSetAttribute(policy_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaError_t err = cudaFuncSetAttribute(policy_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
-        configured = 227 * 1024;
+        configured = smem;
     }
     const int n_tiles = (a.rows + TILE - 1) / TILE;
     int grid = n_tiles < 2 * 152 ? n_tiles : 2 * 152;

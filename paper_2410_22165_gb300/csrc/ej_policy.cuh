@@ -212,5 +212,7 @@ __device__ inline void value_tile(const float* in, int ldi, int K, const float* 
 
 size_t policy_fp32_smem(int in_pad, int H, int O);
 ej_status launch_policy_fp32(const PolicyArgs& a, cudaStream_t stream);
+size_t policy_bf16_smem(int H, int O);
+ej_status launch_policy_bf16(const PolicyArgs& a, cudaStream_t stream);
 
 }  // namespace ej

@@ -1,0 +1,276 @@
+// Policy forward on the 5th-generation tensor cores: BF16 operands, FP32
+// accumulation in tensor memory (tcgen05.mma, kind::f16, M = 128).
+//
+// One CTA per SM, persistent over tiles of 128 rows (thread i of the 4 warps
+// owns row i, i.e. TMEM lane i).  At start the CTA packs the actor and
+// critic weights into shared memory as K-major BF16 operands in the 128-byte
+// swizzled layout.  Per tile: observations -> BF16 operand; layer 1 of actor
+// and critic as one N = 2H MMA chain; epilogue (bias, ReLU, BF16) back into
+// shared memory as the next operand; layer 2 of actor and critic; the two
+// heads; the last epilogue adds the biases and samples the action with the
+// same sampler as the float32 path.  Thread 0 issues the MMAs; completion is
+// signalled through tcgen05.commit to an mbarrier; every wait is bounded.
+#include <cfloat>
+#include <cmath>
+
+#include "ej_internal.cuh"
+#include "ej_policy.cuh"
+
+namespace ej {
+__device__ int g_ej_fault = 0;   // fault word of the bounded waits in this library
+}
+
+#include "ej_tc.cuh"
+
+namespace ej {
+
+namespace {
+
+constexpr int BM = 128;     // rows per tile = TMEM lanes
+constexpr int BT = 128;     // threads per CTA
+constexpr int KX = 64;      // observation width padded to one 64-element panel
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t COL_D3 = 256, COL_D4 = 384;
+
+struct BfLayout {
+    uint32_t w1, w2a, w2c, w3, v3, x, h, total;
+    int N3;
+};
+
+__host__ __device__ inline BfLayout bf_layout(int H, int O) {
+    BfLayout L;
+    L.N3 = (O + 15) / 16 * 16;
+    uint32_t b = 0;
+    L.w1 = b;  b += 2u * H * KX * 2;           // [2H][KX]
+    L.w2a = b; b += (uint32_t)H * H * 2;       // [H][H]
+    L.w2c = b; b += (uint32_t)H * H * 2;
+    L.w3 = b;  b += (uint32_t)L.N3 * H * 2;    // [N3][H]
+    L.v3 = b;  b += 16u * H * 2;               // [16][H]
+    L.x = b;   b += BM * KX * 2;               // [BM][KX]
+    L.h = b;   b += BM * 2u * H * 2;           // [BM][2H]
+    L.total = b;
+    return L;
+}
+
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void st_shared_v4(uint8_t* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(smem_u32(p)), "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
+}
+
+// Packs rows x K of a K-major operand from a float source: element (n, k) =
+// get(n, k).  Work items (chunk of 8 k, row n), rows fastest.
+template <class F>
+__device__ void pack_operand(uint8_t* dst, int rows, int K, F get) {
+    const int items = rows * (K / 8);
+    for (int it = threadIdx.x; it < items; it += BT) {
+        const int n = it % rows, kc = it / rows;
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = get(n, kc * 8 + q);
+        st_shared_v4(dst + sw128_offset(n, kc * 8, rows), pack2(v[0], v[1]), pack2(v[2], v[3]),
+                     pack2(v[4], v[5]), pack2(v[6], v[7]));
+    }
+}
+
+// 32 accumulator columns of this thread's row -> bias, ReLU, BF16 -> operand
+// columns [k0, k0 + 32) of row `row` in the swizzled [BM][K] operand.
+__device__ __forceinline__ void epilogue32(uint32_t taddr, const float* __restrict__ bias, uint8_t* dst,
+                                           int row, int k0) {
+    float v[32];
+    tmem_ld32(taddr, v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float y[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) y[j] = fmaxf(v[q * 8 + j] + __ldg(bias + q * 8 + j), 0.0f);
+        st_shared_v4(dst + sw128_offset(row, k0 + q * 8, BM), pack2(y[0], y[1]), pack2(y[2], y[3]),
+                     pack2(y[4], y[5]), pack2(y[6], y[7]));
+    }
+}
+
+__device__ __forceinline__ void sync_for_mma() {
+    fence_async_shared();      // generic-proxy writes of operands -> visible to the tensor core
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+
+// K-loop of one MMA chain: D[128 x N] (+)= A[128 x K] * B[N x K]^T, both
+// operands K-major 128B-swizzled with panels of 64 K.
+__device__ __forceinline__ void mma_chain(uint32_t d, uint32_t a_base, int a_rows, uint32_t b_base, int b_rows,
+                                          int K, uint32_t idesc) {
+    for (int kk = 0; kk < K / 16; ++kk) {
+        const int panel = kk >> 2, sub = kk & 3;
+        const uint64_t ad = sw128_desc(a_base + panel * (a_rows / 8) * 1024 + sub * 32);
+        const uint64_t bd = sw128_desc(b_base + panel * (b_rows / 8) * 1024 + sub * 32);
+        mma_bf16(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
+    }
+}
+
+__global__ void __launch_bounds__(BT, 1) policy_bf16_kernel(PolicyArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int H = a.H, O = a.O, I = a.in_dim;
+    const BfLayout L = bf_layout(H, O);
+    const NetOffsets off = net_offsets(I, H, O);
+    const float* w = a.weights;
+    const int ldo = O | 1;
+
+    // weights -> shared memory, BF16, K-major (row n of B = output unit n)
+    pack_operand(smem + L.w1, 2 * H, KX, [&](int n, int k) {
+        if (k >= I) return 0.0f;
+        return n < H ? __ldg(w + off.W1 + (size_t)k * H + n) : __ldg(w + off.V1 + (size_t)k * H + (n - H));
+    });
+    pack_operand(smem + L.w2a, H, H, [&](int n, int k) { return __ldg(w + off.W2 + (size_t)k * H + n); });
+    pack_operand(smem + L.w2c, H, H, [&](int n, int k) { return __ldg(w + off.V2 + (size_t)k * H + n); });
+    pack_operand(smem + L.w3, L.N3, H, [&](int n, int k) {
+        return n < O ? __ldg(w + off.W3 + (size_t)k * O + n) : 0.0f;
+    });
+    pack_operand(smem + L.v3, 16, H, [&](int n, int k) { return n == 0 ? __ldg(w + off.V3 + k) : 0.0f; });
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_slot, TMEM_COLS);
+    sync_for_mma();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t sx = smem_u32(smem + L.x), sh = smem_u32(smem + L.h);
+    const uint32_t sw1 = smem_u32(smem + L.w1), sw2a = smem_u32(smem + L.w2a), sw2c = smem_u32(smem + L.w2c);
+    const uint32_t sw3 = smem_u32(smem + L.w3), sv3 = smem_u32(smem + L.v3);
+    float* stage = (float*)(smem + L.h);       // logits staging reuses the activation operand
+    uint32_t phase = 0;
+    bool ok = true;
+    const int n_tiles = (a.rows + BM - 1) / BM;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int row = tile * BM + tid;
+        const bool valid = row < a.rows;
+        // observations -> BF16 operand [BM][KX]
+#pragma unroll
+        for (int c = 0; c < KX / 8; ++c) {
+            float y[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int k = c * 8 + q;
+                y[q] = (valid && k < I) ? a.x[(size_t)row * I + k] : 0.0f;
+            }
+            st_shared_v4(smem + L.x + sw128_offset(tid, c * 8, BM), pack2(y[0], y[1]), pack2(y[2], y[3]),
+                         pack2(y[4], y[5]), pack2(y[6], y[7]));
+        }
+        sync_for_mma();
+        // layer 1 of actor and critic: D[:, 0:2H] = X W1cat
+        if (tid == 0) {
+            mma_chain(tmem, sx, BM, sw1, 2 * H, KX, idesc_bf16(BM, 2 * H));
+            mma_commit(&bar);
+        }
+        ok = mbar_wait(&bar, phase);
+        phase ^= 1;
+        if (!__syncthreads_and(ok)) break;
+        tc_fence_after();
+        for (int c = 0; c < 2 * H / 32; ++c) {
+            const int col = c * 32;
+            epilogue32(lane_base + col, col < H ? w + off.b1 + col : w + off.c1 + (col - H), smem + L.h, tid, col);
+        }
+        sync_for_mma();
+        // layer 2: D[:, 0:H] = H1a W2, D[:, H:2H] = H1c V2
+        if (tid == 0) {
+            mma_chain(tmem, sh, BM, sw2a, H, H, idesc_bf16(BM, H));
+            mma_chain(tmem + H, sh + (H / 64) * (BM / 8) * 1024, BM, sw2c, H, H, idesc_bf16(BM, H));
+            mma_commit(&bar);
+        }
+        ok = mbar_wait(&bar, phase);
+        phase ^= 1;
+        if (!__syncthreads_and(ok)) break;
+        tc_fence_after();
+        for (int c = 0; c < 2 * H / 32; ++c) {
+            const int col = c * 32;
+            epilogue32(lane_base + col, col < H ? w + off.b2 + col : w + off.c2 + (col - H), smem + L.h, tid, col);
+        }
+        sync_for_mma();
+        // heads: logits = H2a W3 (N3 columns), value = H2c V3 (column 0 of 16)
+        if (tid == 0) {
+            mma_chain(tmem + COL_D3, sh, BM, sw3, L.N3, H, idesc_bf16(BM, L.N3));
+            mma_chain(tmem + COL_D4, sh + (H / 64) * (BM / 8) * 1024, BM, sv3, 16, H, idesc_bf16(BM, 16));
+            mma_commit(&bar);
+        }
+        ok = mbar_wait(&bar, phase);
+        phase ^= 1;
+        if (!__syncthreads_and(ok)) break;
+        tc_fence_after();
+        float* lrow = stage + tid * ldo;
+        for (int c = 0; c < L.N3 / 32 + ((L.N3 % 32) ? 1 : 0); ++c) {
+            float v[32];
+            tmem_ld32(lane_base + COL_D3 + c * 32, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int col = c * 32 + j;
+                if (col < O) lrow[col] = v[j] + __ldg(w + off.b3 + col);
+            }
+        }
+        float vv[32];
+        tmem_ld32(lane_base + COL_D4, vv);
+        const float value = vv[0] + __ldg(w + off.c3);
+        if (valid) sample_row(a, row, lrow, value);
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
+    if (!ok) {
+        // a wait gave up: give the tensor core one more bounded chance to finish before freeing TMEM
+        mbar_wait(&bar, phase, 200000000LL);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+}  // namespace
+
+size_t policy_bf16_smem(int H, int O) { return bf_layout(H, O).total + 1024; }
+
+ej_status launch_policy_bf16(const PolicyArgs& a, cudaStream_t stream) {
+    if (a.H != 64 && a.H != 128) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: hidden must be 64 or 128");
+    if (a.in_dim > KX) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: input width must be <= %d", KX);
+    if (a.O > 128) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: at most 128 logits");
+    if (a.O + 1 > 2 * a.H) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: logits do not fit the staging area");
+    const size_t smem = policy_bf16_smem(a.H, a.O);
+    if (smem > 227 * 1024) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: %zu bytes of shared memory", smem);
+    static size_t configured = 0;
+    if (configured < smem) {
+        cudaError_t err = cudaFuncSetAttribute(policy_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+        if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
+        configured = smem;
+    }
+    const int n_tiles = (a.rows + BM - 1) / BM;
+    int grid = n_tiles < 152 ? n_tiles : 152;
+    if (grid < 1) grid = 1;
+    policy_bf16_kernel<<<grid, BT, smem, stream>>>(a);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "bf16 policy launch: %s", cudaGetErrorString(err));
+    return EJ_OK;
+}
+
+}  // namespace ej
+
+extern "C" ej_status ej_device_status(int32_t* fault, int32_t clear) {
+    int v = 0;
+    cudaError_t err = cudaMemcpyFromSymbol(&v, ej::g_ej_fault, sizeof(int));
+    if (err != cudaSuccess) return ej::fail(EJ_ERR_CUDA, "ej_device_status: %s", cudaGetErrorString(err));
+    if (fault) *fault = v;
+    if (clear) {
+        const int z = 0;
+        err = cudaMemcpyToSymbol(ej::g_ej_fault, &z, sizeof(int));
+        if (err != cudaSuccess) return ej::fail(EJ_ERR_CUDA, "ej_device_status: %s", cudaGetErrorString(err));
+    }
+    return EJ_OK;
+}

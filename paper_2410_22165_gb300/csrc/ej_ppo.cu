@@ -385,9 +385,9 @@ ej_status launch_minibatch_grad(const FbArgs& fa, const WgJobs& jobs, int n_jobs
     const size_t smem = fwd_bwd_smem(fa.in_pad, fa.H, fa.O);
     static size_t configured = 0;
     if (configured < smem) {
-        if (cudaFuncSetAttribute(fwd_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
+        if (cudaFuncSetAttribute(fwd_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute failed");
-        configured = 227 * 1024;
+        configured = smem;
     }
     const int n_tiles = (fa.mb.count + TILE - 1) / TILE;
     int g2 = n_tiles < 152 ? n_tiles : 152;

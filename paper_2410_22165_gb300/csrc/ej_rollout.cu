@@ -54,6 +54,7 @@ static ej_status make_args(const EjParams* p, const KParams& kp, const Layout& l
 
 static ej_status launch_policy(const PolicyArgs& a, int precision, cudaStream_t stream) {
     if (precision == EJ_FP32) return launch_policy_fp32(a, stream);
+    if (precision == EJ_BF16) return launch_policy_bf16(a, stream);
     return fail(EJ_ERR_UNSUPPORTED, "precision %d is not available", precision);
 }
 

@@ -4,6 +4,10 @@ Float32 forward tolerance, derived from the arithmetic: every output is a
 chain of three dot products of lengths K1 = in, K2 = K3 = H; with float32
 rounding u = 2^-24 its error is at most (K1 + K2 + K3) u times the magnitude
 obtained by running the network on |x| with |W| and |b| (float64).
+BF16 forward tolerance: every product of a layer has both operands rounded to
+bfloat16 (relative error <= 2^-9 each) and the activations between layers are
+rounded again; over three layers the error is at most 8 * 2^-9 times the same
+magnitude (accumulation is float32 and contributes far less).
 Sampled actions are integers decided by float32 arithmetic: the oracle
 takes the same decision in float32 (same exp, same summation order) from
 the GPU's logits and must agree exactly.
@@ -49,7 +53,7 @@ def magnitude(w, x):
     return lg, v
 
 
-def _setup(E, A, seed=0, steps=37, **kw):
+def _setup(E, A, seed=0, steps=37, precision="fp32", **kw):
     P, N = _mods()
     env = P.VecEnv(E, A, **kw)
     env.reset(seed=seed)
@@ -61,28 +65,33 @@ def _setup(E, A, seed=0, steps=37, **kw):
     O_pop, O_gov = env.nA, env.p.nb * env.p.tax_levels
     pw = synth.net_weights(seed, 0, D, H, O_pop)
     gw = synth.net_weights(seed, 1, G, H, O_gov)
-    pol = P.Policy(env, torch.from_numpy(pw), torch.from_numpy(gw), hidden=H)
+    pol = P.Policy(env, torch.from_numpy(pw), torch.from_numpy(gw), hidden=H, precision=precision)
     return env, pol, obs, gobs, mask, pw, gw
 
 
-def _check_forward(logits, value, w, x, in_dim):
+def _bound(precision, in_dim):
+    return (in_dim + 2 * H) * 2.0 ** -24 if precision == "fp32" else 8 * 2.0 ** -9
+
+
+def _check_forward(logits, value, w, x, in_dim, precision="fp32"):
     lg64, v64 = op.mlp64(w, x)
     mlg, mv = magnitude(w, x)
-    bound = (in_dim + 2 * H) * 2.0 ** -24
+    bound = _bound(precision, in_dim)
     assert np.all(np.abs(logits - lg64) <= bound * mlg + 1e-30), np.max(np.abs(logits - lg64) / mlg)
     assert np.all(np.abs(value - v64) <= bound * mv + 1e-30)
 
 
-def test_population_forward_and_sampling():
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_population_forward_and_sampling(precision):
     E, A = 3, 37
-    env, pol, obs, gobs, mask, pw, gw = _setup(E, A)
+    env, pol, obs, gobs, mask, pw, gw = _setup(E, A, precision=precision)
     P, N = _mods()
     out = pol.forward(N.NET_POP, obs, mask, logits=True, entropy=True)
     lg = out["logits"].cpu().numpy()
     val = out["value"].cpu().numpy()
     x = obs.cpu().numpy().reshape(E * A, env.D)
     w = synth.unpack(pw, env.D, H, env.nA)
-    _check_forward(lg, val, w, x, env.D)
+    _check_forward(lg, val, w, x, env.D, precision)
     valid = op.mask_bits(mask.cpu().numpy().view(np.uint32).reshape(E * A, env.W), env.nA)
     g = int(env.field("gstep")[0].item())
     u = synth.pop_draws(0, np.arange(E), A, g, 1, env.nA)[3][0].reshape(E * A)
@@ -107,15 +116,16 @@ def test_given_uniforms_and_values_only():
     assert torch.equal(v_only["value"], out["value"])
 
 
-def test_government_forward_and_sampling():
-    E, A = 70, 10                     # 70 government rows: one full tile and a ragged one
-    env, pol, obs, gobs, mask, pw, gw = _setup(E, A, seed=2, T_ep=50, T_tax=10)
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_government_forward_and_sampling(precision):
+    E, A = 170, 10                    # 170 government rows: full tiles and a ragged one
+    env, pol, obs, gobs, mask, pw, gw = _setup(E, A, seed=2, precision=precision, T_ep=50, T_tax=10)
     P, N = _mods()
     out = pol.forward(N.NET_GOV, gobs, logits=True, entropy=True)
     lg = out["logits"].cpu().numpy()
     L = env.p.tax_levels
     w = synth.unpack(gw, env.G, H, env.p.nb * L)
-    _check_forward(lg, out["value"].cpu().numpy(), w, gobs.cpu().numpy(), env.G)
+    _check_forward(lg, out["value"].cpu().numpy(), w, gobs.cpu().numpy(), env.G, precision)
     g = int(env.field("gstep")[0].item())
     _, gu = synth.gov_draws(2, np.arange(E), g, 1, env.p.nb, L)
     got = out["act"].cpu().numpy()
@@ -130,7 +140,8 @@ def test_government_forward_and_sampling():
     assert np.allclose(out["logp"].cpu().numpy(), lp_tot, atol=1e-5 * (1 + np.abs(lp_tot)).max())
 
 
-def test_rollout_fp32_matches_oracle_step_by_step():
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_rollout_matches_oracle_step_by_step(precision):
     """T = 25 steps across an episode end: every sampled action is the oracle's
     decision on the GPU's logits; the environment transitions equal the oracle
     run with the GPU's actions; stored values and log-probabilities are the
@@ -141,7 +152,7 @@ def test_rollout_fp32_matches_oracle_step_by_step():
     env = P.VecEnv(E, A, **kw)
     pw = synth.net_weights(9, 0, env.D, H, env.nA)
     gw = synth.net_weights(9, 1, env.G, H, env.p.nb * env.p.tax_levels)
-    pol = P.Policy(env, torch.from_numpy(pw), torch.from_numpy(gw), hidden=H)
+    pol = P.Policy(env, torch.from_numpy(pw), torch.from_numpy(gw), hidden=H, precision=precision)
     ro = P.Rollout(env, pol, T)
     ro.reset(seed=9)
     b = {k: v.cpu().numpy() for k, v in ro.run().items()}
@@ -149,7 +160,7 @@ def test_rollout_fp32_matches_oracle_step_by_step():
     # a second environment replays the observations through policy_forward
     probe = P.VecEnv(E, A, **kw)
     probe.reset(seed=9)
-    pprobe = P.Policy(probe, torch.from_numpy(pw), torch.from_numpy(gw), hidden=H)
+    pprobe = P.Policy(probe, torch.from_numpy(pw), torch.from_numpy(gw), hidden=H, precision=precision)
     wp = synth.unpack(pw, env.D, H, env.nA)
     L = env.p.tax_levels
     for t in range(T + 1):
@@ -165,7 +176,7 @@ def test_rollout_fp32_matches_oracle_step_by_step():
         assert np.array_equal(b["act"][t].reshape(-1), op.sample32(lg, valid, u.cpu().numpy()[:, 0]))
         assert np.array_equal(o["act"].cpu().numpy()[:, 0], b["act"][t].reshape(-1))
         assert np.array_equal(o["logp"].cpu().numpy(), b["logp"][t].reshape(-1))
-        _check_forward(lg, o["value"].cpu().numpy(), wp, b["obs"][t].reshape(E * A, env.D), env.D)
+        _check_forward(lg, o["value"].cpu().numpy(), wp, b["obs"][t].reshape(E * A, env.D), env.D, precision)
         _, gu = synth.gov_draws(9, np.arange(E), t, 1, env.p.nb, L)
         og = pprobe.forward(N.NET_GOV, torch.from_numpy(b["gobs"][t]).cuda(),
                             u=torch.from_numpy(gu[0]).cuda(), logits=True)
@@ -182,3 +193,11 @@ def test_rollout_fp32_matches_oracle_step_by_step():
         g = dict(rew=b["rew"][:, e], grew=b["grew"][:, e], done=b["done"][:, e],
                  obs=b["obs"][1:, e], gobs=b["gobs"][1:, e], mask=b["mask"][1:, e])
         compare_env(g, ref, env.params, A)
+
+
+def test_no_device_fault_recorded():
+    P, N = _mods()
+    import ctypes as C
+    f = C.c_int32(-1)
+    N.check(N.load().ej_device_status(C.byref(f), 0), "ej_device_status")
+    assert f.value == 0
