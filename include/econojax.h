@@ -353,6 +353,30 @@ ej_status ppo_update(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_
                      uint32_t update_index, const EjRollout* buf, void* workspace,
                      float* stats_out, void* stream);
 
+/* ppo_minibatch_grad_static: ppo_minibatch_grad for callers that cannot
+ * allocate device memory (code running inside a CUDA stream capture, where
+ * cudaMalloc is not allowed; hosts whose device memory belongs to another
+ * runtime's pool; C programs without an allocator of their own).  It needs no
+ * workspace: the advantages of `net`, the activations and the split-K partial
+ * sums live in a static device array of 48 MiB that the library holds on every
+ * GPU that loads it, until the process exits.  It computes the advantages of
+ * `net` itself (no ppo_advantages call), otherwise arguments, layout and the
+ * gradient are those of ppo_minibatch_grad (the partial sums are reduced in
+ * 16 chunks instead of 96, so results agree to rounding).  The paper has no
+ * counterpart: this is a convenience of this library.
+ * Limits: the rollout's advantages and one minibatch of activations must fit
+ * 48 MiB (about 8 thousand minibatch rows at hidden 128); larger sizes return
+ * EJ_ERR_UNSUPPORTED with the bytes needed, before anything is enqueued.
+ * The first call on a device, with that device current, looks the array's
+ * address up (cudaGetSymbolAddress): make it before any stream capture.
+ * Every call shares the array and leaves its contents behind; calls that
+ * overlap on the GPU race on it and must be serialised by the caller.
+ * It calls no cudaMalloc, cudaFree or other allocating routine. */
+ej_status ppo_minibatch_grad_static(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_t hidden,
+                                    int32_t precision, int32_t net, const float* weights,
+                                    const EjRollout* buf, uint32_t shuffle_ctr, int32_t minibatch,
+                                    float* grad, double* stats_out, void* stream);
+
 /* Synchronous read of the device fault word: *fault != 0 when a bounded
  * wait of a tensor-core kernel gave up (the kernel then freed its tensor
  * memory and returned without finishing).  clear != 0 resets it. */

@@ -94,6 +94,9 @@ _PROTOS = {
                             C.c_float, _VP]),
     "ppo_update": (C.c_int, [C.POINTER(EjParams), C.POINTER(EjPpoParams), C.c_int32, C.c_int32, C.c_int32,
                              _VP, _VP, _VP, _VP, _VP, _VP, C.c_int32, C.c_uint32, C.c_void_p, _VP, _VP, _VP]),
+    "ppo_minibatch_grad_static": (C.c_int, [C.POINTER(EjParams), C.POINTER(EjPpoParams), C.c_int32, C.c_int32,
+                                            C.c_int32, C.c_int32, _VP, C.c_void_p, C.c_uint32, C.c_int32,
+                                            _VP, _VP, _VP]),
     "ej_device_status": (C.c_int, [C.POINTER(C.c_int32), C.c_int32]),
     "ej_last_error": (C.c_char_p, []),
 }
