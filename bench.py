@@ -206,11 +206,87 @@ def run_gpu(args):
     }
     if e2e is not None:
         line["e2e"] = e2e
+    if not args.no_train:
+        del d, out
+        torch.cuda.empty_cache()
+        line["rollout"] = {"workload": "E=4096 x A=100, 1000 steps: policy + sampling + government policy + "
+                                       "env_step per step",
+                           "bf16": run_rollout(args, dev, "bf16"), "fp32": run_rollout(args, dev, "fp32")}
+        line["ppo"] = {"workload": "E=2048 x A=100 x 128 steps, GAE, 4 epochs x 8 minibatches, both networks",
+                       **run_ppo(args, dev)}
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if world > 1:
         dist.destroy_process_group()
     return line
+
+
+def run_rollout(args, dev, precision, E_r=4096, T_r=1000, seed=2000):
+    """Full rollout: E_r x A policy forward + masked sampling + government
+    policy + env_step per step (3 launches per step), T_r steps."""
+    import torch
+
+    import synth
+    from paper_2410_22165_gb300 import Policy, Rollout, VecEnv
+
+    env = VecEnv(E_r, A, device=dev, T_ep=T_EP, T_tax=T_TAX)
+    pw = torch.from_numpy(synth.net_weights(seed, 0, env.D, 128, env.nA))
+    gw = torch.from_numpy(synth.net_weights(seed, 1, env.G, 128, env.p.nb * env.p.tax_levels))
+    pol = Policy(env, pw, gw, hidden=128, precision=precision)
+    ro = Rollout(env, pol, T_r)
+    ro.reset(seed=seed)
+    ro.run()
+    torch.cuda.synchronize(dev)
+    steps = max(1, min(args.steps, 2))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        ro.carry_over()
+        ro.run()
+    b.record()
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / steps
+    mean_rew = float(ro.buf["rew"].double().mean().item())
+    out = {"value": E_r * A * T_r / (ms / 1e3), "unit": UNIT, "ms_per_rollout": ms,
+           "mean_population_reward": mean_rew, "launches_per_rollout": 3 * T_r + 2}
+    del ro, pol, env
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_ppo(args, dev, E_p=2048, T_p=128, seed=3000):
+    """PPO update of config 4: E_p x A x T_p transitions, GAE, 4 epochs x 8
+    minibatches of the population and government networks, float32."""
+    import torch
+
+    import synth
+    from paper_2410_22165_gb300 import PPO, Policy, Rollout, VecEnv
+
+    env = VecEnv(E_p, A, device=dev, T_ep=T_EP, T_tax=T_TAX)
+    pw = torch.from_numpy(synth.net_weights(seed, 0, env.D, 128, env.nA))
+    gw = torch.from_numpy(synth.net_weights(seed, 1, env.G, 128, env.p.nb * env.p.tax_levels))
+    pol = Policy(env, pw, gw, hidden=128, precision="bf16")
+    ro = Rollout(env, pol, T_p)
+    ro.reset(seed=seed)
+    ro.run()
+    ppo = PPO(pol, T_p)
+    ppo.update(ro)
+    torch.cuda.synchronize(dev)
+    steps = max(1, min(args.steps, 2))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        stats = ppo.update(ro)
+    b.record()
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / steps
+    st = stats.cpu().numpy()
+    out = {"updates_per_s": 1e3 / ms, "ms_per_update": ms, "precision": "fp32",
+           "transitions_per_update": E_p * A * T_p, "epochs": ppo.pp.epochs, "minibatches": ppo.pp.minibatches,
+           "population_loss": {"policy": float(st[0, 0]), "value": float(st[0, 1]), "entropy": float(st[0, 2])}}
+    del ppo, ro, pol, env
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_e2e(env, d, out, args, dev, world):
@@ -312,11 +388,62 @@ def run_reference(args):
 
 
 def run_profile_case(args):
-    """Small case for profilers: E = 1024 x A = 100, 100-step launches (inputs
-    123 MB, outputs 1.1 GB: larger than L2, a few GB on the device)."""
+    """Small cases for profilers (a few GB on the device at most).
+    env: E = 1024 x A = 100, 100-step launches (inputs 123 MB, outputs 1.1 GB).
+    policy: population policy forward on E = 4096 x A = 100 rows, bf16 then fp32.
+    ppo: one PPO update of E = 256 x A = 100 x 32 steps (8 minibatches)."""
     import torch
 
     from paper_2410_22165_gb300 import VecEnv
+
+    if args.profile_case == "policy":
+        import synth
+        from paper_2410_22165_gb300 import Policy
+        from paper_2410_22165_gb300 import _native as N
+        env = VecEnv(4096, A, device="cuda", T_ep=T_EP, T_tax=T_TAX)
+        env.reset(seed=7)
+        o = env.step(3)
+        obs, mask = o["obs"][-1].contiguous(), o["mask"][-1].contiguous()
+        pw = torch.from_numpy(synth.net_weights(7, 0, env.D, 128, env.nA))
+        gw = torch.from_numpy(synth.net_weights(7, 1, env.G, 128, env.p.nb * env.p.tax_levels))
+        res = {}
+        for prec in ("bf16", "fp32"):
+            pol = Policy(env, pw, gw, hidden=128, precision=prec)
+            ms = []
+            for k in range(args.warmup + args.steps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                pol.forward(N.NET_POP, obs, mask)
+                b.record()
+                torch.cuda.synchronize()
+                if k >= args.warmup:
+                    ms.append(a.elapsed_time(b))
+            flops = 4096 * A * 2 * (env.D * 128 * 2 + 128 * 128 * 2 + 128 * env.nA + 128)
+            res[prec] = {"launch_ms": ms, "useful_TFLOPs": flops / (statistics.mean(ms) / 1e3) / 1e12}
+        print(json.dumps({"profile_case": "policy E=4096 A=100", **res}))
+        return
+    if args.profile_case == "ppo":
+        import synth
+        from paper_2410_22165_gb300 import PPO, Policy, Rollout
+        env = VecEnv(256, A, device="cuda", T_ep=T_EP, T_tax=T_TAX)
+        pw = torch.from_numpy(synth.net_weights(7, 0, env.D, 128, env.nA))
+        gw = torch.from_numpy(synth.net_weights(7, 1, env.G, 128, env.p.nb * env.p.tax_levels))
+        pol = Policy(env, pw, gw, hidden=128, precision="bf16")
+        ro = Rollout(env, pol, 32)
+        ro.reset(seed=7)
+        ro.run()
+        ppo = PPO(pol, 32)
+        ms = []
+        for k in range(args.warmup + args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ppo.update(ro)
+            b.record()
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                ms.append(a.elapsed_time(b))
+        print(json.dumps({"profile_case": "ppo E=256 A=100 T=32", "update_ms": ms}))
+        return
 
     n = 100
     env = VecEnv(E, A, device="cuda", T_ep=T_EP, T_tax=T_TAX)
@@ -340,13 +467,14 @@ def run_profile_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-case", action="store_true")
+    ap.add_argument("--profile-case", nargs="?", const="env", default=None, choices=["env", "policy", "ppo"])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-train", action="store_true", help="skip the rollout and PPO measurements")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     args = ap.parse_args()

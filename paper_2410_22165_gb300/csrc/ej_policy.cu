@@ -25,6 +25,7 @@ __global__ void __launch_bounds__(NTH, 2) policy_fp32_kernel(PolicyArgs a) {
     float* hB = hA + TILE * ldh;                     // [TILE][ldh]
     float* lg = hB + TILE * ldh;                     // [TILE][ldo]
     float* val = lg + TILE * ldo;                    // [TILE]
+    float* wsc = val + TILE;                         // [TILE][ldo] sampler scratch
     const NetOffsets off = net_offsets(in_dim, H, O);
     const float* w = a.weights;
     const int n_tiles = (a.rows + TILE - 1) / TILE;
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__(NTH, 2) policy_fp32_kernel(PolicyArgs a) {
         // sampling, one thread per row
         if (threadIdx.x < TILE) {
             const int r = threadIdx.x, row = row0 + r;
-            if (row < a.rows) sample_row(a, row, lg + r * ldo, val[r]);
+            if (row < a.rows) sample_row(a, row, lg + r * ldo, val[r], wsc + r * ldo);
         }
         __syncthreads();
     }
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(NTH, 2) policy_fp32_kernel(PolicyArgs a) {
 }  // namespace
 
 size_t policy_fp32_smem(int in_pad, int H, int O) {
-    return sizeof(float) * ((size_t)TILE * in_pad + 2 * (size_t)TILE * (H + 4) + (size_t)TILE * (O + 1) + TILE);
+    return sizeof(float) * ((size_t)TILE * in_pad + 2 * (size_t)TILE * (H + 4) + 2 * (size_t)TILE * (O + 1) + TILE);
 }
 
 ej_status launch_policy_fp32(const PolicyArgs& a, cudaStream_t stream) {

@@ -79,9 +79,10 @@ __device__ __forceinline__ float exp32(float x) {
 
 // Inverse-CDF draw of one head from its logits l[0..K) under `valid` bits.
 // Returns the action (-1 if nothing is allowed) and adds the head's log
-// probability and entropy.
+// probability and entropy.  w[0..K) is scratch for the exp weights (each is
+// computed once and reused for the draw); NULL: they are recomputed.
 __device__ __forceinline__ int sample_head(const float* l, int K, const uint32_t* valid_words,
-                                           int bit0, float u, float& logp, float& ent) {
+                                           int bit0, float u, float& logp, float& ent, float* w) {
     float m = -FLT_MAX;
     bool any = false;
     for (int j = 0; j < K; ++j) {
@@ -92,21 +93,29 @@ __device__ __forceinline__ int sample_head(const float* l, int K, const uint32_t
     float S = 0.0f, dot = 0.0f;
     for (int j = 0; j < K; ++j) {
         const bool ok = !valid_words || ((valid_words[(bit0 + j) >> 5] >> ((bit0 + j) & 31)) & 1u);
+        float wj = 0.0f;
         if (ok) {
             const float d = __fsub_rn(l[j], m);
-            const float w = exp32(d);
-            S = __fadd_rn(S, w);
-            dot = fmaf(w, d, dot);
+            wj = exp32(d);
+            S = __fadd_rn(S, wj);
+            dot = fmaf(wj, d, dot);
         }
+        if (w) w[j] = ok ? wj : -1.0f;          // -1 marks a forbidden action
     }
     const float thr = __fmul_rn(u, S);
     float c = 0.0f;
     int act = -1, last = -1;
     for (int j = 0; j < K; ++j) {
-        const bool ok = !valid_words || ((valid_words[(bit0 + j) >> 5] >> ((bit0 + j) & 31)) & 1u);
-        if (ok) {
+        float wj;
+        if (w) {
+            wj = w[j];
+        } else {                                 // no scratch: the same weights, recomputed
+            const bool ok = !valid_words || ((valid_words[(bit0 + j) >> 5] >> ((bit0 + j) & 31)) & 1u);
+            wj = ok ? exp32(__fsub_rn(l[j], m)) : -1.0f;
+        }
+        if (wj >= 0.0f) {
             last = j;
-            c = __fadd_rn(c, exp32(__fsub_rn(l[j], m)));
+            c = __fadd_rn(c, wj);
             if (act < 0 && c > thr) act = j;
         }
     }
@@ -117,7 +126,7 @@ __device__ __forceinline__ int sample_head(const float* l, int K, const uint32_t
     return act;
 }
 
-__device__ __forceinline__ void sample_row(const PolicyArgs& a, int row, const float* l, float value) {
+__device__ __forceinline__ void sample_row(const PolicyArgs& a, int row, const float* l, float value, float* w) {
     a.value[row] = value;
     if (a.logits)
         for (int j = 0; j < a.O; ++j) a.logits[(size_t)row * a.O + j] = l[j];
@@ -137,7 +146,7 @@ __device__ __forceinline__ void sample_row(const PolicyArgs& a, int row, const f
     const uint32_t* mw = a.W ? a.mask + (size_t)row * a.W : nullptr;
     bool none = false;
     for (int h = 0; h < a.n_heads; ++h) {
-        int act = sample_head(l + h * a.head, a.head, mw, h * a.head, us[h < EJ_MAX_NB ? h : 0], logp, ent);
+        int act = sample_head(l + h * a.head, a.head, mw, h * a.head, us[h < EJ_MAX_NB ? h : 0], logp, ent, w);
         if (act < 0) { act = 0; none = true; }
         a.act[(size_t)row * a.n_heads + h] = act;
     }

@@ -27,13 +27,13 @@ namespace ej {
 namespace {
 
 constexpr int BM = 128;     // rows per tile = TMEM lanes
-constexpr int BT = 128;     // threads per CTA
+constexpr int BT = 256;     // threads per CTA: two warpgroups share the 128 TMEM lanes
 constexpr int KX = 64;      // observation width padded to one 64-element panel
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t COL_D3 = 256, COL_D4 = 384;
 
 struct BfLayout {
-    uint32_t w1, w2a, w2c, w3, v3, x, h, total;
+    uint32_t w1, w2a, w2c, w3, v3, x, h, bias, vals, total;
     int N3;
 };
 
@@ -47,7 +47,9 @@ __host__ __device__ inline BfLayout bf_layout(int H, int O) {
     L.w3 = b;  b += (uint32_t)L.N3 * H * 2;    // [N3][H]
     L.v3 = b;  b += 16u * H * 2;               // [16][H]
     L.x = b;   b += BM * KX * 2;               // [BM][KX]
-    L.h = b;   b += BM * 2u * H * 2;           // [BM][2H]
+    L.h = b;   b += BM * 2u * H * 2;           // [BM][2H]; later logits + sampler scratch
+    L.bias = b; b += ((4u * H + (uint32_t)O + 4) * 4 + 1023) & ~1023u;   // b1|c1, b2|c2, b3, c3
+    L.vals = b; b += BM * 4;
     L.total = b;
     return L;
 }
@@ -79,17 +81,19 @@ __device__ void pack_operand(uint8_t* dst, int rows, int K, F get) {
 
 // 32 accumulator columns of this thread's row -> bias, ReLU, BF16 -> operand
 // columns [k0, k0 + 32) of row `row` in the swizzled [BM][K] operand.
-__device__ __forceinline__ void epilogue32(uint32_t taddr, const float* __restrict__ bias, uint8_t* dst,
-                                           int row, int k0) {
+__device__ __forceinline__ void epilogue32(uint32_t taddr, const float* bias, uint8_t* dst, int row, int k0) {
     float v[32];
     tmem_ld32(taddr, v);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        float y[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) y[j] = fmaxf(v[q * 8 + j] + __ldg(bias + q * 8 + j), 0.0f);
-        st_shared_v4(dst + sw128_offset(row, k0 + q * 8, BM), pack2(y[0], y[1]), pack2(y[2], y[3]),
-                     pack2(y[4], y[5]), pack2(y[6], y[7]));
+        const float4 b0 = *reinterpret_cast<const float4*>(bias + q * 8);
+        const float4 b1 = *reinterpret_cast<const float4*>(bias + q * 8 + 4);
+        const float y0 = fmaxf(v[q * 8 + 0] + b0.x, 0.0f), y1 = fmaxf(v[q * 8 + 1] + b0.y, 0.0f);
+        const float y2 = fmaxf(v[q * 8 + 2] + b0.z, 0.0f), y3 = fmaxf(v[q * 8 + 3] + b0.w, 0.0f);
+        const float y4 = fmaxf(v[q * 8 + 4] + b1.x, 0.0f), y5 = fmaxf(v[q * 8 + 5] + b1.y, 0.0f);
+        const float y6 = fmaxf(v[q * 8 + 6] + b1.z, 0.0f), y7 = fmaxf(v[q * 8 + 7] + b1.w, 0.0f);
+        st_shared_v4(dst + sw128_offset(row, k0 + q * 8, BM), pack2(y0, y1), pack2(y2, y3), pack2(y4, y5),
+                     pack2(y6, y7));
     }
 }
 
@@ -112,12 +116,23 @@ __device__ __forceinline__ void mma_chain(uint32_t d, uint32_t a_base, int a_row
     }
 }
 
+// Waits for the tensor core and agrees across the CTA on success.
+__device__ __forceinline__ bool wait_mma(uint64_t* bar, uint32_t& phase) {
+    const bool ok = mbar_wait(bar, phase);
+    phase ^= 1;
+    const bool all = __syncthreads_and(ok);
+    tc_fence_after();
+    return all;
+}
+
 __global__ void __launch_bounds__(BT, 1) policy_bf16_kernel(PolicyArgs a) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bar;
     __shared__ uint32_t tmem_slot;
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row_in_tile = quarter * 32 + lane;     // TMEM lane of this thread
     const int H = a.H, O = a.O, I = a.in_dim;
     const BfLayout L = bf_layout(H, O);
     const NetOffsets off = net_offsets(I, H, O);
@@ -135,6 +150,19 @@ __global__ void __launch_bounds__(BT, 1) policy_bf16_kernel(PolicyArgs a) {
         return n < O ? __ldg(w + off.W3 + (size_t)k * O + n) : 0.0f;
     });
     pack_operand(smem + L.v3, 16, H, [&](int n, int k) { return n == 0 ? __ldg(w + off.V3 + k) : 0.0f; });
+    float* bias = (float*)(smem + L.bias);           // [b1 | c1 | b2 | c2 | b3 | c3]
+    for (int k = tid; k < 4 * H + O + 1; k += BT) {
+        float v;
+        if (k < H) v = w[off.b1 + k];
+        else if (k < 2 * H) v = w[off.c1 + k - H];
+        else if (k < 3 * H) v = w[off.b2 + k - 2 * H];
+        else if (k < 4 * H) v = w[off.c2 + k - 3 * H];
+        else if (k < 4 * H + O) v = w[off.b3 + k - 4 * H];
+        else v = w[off.c3];
+        bias[k] = v;
+    }
+    // padding columns of the observation operand stay zero for every tile
+    for (int k = tid; k < BM * KX * 2 / 16; k += BT) st_shared_v4(smem + L.x + k * 16, 0u, 0u, 0u, 0u);
     if (tid == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
@@ -142,28 +170,28 @@ __global__ void __launch_bounds__(BT, 1) policy_bf16_kernel(PolicyArgs a) {
     if (warp == 0) tmem_alloc(&tmem_slot, TMEM_COLS);
     sync_for_mma();
     const uint32_t tmem = tmem_slot;
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
     const uint32_t sx = smem_u32(smem + L.x), sh = smem_u32(smem + L.h);
     const uint32_t sw1 = smem_u32(smem + L.w1), sw2a = smem_u32(smem + L.w2a), sw2c = smem_u32(smem + L.w2c);
     const uint32_t sw3 = smem_u32(smem + L.w3), sv3 = smem_u32(smem + L.v3);
-    float* stage = (float*)(smem + L.h);       // logits staging reuses the activation operand
+    float* stage = (float*)(smem + L.h);             // logits [BM][ldo], then sampler scratch [BM][ldo]
+    float* wscr = (2 * ldo <= H) ? stage + BM * ldo : nullptr;   // scratch only if both fit the region
+    float* vals = (float*)(smem + L.vals);
     uint32_t phase = 0;
     bool ok = true;
     const int n_tiles = (a.rows + BM - 1) / BM;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int row = tile * BM + tid;
-        const bool valid = row < a.rows;
-        // observations -> BF16 operand [BM][KX]
-#pragma unroll
-        for (int c = 0; c < KX / 8; ++c) {
-            float y[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int k = c * 8 + q;
-                y[q] = (valid && k < I) ? a.x[(size_t)row * I + k] : 0.0f;
+        const int row0 = tile * BM;
+        const int nrows = min(BM, a.rows - row0);
+        // observations -> BF16 operand [BM][KX], coalesced over the tile's contiguous rows
+        {
+            const float* src = a.x + (size_t)row0 * I;
+            const int n = nrows * I;
+            for (int idx = tid; idx < n; idx += BT) {
+                const int r = idx / I, k = idx - r * I;
+                const __nv_bfloat16 v = __float2bfloat16_rn(__ldg(src + idx));
+                *reinterpret_cast<__nv_bfloat16*>(smem + L.x + sw128_offset(r, k, BM)) = v;
             }
-            st_shared_v4(smem + L.x + sw128_offset(tid, c * 8, BM), pack2(y[0], y[1]), pack2(y[2], y[3]),
-                         pack2(y[4], y[5]), pack2(y[6], y[7]));
         }
         sync_for_mma();
         // layer 1 of actor and critic: D[:, 0:2H] = X W1cat
@@ -171,13 +199,10 @@ __global__ void __launch_bounds__(BT, 1) policy_bf16_kernel(PolicyArgs a) {
             mma_chain(tmem, sx, BM, sw1, 2 * H, KX, idesc_bf16(BM, 2 * H));
             mma_commit(&bar);
         }
-        ok = mbar_wait(&bar, phase);
-        phase ^= 1;
-        if (!__syncthreads_and(ok)) break;
-        tc_fence_after();
-        for (int c = 0; c < 2 * H / 32; ++c) {
-            const int col = c * 32;
-            epilogue32(lane_base + col, col < H ? w + off.b1 + col : w + off.c1 + (col - H), smem + L.h, tid, col);
+        if (!(ok = wait_mma(&bar, phase))) break;
+        for (int c = 0; c < H / 32; ++c) {           // this warpgroup: actor (half 0) or critic (half 1)
+            const int col = half * H + c * 32;
+            epilogue32(lane_base + col, bias + col, smem + L.h, row_in_tile, col);
         }
         sync_for_mma();
         // layer 2: D[:, 0:H] = H1a W2, D[:, H:2H] = H1c V2
@@ -186,13 +211,10 @@ __global__ void __launch_bounds__(BT, 1) policy_bf16_kernel(PolicyArgs a) {
             mma_chain(tmem + H, sh + (H / 64) * (BM / 8) * 1024, BM, sw2c, H, H, idesc_bf16(BM, H));
             mma_commit(&bar);
         }
-        ok = mbar_wait(&bar, phase);
-        phase ^= 1;
-        if (!__syncthreads_and(ok)) break;
-        tc_fence_after();
-        for (int c = 0; c < 2 * H / 32; ++c) {
-            const int col = c * 32;
-            epilogue32(lane_base + col, col < H ? w + off.b2 + col : w + off.c2 + (col - H), smem + L.h, tid, col);
+        if (!(ok = wait_mma(&bar, phase))) break;
+        for (int c = 0; c < H / 32; ++c) {
+            const int col = half * H + c * 32;
+            epilogue32(lane_base + col, bias + 2 * H + col, smem + L.h, row_in_tile, col);
         }
         sync_for_mma();
         // heads: logits = H2a W3 (N3 columns), value = H2c V3 (column 0 of 16)
@@ -201,27 +223,29 @@ __global__ void __launch_bounds__(BT, 1) policy_bf16_kernel(PolicyArgs a) {
             mma_chain(tmem + COL_D4, sh + (H / 64) * (BM / 8) * 1024, BM, sv3, 16, H, idesc_bf16(BM, 16));
             mma_commit(&bar);
         }
-        ok = mbar_wait(&bar, phase);
-        phase ^= 1;
-        if (!__syncthreads_and(ok)) break;
-        tc_fence_after();
-        float* lrow = stage + tid * ldo;
-        for (int c = 0; c < L.N3 / 32 + ((L.N3 % 32) ? 1 : 0); ++c) {
-            float v[32];
-            tmem_ld32(lane_base + COL_D3 + c * 32, v);
+        if (!(ok = wait_mma(&bar, phase))) break;
+        float* lrow = stage + row_in_tile * ldo;
+        if (half == 0) {
+            for (int c = 0; c * 32 < L.N3; ++c) {
+                float v[32];
+                tmem_ld32(lane_base + COL_D3 + c * 32, v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int col = c * 32 + j;
-                if (col < O) lrow[col] = v[j] + __ldg(w + off.b3 + col);
+                for (int j = 0; j < 32; ++j) {
+                    const int col = c * 32 + j;
+                    if (col < O) lrow[col] = v[j] + bias[4 * H + col];
+                }
             }
+        } else {
+            float vv[32];
+            tmem_ld32(lane_base + COL_D4, vv);
+            vals[row_in_tile] = vv[0] + bias[4 * H + O];
         }
-        float vv[32];
-        tmem_ld32(lane_base + COL_D4, vv);
-        const float value = vv[0] + __ldg(w + off.c3);
-        if (valid) sample_row(a, row, lrow, value);
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
+        if (half == 0 && row_in_tile < nrows)
+            sample_row(a, row0 + row_in_tile, lrow, vals[row_in_tile], wscr ? wscr + row_in_tile * ldo : nullptr);
+        __syncthreads();
     }
     if (!ok) {
         // a wait gave up: give the tensor core one more bounded chance to finish before freeing TMEM
@@ -241,7 +265,7 @@ ej_status launch_policy_bf16(const PolicyArgs& a, cudaStream_t stream) {
     if (a.H != 64 && a.H != 128) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: hidden must be 64 or 128");
     if (a.in_dim > KX) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: input width must be <= %d", KX);
     if (a.O > 128) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: at most 128 logits");
-    if (a.O + 1 > 2 * a.H) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: logits do not fit the staging area");
+    if ((a.O | 1) > a.H) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: logits do not fit the staging area");
     const size_t smem = policy_bf16_smem(a.H, a.O);
     if (smem > 227 * 1024) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: %zu bytes of shared memory", smem);
     static size_t configured = 0;

@@ -13,8 +13,12 @@ from .policy import Policy, Rollout
 class PPO:
     """Adam state, workspace and the update calls for a Policy and its rollouts."""
 
-    def __init__(self, policy: Policy, T: int, **overrides):
+    def __init__(self, policy: Policy, T: int, precision: str = "fp32", **overrides):
+        """precision of the update's GEMMs (independent of the policy's
+        forward precision used by rollouts)."""
+        from .policy import PRECISION
         self.policy, self.env, self.T = policy, policy.env, T
+        self.precision = PRECISION[precision]
         self.pp = N.EjPpoParams()
         N.check(N.load().ej_ppo_params_default(C.byref(self.pp)), "ej_ppo_params_default")
         for k, v in overrides.items():
@@ -53,7 +57,7 @@ class PPO:
         grad = torch.empty_like(w)
         stats = torch.empty(8, dtype=torch.float64, device=w.device)
         N.check(N.load().ppo_minibatch_grad(C.byref(self.env.p), C.byref(self.pp), self.T, pol.hidden,
-                                            pol.precision, net, _ptr(w), C.byref(rollout._c),
+                                            self.precision, net, _ptr(w), C.byref(rollout._c),
                                             _ptr(self.workspace), shuffle_ctr, minibatch, _ptr(grad),
                                             _ptr(stats), _stream(stream)), "ppo_minibatch_grad")
         return grad, stats
@@ -61,7 +65,7 @@ class PPO:
     def update(self, rollout: Rollout, stream=None):
         pol = self.policy
         stats = torch.empty((2, 8), dtype=torch.float32, device=pol.pop_w.device)
-        N.check(N.load().ppo_update(C.byref(self.env.p), C.byref(self.pp), self.T, pol.hidden, pol.precision,
+        N.check(N.load().ppo_update(C.byref(self.env.p), C.byref(self.pp), self.T, pol.hidden, self.precision,
                                     _ptr(pol.pop_w), _ptr(pol.gov_w), _ptr(self.m[0]), _ptr(self.v[0]),
                                     _ptr(self.m[1]), _ptr(self.v[1]), self.adam_steps, self.updates,
                                     C.byref(rollout._c), _ptr(self.workspace), _ptr(stats), _stream(stream)),

@@ -1,0 +1,89 @@
+"""Uneven populations and action-space sizes in one captured rollout."""
+import numpy as np
+import pytest
+
+import synth
+from oracle.env import OracleEnv, default_params
+from tests.parity import compare_env
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+H = 128
+POPS = [10, 50, 37, 100, 5, 70, 10]
+LEVELS = [5, 10, 20, 5, 10, 20, 20]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_22165_gb300 import build
+    build.build()
+
+
+def _weights(seed):
+    import paper_2410_22165_gb300 as P
+    w = {}
+    for L in sorted(set(LEVELS)):
+        env = P.VecEnv(1, 10, **P.price_grid(L))
+        w[("pop", L)] = torch.from_numpy(synth.net_weights(seed + L, 0, env.D, H, env.nA))
+        w[("gov",)] = torch.from_numpy(synth.net_weights(seed, 1, env.G, H, env.p.nb * env.p.tax_levels))
+    return w
+
+
+@pytest.mark.parametrize("granularity", ["exact", "by_actions"])
+def test_batched_rollout_matches_oracle(granularity):
+    import paper_2410_22165_gb300 as P
+    T = 14
+    kw = dict(T_ep=10, T_tax=4)
+    br = P.BatchedRollout(POPS, LEVELS, T, _weights(3), hidden=H, precision="bf16", granularity=granularity, **kw)
+    br.reset(seed=5)
+    br.run()
+    torch.cuda.synchronize()
+    seen = set()
+    for k, c in enumerate(br.classes):
+        b = {n: v.cpu().numpy() for n, v in c["ro"].buf.items()}
+        env = c["env"]
+        p = default_params(**kw, **P.price_grid(c["P"]))
+        for j, e in enumerate(c["idx"]):
+            A_e = POPS[e]
+            seen.add(e)
+            o = OracleEnv(p, A_e)
+            inp = synth.episode_inputs(5 + 7919 * k, [j], A_e, p["R"], p["nb"], o.nA, p["tax_levels"], T, p["T_ep"])
+            o.reset(inp["sg0"][0], inp["sc0"][0])
+            ref = o.run(b["act"][:, j, :A_e], b["gact"][:, j], inp["gather_u"][:, 0], inp["tb"][:, 0],
+                        inp["later_sg"][:, 0], inp["later_sc"][:, 0])
+            g = dict(rew=b["rew"][:, j], grew=b["grew"][:, j], done=b["done"][:, j], obs=b["obs"][1:, j],
+                     gobs=b["gobs"][1:, j], mask=b["mask"][1:, j])
+            compare_env(g, ref, env.params, A_e)
+            # inactive agents of a shared-size class take no action
+            assert not b["act"][:, j, A_e:].any()
+    assert seen == set(range(len(POPS)))
+
+
+def test_captured_graph_equals_eager():
+    import paper_2410_22165_gb300 as P
+    T = 6
+    kw = dict(T_ep=20, T_tax=5)
+    w = _weights(4)
+    a = P.BatchedRollout(POPS, LEVELS, T, w, granularity="coarse", **kw)
+    b = P.BatchedRollout(POPS, LEVELS, T, w, granularity="coarse", **kw)
+    a.reset(seed=8)
+    b.reset(seed=8)
+    for _ in range(3):
+        a.run()                 # eager
+    b.capture()                 # one eager run inside, then the graph
+    b.run()
+    b.run()
+    torch.cuda.synchronize()
+    for ca, cb in zip(a.classes, b.classes):
+        for n in ("obs", "act", "rew", "value", "logp", "done"):
+            assert torch.equal(ca["ro"].buf[n], cb["ro"].buf[n]), n
+        assert torch.equal(ca["env"].state, cb["env"].state)
+
+
+def test_autotune_returns_a_candidate():
+    import paper_2410_22165_gb300 as P
+    best, rates = P.autotune(POPS, LEVELS, _weights(5), T_probe=4, repeats=1, T_ep=20, T_tax=5)
+    assert best in rates and all(r > 0 for r in rates.values())
