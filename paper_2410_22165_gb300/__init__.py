@@ -7,5 +7,5 @@ built by ``paper_2410_22165_gb300.build``).
 from ._native import EjError, load  # noqa: F401
 from .env import VecEnv  # noqa: F401
 from .policy import Policy, Rollout  # noqa: F401
-from .ppo import PPO  # noqa: F401
+from .ppo import PPO, PPOLoss  # noqa: F401
 from .batch import BatchedRollout, autotune, plan_classes, price_grid  # noqa: F401

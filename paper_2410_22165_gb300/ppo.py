@@ -51,9 +51,19 @@ class PPO:
         return dict(adv=view(o[0], T * E * A).view(T, E, A), ret=view(o[1], T * E * A).view(T, E, A),
                     gadv=view(o[2], T * E).view(T, E), gret=view(o[3], T * E).view(T, E))
 
-    def minibatch_grad(self, rollout: Rollout, net: int, shuffle_ctr: int, minibatch: int, stream=None):
+    def minibatch_rows(self, net: int, minibatch: int) -> int:
+        """Rows of minibatch `minibatch` (floor((m+1)N/M) - floor(mN/M))."""
+        n = self.T * (self.env.E * self.env.A if net == N.NET_POP else self.env.E)
+        M = self.pp.minibatches
+        return (minibatch + 1) * n // M - minibatch * n // M
+
+    def minibatch_grad(self, rollout: Rollout, net: int, shuffle_ctr: int, minibatch: int, stream=None,
+                       weights: torch.Tensor | None = None):
+        """Gradient of one minibatch's loss (and the loss sums, float64[8]);
+        `weights` defaults to the policy's current vector of `net`."""
         pol = self.policy
-        w = pol.pop_w if net == N.NET_POP else pol.gov_w
+        w = weights if weights is not None else (pol.pop_w if net == N.NET_POP else pol.gov_w)
+        w = w.contiguous()
         grad = torch.empty_like(w)
         stats = torch.empty(8, dtype=torch.float64, device=w.device)
         N.check(N.load().ppo_minibatch_grad(C.byref(self.env.p), C.byref(self.pp), self.T, pol.hidden,
@@ -61,6 +71,11 @@ class PPO:
                                             _ptr(self.workspace), shuffle_ctr, minibatch, _ptr(grad),
                                             _ptr(stats), _stream(stream)), "ppo_minibatch_grad")
         return grad, stats
+
+    def loss(self, weights: torch.Tensor, rollout: Rollout, net: int, shuffle_ctr: int, minibatch: int):
+        """Differentiable minibatch loss: forward and backward are the library's
+        hand-written kernels (see PPOLoss)."""
+        return PPOLoss.apply(weights, self, rollout, net, shuffle_ctr, minibatch)
 
     def update(self, rollout: Rollout, stream=None):
         pol = self.policy
@@ -73,3 +88,29 @@ class PPO:
         self.adam_steps += self.pp.epochs * self.pp.minibatches
         self.updates += 1
         return stats
+
+
+class PPOLoss(torch.autograd.Function):
+    """Clipped PPO loss of one minibatch (Section 4) as a torch autograd node.
+
+    forward: one ppo_minibatch_grad call, which runs actor and critic forward,
+    the loss and the hand-written backward in the library's kernels; the loss
+    is (sum policy loss + vf_coef sum value loss - ent_coef sum entropy) / n
+    over the n minibatch rows, from the call's float64 sums.  backward: the
+    saved gradient scaled by the incoming gradient.  The advantages come from
+    the last PPO.advantages call, as for ppo_minibatch_grad.
+    """
+
+    @staticmethod
+    def forward(ctx, weights, ppo, rollout, net, shuffle_ctr, minibatch):
+        grad, stats = ppo.minibatch_grad(rollout, net, shuffle_ctr, minibatch, weights=weights.detach())
+        n = ppo.minibatch_rows(net, minibatch)
+        pp = ppo.pp
+        loss = (stats[2] + pp.vf_coef * stats[3] - pp.ent_coef * stats[4]) / n
+        ctx.save_for_backward(grad)
+        return loss.to(weights.dtype)
+
+    @staticmethod
+    def backward(ctx, g):
+        (grad,) = ctx.saved_tensors
+        return g * grad, None, None, None, None, None
