@@ -11,6 +11,8 @@ GAE lambda 0.95); the benchmark configuration sets gamma 0.99.
   entropy bonus of a minibatch, and their gradient with respect to every
   parameter of the actor and critic, by hand-written backpropagation in
   float64 (ReLU networks of ``policy.mlp64``).
+  With ``operand=bf16_round`` every product operand is first rounded to
+  bfloat16 (the BF16 tensor-core form of the update, FP32/FP64 sums).
 * ``adam64``: one Adam step (Kingma and Ba, 2015).
 """
 from __future__ import annotations
@@ -51,12 +53,27 @@ def _heads_softmax(logits, valid, heads, head):
     return p, logp, ent
 
 
+def bf16_round(a):
+    """Nearest bfloat16 value (ties to even) of each entry, via float32: the
+    rounding a BF16 GEMM operand goes through (8-bit significand)."""
+    f = np.ascontiguousarray(np.asarray(a, np.float64).astype(np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
 def ppo_loss_grad64(w, x, act, valid, logp_old, v_old, adv, ret, *, clip, vf_coef, vclip,
-                    ent_coef, heads=1, head=None, normalize_adv=True):
+                    ent_coef, heads=1, head=None, normalize_adv=True, operand=None):
     """Loss (float) and gradients (dict like w) of one minibatch.
 
     x [N, in], act [N, heads] int, valid [N, heads*head] bool, logp_old [N],
-    v_old [N], adv [N] (raw GAE), ret [N]."""
+    v_old [N], adv [N] (raw GAE), ret [N].
+
+    operand: applied to every matrix-product operand (weights, inputs,
+    activations, backward signals) before the product; None = exact.  With
+    bf16_round this is the BF16-operand form: operands rounded to bfloat16,
+    products and sums in float64."""
+    R = operand if operand is not None else (lambda t: t)
     x = np.asarray(x, np.float64)
     N = x.shape[0]
     act = np.asarray(act).reshape(N, heads)
@@ -66,12 +83,15 @@ def ppo_loss_grad64(w, x, act, valid, logp_old, v_old, adv, ret, *, clip, vf_coe
     if normalize_adv:
         a = (a - a.mean()) / (a.std() + 1e-8)
     # forward
-    z1 = x @ w["W1"] + w["b1"]; h1 = np.maximum(z1, 0)
-    z2 = h1 @ w["W2"] + w["b2"]; h2 = np.maximum(z2, 0)
-    logits = h2 @ w["W3"] + w["b3"]
-    y1 = x @ w["V1"] + w["c1"]; g1 = np.maximum(y1, 0)
-    y2 = g1 @ w["V2"] + w["c2"]; g2 = np.maximum(y2, 0)
-    v = (g2 @ w["V3"] + w["c3"])[:, 0]
+    x = R(x)
+    W1, W2, W3 = R(w["W1"]), R(w["W2"]), R(w["W3"])
+    V1, V2, V3 = R(w["V1"]), R(w["V2"]), R(w["V3"])
+    z1 = x @ W1 + w["b1"]; h1 = R(np.maximum(z1, 0))
+    z2 = h1 @ W2 + w["b2"]; h2 = R(np.maximum(z2, 0))
+    logits = h2 @ W3 + w["b3"]
+    y1 = x @ V1 + w["c1"]; g1 = R(np.maximum(y1, 0))
+    y2 = g1 @ V2 + w["c2"]; g2 = R(np.maximum(y2, 0))
+    v = (g2 @ V3 + w["c3"])[:, 0]
     p, logp_all, ent = _heads_softmax(logits, valid, heads, head)
     logp = sum(logp_all[np.arange(N), h * head + act[:, h]] for h in range(heads))
     ratio = np.exp(logp - logp_old)
@@ -96,16 +116,17 @@ def ppo_loss_grad64(w, x, act, valid, logp_old, v_old, adv, ret, *, clip, vf_coe
     dlog = np.where(valid, dlog, 0.0)
     dv = np.where(la >= lb, v - ret, (vc - ret) * (np.abs(v - v_old) < vclip)) * (vf_coef / N)
     g = {}
+    dlog = R(dlog)
     g["W3"] = h2.T @ dlog; g["b3"] = dlog.sum(0)
-    dz2 = (dlog @ w["W3"].T) * (z2 > 0)
+    dz2 = R((dlog @ W3.T) * (z2 > 0))
     g["W2"] = h1.T @ dz2; g["b2"] = dz2.sum(0)
-    dz1 = (dz2 @ w["W2"].T) * (z1 > 0)
+    dz1 = R((dz2 @ W2.T) * (z1 > 0))
     g["W1"] = x.T @ dz1; g["b1"] = dz1.sum(0)
     dvv = dv[:, None]
-    g["V3"] = g2.T @ dvv; g["c3"] = dvv.sum(0)
-    dy2 = (dvv @ w["V3"].T) * (y2 > 0)
+    g["V3"] = g2.T @ R(dvv); g["c3"] = R(dvv).sum(0)
+    dy2 = R((dvv @ w["V3"].T) * (y2 > 0))      # a rank-1 product, formed before rounding
     g["V2"] = g1.T @ dy2; g["c2"] = dy2.sum(0)
-    dy1 = (dy2 @ w["V2"].T) * (y1 > 0)
+    dy1 = R((dy2 @ V2.T) * (y1 > 0))
     g["V1"] = x.T @ dy1; g["c1"] = dy1.sum(0)
     stats = dict(loss=loss, pg=-surr.mean(), vf=lv.mean(), ent=ent.mean(),
                  clipfrac=float(np.mean(np.abs(ratio - 1) > clip)))

@@ -15,6 +15,7 @@
 
 #include "ej_internal.cuh"
 #include "ej_policy.cuh"
+#include "ej_ppo.cuh"
 
 namespace ej {
 __device__ int g_ej_fault = 0;   // fault word of the bounded waits in this library
@@ -290,6 +291,7 @@ extern "C" ej_status ej_device_status(int32_t* fault, int32_t clear) {
     int v = 0;
     cudaError_t err = cudaMemcpyFromSymbol(&v, ej::g_ej_fault, sizeof(int));
     if (err != cudaSuccess) return ej::fail(EJ_ERR_CUDA, "ej_device_status: %s", cudaGetErrorString(err));
+    v |= ej::ppo_bf16_fault(clear);
     if (fault) *fault = v;
     if (clear) {
         const int z = 0;

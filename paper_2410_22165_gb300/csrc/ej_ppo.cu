@@ -35,28 +35,6 @@ __global__ void gae_kernel(const float* __restrict__ rew, const float* __restric
     }
 }
 
-// ------------------------------------------------ minibatch shuffle
-// Feistel permutation of [0, 4^half) restricted to [0, N) by cycle walking
-// (Luby-Rackoff; Black-Rogaway), round function = Philox word x0.
-__device__ __forceinline__ uint32_t feistel(uint32_t x, int half, uint32_t k0, uint32_t k1, uint32_t ctr) {
-    const uint32_t mask = (1u << half) - 1u;
-    uint32_t L = (x >> half) & mask, R = x & mask;
-#pragma unroll
-    for (uint32_t rnd = 0; rnd < 4; ++rnd) {
-        const uint32_t F = philox4x32_10(make_uint4(R, rnd, ctr, 4u), k0, k1).x & mask;
-        const uint32_t nL = R;
-        R = (L ^ F) & mask;
-        L = nL;
-    }
-    return (L << half) | R;
-}
-
-__device__ __forceinline__ uint32_t mb_row(const MbDesc& d, int j) {
-    uint32_t x = feistel((uint32_t)(d.lo + j), d.half, d.k0, d.k1, d.ctr);
-    while (x >= d.N) x = feistel(x, d.half, d.k0, d.k1, d.ctr);
-    return x;
-}
-
 // ------------------------------------- minibatch advantage statistics
 __global__ void adv_stats_kernel(MbDesc d, const float* __restrict__ adv, double* stats) {
     double s = 0.0, q = 0.0;
@@ -369,6 +347,15 @@ ej_status launch_gae(const float* rew, const float* value, const uint8_t* done, 
     if (grid > 152 * 8) grid = 152 * 8;
     gae_kernel<<<grid, 256, 0, s>>>(rew, value, done, T, rows, per_env, gamma, lam, adv, ret);
     return cudaGetLastError() == cudaSuccess ? EJ_OK : fail(EJ_ERR_CUDA, "gae launch failed");
+}
+
+ej_status launch_adv_stats(const MbDesc& mb, const float* adv, double* stats, cudaStream_t s) {
+    zero_kernel<<<1, 32, 0, s>>>(stats, ST_COUNT_);
+    int grid = (mb.count + 255) / 256;
+    if (grid > 152 * 4) grid = 152 * 4;
+    if (grid < 1) grid = 1;
+    adv_stats_kernel<<<grid, 256, 0, s>>>(mb, adv, stats);
+    return cudaGetLastError() == cudaSuccess ? EJ_OK : fail(EJ_ERR_CUDA, "advantage statistics launch failed");
 }
 
 ej_status launch_minibatch_grad(const FbArgs& fa, const WgJobs& jobs, int n_jobs, float* partial,

@@ -17,6 +17,27 @@ struct MbDesc {
     uint32_t k0, k1, ctr;
 };
 
+// Feistel permutation of [0, 4^half) restricted to [0, N) by cycle walking
+// (Luby-Rackoff; Black-Rogaway), round function = Philox word x0.
+__device__ __forceinline__ uint32_t feistel(uint32_t x, int half, uint32_t k0, uint32_t k1, uint32_t ctr) {
+    const uint32_t mask = (1u << half) - 1u;
+    uint32_t L = (x >> half) & mask, R = x & mask;
+#pragma unroll
+    for (uint32_t rnd = 0; rnd < 4; ++rnd) {
+        const uint32_t F = philox4x32_10(make_uint4(R, rnd, ctr, 4u), k0, k1).x & mask;
+        const uint32_t nL = R;
+        R = (L ^ F) & mask;
+        L = nL;
+    }
+    return (L << half) | R;
+}
+
+__device__ __forceinline__ uint32_t mb_row(const MbDesc& d, int j) {
+    uint32_t x = feistel((uint32_t)(d.lo + j), d.half, d.k0, d.k1, d.ctr);
+    while (x >= d.N) x = feistel(x, d.half, d.k0, d.k1, d.ctr);
+    return x;
+}
+
 struct FbArgs {
     MbDesc mb;
     int in_dim, in_pad, H, O, n_heads, head, W;
@@ -64,6 +85,12 @@ ej_status launch_gae(const float* rew, const float* value, const uint8_t* done, 
 ej_status launch_minibatch_grad(const FbArgs& fa, const WgJobs& jobs, int n_jobs, float* partial,
                                 int chunks, const float* w2, const float* w3, const float* v2,
                                 float* grad, cudaStream_t s);
+// BF16 tensor-core minibatch gradient (ej_ppo_bf16.cu): advantage statistics,
+// the fused kernel and the reduction into grad; partial: scratch of
+// partial_bytes for the per-CTA accumulators.
+ej_status launch_ppo_bf16(const FbArgs& fa, float* partial, size_t partial_bytes, float* grad, cudaStream_t s);
+int ppo_bf16_fault(int clear);
+ej_status launch_adv_stats(const MbDesc& mb, const float* adv, double* stats, cudaStream_t s);
 ej_status launch_adam(float* p, const float* g, float* m, float* v, size_t n, float lr, float b1, float b2,
                       float eps, int step, cudaStream_t s);
 

@@ -88,7 +88,7 @@ ej_status check_common(const EjParams* p, const EjPpoParams* pp, int T, int H, L
     return EJ_OK;
 }
 
-ej_status minibatch_grad(const KParams& kp, const EjPpoParams* pp, int T, int H, int net,
+ej_status minibatch_grad(const KParams& kp, const EjPpoParams* pp, int T, int H, int precision, int net,
                          const float* weights, const EjRollout* b, char* ws, const Ws& W, uint32_t ctr,
                          int m, float* grad, double* stats, cudaStream_t s) {
     const NetDims d = dims(kp, net);
@@ -116,6 +116,8 @@ ej_status minibatch_grad(const KParams& kp, const EjPpoParams* pp, int T, int H,
     fa.ret = (const float*)(ws + W.ret[net]);
     fa.w3t = (float*)(ws + W.wt3); fa.w2t = (float*)(ws + W.wt2); fa.v2t = (float*)(ws + W.wv2);
     fa.stats = stats;
+    if (precision == EJ_BF16)
+        return launch_ppo_bf16(fa, (float*)(ws + W.partial), 4ull * 6 * WG_CHUNKS * WG_STRIDE, grad, s);
     const uint64_t R = (uint64_t)fa.mb.count;
     float* rb = (float*)(ws + W.rows);
     fa.ws_x = rb; rb += R * d.in;
@@ -226,7 +228,7 @@ ej_status ppo_minibatch_grad(const EjParams* p, const EjPpoParams* pp, int32_t T
     KParams kp;
     ej_status st = check_common(p, pp, T, hidden, &lay, &kp);
     if (st != EJ_OK) return st;
-    if (precision != EJ_FP32) return fail(EJ_ERR_UNSUPPORTED, "PPO gradients: precision %d not available", precision);
+    if (precision != EJ_FP32 && precision != EJ_BF16) return fail(EJ_ERR_ARG, "unknown precision %d", precision);
     if (net != EJ_NET_POP && net != EJ_NET_GOV) return fail(EJ_ERR_ARG, "unknown network %d", net);
     if (!b || !workspace || !weights || !grad) return fail(EJ_ERR_ARG, "NULL argument");
     if ((uintptr_t)workspace % 256 || (uintptr_t)weights % 16) return fail(EJ_ERR_ARG, "misaligned buffer");
@@ -235,7 +237,7 @@ ej_status ppo_minibatch_grad(const EjParams* p, const EjPpoParams* pp, int32_t T
     char* ws = (char*)workspace;
     cudaStream_t s = (cudaStream_t)stream;
     double* stats = (double*)(ws + W.stats[net]);
-    st = minibatch_grad(kp, pp, T, hidden, net, weights, b, ws, W, shuffle_ctr, minibatch, grad, stats, s);
+    st = minibatch_grad(kp, pp, T, hidden, precision, net, weights, b, ws, W, shuffle_ctr, minibatch, grad, stats, s);
     if (st != EJ_OK) return st;
     if (stats_out) {
         if (cudaMemcpyAsync(stats_out, stats, sizeof(double) * ST_COUNT_, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
@@ -259,7 +261,7 @@ ej_status ppo_update(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_
     KParams kp;
     ej_status st = check_common(p, pp, T, hidden, &lay, &kp);
     if (st != EJ_OK) return st;
-    if (precision != EJ_FP32) return fail(EJ_ERR_UNSUPPORTED, "PPO update: precision %d not available", precision);
+    if (precision != EJ_FP32 && precision != EJ_BF16) return fail(EJ_ERR_ARG, "unknown precision %d", precision);
     if (!pop_w || !gov_w || !pop_m || !pop_v || !gov_m || !gov_v || !b || !workspace)
         return fail(EJ_ERR_ARG, "NULL argument");
     if ((uintptr_t)workspace % 256 || (uintptr_t)pop_w % 16 || (uintptr_t)gov_w % 16)
@@ -284,7 +286,7 @@ ej_status ppo_update(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_
                 const size_t n = net_offsets(d.in, hidden, d.O).total;
                 float* grad = (float*)(ws + W.grad[net]);
                 double* stats = (double*)(ws + W.stats[net]);
-                st = minibatch_grad(kp, pp, T, hidden, net, w[net], b, ws, W, ctr ^ (net ? 0x80000000u : 0u),
+                st = minibatch_grad(kp, pp, T, hidden, precision, net, w[net], b, ws, W, ctr ^ (net ? 0x80000000u : 0u),
                                     mb, grad, stats, s);
                 if (st != EJ_OK) return st;
                 accumulate_stats_kernel<<<1, 32, 0, s>>>(stats, totals + net * ST_COUNT_);

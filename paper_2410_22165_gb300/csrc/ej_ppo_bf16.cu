@@ -1,0 +1,663 @@
+// PPO minibatch gradient on the 5th-generation tensor cores: BF16 operands,
+// FP32 accumulation in tensor memory (tcgen05.mma kind::f16, M = 128).
+//
+// The loss of Section 4 separates: the clipped surrogate and the entropy
+// bonus depend only on the actor, the clipped value loss only on the critic
+// (the advantages come from GAE on the rollout's values).  So the grid is
+// split: CTAs [0, n_actor) run the actor, the others the critic, each
+// persistent over 128-row tiles of the minibatch (one CTA per SM).
+//
+// Per tile, everything stays on chip: forward layers (MMA, then an epilogue
+// that adds the bias, applies ReLU, keeps the ReLU mask bits in registers and
+// writes the BF16 activation back to shared memory as the next operand), the
+// loss gradient per row, the backward-data products, and the weight-gradient
+// products.  The weight gradients of all tiles accumulate in tensor memory
+// (they are sums over rows, i.e. MMAs with K = rows): dW = A^T dZ reads the
+// stored activation tiles as MN-major (transposed) operands, so no transposed
+// copy is ever written.  Bias gradients are MMAs against an all-ones operand.
+// At the end each CTA writes its accumulators once; a reduction kernel sums
+// the CTAs into the gradient vector.
+//
+// Operand layouts: every tile buffer is [rows][cols] BF16 in the 128-byte
+// swizzled K-major layout of sw128_offset (panels of 64 columns).  Read with
+// K along the columns it is a K-major operand; read with K along the rows
+// (weight gradients, and weights multiplied transposed in the backward pass)
+// it is an MN-major operand whose leading byte offset is the panel stride and
+// whose stride byte offset is one 8-row atom (1024 bytes).
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+
+#include "ej_internal.cuh"
+#include "ej_policy.cuh"
+#include "ej_ppo.cuh"
+
+namespace ej {
+namespace {
+__device__ int g_ej_fault = 0;   // set when a bounded wait of this file's kernel gives up
+}
+}  // namespace ej
+
+#include "ej_tc.cuh"
+
+namespace ej {
+
+namespace {
+
+constexpr int BM = 128;        // rows per tile = TMEM lanes
+constexpr int BT = 256;        // threads: two warpgroups share the 128 lanes (64 columns each)
+constexpr int HID = 128;       // hidden width of this path
+constexpr int KX = 64;         // input operand width: inputs, then a ones column (bias gradients)
+constexpr int KO = 64;         // logit operand width
+constexpr uint32_t TMEM_COLS = 512;
+constexpr int PC = 352;        // accumulator columns written per TMEM lane
+
+// TMEM columns.  Actor: dW1^T [h][in] 0..63, dW2 [h_in][h_out] 64..191,
+// dW3 [h][o] 192..255, db2 (column 256), db3 [o] 272..335 (every lane).
+// Critic: dV1^T 0..63, dV2 64..191, dV3 (192), dc2 (208), dc3 (224).
+// Both: per-tile products in 384..511.
+constexpr uint32_t C_W1T = 0, C_W2 = 64, C_W3 = 192, C_B2 = 256, C_B3 = 272;
+constexpr uint32_t C_V3 = 192, C_C2 = 208, C_C3 = 224;
+constexpr uint32_t C_SLOT = 384;
+
+// Shared memory (bytes from the 1024-aligned base).
+struct PpoSmem {
+    uint32_t w1, w2, w3, x, h1, h2, dl, dz2, ones, dv, bias, total;
+};
+
+// Actor and critic use the same regions under different names:
+//   w1: W1 / V1 [128][KX]        w2: W2 / V2 [128][128]      w3: W3 [KO][128] / V3 [16][128]
+//   x:  inputs [128][KX]         h1: H1 / G1 [128][128]      h2: H2 / G2, later dZ1 / dY1
+//   dl: dL [128][KO] (actor)     dz2: dZ2 / dY2 [128][128]   dv: dv [16][128] (critic)
+//   ones: all-ones [128][64]     bias: floats
+__host__ __device__ inline PpoSmem ppo_smem() {
+    PpoSmem L;
+    uint32_t b = 0;
+    L.w1 = b;   b += HID * KX * 2;
+    L.w2 = b;   b += HID * HID * 2;
+    L.w3 = b;   b += KO * HID * 2;
+    L.x = b;    b += BM * KX * 2;
+    L.h1 = b;   b += BM * HID * 2;
+    L.h2 = b;   b += BM * HID * 2;
+    L.dl = b;   b += BM * KO * 2;
+    L.dz2 = b;  b += BM * HID * 2;
+    L.ones = b; b += BM * 64 * 2;
+    L.dv = b;   b += 16 * BM * 2;
+    L.bias = b; b += (3 * HID + KO + 2 * BM + 8) * 4;
+    L.total = b;
+    return L;
+}
+
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void st_shared_v4(uint8_t* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(smem_u32(p)), "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
+}
+
+// Shared-memory descriptor of a 128-byte swizzled operand with explicit
+// leading and stride byte offsets.
+__device__ __forceinline__ uint64_t sw128_desc_ls(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// K-major operand: buffer of `rows` rows, K step kk (16 columns).
+__device__ __forceinline__ uint64_t kmaj(uint32_t base, int rows, int kk) {
+    return sw128_desc(base + (kk >> 2) * (rows / 8) * 1024 + (kk & 3) * 32);
+}
+// MN-major operand: buffer of `rows` rows read with K along the rows, K step kk (16 rows).
+__device__ __forceinline__ uint64_t mnmaj(uint32_t base, int rows, int kk) {
+    return sw128_desc_ls(base + kk * 2048, (rows / 8) * 1024, 1024);
+}
+
+constexpr uint32_t TA = 1u << 15, TB = 1u << 16;   // MN-major A / B in the instruction descriptor
+
+template <class FA, class FB>
+__device__ __forceinline__ void chain(uint32_t d, int ksteps, uint32_t idesc, bool acc, FA fa, FB fb) {
+    for (int kk = 0; kk < ksteps; ++kk) mma_bf16(d, fa(kk), fb(kk), idesc, (acc || kk > 0) ? 1u : 0u);
+}
+
+__device__ __forceinline__ void sync_for_mma() {
+    fence_async_shared();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+
+__device__ __forceinline__ bool wait_mma(uint64_t* bar, uint32_t& phase) {
+    const bool ok = mbar_wait(bar, phase);
+    phase ^= 1;
+    const bool all = __syncthreads_and(ok);
+    tc_fence_after();
+    return all;
+}
+
+// Packs rows x K of a K-major operand from a float source get(n, k).
+template <class F>
+__device__ void pack_operand(uint8_t* dst, int rows, int K, F get) {
+    const int items = rows * (K / 8);
+    for (int it = threadIdx.x; it < items; it += BT) {
+        const int n = it % rows, kc = it / rows;
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = get(n, kc * 8 + q);
+        st_shared_v4(dst + sw128_offset(n, kc * 8, rows), pack2(v[0], v[1]), pack2(v[2], v[3]),
+                     pack2(v[4], v[5]), pack2(v[6], v[7]));
+    }
+}
+
+// 32 accumulator columns [col, col+32) of this thread's row: add the bias,
+// ReLU, record the mask bits, write BF16 to columns [col, col+32) of dst.
+__device__ __forceinline__ uint32_t relu_epilogue32(uint32_t taddr, const float* bias, uint8_t* dst, int row,
+                                                    int col) {
+    float v[32];
+    tmem_ld32(taddr, v);
+    uint32_t bits = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float y[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            y[j] = fmaxf(v[q * 8 + j] + bias[q * 8 + j], 0.0f);
+            bits |= (y[j] > 0.0f ? 1u : 0u) << (q * 8 + j);
+        }
+        st_shared_v4(dst + sw128_offset(row, col + q * 8, BM), pack2(y[0], y[1]), pack2(y[2], y[3]),
+                     pack2(y[4], y[5]), pack2(y[6], y[7]));
+    }
+    return bits;
+}
+
+// 32 accumulator columns times the ReLU mask bits -> BF16 columns of dst.
+__device__ __forceinline__ void mask_epilogue32(uint32_t taddr, uint32_t bits, uint8_t* dst, int row, int col) {
+    float v[32];
+    tmem_ld32(taddr, v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float y[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) y[j] = ((bits >> (q * 8 + j)) & 1u) ? v[q * 8 + j] : 0.0f;
+        st_shared_v4(dst + sw128_offset(row, col + q * 8, BM), pack2(y[0], y[1]), pack2(y[2], y[3]),
+                     pack2(y[4], y[5]), pack2(y[6], y[7]));
+    }
+}
+
+struct BfPpoArgs {
+    FbArgs f;
+    float* partial;   // [grid][BM][PC] accumulators of each CTA
+    int n_actor;      // CTAs [0, n_actor) run the actor, the rest the critic
+};
+
+// Up to four per-head values in registers (heads <= EJ_MAX_NB), indexed by a
+// uniform head number without local memory.
+struct Head4 {
+    float v0 = 0.0f, v1 = 0.0f, v2 = 0.0f, v3 = 0.0f;
+    __device__ __forceinline__ void set(int h, float x) {
+        if (h == 0) v0 = x; else if (h == 1) v1 = x; else if (h == 2) v2 = x; else v3 = x;
+    }
+    __device__ __forceinline__ float get(int h) const { return h == 0 ? v0 : h == 1 ? v1 : h == 2 ? v2 : v3; }
+};
+
+struct ActorRow { float pg, ent, clip, kl; };
+
+// Section 4, actor part of one minibatch row: per-head masked log-softmax of
+// the logits l[0, O), the clipped surrogate on the normalised advantage and
+// the entropy bonus; l is overwritten with d loss / d logits (0 beyond O).
+__device__ __forceinline__ ActorRow actor_row(const FbArgs& a, uint32_t row, float (&l)[KO], float mean,
+                                              float inv_std, float inv_n) {
+    uint32_t w0 = 0xFFFFFFFFu, w1 = 0xFFFFFFFFu;
+    if (a.W) {
+        const uint32_t* mw = a.mask + (size_t)row * a.W;
+        w0 = mw[0];
+        w1 = a.W > 1 ? mw[1] : 0u;
+    }
+    Head4 off, ent_h;
+    float logp = 0.0f, ent = 0.0f;
+    for (int h = 0; h < a.n_heads; ++h) {
+        const int lo = h * a.head, hi = lo + a.head;
+        const int act = lo + a.act[(size_t)row * a.n_heads + h];
+        float m = -FLT_MAX;
+#pragma unroll
+        for (int k = 0; k < KO; ++k) {
+            const bool ok = k >= lo && k < hi && (((k < 32 ? w0 : w1) >> (k & 31)) & 1u);
+            if (ok) m = fmaxf(m, l[k]);
+        }
+        float S = 0.0f, la = 0.0f;
+#pragma unroll
+        for (int k = 0; k < KO; ++k) {
+            const bool ok = k >= lo && k < hi && (((k < 32 ? w0 : w1) >> (k & 31)) & 1u);
+            if (ok) S += expf(l[k] - m);
+            if (k == act) la = l[k];
+        }
+        const float logS = logf(S);
+        logp += la - m - logS;
+        float Hh = 0.0f;
+#pragma unroll
+        for (int k = 0; k < KO; ++k) {
+            const bool ok = k >= lo && k < hi && (((k < 32 ? w0 : w1) >> (k & 31)) & 1u);
+            if (ok) {
+                const float lp = l[k] - m - logS;
+                Hh -= expf(lp) * lp;
+            }
+        }
+        ent += Hh;
+        off.set(h, m + logS);
+        ent_h.set(h, Hh);
+    }
+    ActorRow st;
+    const float lpo = a.logp_old[row];
+    const float ratio = expf(logp - lpo);
+    const float an = (a.adv[row] - mean) * inv_std;
+    const float cr = fminf(fmaxf(ratio, 1.0f - a.clip), 1.0f + a.clip);
+    const float s1 = ratio * an, s2 = cr * an;
+    st.pg = -fminf(s1, s2);
+    const bool inside = ratio > 1.0f - a.clip && ratio < 1.0f + a.clip;
+    const float dratio = (s1 <= s2 || inside) ? -an : 0.0f;
+    const float dlogp = dratio * ratio * inv_n;
+    st.clip = fabsf(ratio - 1.0f) > a.clip ? 1.0f : 0.0f;
+    st.kl = lpo - logp;
+    st.ent = ent;
+    const float ec = a.ent_coef * inv_n;
+    // in place: column k of head h only needs its own logit (columns >= O are already 0)
+    for (int h = 0; h < a.n_heads; ++h) {
+        const int lo = h * a.head, hi = lo + a.head;
+        const int act = lo + a.act[(size_t)row * a.n_heads + h];
+        const float o = off.get(h), Hh = ent_h.get(h);
+#pragma unroll
+        for (int k = 0; k < KO; ++k) {
+            if (k >= lo && k < hi) {
+                float g = 0.0f;
+                if (((k < 32 ? w0 : w1) >> (k & 31)) & 1u) {
+                    const float lp = l[k] - o;
+                    const float p = expf(lp);
+                    g = dlogp * ((k == act ? 1.0f : 0.0f) - p) + ec * p * (lp + Hh);
+                }
+                l[k] = g;
+            }
+        }
+    }
+    return st;
+}
+
+__global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ uint32_t src_row[BM];
+    __shared__ float red[5][BT / 32];
+    const FbArgs& a = P.f;
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const PpoSmem L = ppo_smem();
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = quarter * 32 + lane;             // TMEM lane of this thread
+    const bool actor = (int)blockIdx.x < P.n_actor;
+    const int role_cta = actor ? (int)blockIdx.x : (int)blockIdx.x - P.n_actor;
+    const int role_ctas = actor ? P.n_actor : (int)gridDim.x - P.n_actor;
+    const int I = a.in_dim, O = a.O;
+    const NetOffsets off = net_offsets(I, HID, O);
+    const float* w = a.weights;
+    float* bias = (float*)(smem + L.bias);           // [0,128) b1|c1, [128,256) b2|c2, [256,320) b3|c3, [320,448) V3
+    float* dv_s = bias + 448;                        // [BM] critic: d loss / d value per row
+
+    // weights -> BF16 operands (row n of a B operand = output unit n)
+    const size_t oW1 = actor ? off.W1 : off.V1, oW2 = actor ? off.W2 : off.V2;
+    pack_operand(smem + L.w1, HID, KX, [&](int n, int k) { return k < I ? __ldg(w + oW1 + (size_t)k * HID + n) : 0.0f; });
+    pack_operand(smem + L.w2, HID, HID, [&](int n, int k) { return __ldg(w + oW2 + (size_t)k * HID + n); });
+    if (actor)
+        pack_operand(smem + L.w3, KO, HID, [&](int n, int k) { return n < O ? __ldg(w + off.W3 + (size_t)k * O + n) : 0.0f; });
+    else
+        pack_operand(smem + L.w3, 16, HID, [&](int n, int k) { return n == 0 ? __ldg(w + off.V3 + k) : 0.0f; });
+    for (int k = tid; k < 448; k += BT) {
+        float v = 0.0f;
+        if (k < HID) v = w[(actor ? off.b1 : off.c1) + k];
+        else if (k < 2 * HID) v = w[(actor ? off.b2 : off.c2) + k - HID];
+        else if (k < 2 * HID + KO) v = actor ? (k - 2 * HID < O ? w[off.b3 + k - 2 * HID] : 0.0f) : (k == 2 * HID ? w[off.c3] : 0.0f);
+        else if (!actor && k >= 320) v = w[off.V3 + k - 320];
+        bias[k] = v;
+    }
+    for (int k = tid; k < BM * 64 * 2 / 16; k += BT) st_shared_v4(smem + L.ones + k * 16, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+    for (int k = tid; k < 16 * BM * 2 / 16; k += BT) st_shared_v4(smem + L.dv + k * 16, 0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_slot, TMEM_COLS);
+    sync_for_mma();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    const uint32_t sw1 = smem_u32(smem + L.w1), sw2 = smem_u32(smem + L.w2), sw3 = smem_u32(smem + L.w3);
+    const uint32_t sx = smem_u32(smem + L.x), sh1 = smem_u32(smem + L.h1), sh2 = smem_u32(smem + L.h2);
+    const uint32_t sdl = smem_u32(smem + L.dl), sdz2 = smem_u32(smem + L.dz2), sones = smem_u32(smem + L.ones);
+    const uint32_t sdv = smem_u32(smem + L.dv);
+
+    const double nrows_mb = (double)a.mb.count;
+    const float mean = (float)(a.stats[ST_ADV_SUM] / nrows_mb);
+    const float var = (float)fmax(a.stats[ST_ADV_SQ] / nrows_mb - (a.stats[ST_ADV_SUM] / nrows_mb) * (a.stats[ST_ADV_SUM] / nrows_mb), 0.0);
+    const float inv_std = 1.0f / (sqrtf(var) + 1e-8f);
+    const float inv_n = 1.0f / (float)a.mb.count;
+
+    float acc_st[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};   // pg, vf, ent, clip, kl of this thread's rows
+    uint32_t phase = 0;
+    bool ok = true, first = true, pending = false;
+    const int n_tiles = (a.mb.count + BM - 1) / BM;
+    for (int tile = role_cta; tile < n_tiles; tile += role_ctas) {
+        const int j0 = tile * BM;
+        const int nrows = min(BM, a.mb.count - j0);
+        // the previous tile's last products read x and h2: wait before overwriting them
+        if (pending) {
+            if (!(ok = wait_mma(&bar, phase))) break;
+            pending = false;
+        }
+        if (tid < BM) src_row[tid] = tid < nrows ? mb_row(a.mb, j0 + tid) : 0u;
+        __syncthreads();
+        // gathered rollout inputs -> x operand: inputs, 1 (bias column), zeros
+        for (int it = tid; it < BM * (KX / 8); it += BT) {
+            const int r = it % BM, c = it / BM;
+            float v[8];
+            const float* src = a.x + (size_t)src_row[r] * I;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int k = c * 8 + q;
+                v[q] = r >= nrows ? 0.0f : (k < I ? __ldg(src + k) : (k == I ? 1.0f : 0.0f));
+            }
+            st_shared_v4(smem + L.x + sw128_offset(r, c * 8, BM), pack2(v[0], v[1]), pack2(v[2], v[3]),
+                         pack2(v[4], v[5]), pack2(v[6], v[7]));
+        }
+        sync_for_mma();
+        // layer 1
+        if (tid == 0) {
+            chain(tmem + C_SLOT, KX / 16, idesc_bf16(BM, HID), false, [&](int kk) { return kmaj(sx, BM, kk); },
+                  [&](int kk) { return kmaj(sw1, HID, kk); });
+            mma_commit(&bar);
+        }
+        if (!(ok = wait_mma(&bar, phase))) break;
+        uint32_t m1[2], m2[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int col = half * 64 + c * 32;
+            m1[c] = relu_epilogue32(lane_base + C_SLOT + col, bias + col, smem + L.h1, row, col);
+        }
+        sync_for_mma();
+        // layer 2
+        if (tid == 0) {
+            chain(tmem + C_SLOT, HID / 16, idesc_bf16(BM, HID), false, [&](int kk) { return kmaj(sh1, BM, kk); },
+                  [&](int kk) { return kmaj(sw2, HID, kk); });
+            mma_commit(&bar);
+        }
+        if (!(ok = wait_mma(&bar, phase))) break;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int col = half * 64 + c * 32;
+            m2[c] = relu_epilogue32(lane_base + C_SLOT + col, bias + HID + col, smem + L.h2, row, col);
+        }
+        sync_for_mma();
+        if (actor) {
+            // head: logits = H2 W3
+            const int N3 = (O + 15) & ~15;
+            if (tid == 0) {
+                chain(tmem + C_SLOT, HID / 16, idesc_bf16(BM, N3), false, [&](int kk) { return kmaj(sh2, BM, kk); },
+                      [&](int kk) { return kmaj(sw3, KO, kk); });
+                mma_commit(&bar);
+            }
+            if (!(ok = wait_mma(&bar, phase))) break;
+            if (half == 0) {
+                float l[KO];
+                {
+                    float v[32];
+                    tmem_ld32(lane_base + C_SLOT, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) l[j] = v[j];
+                    tmem_ld32(lane_base + C_SLOT + 32, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) l[32 + j] = v[j];
+                }
+#pragma unroll
+                for (int k = 0; k < KO; ++k) l[k] = k < O ? l[k] + bias[2 * HID + k] : 0.0f;
+                if (row < nrows) {
+                    const ActorRow s = actor_row(a, src_row[row], l, mean, inv_std, inv_n);
+                    acc_st[0] += s.pg; acc_st[2] += s.ent; acc_st[3] += s.clip; acc_st[4] += s.kl;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < KO; ++k) l[k] = 0.0f;
+                }
+#pragma unroll
+                for (int q = 0; q < KO / 8; ++q)
+                    st_shared_v4(smem + L.dl + sw128_offset(row, q * 8, BM), pack2(l[q * 8], l[q * 8 + 1]),
+                                 pack2(l[q * 8 + 2], l[q * 8 + 3]), pack2(l[q * 8 + 4], l[q * 8 + 5]),
+                                 pack2(l[q * 8 + 6], l[q * 8 + 7]));
+            }
+            sync_for_mma();
+            if (tid == 0) {
+                // dW3 += H2^T dL;  db3 (every lane) += 1^T dL;  dZ2 (before the mask) = dL W3^T
+                chain(tmem + C_W3, BM / 16, idesc_bf16(BM, KO) | TA | TB, !first,
+                      [&](int kk) { return mnmaj(sh2, BM, kk); }, [&](int kk) { return mnmaj(sdl, BM, kk); });
+                chain(tmem + C_B3, BM / 16, idesc_bf16(BM, KO) | TB, !first,
+                      [&](int kk) { return kmaj(sones, BM, kk & 3); }, [&](int kk) { return mnmaj(sdl, BM, kk); });
+                chain(tmem + C_SLOT, KO / 16, idesc_bf16(BM, HID) | TB, false,
+                      [&](int kk) { return kmaj(sdl, BM, kk); }, [&](int kk) { return mnmaj(sw3, KO, kk); });
+                mma_commit(&bar);
+            }
+            if (!(ok = wait_mma(&bar, phase))) break;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int col = half * 64 + c * 32;
+                mask_epilogue32(lane_base + C_SLOT + col, m2[c], smem + L.dz2, row, col);
+            }
+            sync_for_mma();
+            if (tid == 0) {
+                // dW2 += H1^T dZ2;  db2 += dZ2^T 1;  dZ1 (before the mask) = dZ2 W2^T
+                chain(tmem + C_W2, BM / 16, idesc_bf16(BM, HID) | TA | TB, !first,
+                      [&](int kk) { return mnmaj(sh1, BM, kk); }, [&](int kk) { return mnmaj(sdz2, BM, kk); });
+                chain(tmem + C_B2, BM / 16, idesc_bf16(BM, 16) | TA, !first,
+                      [&](int kk) { return mnmaj(sdz2, BM, kk); }, [&](int kk) { return kmaj(sones, BM, kk & 3); });
+                chain(tmem + C_SLOT, HID / 16, idesc_bf16(BM, HID) | TB, false,
+                      [&](int kk) { return kmaj(sdz2, BM, kk); }, [&](int kk) { return mnmaj(sw2, HID, kk); });
+                mma_commit(&bar);
+            }
+        } else {
+            // value head: column 0 of G2 V3
+            if (tid == 0) {
+                chain(tmem + C_SLOT, HID / 16, idesc_bf16(BM, 16), false, [&](int kk) { return kmaj(sh2, BM, kk); },
+                      [&](int kk) { return kmaj(sw3, 16, kk); });
+                mma_commit(&bar);
+            }
+            if (!(ok = wait_mma(&bar, phase))) break;
+            if (half == 0) {
+                float vv[32];
+                tmem_ld32(lane_base + C_SLOT, vv);
+                float dv = 0.0f;
+                if (row < nrows) {
+                    // Section 4 clipped value loss, 0.5 max((v - R)^2, (v_clipped - R)^2)
+                    const uint32_t r = src_row[row];
+                    const float v = vv[0] + bias[2 * HID], vo = a.v_old[r], R = a.ret[r];
+                    const float dvv = v - vo;
+                    const float vc = vo + fminf(fmaxf(dvv, -a.vclip), a.vclip);
+                    const float la = (v - R) * (v - R), lb = (vc - R) * (vc - R);
+                    acc_st[1] += 0.5f * fmaxf(la, lb);
+                    dv = (la >= lb ? (v - R) : ((vc - R) * (fabsf(dvv) < a.vclip ? 1.0f : 0.0f))) * a.vf_coef * inv_n;
+                }
+                dv_s[row] = dv;
+                *reinterpret_cast<__nv_bfloat16*>(smem + L.dv + sw128_offset(0, row, 16)) = __float2bfloat16_rn(dv);
+            }
+            __syncthreads();
+            // dY2 = dv V3^T, masked by [g2 > 0]
+            {
+                const float dv = dv_s[row];
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int col = half * 64 + c * 32;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float y[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            y[j] = ((m2[c] >> (q * 8 + j)) & 1u) ? dv * bias[320 + col + q * 8 + j] : 0.0f;
+                        st_shared_v4(smem + L.dz2 + sw128_offset(row, col + q * 8, BM), pack2(y[0], y[1]),
+                                     pack2(y[2], y[3]), pack2(y[4], y[5]), pack2(y[6], y[7]));
+                    }
+                }
+            }
+            sync_for_mma();
+            if (tid == 0) {
+                // dV2 += G1^T dY2;  dc2 += dY2^T 1;  dV3 += G2^T dv;  dc3 += 1^T dv;  dY1 (before the mask) = dY2 V2^T
+                chain(tmem + C_W2, BM / 16, idesc_bf16(BM, HID) | TA | TB, !first,
+                      [&](int kk) { return mnmaj(sh1, BM, kk); }, [&](int kk) { return mnmaj(sdz2, BM, kk); });
+                chain(tmem + C_C2, BM / 16, idesc_bf16(BM, 16) | TA, !first,
+                      [&](int kk) { return mnmaj(sdz2, BM, kk); }, [&](int kk) { return kmaj(sones, BM, kk & 3); });
+                chain(tmem + C_V3, BM / 16, idesc_bf16(BM, 16) | TA, !first,
+                      [&](int kk) { return mnmaj(sh2, BM, kk); }, [&](int kk) { return kmaj(sdv, 16, kk); });
+                chain(tmem + C_C3, BM / 16, idesc_bf16(BM, 16), !first,
+                      [&](int kk) { return kmaj(sones, BM, kk & 3); }, [&](int kk) { return kmaj(sdv, 16, kk); });
+                chain(tmem + C_SLOT, HID / 16, idesc_bf16(BM, HID) | TB, false,
+                      [&](int kk) { return kmaj(sdz2, BM, kk); }, [&](int kk) { return mnmaj(sw2, HID, kk); });
+                mma_commit(&bar);
+            }
+        }
+        if (!(ok = wait_mma(&bar, phase))) break;
+        // first-layer gradient of the pre-activation: dZ1 / dY1 into the h2 buffer
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int col = half * 64 + c * 32;
+            mask_epilogue32(lane_base + C_SLOT + col, m1[c], smem + L.h2, row, col);
+        }
+        sync_for_mma();
+        if (tid == 0) {
+            // dW1^T += dZ1^T X (column I of X is 1: the first-layer bias gradient)
+            chain(tmem + C_W1T, BM / 16, idesc_bf16(BM, KX) | TA | TB, !first,
+                  [&](int kk) { return mnmaj(sh2, BM, kk); }, [&](int kk) { return mnmaj(sx, BM, kk); });
+            mma_commit(&bar);
+        }
+        pending = true;
+        first = false;
+    }
+    if (ok && pending) ok = wait_mma(&bar, phase);
+    if (ok) {
+        float* out = P.partial + (size_t)blockIdx.x * BM * PC;
+        const int c0 = half == 0 ? 0 : 6, c1 = half == 0 ? 6 : PC / 32;
+        for (int ch = c0; ch < c1; ++ch) {
+            float v[32];
+            tmem_ld32(lane_base + ch * 32, v);
+            float4* dst = reinterpret_cast<float4*>(out + (size_t)row * PC + ch * 32);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+    } else {
+        // a wait gave up: give the tensor core one more bounded chance to finish before freeing TMEM
+        mbar_wait(&bar, phase, 200000000LL);
+    }
+    // loss statistics of this CTA's rows
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        float v = acc_st[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        if (lane == 0) red[q][warp] = v;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid < 5) {
+        double s = 0.0;
+        for (int k = 0; k < BT / 32; ++k) s += red[tid][k];
+        if (s != 0.0) atomicAdd(&a.stats[ST_PG + tid], s);
+    }
+    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// Sums the CTAs' accumulators into the gradient vector (padding = 0).
+__global__ void ppo_bf16_reduce_kernel(const float* __restrict__ partial, int n_actor, int n_critic, int I, int O,
+                                       float* __restrict__ grad) {
+    const NetOffsets o = net_offsets(I, HID, O);
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < o.total; p += (size_t)gridDim.x * blockDim.x) {
+        int lane = -1, col = 0;
+        bool act = true;
+        auto in = [&](size_t base, size_t n) { return p >= base && p < base + n; };
+        if (in(o.W1, (size_t)I * HID)) { lane = (int)((p - o.W1) % HID); col = C_W1T + (int)((p - o.W1) / HID); }
+        else if (in(o.b1, HID)) { lane = (int)(p - o.b1); col = C_W1T + I; }
+        else if (in(o.W2, HID * HID)) { lane = (int)((p - o.W2) / HID); col = C_W2 + (int)((p - o.W2) % HID); }
+        else if (in(o.b2, HID)) { lane = (int)(p - o.b2); col = C_B2; }
+        else if (in(o.W3, (size_t)HID * O)) { lane = (int)((p - o.W3) / O); col = C_W3 + (int)((p - o.W3) % O); }
+        else if (in(o.b3, O)) { lane = 0; col = C_B3 + (int)(p - o.b3); }
+        else {
+            act = false;
+            if (in(o.V1, (size_t)I * HID)) { lane = (int)((p - o.V1) % HID); col = C_W1T + (int)((p - o.V1) / HID); }
+            else if (in(o.c1, HID)) { lane = (int)(p - o.c1); col = C_W1T + I; }
+            else if (in(o.V2, HID * HID)) { lane = (int)((p - o.V2) / HID); col = C_W2 + (int)((p - o.V2) % HID); }
+            else if (in(o.c2, HID)) { lane = (int)(p - o.c2); col = C_C2; }
+            else if (in(o.V3, HID)) { lane = (int)(p - o.V3); col = C_V3; }
+            else if (in(o.c3, 1)) { lane = 0; col = C_C3; }
+        }
+        float s = 0.0f;
+        if (lane >= 0) {
+            const int c0 = act ? 0 : n_actor, c1 = act ? n_actor : n_actor + n_critic;
+            for (int c = c0; c < c1; ++c) s += partial[((size_t)c * BM + lane) * PC + col];
+        }
+        grad[p] = s;
+    }
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 2)
+        return 2;
+    return n;
+}
+
+}  // namespace
+
+ej_status launch_ppo_bf16(const FbArgs& fa, float* partial, size_t partial_bytes, float* grad, cudaStream_t s) {
+    if (fa.H != HID) return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: hidden must be %d", HID);
+    if (fa.in_dim + 1 > KX) return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: input width must be <= %d", KX - 1);
+    if (fa.O > KO) return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: at most %d logits", KO);
+    if (fa.n_heads < 1 || fa.n_heads > 4) return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: 1 to 4 action heads");
+    if (fa.W > 2) return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: at most 2 mask words");
+    ej_status st = launch_adv_stats(fa.mb, fa.adv, fa.stats, s);
+    if (st != EJ_OK) return st;
+    const NetOffsets off = net_offsets(fa.in_dim, HID, fa.O);
+    const int n_tiles = (fa.mb.count + BM - 1) / BM;
+    int per_role = sm_count() / 2;
+    if (per_role > n_tiles) per_role = n_tiles;
+    if (per_role < 1) {
+        if (cudaMemsetAsync(grad, 0, sizeof(float) * off.total, s) != cudaSuccess) return fail(EJ_ERR_CUDA, "memset failed");
+        return EJ_OK;
+    }
+    if ((size_t)2 * per_role * BM * PC * sizeof(float) > partial_bytes)
+        return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: workspace too small for %d CTAs", 2 * per_role);
+    const size_t smem = ppo_smem().total + 1024;
+    static size_t configured = 0;
+    if (configured < smem) {
+        cudaError_t err = cudaFuncSetAttribute(ppo_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
+        configured = smem;
+    }
+    BfPpoArgs P;
+    P.f = fa;
+    P.partial = partial;
+    P.n_actor = per_role;
+    ppo_bf16_kernel<<<2 * per_role, BT, smem, s>>>(P);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "bf16 PPO launch: %s", cudaGetErrorString(err));
+    ppo_bf16_reduce_kernel<<<128, 256, 0, s>>>(partial, per_role, per_role, fa.in_dim, fa.O, grad);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "bf16 PPO reduce launch: %s", cudaGetErrorString(err));
+    return EJ_OK;
+}
+
+int ppo_bf16_fault(int clear) {
+    int v = 0;
+    cudaMemcpyFromSymbol(&v, g_ej_fault, sizeof(int));
+    if (clear) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_ej_fault, &z, sizeof(int));
+    }
+    return v;
+}
+
+}  // namespace ej

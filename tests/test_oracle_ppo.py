@@ -85,3 +85,39 @@ def test_adam_first_step_is_signed_lr():
     p = np.array([1.0, -2.0, 3.0]); gr = np.array([0.5, -4.0, 1e-3])
     q, m, v = ppo.adam64(p, gr, np.zeros(3), np.zeros(3), 1, lr=1e-2, eps=1e-12)
     assert np.allclose(q, p - 1e-2 * np.sign(gr))
+
+
+def test_bf16_round_matches_torch_bfloat16():
+    """The oracle's bfloat16 rounding against torch's float32 -> bfloat16
+    conversion (round to nearest, ties to even), including exact ties."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    vals = np.concatenate([rng.normal(size=4000) * 10.0 ** rng.integers(-30, 30, 4000),
+                           [0.0, 1.0, -1.0, 0.5, 3.0, 1e-38, -2.5e38]])
+    # float32 values exactly halfway between two bfloat16 values: low 16 bits 0x8000
+    expo = rng.integers(100, 150, 500, dtype=np.uint64) << np.uint64(23)
+    mant = rng.integers(0, 1 << 7, 500, dtype=np.uint64) << np.uint64(16)
+    ties = (expo | mant | np.uint64(0x8000)).astype(np.uint32).view(np.float32).astype(np.float64)
+    for v in (vals, ties, -ties):
+        ref = torch.from_numpy(v.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+        assert np.array_equal(ppo.bf16_round(v), ref)
+    r = ppo.bf16_round(vals)
+    assert np.array_equal(ppo.bf16_round(r), r)
+
+
+def test_bf16_operand_form_reduces_to_exact_and_stays_close():
+    """With the identity as operand rounding the BF16-operand form is the exact
+    gradient; with bfloat16 rounding it differs from it, by a few per cent of
+    the gradient's norm at most."""
+    coef = dict(clip=0.2, vf_coef=0.25, vclip=10.0, ent_coef=0.1)
+    w, x, act, valid, lo, vo, adv, ret = _rand_problem(5, heads=1)
+    head = valid.shape[1]
+    f = lambda **kw: ppo.ppo_loss_grad64(w, x, act, valid, lo, vo, adv, ret, heads=1, head=head, **coef, **kw)
+    l0, g0, _ = f()
+    l1, g1, _ = f(operand=lambda t: t)
+    assert l0 == l1 and all(np.array_equal(g0[k], g1[k]) for k in g0)
+    l2, g2, _ = f(operand=ppo.bf16_round)
+    assert l2 == pytest.approx(l0, rel=5e-2)
+    a = np.concatenate([g0[k].ravel() for k in g0])
+    b = np.concatenate([g2[k].ravel() for k in g0])
+    assert 0 < np.linalg.norm(b - a) <= 5e-2 * np.linalg.norm(a)
