@@ -213,7 +213,7 @@ def run_gpu(args):
                                        "env_step per step",
                            "bf16": run_rollout(args, dev, "bf16"), "fp32": run_rollout(args, dev, "fp32")}
         line["ppo"] = {"workload": "E=2048 x A=100 x 128 steps, GAE, 4 epochs x 8 minibatches, both networks",
-                       **run_ppo(args, dev)}
+                       "bf16": run_ppo(args, dev, "bf16"), "fp32": run_ppo(args, dev, "fp32")}
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if world > 1:
@@ -254,9 +254,20 @@ def run_rollout(args, dev, precision, E_r=4096, T_r=1000, seed=2000):
     return out
 
 
-def run_ppo(args, dev, E_p=2048, T_p=128, seed=3000):
-    """PPO update of config 4: E_p x A x T_p transitions, GAE, 4 epochs x 8
-    minibatches of the population and government networks, float32."""
+def ppo_flops_per_row(in_dim, H, O):
+    """Useful FLOPs of one minibatch row of the PPO gradient: actor and critic
+    forward, backward-data through the hidden layers (not into the inputs),
+    and the weight gradients (as many multiply-adds as the forward)."""
+    fwd = in_dim * H + H * H + H * O + in_dim * H + H * H + H
+    bwd_data = O * H + H * H + H * H
+    return 2 * (2 * fwd + bwd_data)
+
+
+def run_ppo(args, dev, precision, E_p=2048, T_p=128, seed=3000):
+    """One training iteration of config 4 in the given precision: a T_p-step
+    rollout of E_p x A agents (policy, sampling, env_step), then the PPO update
+    (GAE, 4 epochs x 8 minibatches of the population and government
+    networks).  Reports updates/s and rollout+update agent-steps/s."""
     import torch
 
     import synth
@@ -265,23 +276,32 @@ def run_ppo(args, dev, E_p=2048, T_p=128, seed=3000):
     env = VecEnv(E_p, A, device=dev, T_ep=T_EP, T_tax=T_TAX)
     pw = torch.from_numpy(synth.net_weights(seed, 0, env.D, 128, env.nA))
     gw = torch.from_numpy(synth.net_weights(seed, 1, env.G, 128, env.p.nb * env.p.tax_levels))
-    pol = Policy(env, pw, gw, hidden=128, precision="bf16")
+    pol = Policy(env, pw, gw, hidden=128, precision=precision)
     ro = Rollout(env, pol, T_p)
     ro.reset(seed=seed)
     ro.run()
-    ppo = PPO(pol, T_p)
+    ppo = PPO(pol, T_p, precision=precision)
     ppo.update(ro)
     torch.cuda.synchronize(dev)
     steps = max(1, min(args.steps, 2))
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ms = ro_ms = 0.0
     for _ in range(steps):
+        ev[0].record()
+        ro.carry_over()
+        ro.run()
+        ev[1].record()
         stats = ppo.update(ro)
-    b.record()
-    torch.cuda.synchronize(dev)
-    ms = a.elapsed_time(b) / steps
+        ev[2].record()
+        torch.cuda.synchronize(dev)
+        ro_ms += ev[0].elapsed_time(ev[1]) / steps
+        ms += ev[1].elapsed_time(ev[2]) / steps
     st = stats.cpu().numpy()
-    out = {"updates_per_s": 1e3 / ms, "ms_per_update": ms, "precision": "fp32",
+    rows = ppo.pp.epochs * T_p * E_p
+    flops = rows * (A * ppo_flops_per_row(env.D, 128, env.nA) + ppo_flops_per_row(env.G, 128, env.p.nb * env.p.tax_levels))
+    out = {"updates_per_s": 1e3 / ms, "ms_per_update": ms, "precision": precision,
+           "rollout_ms": ro_ms, "train_agent_steps_per_s": E_p * A * T_p / ((ro_ms + ms) / 1e3),
+           "useful_TFLOPs": flops / (ms / 1e3) / 1e12, "useful_TFLOP_per_update": flops / 1e12,
            "transitions_per_update": E_p * A * T_p, "epochs": ppo.pp.epochs, "minibatches": ppo.pp.minibatches,
            "population_loss": {"policy": float(st[0, 0]), "value": float(st[0, 1]), "entropy": float(st[0, 2])}}
     del ppo, ro, pol, env
@@ -432,17 +452,20 @@ def run_profile_case(args):
         ro = Rollout(env, pol, 32)
         ro.reset(seed=7)
         ro.run()
-        ppo = PPO(pol, 32)
-        ms = []
-        for k in range(args.warmup + args.steps):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            ppo.update(ro)
-            b.record()
-            torch.cuda.synchronize()
-            if k >= args.warmup:
-                ms.append(a.elapsed_time(b))
-        print(json.dumps({"profile_case": "ppo E=256 A=100 T=32", "update_ms": ms}))
+        res = {}
+        for prec in ("bf16", "fp32"):
+            ppo = PPO(pol, 32, precision=prec)
+            ms = []
+            for k in range(args.warmup + args.steps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                ppo.update(ro)
+                b.record()
+                torch.cuda.synchronize()
+                if k >= args.warmup:
+                    ms.append(a.elapsed_time(b))
+            res[prec] = {"update_ms": ms}
+        print(json.dumps({"profile_case": "ppo E=256 A=100 T=32", **res}))
         return
 
     n = 100
