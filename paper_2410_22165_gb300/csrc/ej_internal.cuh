@@ -48,10 +48,12 @@ DevState state_pointers(const Layout& lay, void* base);
 // Records the error message of the calling thread and returns s.
 ej_status fail(ej_status s, const char* fmt, ...);
 
-// Launchers (ej_env.cu).
+// Launchers (ej_env.cu; the 2-resource, 5-level instantiations in ej_env_r2p5.cu).
 enum : int { MODE_RESET = 1, MODE_POP_DRAW = 2, MODE_GOV_DRAW = 4, MODE_AUX_DRAW = 8 };
 ej_status launch_env(const KParams& kp, const Layout& lay, const DevState& st, const DevIO& io,
                      int n_steps, int mode, uint64_t seed, cudaStream_t stream);
+ej_status launch_env_r2p5(const KParams& kp, const Layout& lay, const DevState& st, const DevIO& io,
+                          int n_steps, int mode, uint64_t seed, cudaStream_t stream);
 ej_status launch_fill_draws(const KParams& kp, uint64_t seed, uint32_t g0, int n_steps,
                             int32_t* act, float* gather_u, uint32_t* tb, float* policy_u,
                             int32_t* gov_act, cudaStream_t stream);
@@ -80,7 +82,7 @@ __host__ __device__ inline SmemLayout smem_layout(int NT, int R, int P, int L, i
     s.lvl = b;   b = align16(b + 4u * (9u * L + 9u));
     s.kb = b;    b = align16(b + 4u * (R + 2u * R * P));
     const uint32_t nw = NT / 32;
-    s.fl = b;    b = align16(b + 4u * (EJ_MAX_NB + 4u * R + nw * (M + 1u) + (M + 1u) + 3u * M + 16u));
+    s.fl = b;    b = align16(b + 4u * (EJ_MAX_NB + 4u * R + nw * (M + 1u) + (M + 1u) + 3u * M + 16u + EJ_MAX_ORDERS + 1u));
     s.alias = b;
     // phase A: new-order keys, sorted new orders, per-agent integer deltas, tax
     uint32_t a = align16(8u * NT) + align16(4u * NT) + 4u * align16(4u * NT) +
