@@ -53,6 +53,28 @@ __global__ void adv_stats_kernel(MbDesc d, const float* __restrict__ adv, double
     }
 }
 
+// rows[j] = the rollout row at position lo + j of the minibatch permutation,
+// and the advantage sums over those rows.
+__global__ void mb_rows_stats_kernel(MbDesc d, const float* __restrict__ adv, uint32_t* __restrict__ rows,
+                                     double* stats) {
+    double s = 0.0, q = 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.count; j += gridDim.x * blockDim.x) {
+        const uint32_t r = mb_row(d, j);
+        rows[j] = r;
+        const double a = adv[r];
+        s += a;
+        q += a * a;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+        q += __shfl_xor_sync(0xFFFFFFFFu, q, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&stats[ST_ADV_SUM], s);
+        atomicAdd(&stats[ST_ADV_SQ], q);
+    }
+}
+
 __global__ void zero_kernel(double* p, int n) {
     for (int k = threadIdx.x; k < n; k += blockDim.x) p[k] = 0.0;
 }
@@ -356,6 +378,15 @@ ej_status launch_adv_stats(const MbDesc& mb, const float* adv, double* stats, cu
     if (grid < 1) grid = 1;
     adv_stats_kernel<<<grid, 256, 0, s>>>(mb, adv, stats);
     return cudaGetLastError() == cudaSuccess ? EJ_OK : fail(EJ_ERR_CUDA, "advantage statistics launch failed");
+}
+
+ej_status launch_mb_rows_stats(const MbDesc& mb, const float* adv, uint32_t* rows, double* stats, cudaStream_t s) {
+    zero_kernel<<<1, 32, 0, s>>>(stats, ST_COUNT_);
+    int grid = (mb.count + 255) / 256;
+    if (grid > 152 * 8) grid = 152 * 8;
+    if (grid < 1) grid = 1;
+    mb_rows_stats_kernel<<<grid, 256, 0, s>>>(mb, adv, rows, stats);
+    return cudaGetLastError() == cudaSuccess ? EJ_OK : fail(EJ_ERR_CUDA, "minibatch rows launch failed");
 }
 
 ej_status launch_minibatch_grad(const FbArgs& fa, const WgJobs& jobs, int n_jobs, float* partial,

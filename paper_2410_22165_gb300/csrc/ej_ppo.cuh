@@ -45,6 +45,7 @@ struct FbArgs {
     const float* weights;
     const float* x;             // [N][in] rollout inputs (flat rows)
     const uint32_t* mask;       // [N][W] or NULL
+    uint32_t* rows;             // [count] minibatch row table (BF16 path), or NULL
     const int32_t* act;         // [N][n_heads]
     const float* logp_old;      // [N]
     const float* v_old;         // [N]
@@ -91,6 +92,8 @@ ej_status launch_minibatch_grad(const FbArgs& fa, const WgJobs& jobs, int n_jobs
 ej_status launch_ppo_bf16(const FbArgs& fa, float* partial, size_t partial_bytes, float* grad, cudaStream_t s);
 int ppo_bf16_fault(int clear);
 ej_status launch_adv_stats(const MbDesc& mb, const float* adv, double* stats, cudaStream_t s);
+// Writes the minibatch's rollout rows (the permutation, once) and their advantage sums.
+ej_status launch_mb_rows_stats(const MbDesc& mb, const float* adv, uint32_t* rows, double* stats, cudaStream_t s);
 ej_status launch_adam(float* p, const float* g, float* m, float* v, size_t n, float lr, float b1, float b2,
                       float eps, int step, cudaStream_t s);
 

@@ -116,8 +116,10 @@ ej_status minibatch_grad(const KParams& kp, const EjPpoParams* pp, int T, int H,
     fa.ret = (const float*)(ws + W.ret[net]);
     fa.w3t = (float*)(ws + W.wt3); fa.w2t = (float*)(ws + W.wt2); fa.v2t = (float*)(ws + W.wv2);
     fa.stats = stats;
-    if (precision == EJ_BF16)
+    if (precision == EJ_BF16) {
+        fa.rows = (uint32_t*)(ws + W.rows);      // the float32 path's per-row region holds >= count entries
         return launch_ppo_bf16(fa, (float*)(ws + W.partial), 4ull * 6 * WG_CHUNKS * WG_STRIDE, grad, s);
+    }
     const uint64_t R = (uint64_t)fa.mb.count;
     float* rb = (float*)(ws + W.rows);
     fa.ws_x = rb; rb += R * d.in;

@@ -154,38 +154,68 @@ __device__ void pack_operand(uint8_t* dst, int rows, int K, F get) {
     }
 }
 
-// 32 accumulator columns [col, col+32) of this thread's row: add the bias,
-// ReLU, record the mask bits, write BF16 to columns [col, col+32) of dst.
-__device__ __forceinline__ uint32_t relu_epilogue32(uint32_t taddr, const float* bias, uint8_t* dst, int row,
-                                                    int col) {
-    float v[32];
-    tmem_ld32(taddr, v);
-    uint32_t bits = 0;
+// 64 consecutive accumulator columns of this thread's TMEM lane (two loads, one wait).
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
+    uint32_t r[64];
+#define EJ_LD32(OFF, B)                                                                                         \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "                                                    \
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"                                     \
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                    \
+                 : "=r"(r[B + 0]), "=r"(r[B + 1]), "=r"(r[B + 2]), "=r"(r[B + 3]), "=r"(r[B + 4]),             \
+                   "=r"(r[B + 5]), "=r"(r[B + 6]), "=r"(r[B + 7]), "=r"(r[B + 8]), "=r"(r[B + 9]),             \
+                   "=r"(r[B + 10]), "=r"(r[B + 11]), "=r"(r[B + 12]), "=r"(r[B + 13]), "=r"(r[B + 14]),        \
+                   "=r"(r[B + 15]), "=r"(r[B + 16]), "=r"(r[B + 17]), "=r"(r[B + 18]), "=r"(r[B + 19]),        \
+                   "=r"(r[B + 20]), "=r"(r[B + 21]), "=r"(r[B + 22]), "=r"(r[B + 23]), "=r"(r[B + 24]),        \
+                   "=r"(r[B + 25]), "=r"(r[B + 26]), "=r"(r[B + 27]), "=r"(r[B + 28]), "=r"(r[B + 29]),        \
+                   "=r"(r[B + 30]), "=r"(r[B + 31])                                                            \
+                 : "r"(OFF))
+    EJ_LD32(taddr, 0);
+    EJ_LD32(taddr + 32, 32);
+#undef EJ_LD32
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        float y[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            y[j] = fmaxf(v[q * 8 + j] + bias[q * 8 + j], 0.0f);
-            bits |= (y[j] > 0.0f ? 1u : 0u) << (q * 8 + j);
-        }
-        st_shared_v4(dst + sw128_offset(row, col + q * 8, BM), pack2(y[0], y[1]), pack2(y[2], y[3]),
-                     pack2(y[4], y[5]), pack2(y[6], y[7]));
-    }
-    return bits;
+    for (int k = 0; k < 64; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-// 32 accumulator columns times the ReLU mask bits -> BF16 columns of dst.
-__device__ __forceinline__ void mask_epilogue32(uint32_t taddr, uint32_t bits, uint8_t* dst, int row, int col) {
-    float v[32];
-    tmem_ld32(taddr, v);
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t*>(&v); }
+__device__ __forceinline__ __nv_bfloat162 bits_bf2(uint32_t u) { return *reinterpret_cast<__nv_bfloat162*>(&u); }
+
+// 64 accumulator columns [col, col+64) of this thread's row: add the bias,
+// round to BF16 pairs, ReLU on the pairs (max with 0 commutes with the
+// rounding), write to columns [col, col+64) of dst.
+__device__ __forceinline__ void relu_epilogue64(uint32_t taddr, const float* bias, uint8_t* dst, int row, int col) {
+    float v[64];
+    tmem_ld64(taddr, v);
+    const __nv_bfloat162 zero = __floats2bfloat162_rn(0.0f, 0.0f);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        float y[8];
+    for (int q = 0; q < 8; ++q) {
+        uint32_t w[4];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) y[j] = ((bits >> (q * 8 + j)) & 1u) ? v[q * 8 + j] : 0.0f;
-        st_shared_v4(dst + sw128_offset(row, col + q * 8, BM), pack2(y[0], y[1]), pack2(y[2], y[3]),
-                     pack2(y[4], y[5]), pack2(y[6], y[7]));
+        for (int j = 0; j < 4; ++j) {
+            const int k = q * 8 + 2 * j;
+            w[j] = bf2_bits(__hmax2(__floats2bfloat162_rn(v[k] + bias[k], v[k + 1] + bias[k + 1]), zero));
+        }
+        st_shared_v4(dst + sw128_offset(row, col + q * 8, BM), w[0], w[1], w[2], w[3]);
+    }
+}
+
+// 64 accumulator columns times the ReLU derivative of the activation stored
+// in act (BF16, same row and columns: [h > 0]) -> BF16 columns of dst.
+__device__ __forceinline__ void mask_epilogue64(uint32_t taddr, const uint8_t* act, uint8_t* dst, int row, int col) {
+    float v[64];
+    tmem_ld64(taddr, v);
+    const __nv_bfloat162 zero = __floats2bfloat162_rn(0.0f, 0.0f);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const uint4 h = *reinterpret_cast<const uint4*>(act + sw128_offset(row, col + q * 8, BM));
+        const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int k = q * 8 + 2 * j;
+            w[j] = bf2_bits(__hmul2(__floats2bfloat162_rn(v[k], v[k + 1]), __hgt2(bits_bf2(hw[j]), zero)));
+        }
+        st_shared_v4(dst + sw128_offset(row, col + q * 8, BM), w[0], w[1], w[2], w[3]);
     }
 }
 
@@ -208,48 +238,49 @@ struct Head4 {
 struct ActorRow { float pg, ent, clip, kl; };
 
 // Section 4, actor part of one minibatch row: per-head masked log-softmax of
-// the logits l[0, O), the clipped surrogate on the normalised advantage and
-// the entropy bonus; l is overwritten with d loss / d logits (0 beyond O).
-__device__ __forceinline__ ActorRow actor_row(const FbArgs& a, uint32_t row, float (&l)[KO], float mean,
+// the logits l[0, O) (O <= KT), the clipped surrogate on the normalised
+// advantage and the entropy bonus; l is overwritten with d loss / d logits
+// (0 beyond O and at masked actions).  One exp per logit: e[k] = exp(l_k - max)
+// serves the normaliser, the entropy and the gradient.
+template <int KT>
+__device__ __forceinline__ ActorRow actor_row(const FbArgs& a, uint32_t row, float (&l)[KT], float mean,
                                               float inv_std, float inv_n) {
     uint32_t w0 = 0xFFFFFFFFu, w1 = 0xFFFFFFFFu;
     if (a.W) {
         const uint32_t* mw = a.mask + (size_t)row * a.W;
         w0 = mw[0];
-        w1 = a.W > 1 ? mw[1] : 0u;
+        w1 = (KT > 32 && a.W > 1) ? mw[1] : 0u;
     }
-    Head4 off, ent_h;
+    auto valid = [&](int k) { return (((k < 32 ? w0 : w1) >> (k & 31)) & 1u) != 0; };
+    float e[KT];
+    Head4 lse, ent_h, rS;
     float logp = 0.0f, ent = 0.0f;
     for (int h = 0; h < a.n_heads; ++h) {
         const int lo = h * a.head, hi = lo + a.head;
         const int act = lo + a.act[(size_t)row * a.n_heads + h];
         float m = -FLT_MAX;
 #pragma unroll
-        for (int k = 0; k < KO; ++k) {
-            const bool ok = k >= lo && k < hi && (((k < 32 ? w0 : w1) >> (k & 31)) & 1u);
-            if (ok) m = fmaxf(m, l[k]);
-        }
+        for (int k = 0; k < KT; ++k)
+            if (k >= lo && k < hi && valid(k)) m = fmaxf(m, l[k]);
         float S = 0.0f, la = 0.0f;
 #pragma unroll
-        for (int k = 0; k < KO; ++k) {
-            const bool ok = k >= lo && k < hi && (((k < 32 ? w0 : w1) >> (k & 31)) & 1u);
-            if (ok) S += expf(l[k] - m);
+        for (int k = 0; k < KT; ++k) {
+            if (k >= lo && k < hi) {
+                e[k] = valid(k) ? expf(l[k] - m) : 0.0f;
+                S += e[k];
+            }
             if (k == act) la = l[k];
         }
-        const float logS = logf(S);
+        const float logS = logf(S), inv_S = 1.0f / S;
         logp += la - m - logS;
         float Hh = 0.0f;
 #pragma unroll
-        for (int k = 0; k < KO; ++k) {
-            const bool ok = k >= lo && k < hi && (((k < 32 ? w0 : w1) >> (k & 31)) & 1u);
-            if (ok) {
-                const float lp = l[k] - m - logS;
-                Hh -= expf(lp) * lp;
-            }
-        }
+        for (int k = 0; k < KT; ++k)
+            if (k >= lo && k < hi && valid(k)) Hh -= (e[k] * inv_S) * (l[k] - m - logS);
         ent += Hh;
-        off.set(h, m + logS);
+        lse.set(h, m + logS);
         ent_h.set(h, Hh);
+        rS.set(h, inv_S);
     }
     ActorRow st;
     const float lpo = a.logp_old[row];
@@ -265,19 +296,18 @@ __device__ __forceinline__ ActorRow actor_row(const FbArgs& a, uint32_t row, flo
     st.kl = lpo - logp;
     st.ent = ent;
     const float ec = a.ent_coef * inv_n;
-    // in place: column k of head h only needs its own logit (columns >= O are already 0)
     for (int h = 0; h < a.n_heads; ++h) {
         const int lo = h * a.head, hi = lo + a.head;
         const int act = lo + a.act[(size_t)row * a.n_heads + h];
-        const float o = off.get(h), Hh = ent_h.get(h);
+        const float o = lse.get(h), Hh = ent_h.get(h), inv_S = rS.get(h);
 #pragma unroll
-        for (int k = 0; k < KO; ++k) {
+        for (int k = 0; k < KT; ++k) {
             if (k >= lo && k < hi) {
                 float g = 0.0f;
-                if (((k < 32 ? w0 : w1) >> (k & 31)) & 1u) {
+                if (valid(k)) {
                     const float lp = l[k] - o;
-                    const float p = expf(lp);
-                    g = dlogp * ((k == act ? 1.0f : 0.0f) - p) + ec * p * (lp + Hh);
+                    const float pk = e[k] * inv_S;
+                    g = dlogp * ((k == act ? 1.0f : 0.0f) - pk) + ec * pk * (lp + Hh);
                 }
                 l[k] = g;
             }
@@ -286,6 +316,7 @@ __device__ __forceinline__ ActorRow actor_row(const FbArgs& a, uint32_t row, flo
     return st;
 }
 
+template <int KT>
 __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bar;
@@ -325,6 +356,10 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
     }
     for (int k = tid; k < BM * 64 * 2 / 16; k += BT) st_shared_v4(smem + L.ones + k * 16, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
     for (int k = tid; k < 16 * BM * 2 / 16; k += BT) st_shared_v4(smem + L.dv + k * 16, 0u, 0u, 0u, 0u);
+    // columns of x beyond the inputs and the ones column, and of dL beyond the
+    // logits in registers, stay zero for every tile
+    for (int k = tid; k < BM * KX * 2 / 16; k += BT) st_shared_v4(smem + L.x + k * 16, 0u, 0u, 0u, 0u);
+    for (int k = tid; k < BM * KO * 2 / 16; k += BT) st_shared_v4(smem + L.dl + k * 16, 0u, 0u, 0u, 0u);
     if (tid == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
@@ -356,10 +391,11 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
             if (!(ok = wait_mma(&bar, phase))) break;
             pending = false;
         }
-        if (tid < BM) src_row[tid] = tid < nrows ? mb_row(a.mb, j0 + tid) : 0u;
+        if (tid < BM) src_row[tid] = tid < nrows ? (a.rows ? a.rows[j0 + tid] : mb_row(a.mb, j0 + tid)) : 0u;
         __syncthreads();
-        // gathered rollout inputs -> x operand: inputs, 1 (bias column), zeros
-        for (int it = tid; it < BM * (KX / 8); it += BT) {
+        // gathered rollout inputs -> x operand: inputs, then 1 (the bias column)
+        const int xchunks = I / 8 + 1;
+        for (int it = tid; it < BM * xchunks; it += BT) {
             const int r = it % BM, c = it / BM;
             float v[8];
             const float* src = a.x + (size_t)src_row[r] * I;
@@ -379,12 +415,7 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
             mma_commit(&bar);
         }
         if (!(ok = wait_mma(&bar, phase))) break;
-        uint32_t m1[2], m2[2];
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int col = half * 64 + c * 32;
-            m1[c] = relu_epilogue32(lane_base + C_SLOT + col, bias + col, smem + L.h1, row, col);
-        }
+        relu_epilogue64(lane_base + C_SLOT + half * 64, bias + half * 64, smem + L.h1, row, half * 64);
         sync_for_mma();
         // layer 2
         if (tid == 0) {
@@ -393,11 +424,7 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
             mma_commit(&bar);
         }
         if (!(ok = wait_mma(&bar, phase))) break;
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int col = half * 64 + c * 32;
-            m2[c] = relu_epilogue32(lane_base + C_SLOT + col, bias + HID + col, smem + L.h2, row, col);
-        }
+        relu_epilogue64(lane_base + C_SLOT + half * 64, bias + HID + half * 64, smem + L.h2, row, half * 64);
         sync_for_mma();
         if (actor) {
             // head: logits = H2 W3
@@ -409,27 +436,23 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
             }
             if (!(ok = wait_mma(&bar, phase))) break;
             if (half == 0) {
-                float l[KO];
-                {
-                    float v[32];
-                    tmem_ld32(lane_base + C_SLOT, v);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) l[j] = v[j];
-                    tmem_ld32(lane_base + C_SLOT + 32, v);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) l[32 + j] = v[j];
+                float l[KT];
+                if constexpr (KT == 64) {
+                    tmem_ld64(lane_base + C_SLOT, l);
+                } else {
+                    tmem_ld32(lane_base + C_SLOT, l);
                 }
 #pragma unroll
-                for (int k = 0; k < KO; ++k) l[k] = k < O ? l[k] + bias[2 * HID + k] : 0.0f;
+                for (int k = 0; k < KT; ++k) l[k] = k < O ? l[k] + bias[2 * HID + k] : 0.0f;
                 if (row < nrows) {
-                    const ActorRow s = actor_row(a, src_row[row], l, mean, inv_std, inv_n);
+                    const ActorRow s = actor_row<KT>(a, src_row[row], l, mean, inv_std, inv_n);
                     acc_st[0] += s.pg; acc_st[2] += s.ent; acc_st[3] += s.clip; acc_st[4] += s.kl;
                 } else {
 #pragma unroll
-                    for (int k = 0; k < KO; ++k) l[k] = 0.0f;
+                    for (int k = 0; k < KT; ++k) l[k] = 0.0f;
                 }
 #pragma unroll
-                for (int q = 0; q < KO / 8; ++q)
+                for (int q = 0; q < KT / 8; ++q)
                     st_shared_v4(smem + L.dl + sw128_offset(row, q * 8, BM), pack2(l[q * 8], l[q * 8 + 1]),
                                  pack2(l[q * 8 + 2], l[q * 8 + 3]), pack2(l[q * 8 + 4], l[q * 8 + 5]),
                                  pack2(l[q * 8 + 6], l[q * 8 + 7]));
@@ -441,16 +464,12 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
                       [&](int kk) { return mnmaj(sh2, BM, kk); }, [&](int kk) { return mnmaj(sdl, BM, kk); });
                 chain(tmem + C_B3, BM / 16, idesc_bf16(BM, KO) | TB, !first,
                       [&](int kk) { return kmaj(sones, BM, kk & 3); }, [&](int kk) { return mnmaj(sdl, BM, kk); });
-                chain(tmem + C_SLOT, KO / 16, idesc_bf16(BM, HID) | TB, false,
+                chain(tmem + C_SLOT, KT / 16, idesc_bf16(BM, HID) | TB, false,
                       [&](int kk) { return kmaj(sdl, BM, kk); }, [&](int kk) { return mnmaj(sw3, KO, kk); });
                 mma_commit(&bar);
             }
             if (!(ok = wait_mma(&bar, phase))) break;
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int col = half * 64 + c * 32;
-                mask_epilogue32(lane_base + C_SLOT + col, m2[c], smem + L.dz2, row, col);
-            }
+            mask_epilogue64(lane_base + C_SLOT + half * 64, smem + L.h2, smem + L.dz2, row, half * 64);
             sync_for_mma();
             if (tid == 0) {
                 // dW2 += H1^T dZ2;  db2 += dZ2^T 1;  dZ1 (before the mask) = dZ2 W2^T
@@ -488,21 +507,22 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
                 *reinterpret_cast<__nv_bfloat16*>(smem + L.dv + sw128_offset(0, row, 16)) = __float2bfloat16_rn(dv);
             }
             __syncthreads();
-            // dY2 = dv V3^T, masked by [g2 > 0]
+            // dY2 = dv V3^T, masked by [g2 > 0] (G2 is in the h2 buffer)
             {
                 const float dv = dv_s[row];
+                const __nv_bfloat162 zero = __floats2bfloat162_rn(0.0f, 0.0f);
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const int col = half * 64 + c * 32;
+                for (int q = 0; q < 8; ++q) {
+                    const int col = half * 64 + q * 8;
+                    const uint4 hq = *reinterpret_cast<const uint4*>(smem + L.h2 + sw128_offset(row, col, BM));
+                    const uint32_t hw[4] = {hq.x, hq.y, hq.z, hq.w};
+                    uint32_t wv[4];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        float y[8];
-#pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            y[j] = ((m2[c] >> (q * 8 + j)) & 1u) ? dv * bias[320 + col + q * 8 + j] : 0.0f;
-                        st_shared_v4(smem + L.dz2 + sw128_offset(row, col + q * 8, BM), pack2(y[0], y[1]),
-                                     pack2(y[2], y[3]), pack2(y[4], y[5]), pack2(y[6], y[7]));
+                    for (int j = 0; j < 4; ++j) {
+                        const float* v3 = bias + 320 + col + 2 * j;
+                        wv[j] = bf2_bits(__hmul2(__floats2bfloat162_rn(dv * v3[0], dv * v3[1]), __hgt2(bits_bf2(hw[j]), zero)));
                     }
+                    st_shared_v4(smem + L.dz2 + sw128_offset(row, col, BM), wv[0], wv[1], wv[2], wv[3]);
                 }
             }
             sync_for_mma();
@@ -523,11 +543,7 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
         }
         if (!(ok = wait_mma(&bar, phase))) break;
         // first-layer gradient of the pre-activation: dZ1 / dY1 into the h2 buffer
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int col = half * 64 + c * 32;
-            mask_epilogue32(lane_base + C_SLOT + col, m1[c], smem + L.h2, row, col);
-        }
+        mask_epilogue64(lane_base + C_SLOT + half * 64, smem + L.h1, smem + L.h2, row, half * 64);
         sync_for_mma();
         if (tid == 0) {
             // dW1^T += dZ1^T X (column I of X is 1: the first-layer bias gradient)
@@ -618,8 +634,8 @@ ej_status launch_ppo_bf16(const FbArgs& fa, float* partial, size_t partial_bytes
     if (fa.O > KO) return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: at most %d logits", KO);
     if (fa.n_heads < 1 || fa.n_heads > 4) return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: 1 to 4 action heads");
     if (fa.W > 2) return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: at most 2 mask words");
-    ej_status st = launch_adv_stats(fa.mb, fa.adv, fa.stats, s);
-    if (st != EJ_OK) return st;
+    ej_status st = EJ_OK;
+    if (!fa.rows && (st = launch_adv_stats(fa.mb, fa.adv, fa.stats, s)) != EJ_OK) return st;
     const NetOffsets off = net_offsets(fa.in_dim, HID, fa.O);
     const int n_tiles = (fa.mb.count + BM - 1) / BM;
     int per_role = sm_count() / 2;
@@ -631,17 +647,24 @@ ej_status launch_ppo_bf16(const FbArgs& fa, float* partial, size_t partial_bytes
     if ((size_t)2 * per_role * BM * PC * sizeof(float) > partial_bytes)
         return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: workspace too small for %d CTAs", 2 * per_role);
     const size_t smem = ppo_smem().total + 1024;
-    static size_t configured = 0;
-    if (configured < smem) {
-        cudaError_t err = cudaFuncSetAttribute(ppo_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static size_t configured[2] = {0, 0};
+    const int kt = fa.O <= 32 ? 0 : 1;
+    if (configured[kt] < smem) {
+        cudaError_t err = cudaFuncSetAttribute(kt == 0 ? ppo_bf16_kernel<32> : ppo_bf16_kernel<64>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
-        configured = smem;
+        configured[kt] = smem;
     }
     BfPpoArgs P;
     P.f = fa;
     P.partial = partial;
     P.n_actor = per_role;
-    ppo_bf16_kernel<<<2 * per_role, BT, smem, s>>>(P);
+    if (fa.rows) {
+        st = launch_mb_rows_stats(fa.mb, fa.adv, fa.rows, fa.stats, s);
+        if (st != EJ_OK) return st;
+    }
+    if (kt == 0) ppo_bf16_kernel<32><<<2 * per_role, BT, smem, s>>>(P);
+    else ppo_bf16_kernel<64><<<2 * per_role, BT, smem, s>>>(P);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "bf16 PPO launch: %s", cudaGetErrorString(err));
     ppo_bf16_reduce_kernel<<<128, 256, 0, s>>>(partial, per_role, per_role, fa.in_dim, fa.O, grad);
