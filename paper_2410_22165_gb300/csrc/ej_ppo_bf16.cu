@@ -242,22 +242,40 @@ struct ActorRow { float pg, ent, clip, kl; };
 // advantage and the entropy bonus; l is overwritten with d loss / d logits
 // (0 beyond O and at masked actions).  One exp per logit: e[k] = exp(l_k - max)
 // serves the normaliser, the entropy and the gradient.
-template <int KT>
-__device__ __forceinline__ ActorRow actor_row(const FbArgs& a, uint32_t row, float (&l)[KT], float mean,
-                                              float inv_std, float inv_n) {
-    uint32_t w0 = 0xFFFFFFFFu, w1 = 0xFFFFFFFFu;
+// Per-row inputs of the actor's loss, loaded at the start of a tile so that
+// their latency overlaps the forward products.
+struct RowIn {
+    uint32_t w0, w1;      // action-mask words (all ones without a mask)
+    int act0;             // action of head 0
+    float lpo, adv;       // log-probability at sampling time, raw advantage
+};
+
+__device__ __forceinline__ RowIn load_row_in(const FbArgs& a, uint32_t row, bool two_words) {
+    RowIn q;
+    q.w0 = 0xFFFFFFFFu;
+    q.w1 = 0xFFFFFFFFu;
     if (a.W) {
         const uint32_t* mw = a.mask + (size_t)row * a.W;
-        w0 = mw[0];
-        w1 = (KT > 32 && a.W > 1) ? mw[1] : 0u;
+        q.w0 = mw[0];
+        q.w1 = (two_words && a.W > 1) ? mw[1] : 0u;
     }
+    q.act0 = a.act[(size_t)row * a.n_heads];
+    q.lpo = a.logp_old[row];
+    q.adv = a.adv[row];
+    return q;
+}
+
+template <int KT>
+__device__ __forceinline__ ActorRow actor_row(const FbArgs& a, uint32_t row, const RowIn& in, float (&l)[KT],
+                                              float mean, float inv_std, float inv_n) {
+    const uint32_t w0 = in.w0, w1 = in.w1;
     auto valid = [&](int k) { return (((k < 32 ? w0 : w1) >> (k & 31)) & 1u) != 0; };
     float e[KT];
     Head4 lse, ent_h, rS;
     float logp = 0.0f, ent = 0.0f;
     for (int h = 0; h < a.n_heads; ++h) {
         const int lo = h * a.head, hi = lo + a.head;
-        const int act = lo + a.act[(size_t)row * a.n_heads + h];
+        const int act = lo + (h == 0 ? in.act0 : a.act[(size_t)row * a.n_heads + h]);
         float m = -FLT_MAX;
 #pragma unroll
         for (int k = 0; k < KT; ++k)
@@ -283,9 +301,9 @@ __device__ __forceinline__ ActorRow actor_row(const FbArgs& a, uint32_t row, flo
         rS.set(h, inv_S);
     }
     ActorRow st;
-    const float lpo = a.logp_old[row];
+    const float lpo = in.lpo;
     const float ratio = expf(logp - lpo);
-    const float an = (a.adv[row] - mean) * inv_std;
+    const float an = (in.adv - mean) * inv_std;
     const float cr = fminf(fmaxf(ratio, 1.0f - a.clip), 1.0f + a.clip);
     const float s1 = ratio * an, s2 = cr * an;
     st.pg = -fminf(s1, s2);
@@ -298,7 +316,7 @@ __device__ __forceinline__ ActorRow actor_row(const FbArgs& a, uint32_t row, flo
     const float ec = a.ent_coef * inv_n;
     for (int h = 0; h < a.n_heads; ++h) {
         const int lo = h * a.head, hi = lo + a.head;
-        const int act = lo + a.act[(size_t)row * a.n_heads + h];
+        const int act = lo + (h == 0 ? in.act0 : a.act[(size_t)row * a.n_heads + h]);
         const float o = lse.get(h), Hh = ent_h.get(h), inv_S = rS.get(h);
 #pragma unroll
         for (int k = 0; k < KT; ++k) {
@@ -321,7 +339,7 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bar;
     __shared__ uint32_t tmem_slot;
-    __shared__ uint32_t src_row[BM];
+    __shared__ uint32_t src_rows[2][BM];      // rollout rows of this tile and of the next
     __shared__ float red[5][BT / 32];
     const FbArgs& a = P.f;
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -383,6 +401,50 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
     uint32_t phase = 0;
     bool ok = true, first = true, pending = false;
     const int n_tiles = (a.mb.count + BM - 1) / BM;
+    // Inputs of the next tile are loaded into registers during the current one
+    // (when a tile's inputs fit two 8-column items per thread).
+    const int xchunks = I / 8 + 1;
+    const bool pf = xchunks * BM <= 2 * BT;
+    uint32_t* rows_cur = src_rows[0];
+    uint32_t* rows_nxt = src_rows[1];
+    float xv[2][8];
+    auto load_rows = [&](int t, uint32_t* dst) {
+        if (tid < BM) {
+            const int j = t * BM + tid;
+            dst[tid] = (t < n_tiles && j < a.mb.count) ? (a.rows ? a.rows[j] : mb_row(a.mb, j)) : 0u;
+        }
+    };
+    auto load_x = [&](int t, const uint32_t* rr) {
+        const int nr = t < n_tiles ? min(BM, a.mb.count - t * BM) : 0;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int it = tid + q * BT;
+            const int r = it % BM, c = it / BM;
+            const bool live = it < BM * xchunks && r < nr;
+            const float* src = a.x + (size_t)(live ? rr[r] : 0u) * I;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = c * 8 + u;
+                xv[q][u] = !live ? 0.0f : (k < I ? __ldg(src + k) : (k == I ? 1.0f : 0.0f));
+            }
+        }
+    };
+    auto store_x = [&]() {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int it = tid + q * BT;
+            if (it < BM * xchunks) {
+                const int r = it % BM, c = it / BM;
+                st_shared_v4(smem + L.x + sw128_offset(r, c * 8, BM), pack2(xv[q][0], xv[q][1]),
+                             pack2(xv[q][2], xv[q][3]), pack2(xv[q][4], xv[q][5]), pack2(xv[q][6], xv[q][7]));
+            }
+        }
+    };
+    if (pf && role_cta < n_tiles) {
+        load_rows(role_cta, rows_cur);
+        __syncthreads();
+        load_x(role_cta, rows_cur);
+    }
     for (int tile = role_cta; tile < n_tiles; tile += role_ctas) {
         const int j0 = tile * BM;
         const int nrows = min(BM, a.mb.count - j0);
@@ -391,21 +453,33 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
             if (!(ok = wait_mma(&bar, phase))) break;
             pending = false;
         }
-        if (tid < BM) src_row[tid] = tid < nrows ? (a.rows ? a.rows[j0 + tid] : mb_row(a.mb, j0 + tid)) : 0u;
-        __syncthreads();
-        // gathered rollout inputs -> x operand: inputs, then 1 (the bias column)
-        const int xchunks = I / 8 + 1;
-        for (int it = tid; it < BM * xchunks; it += BT) {
-            const int r = it % BM, c = it / BM;
-            float v[8];
-            const float* src = a.x + (size_t)src_row[r] * I;
+        if (pf) {
+            store_x();
+        } else {
+            load_rows(tile, rows_cur);
+            __syncthreads();
+            // gathered rollout inputs -> x operand: inputs, then 1 (the bias column)
+            for (int it = tid; it < BM * xchunks; it += BT) {
+                const int r = it % BM, c = it / BM;
+                float v[8];
+                const float* src = a.x + (size_t)rows_cur[r] * I;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int k = c * 8 + q;
-                v[q] = r >= nrows ? 0.0f : (k < I ? __ldg(src + k) : (k == I ? 1.0f : 0.0f));
+                for (int q = 0; q < 8; ++q) {
+                    const int k = c * 8 + q;
+                    v[q] = r >= nrows ? 0.0f : (k < I ? __ldg(src + k) : (k == I ? 1.0f : 0.0f));
+                }
+                st_shared_v4(smem + L.x + sw128_offset(r, c * 8, BM), pack2(v[0], v[1]), pack2(v[2], v[3]),
+                             pack2(v[4], v[5]), pack2(v[6], v[7]));
             }
-            st_shared_v4(smem + L.x + sw128_offset(r, c * 8, BM), pack2(v[0], v[1]), pack2(v[2], v[3]),
-                         pack2(v[4], v[5]), pack2(v[6], v[7]));
+        }
+        // this thread's row's loss inputs (used after the forward pass)
+        const uint32_t my_src = rows_cur[row];
+        const bool my_live = half == 0 && row < nrows;
+        RowIn rin;
+        float v_old = 0.0f, ret = 0.0f;
+        if (my_live) {
+            if (actor) rin = load_row_in(a, my_src, KT > 32);
+            else { v_old = a.v_old[my_src]; ret = a.ret[my_src]; }
         }
         sync_for_mma();
         // layer 1
@@ -414,6 +488,7 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
                   [&](int kk) { return kmaj(sw1, HID, kk); });
             mma_commit(&bar);
         }
+        if (pf) load_rows(tile + role_ctas, rows_nxt);   // visible after the next barrier
         if (!(ok = wait_mma(&bar, phase))) break;
         relu_epilogue64(lane_base + C_SLOT + half * 64, bias + half * 64, smem + L.h1, row, half * 64);
         sync_for_mma();
@@ -423,6 +498,7 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
                   [&](int kk) { return kmaj(sw2, HID, kk); });
             mma_commit(&bar);
         }
+        if (pf) load_x(tile + role_ctas, rows_nxt);      // the next tile's inputs, into registers
         if (!(ok = wait_mma(&bar, phase))) break;
         relu_epilogue64(lane_base + C_SLOT + half * 64, bias + HID + half * 64, smem + L.h2, row, half * 64);
         sync_for_mma();
@@ -445,7 +521,7 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
 #pragma unroll
                 for (int k = 0; k < KT; ++k) l[k] = k < O ? l[k] + bias[2 * HID + k] : 0.0f;
                 if (row < nrows) {
-                    const ActorRow s = actor_row<KT>(a, src_row[row], l, mean, inv_std, inv_n);
+                    const ActorRow s = actor_row<KT>(a, my_src, rin, l, mean, inv_std, inv_n);
                     acc_st[0] += s.pg; acc_st[2] += s.ent; acc_st[3] += s.clip; acc_st[4] += s.kl;
                 } else {
 #pragma unroll
@@ -495,8 +571,7 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
                 float dv = 0.0f;
                 if (row < nrows) {
                     // Section 4 clipped value loss, 0.5 max((v - R)^2, (v_clipped - R)^2)
-                    const uint32_t r = src_row[row];
-                    const float v = vv[0] + bias[2 * HID], vo = a.v_old[r], R = a.ret[r];
+                    const float v = vv[0] + bias[2 * HID], vo = v_old, R = ret;
                     const float dvv = v - vo;
                     const float vc = vo + fminf(fmaxf(dvv, -a.vclip), a.vclip);
                     const float la = (v - R) * (v - R), lb = (vc - R) * (vc - R);
@@ -553,6 +628,9 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
         }
         pending = true;
         first = false;
+        uint32_t* tmp = rows_cur;
+        rows_cur = rows_nxt;
+        rows_nxt = tmp;
     }
     if (ok && pending) ok = wait_mma(&bar, phase);
     if (ok) {
