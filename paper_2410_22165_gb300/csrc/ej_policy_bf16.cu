@@ -258,6 +258,278 @@ __global__ void __launch_bounds__(BT, 1) policy_bf16_kernel(PolicyArgs a) {
     if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
 }
 
+// ---------------------------------------------------------------------------
+// Fast path for up to 64 logits and 32 inputs: the next tile's observations
+// are loaded (coalesced 16-byte loads of the tile's contiguous rows) into
+// registers while the current tile runs; ReLU epilogues on BF16 pairs; the
+// sampler reads the logits from registers (same operations, same order as
+// sample_head, so the drawn action is the same); the critic warpgroup writes
+// the value.
+
+template <int KT>
+__device__ __forceinline__ int sample_head_reg(const float (&l)[KT], int lo, int K, uint32_t w0, uint32_t w1,
+                                               float u, float& logp, float& ent) {
+    auto ok = [&](int j) { return j >= lo && j < lo + K && ((((j < 32 ? w0 : w1) >> (j & 31)) & 1u) != 0); };
+    float m = -FLT_MAX;
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < KT; ++j)
+        if (ok(j)) { any = true; m = fmaxf(m, l[j]); }
+    if (!any) return -1;
+    float S = 0.0f, dot = 0.0f;
+    float wv[KT];
+#pragma unroll
+    for (int j = 0; j < KT; ++j) {
+        wv[j] = -1.0f;
+        if (ok(j)) {
+            const float d = __fsub_rn(l[j], m);
+            wv[j] = exp32(d);
+            S = __fadd_rn(S, wv[j]);
+            dot = fmaf(wv[j], d, dot);
+        }
+    }
+    const float thr = __fmul_rn(u, S);
+    float c = 0.0f, la = 0.0f, ll = 0.0f;
+    int act = -1, last = -1;
+#pragma unroll
+    for (int j = 0; j < KT; ++j) {
+        if (wv[j] >= 0.0f) {
+            last = j;
+            ll = l[j];
+            c = __fadd_rn(c, wv[j]);
+            if (act < 0 && c > thr) { act = j; la = l[j]; }
+        }
+    }
+    if (act < 0) { act = last; la = ll; }
+    const float logS = logf(S);
+    logp += (la - m) - logS;
+    ent += logS - dot / S;
+    return act - lo;
+}
+
+template <int KT>
+__global__ void __launch_bounds__(BT, 1) policy_bf16_fast_kernel(PolicyArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row_in_tile = quarter * 32 + lane;
+    const int H = a.H, O = a.O, I = a.in_dim;
+    const BfLayout L = bf_layout(H, O);
+    const NetOffsets off = net_offsets(I, H, O);
+    const float* w = a.weights;
+
+    pack_operand(smem + L.w1, 2 * H, KX, [&](int n, int k) {
+        if (k >= I) return 0.0f;
+        return n < H ? __ldg(w + off.W1 + (size_t)k * H + n) : __ldg(w + off.V1 + (size_t)k * H + (n - H));
+    });
+    pack_operand(smem + L.w2a, H, H, [&](int n, int k) { return __ldg(w + off.W2 + (size_t)k * H + n); });
+    pack_operand(smem + L.w2c, H, H, [&](int n, int k) { return __ldg(w + off.V2 + (size_t)k * H + n); });
+    pack_operand(smem + L.w3, L.N3, H, [&](int n, int k) {
+        return n < O ? __ldg(w + off.W3 + (size_t)k * O + n) : 0.0f;
+    });
+    pack_operand(smem + L.v3, 16, H, [&](int n, int k) { return n == 0 ? __ldg(w + off.V3 + k) : 0.0f; });
+    float* bias = (float*)(smem + L.bias);
+    for (int k = tid; k < 4 * H + O + 1; k += BT) {
+        float v;
+        if (k < H) v = w[off.b1 + k];
+        else if (k < 2 * H) v = w[off.c1 + k - H];
+        else if (k < 3 * H) v = w[off.b2 + k - 2 * H];
+        else if (k < 4 * H) v = w[off.c2 + k - 3 * H];
+        else if (k < 4 * H + O) v = w[off.b3 + k - 4 * H];
+        else v = w[off.c3];
+        bias[k] = v;
+    }
+    for (int k = tid; k < BM * KX * 2 / 16; k += BT) st_shared_v4(smem + L.x + k * 16, 0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_slot, TMEM_COLS);
+    sync_for_mma();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    const uint32_t sx = smem_u32(smem + L.x), sh = smem_u32(smem + L.h);
+    const uint32_t sw1 = smem_u32(smem + L.w1), sw2a = smem_u32(smem + L.w2a), sw2c = smem_u32(smem + L.w2c);
+    const uint32_t sw3 = smem_u32(smem + L.w3), sv3 = smem_u32(smem + L.v3);
+    const __nv_bfloat162 zero2 = __floats2bfloat162_rn(0.0f, 0.0f);
+
+    // observations of a tile: its rows are contiguous; 4 float4 slots per thread
+    float4 xr[4];
+    auto load_obs = [&](int tile) {
+        const int row0 = tile * BM;
+        const int n = tile < (a.rows + BM - 1) / BM ? min(BM, a.rows - row0) * I : 0;
+        const float* src = a.x + (size_t)row0 * I;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int f = (tid + q * BT) * 4;
+            if (f + 3 < n) {
+                xr[q] = __ldg(reinterpret_cast<const float4*>(src + f));
+            } else {
+                xr[q].x = f < n ? __ldg(src + f) : 0.0f;
+                xr[q].y = f + 1 < n ? __ldg(src + f + 1) : 0.0f;
+                xr[q].z = f + 2 < n ? __ldg(src + f + 2) : 0.0f;
+                xr[q].w = f + 3 < n ? __ldg(src + f + 3) : 0.0f;
+            }
+        }
+    };
+    auto store_obs = [&]() {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int f = (tid + q * BT) * 4;
+            if (f < BM * I) {
+                int r = f / I, c = f - r * I;
+                const float v[4] = {xr[q].x, xr[q].y, xr[q].z, xr[q].w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (r < BM)
+                        *reinterpret_cast<__nv_bfloat16*>(smem + L.x + sw128_offset(r, c, BM)) = __float2bfloat16_rn(v[j]);
+                    if (++c == I) { c = 0; ++r; }
+                }
+            }
+        }
+    };
+
+    uint32_t phase = 0;
+    bool ok = true;
+    const int n_tiles = (a.rows + BM - 1) / BM;
+    if ((int)blockIdx.x < n_tiles) load_obs(blockIdx.x);
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int row0 = tile * BM;
+        const int nrows = min(BM, a.rows - row0);
+        store_obs();
+        // this thread's row: sampling inputs, loaded early
+        const int grow = row0 + row_in_tile;
+        const bool live = row_in_tile < nrows;
+        uint32_t w0 = 0xFFFFFFFFu, w1 = 0xFFFFFFFFu;
+        float us[EJ_MAX_NB] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (half == 0 && live && a.act) {
+            if (a.W) {
+                const uint32_t* mw = a.mask + (size_t)grow * a.W;
+                w0 = mw[0];
+                w1 = (KT > 32 && a.W > 1) ? mw[1] : 0u;
+            }
+            if (a.u) {
+#pragma unroll
+                for (int h = 0; h < EJ_MAX_NB; ++h)
+                    if (h < a.n_heads) us[h] = a.u[(size_t)grow * a.n_heads + h];
+            } else {
+                const int e = grow / a.per_env, i = grow % a.per_env;
+                const uint4 x = philox4x32_10(make_uint4(a.stream_id == 0 ? (uint32_t)i : 0u, (uint32_t)e, a.gstep[e],
+                                                         (uint32_t)a.stream_id), a.key[0], a.key[1]);
+                if (a.stream_id == 0) us[0] = u01(x.w);
+                else { us[0] = u01(x.x); us[1] = u01(x.y); us[2] = u01(x.z); us[3] = u01(x.w); }
+            }
+        }
+        sync_for_mma();
+        if (tid == 0) {
+            mma_chain(tmem, sx, BM, sw1, 2 * H, KX, idesc_bf16(BM, 2 * H));
+            mma_commit(&bar);
+        }
+        if (tile + (int)gridDim.x < n_tiles) load_obs(tile + gridDim.x);   // next tile, into registers
+        if (!(ok = wait_mma(&bar, phase))) break;
+        // layer-1 epilogue: this warpgroup's network (half 0 actor, half 1 critic), bias + ReLU on BF16 pairs
+        for (int c = 0; c < H / 32; ++c) {
+            const int col = half * H + c * 32;
+            float v[32];
+            tmem_ld32(lane_base + col, v);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t pk[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int k = q * 8 + 2 * j;
+                    const __nv_bfloat162 y = __hmax2(__floats2bfloat162_rn(v[k] + bias[col + k], v[k + 1] + bias[col + k + 1]), zero2);
+                    pk[j] = *reinterpret_cast<const uint32_t*>(&y);
+                }
+                st_shared_v4(smem + L.h + sw128_offset(row_in_tile, col + q * 8, BM), pk[0], pk[1], pk[2], pk[3]);
+            }
+        }
+        sync_for_mma();
+        if (tid == 0) {
+            mma_chain(tmem, sh, BM, sw2a, H, H, idesc_bf16(BM, H));
+            mma_chain(tmem + H, sh + (H / 64) * (BM / 8) * 1024, BM, sw2c, H, H, idesc_bf16(BM, H));
+            mma_commit(&bar);
+        }
+        if (!(ok = wait_mma(&bar, phase))) break;
+        for (int c = 0; c < H / 32; ++c) {
+            const int col = half * H + c * 32;
+            float v[32];
+            tmem_ld32(lane_base + col, v);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t pk[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int k = q * 8 + 2 * j;
+                    const __nv_bfloat162 y = __hmax2(__floats2bfloat162_rn(v[k] + bias[2 * H + col + k],
+                                                                           v[k + 1] + bias[2 * H + col + k + 1]), zero2);
+                    pk[j] = *reinterpret_cast<const uint32_t*>(&y);
+                }
+                st_shared_v4(smem + L.h + sw128_offset(row_in_tile, col + q * 8, BM), pk[0], pk[1], pk[2], pk[3]);
+            }
+        }
+        sync_for_mma();
+        if (tid == 0) {
+            mma_chain(tmem + COL_D3, sh, BM, sw3, L.N3, H, idesc_bf16(BM, L.N3));
+            mma_chain(tmem + COL_D4, sh + (H / 64) * (BM / 8) * 1024, BM, sv3, 16, H, idesc_bf16(BM, 16));
+            mma_commit(&bar);
+        }
+        if (!(ok = wait_mma(&bar, phase))) break;
+        if (half == 0) {
+            float l[KT];
+            {
+                float v[32];
+                tmem_ld32(lane_base + COL_D3, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) l[j] = v[j];
+                if constexpr (KT == 64) {
+                    tmem_ld32(lane_base + COL_D3 + 32, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) l[32 + j] = v[j];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < KT; ++j) l[j] = j < O ? l[j] + bias[4 * H + j] : 0.0f;
+            if (live) {
+                if (a.logits) {
+#pragma unroll
+                    for (int j = 0; j < KT; ++j)
+                        if (j < O) a.logits[(size_t)grow * O + j] = l[j];
+                }
+                if (a.act) {
+                    float logp = 0.0f, ent = 0.0f;
+                    bool none = false;
+                    for (int h = 0; h < a.n_heads; ++h) {
+                        const float uh = h == 0 ? us[0] : h == 1 ? us[1] : h == 2 ? us[2] : us[3];
+                        int act = sample_head_reg<KT>(l, h * a.head, a.head, w0, w1, uh, logp, ent);
+                        if (act < 0) { act = 0; none = true; }
+                        a.act[(size_t)grow * a.n_heads + h] = act;
+                    }
+                    if (none) { logp = 0.0f; ent = 0.0f; }
+                    a.logp[grow] = logp;
+                    if (a.entropy) a.entropy[grow] = ent;
+                }
+            }
+        } else {
+            // tcgen05.ld is warp-collective: every lane loads, live rows store
+            float vv[32];
+            tmem_ld32(lane_base + COL_D4, vv);
+            if (live) a.value[grow] = vv[0] + bias[4 * H + O];
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
+    if (!ok) mbar_wait(&bar, phase, 200000000LL);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
 }  // namespace
 
 size_t policy_bf16_smem(int H, int O) { return bf_layout(H, O).total + 1024; }
@@ -279,6 +551,22 @@ ej_status launch_policy_bf16(const PolicyArgs& a, cudaStream_t stream) {
     const int n_tiles = (a.rows + BM - 1) / BM;
     int grid = n_tiles < 152 ? n_tiles : 152;
     if (grid < 1) grid = 1;
+    const bool fast = a.O <= 64 && a.in_dim <= 32 && a.W <= 2 && a.n_heads <= EJ_MAX_NB && ((uintptr_t)a.x & 15) == 0;
+    if (fast) {
+        static size_t conf_fast[2] = {0, 0};
+        const int kt = a.O <= 32 ? 0 : 1;
+        if (conf_fast[kt] < smem) {
+            cudaError_t err = cudaFuncSetAttribute(kt == 0 ? policy_bf16_fast_kernel<32> : policy_bf16_fast_kernel<64>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
+            conf_fast[kt] = smem;
+        }
+        if (kt == 0) policy_bf16_fast_kernel<32><<<grid, BT, smem, stream>>>(a);
+        else policy_bf16_fast_kernel<64><<<grid, BT, smem, stream>>>(a);
+        cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "bf16 policy launch: %s", cudaGetErrorString(err));
+        return EJ_OK;
+    }
     policy_bf16_kernel<<<grid, BT, smem, stream>>>(a);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "bf16 policy launch: %s", cudaGetErrorString(err));
