@@ -337,6 +337,29 @@ ej_status ppo_minibatch_grad(const EjParams* p, const EjPpoParams* pp, int32_t T
                              const EjRollout* buf, void* workspace, uint32_t shuffle_ctr,
                              int32_t minibatch, float* grad, double* stats_out, void* stream);
 
+/* Data-parallel form of the minibatch gradient (the exchange step of a
+ * multi-GPU update; Section 4's loss over the union of the ranks' minibatch
+ * rows).  Each rank runs ppo_advantages on its own rollout, then per
+ * minibatch and network:
+ *   ppo_minibatch_moments: moments (device double[3]) = {rows of this rank's
+ *     minibatch, sum of their GAE advantages, sum of squares};
+ *   the caller sums the moments over the ranks (an all-reduce);
+ *   ppo_minibatch_grad_global: this rank's part of the gradient of the union
+ *     minibatch's loss: advantages normalised with the summed moments, means
+ *     taken over moments[0] rows.  Summed over the ranks (a second
+ *     all-reduce) it is the gradient of the union minibatch; with one rank and
+ *     its own moments it equals ppo_minibatch_grad.
+ * Arguments and errors otherwise as ppo_minibatch_grad; stats_out holds this
+ * rank's sums. */
+ej_status ppo_minibatch_moments(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_t net,
+                                const EjRollout* buf, void* workspace, uint32_t shuffle_ctr,
+                                int32_t minibatch, double* moments, void* stream);
+ej_status ppo_minibatch_grad_global(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_t hidden,
+                                    int32_t precision, int32_t net, const float* weights,
+                                    const EjRollout* buf, void* workspace, uint32_t shuffle_ctr,
+                                    int32_t minibatch, const double* moments, float* grad,
+                                    double* stats_out, void* stream);
+
 /* One Adam step (Kingma and Ba, 2015) over n parameters; step counts from 1. */
 ej_status adam_step(uint64_t n, float* params, const float* grad, float* m, float* v, int32_t step,
                     float lr, float beta1, float beta2, float eps, void* stream);

@@ -63,7 +63,7 @@ def bf16_round(a):
 
 
 def ppo_loss_grad64(w, x, act, valid, logp_old, v_old, adv, ret, *, clip, vf_coef, vclip,
-                    ent_coef, heads=1, head=None, normalize_adv=True, operand=None):
+                    ent_coef, heads=1, head=None, normalize_adv=True, operand=None, moments=None):
     """Loss (float) and gradients (dict like w) of one minibatch.
 
     x [N, in], act [N, heads] int, valid [N, heads*head] bool, logp_old [N],
@@ -72,7 +72,14 @@ def ppo_loss_grad64(w, x, act, valid, logp_old, v_old, adv, ret, *, clip, vf_coe
     operand: applied to every matrix-product operand (weights, inputs,
     activations, backward signals) before the product; None = exact.  With
     bf16_round this is the BF16-operand form: operands rounded to bfloat16,
-    products and sums in float64."""
+    products and sums in float64.
+
+    moments: None, or (n, sum, sum of squares) of the advantages of a larger
+    minibatch these rows belong to (the union over the ranks of a
+    data-parallel update): advantages are normalised with its mean and
+    population std and every mean is over its n rows, so the returned loss and
+    gradient are these rows' part of the larger minibatch's (parts sum to the
+    whole)."""
     R = operand if operand is not None else (lambda t: t)
     x = np.asarray(x, np.float64)
     N = x.shape[0]
@@ -80,8 +87,16 @@ def ppo_loss_grad64(w, x, act, valid, logp_old, v_old, adv, ret, *, clip, vf_coe
     if head is None:
         head = valid.shape[1] // heads
     a = np.asarray(adv, np.float64)
-    if normalize_adv:
-        a = (a - a.mean()) / (a.std() + 1e-8)
+    if moments is not None:
+        n_tot = float(moments[0])
+        mu = float(moments[1]) / n_tot
+        sd = np.sqrt(max(float(moments[2]) / n_tot - mu * mu, 0.0))
+        if normalize_adv:
+            a = (a - mu) / (sd + 1e-8)
+    else:
+        n_tot = float(N)
+        if normalize_adv:
+            a = (a - a.mean()) / (a.std() + 1e-8)
     # forward
     x = R(x)
     W1, W2, W3 = R(w["W1"]), R(w["W2"]), R(w["W3"])
@@ -100,11 +115,11 @@ def ppo_loss_grad64(w, x, act, valid, logp_old, v_old, adv, ret, *, clip, vf_coe
     vc = v_old + np.clip(v - v_old, -vclip, vclip)
     la, lb = (v - ret) ** 2, (vc - ret) ** 2
     lv = 0.5 * np.maximum(la, lb)
-    loss = -surr.mean() + vf_coef * lv.mean() - ent_coef * ent.mean()
+    loss = (-surr.sum() + vf_coef * lv.sum() - ent_coef * ent.sum()) / n_tot
     # backward: d loss / d logp, d logits, d value
     unclipped = ratio * a <= cr * a
     inside = (ratio > 1 - clip) & (ratio < 1 + clip)
-    dratio = np.where(unclipped, -a, np.where(inside, -a, 0.0)) / N
+    dratio = np.where(unclipped, -a, np.where(inside, -a, 0.0)) / n_tot
     dlogp = dratio * ratio
     dlog = np.zeros_like(logits)
     for h in range(heads):
@@ -112,9 +127,9 @@ def ppo_loss_grad64(w, x, act, valid, logp_old, v_old, adv, ret, *, clip, vf_coe
         onehot = np.zeros((N, head)); onehot[np.arange(N), act[:, h]] = 1.0
         dlog[:, sl] = dlogp[:, None] * (onehot - p[:, sl])
         Hh = -(p[:, sl] * logp_all[:, sl]).sum(1)
-        dlog[:, sl] += (ent_coef / N) * p[:, sl] * (logp_all[:, sl] + Hh[:, None])
+        dlog[:, sl] += (ent_coef / n_tot) * p[:, sl] * (logp_all[:, sl] + Hh[:, None])
     dlog = np.where(valid, dlog, 0.0)
-    dv = np.where(la >= lb, v - ret, (vc - ret) * (np.abs(v - v_old) < vclip)) * (vf_coef / N)
+    dv = np.where(la >= lb, v - ret, (vc - ret) * (np.abs(v - v_old) < vclip)) * (vf_coef / n_tot)
     g = {}
     dlog = R(dlog)
     g["W3"] = h2.T @ dlog; g["b3"] = dlog.sum(0)

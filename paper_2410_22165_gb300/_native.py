@@ -90,6 +90,11 @@ _PROTOS = {
     "ppo_minibatch_grad": (C.c_int, [C.POINTER(EjParams), C.POINTER(EjPpoParams), C.c_int32, C.c_int32,
                                      C.c_int32, C.c_int32, _VP, C.c_void_p, _VP, C.c_uint32, C.c_int32,
                                      _VP, _VP, _VP]),
+    "ppo_minibatch_moments": (C.c_int, [C.POINTER(EjParams), C.POINTER(EjPpoParams), C.c_int32, C.c_int32,
+                                        C.c_void_p, _VP, C.c_uint32, C.c_int32, _VP, _VP]),
+    "ppo_minibatch_grad_global": (C.c_int, [C.POINTER(EjParams), C.POINTER(EjPpoParams), C.c_int32, C.c_int32,
+                                            C.c_int32, C.c_int32, _VP, C.c_void_p, _VP, C.c_uint32, C.c_int32,
+                                            _VP, _VP, _VP, _VP]),
     "adam_step": (C.c_int, [C.c_uint64, _VP, _VP, _VP, _VP, C.c_int32, C.c_float, C.c_float, C.c_float,
                             C.c_float, _VP]),
     "ppo_update": (C.c_int, [C.POINTER(EjParams), C.POINTER(EjPpoParams), C.c_int32, C.c_int32, C.c_int32,

@@ -107,11 +107,15 @@ __global__ void __launch_bounds__(NTH, 1) fwd_bwd_kernel(FbArgs a) {
     __shared__ float red[8][NTH / 32];
     const NetOffsets off = net_offsets(I, H, O);
     const float* w = a.weights;
-    const double n = (double)a.mb.count;
-    const float mean = (float)(a.stats[ST_ADV_SUM] / n);
-    const float var = (float)fmax(a.stats[ST_ADV_SQ] / n - (a.stats[ST_ADV_SUM] / n) * (a.stats[ST_ADV_SUM] / n), 0.0);
+    // advantage moments over the minibatch (or over the union of the ranks'
+    // minibatches, when given: count, sum, sum of squares)
+    const double n = a.moments ? a.moments[0] : (double)a.mb.count;
+    const double m1 = a.moments ? a.moments[1] : a.stats[ST_ADV_SUM];
+    const double m2 = a.moments ? a.moments[2] : a.stats[ST_ADV_SQ];
+    const float mean = (float)(m1 / n);
+    const float var = (float)fmax(m2 / n - (m1 / n) * (m1 / n), 0.0);
     const float inv_std = 1.0f / (sqrtf(var) + 1e-8f);
-    const float inv_n = 1.0f / (float)a.mb.count;
+    const float inv_n = 1.0f / (float)n;
     const int n_tiles = (a.mb.count + TILE - 1) / TILE;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int j0 = tile * TILE;

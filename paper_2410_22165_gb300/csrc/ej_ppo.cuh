@@ -53,6 +53,7 @@ struct FbArgs {
     const float* ret;           // [N]
     float* w3t; float* w2t; float* v2t;       // transposed weights (workspace)
     double* stats;              // [ST_COUNT_]
+    const double* moments;      // NULL, or {count, sum, sum of squares} of the advantages over all ranks
     float* ws_x; float* ws_h1; float* ws_h2; float* ws_g1; float* ws_g2;
     float* ws_dl; float* ws_dz2; float* ws_dz1; float* ws_dy2; float* ws_dy1; float* ws_dv;
 };

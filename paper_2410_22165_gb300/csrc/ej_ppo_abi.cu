@@ -88,21 +88,38 @@ ej_status check_common(const EjParams* p, const EjPpoParams* pp, int T, int H, L
     return EJ_OK;
 }
 
+// Minibatch m of the permutation keyed by (seed, ctr) over the T x rows-per-step rows of `net`.
+MbDesc mb_desc(const KParams& kp, const EjPpoParams* pp, int T, int net, uint32_t ctr, int m) {
+    const NetDims d = dims(kp, net);
+    const uint64_t N = (uint64_t)T * d.rows_per_step;
+    MbDesc mb;
+    mb.lo = (int)((N * m) / pp->minibatches);
+    mb.count = (int)((N * (m + 1)) / pp->minibatches) - mb.lo;
+    mb.N = (uint32_t)N;
+    mb.half = half_bits(N);
+    mb.k0 = (uint32_t)pp->seed;
+    mb.k1 = (uint32_t)(pp->seed >> 32);
+    mb.ctr = ctr;
+    return mb;
+}
+
+__global__ void moments_out_kernel(const double* stats, int count, double* out) {
+    if (threadIdx.x == 0) {
+        out[0] = (double)count;
+        out[1] = stats[ST_ADV_SUM];
+        out[2] = stats[ST_ADV_SQ];
+    }
+}
+
 ej_status minibatch_grad(const KParams& kp, const EjPpoParams* pp, int T, int H, int precision, int net,
                          const float* weights, const EjRollout* b, char* ws, const Ws& W, uint32_t ctr,
-                         int m, float* grad, double* stats, cudaStream_t s) {
+                         int m, float* grad, double* stats, cudaStream_t s, const double* moments = nullptr) {
     const NetDims d = dims(kp, net);
     const NetOffsets off = net_offsets(d.in, H, d.O);
-    const uint64_t N = (uint64_t)T * d.rows_per_step;
     FbArgs fa;
     memset(&fa, 0, sizeof fa);
-    fa.mb.lo = (int)((N * m) / pp->minibatches);
-    fa.mb.count = (int)((N * (m + 1)) / pp->minibatches) - fa.mb.lo;
-    fa.mb.N = (uint32_t)N;
-    fa.mb.half = half_bits(N);
-    fa.mb.k0 = (uint32_t)pp->seed;
-    fa.mb.k1 = (uint32_t)(pp->seed >> 32);
-    fa.mb.ctr = ctr;
+    fa.mb = mb_desc(kp, pp, T, net, ctr, m);
+    fa.moments = moments;
     fa.in_dim = d.in; fa.in_pad = (d.in + 3) & ~3; fa.H = H; fa.O = d.O;
     fa.n_heads = d.heads; fa.head = d.head; fa.W = net == EJ_NET_POP ? kp.W : 0;
     fa.clip = pp->clip; fa.vf_coef = pp->vf_coef; fa.vclip = pp->vclip; fa.ent_coef = pp->ent_coef;
@@ -240,6 +257,54 @@ ej_status ppo_minibatch_grad(const EjParams* p, const EjPpoParams* pp, int32_t T
     cudaStream_t s = (cudaStream_t)stream;
     double* stats = (double*)(ws + W.stats[net]);
     st = minibatch_grad(kp, pp, T, hidden, precision, net, weights, b, ws, W, shuffle_ctr, minibatch, grad, stats, s);
+    if (st != EJ_OK) return st;
+    if (stats_out) {
+        if (cudaMemcpyAsync(stats_out, stats, sizeof(double) * ST_COUNT_, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return fail(EJ_ERR_CUDA, "stats copy failed");
+    }
+    return EJ_OK;
+}
+
+ej_status ppo_minibatch_moments(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_t net,
+                                const EjRollout* b, void* workspace, uint32_t shuffle_ctr, int32_t minibatch,
+                                double* moments, void* stream) {
+    Layout lay;
+    KParams kp;
+    ej_status st = check_common(p, pp, T, 128, &lay, &kp);
+    if (st != EJ_OK) return st;
+    if (net != EJ_NET_POP && net != EJ_NET_GOV) return fail(EJ_ERR_ARG, "unknown network %d", net);
+    if (!b || !workspace || !moments) return fail(EJ_ERR_ARG, "NULL argument");
+    if ((uintptr_t)workspace % 256) return fail(EJ_ERR_ARG, "misaligned workspace");
+    if (minibatch < 0 || minibatch >= pp->minibatches) return fail(EJ_ERR_ARG, "minibatch out of range");
+    const Ws W = ws_layout(kp, pp, T, 128);
+    char* ws = (char*)workspace;
+    cudaStream_t s = (cudaStream_t)stream;
+    const MbDesc mb = mb_desc(kp, pp, T, net, shuffle_ctr, minibatch);
+    double* stats = (double*)(ws + W.stats[net]);
+    if ((st = launch_adv_stats(mb, (const float*)(ws + W.adv[net]), stats, s)) != EJ_OK) return st;
+    moments_out_kernel<<<1, 32, 0, s>>>(stats, mb.count, moments);
+    return cudaGetLastError() == cudaSuccess ? EJ_OK : fail(EJ_ERR_CUDA, "moments launch failed");
+}
+
+ej_status ppo_minibatch_grad_global(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_t hidden,
+                                    int32_t precision, int32_t net, const float* weights, const EjRollout* b,
+                                    void* workspace, uint32_t shuffle_ctr, int32_t minibatch,
+                                    const double* moments, float* grad, double* stats_out, void* stream) {
+    Layout lay;
+    KParams kp;
+    ej_status st = check_common(p, pp, T, hidden, &lay, &kp);
+    if (st != EJ_OK) return st;
+    if (precision != EJ_FP32 && precision != EJ_BF16) return fail(EJ_ERR_ARG, "unknown precision %d", precision);
+    if (net != EJ_NET_POP && net != EJ_NET_GOV) return fail(EJ_ERR_ARG, "unknown network %d", net);
+    if (!b || !workspace || !weights || !grad || !moments) return fail(EJ_ERR_ARG, "NULL argument");
+    if ((uintptr_t)workspace % 256 || (uintptr_t)weights % 16) return fail(EJ_ERR_ARG, "misaligned buffer");
+    if (minibatch < 0 || minibatch >= pp->minibatches) return fail(EJ_ERR_ARG, "minibatch out of range");
+    const Ws W = ws_layout(kp, pp, T, hidden);
+    char* ws = (char*)workspace;
+    cudaStream_t s = (cudaStream_t)stream;
+    double* stats = (double*)(ws + W.stats[net]);
+    st = minibatch_grad(kp, pp, T, hidden, precision, net, weights, b, ws, W, shuffle_ctr, minibatch, grad, stats, s,
+                        moments);
     if (st != EJ_OK) return st;
     if (stats_out) {
         if (cudaMemcpyAsync(stats_out, stats, sizeof(double) * ST_COUNT_, cudaMemcpyDeviceToDevice, s) != cudaSuccess)

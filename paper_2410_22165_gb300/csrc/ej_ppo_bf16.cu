@@ -391,11 +391,15 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
     const uint32_t sdl = smem_u32(smem + L.dl), sdz2 = smem_u32(smem + L.dz2), sones = smem_u32(smem + L.ones);
     const uint32_t sdv = smem_u32(smem + L.dv);
 
-    const double nrows_mb = (double)a.mb.count;
-    const float mean = (float)(a.stats[ST_ADV_SUM] / nrows_mb);
-    const float var = (float)fmax(a.stats[ST_ADV_SQ] / nrows_mb - (a.stats[ST_ADV_SUM] / nrows_mb) * (a.stats[ST_ADV_SUM] / nrows_mb), 0.0);
+    // advantage moments over the minibatch (or over the union of the ranks'
+    // minibatches, when given: count, sum, sum of squares)
+    const double nrows_mb = a.moments ? a.moments[0] : (double)a.mb.count;
+    const double m1 = a.moments ? a.moments[1] : a.stats[ST_ADV_SUM];
+    const double m2 = a.moments ? a.moments[2] : a.stats[ST_ADV_SQ];
+    const float mean = (float)(m1 / nrows_mb);
+    const float var = (float)fmax(m2 / nrows_mb - (m1 / nrows_mb) * (m1 / nrows_mb), 0.0);
     const float inv_std = 1.0f / (sqrtf(var) + 1e-8f);
-    const float inv_n = 1.0f / (float)a.mb.count;
+    const float inv_n = 1.0f / (float)nrows_mb;
 
     float acc_st[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};   // pg, vf, ent, clip, kl of this thread's rows
     uint32_t phase = 0;

@@ -57,20 +57,46 @@ class PPO:
         M = self.pp.minibatches
         return (minibatch + 1) * n // M - minibatch * n // M
 
+    def minibatch_moments(self, rollout: Rollout, net: int, shuffle_ctr: int, minibatch: int, stream=None):
+        """{rows, sum, sum of squares} of this minibatch's advantages (device float64[3])."""
+        m = torch.empty(3, dtype=torch.float64, device=self.env.device)
+        N.check(N.load().ppo_minibatch_moments(C.byref(self.env.p), C.byref(self.pp), self.T, net,
+                                               C.byref(rollout._c), _ptr(self.workspace), shuffle_ctr, minibatch,
+                                               _ptr(m), _stream(stream)), "ppo_minibatch_moments")
+        return m
+
     def minibatch_grad(self, rollout: Rollout, net: int, shuffle_ctr: int, minibatch: int, stream=None,
-                       weights: torch.Tensor | None = None):
+                       weights: torch.Tensor | None = None, moments: torch.Tensor | None = None):
         """Gradient of one minibatch's loss (and the loss sums, float64[8]);
-        `weights` defaults to the policy's current vector of `net`."""
+        `weights` defaults to the policy's current vector of `net`.  With
+        `moments` (device float64[3], summed over the ranks of a data-parallel
+        update) it is this rank's part of the union minibatch's gradient."""
         pol = self.policy
         w = weights if weights is not None else (pol.pop_w if net == N.NET_POP else pol.gov_w)
         w = w.contiguous()
         grad = torch.empty_like(w)
         stats = torch.empty(8, dtype=torch.float64, device=w.device)
-        N.check(N.load().ppo_minibatch_grad(C.byref(self.env.p), C.byref(self.pp), self.T, pol.hidden,
-                                            self.precision, net, _ptr(w), C.byref(rollout._c),
-                                            _ptr(self.workspace), shuffle_ctr, minibatch, _ptr(grad),
-                                            _ptr(stats), _stream(stream)), "ppo_minibatch_grad")
+        lib = N.load()
+        if moments is None:
+            N.check(lib.ppo_minibatch_grad(C.byref(self.env.p), C.byref(self.pp), self.T, pol.hidden,
+                                           self.precision, net, _ptr(w), C.byref(rollout._c),
+                                           _ptr(self.workspace), shuffle_ctr, minibatch, _ptr(grad),
+                                           _ptr(stats), _stream(stream)), "ppo_minibatch_grad")
+        else:
+            moments = moments.to(torch.float64).contiguous()
+            N.check(lib.ppo_minibatch_grad_global(C.byref(self.env.p), C.byref(self.pp), self.T, pol.hidden,
+                                                  self.precision, net, _ptr(w), C.byref(rollout._c),
+                                                  _ptr(self.workspace), shuffle_ctr, minibatch, _ptr(moments),
+                                                  _ptr(grad), _ptr(stats), _stream(stream)),
+                    "ppo_minibatch_grad_global")
         return grad, stats
+
+    def adam(self, net: int, grad: torch.Tensor, step: int, stream=None):
+        """One Adam step of network `net` with the given gradient (step counts from 1)."""
+        pol, pp = self.policy, self.pp
+        w = pol.pop_w if net == N.NET_POP else pol.gov_w
+        N.check(N.load().adam_step(w.numel(), _ptr(w), _ptr(grad), _ptr(self.m[net]), _ptr(self.v[net]), step,
+                                   pp.lr, pp.beta1, pp.beta2, pp.eps, _stream(stream)), "adam_step")
 
     def loss(self, weights: torch.Tensor, rollout: Rollout, net: int, shuffle_ctr: int, minibatch: int):
         """Differentiable minibatch loss: forward and backward are the library's

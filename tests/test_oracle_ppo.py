@@ -121,3 +121,27 @@ def test_bf16_operand_form_reduces_to_exact_and_stays_close():
     a = np.concatenate([g0[k].ravel() for k in g0])
     b = np.concatenate([g2[k].ravel() for k in g0])
     assert 0 < np.linalg.norm(b - a) <= 5e-2 * np.linalg.norm(a)
+
+
+def test_union_moments_split_sums_to_whole_minibatch():
+    """A minibatch split into two parts, each part given the moments of the
+    whole: the parts' losses and gradients sum to the whole's (the loss is a
+    mean over rows, so it is additive once the normalisation is shared); with
+    the whole's own moments the whole is unchanged."""
+    coef = dict(clip=0.2, vf_coef=0.25, vclip=10.0, ent_coef=0.1)
+    w, x, act, valid, lo, vo, adv, ret = _rand_problem(7, heads=1, N=24)
+    head = valid.shape[1]
+    mom = (len(adv), adv.sum(), (adv * adv).sum())
+
+    def f(sl, **kw):
+        return ppo.ppo_loss_grad64(w, x[sl], act[sl], valid[sl], lo[sl], vo[sl], adv[sl], ret[sl], heads=1,
+                                   head=head, **coef, **kw)
+    l_all, g_all, _ = f(slice(None))
+    l_same, g_same, _ = f(slice(None), moments=mom)
+    assert l_same == pytest.approx(l_all, rel=1e-12)
+    l_a, g_a, _ = f(slice(0, 9), moments=mom)
+    l_b, g_b, _ = f(slice(9, None), moments=mom)
+    assert l_a + l_b == pytest.approx(l_all, rel=1e-12)
+    for k in g_all:
+        assert np.allclose(g_a[k] + g_b[k], g_all[k], rtol=1e-10, atol=1e-14), k
+        assert np.allclose(g_same[k], g_all[k], rtol=1e-12, atol=1e-15), k
