@@ -277,21 +277,28 @@ def run_ppo(args, dev, precision, E_p=2048, T_p=128, seed=3000):
     """One training iteration of config 4 in the given precision: a T_p-step
     rollout of E_p x A agents (policy, sampling, env_step), then the PPO update
     (GAE, 4 epochs x 8 minibatches of the population and government
-    networks).  Reports updates/s and rollout+update agent-steps/s."""
+    networks).  Reports updates/s and rollout+update agent-steps/s.  With N
+    ranks each rank rolls out its own E_p environments and the update is the
+    data-parallel one (DistributedPPO: advantage moments and gradients summed
+    over the ranks by NCCL all-reduces)."""
     import torch
 
     import synth
     from paper_2410_22165_gb300 import PPO, Policy, Rollout, VecEnv
+    from paper_2410_22165_gb300.distributed import DistributedPPO
+
+    rank, world, _ = _dist()
 
     env = VecEnv(E_p, A, device=dev, T_ep=T_EP, T_tax=T_TAX)
     pw = torch.from_numpy(synth.net_weights(seed, 0, env.D, 128, env.nA))
     gw = torch.from_numpy(synth.net_weights(seed, 1, env.G, 128, env.p.nb * env.p.tax_levels))
     pol = Policy(env, pw, gw, hidden=128, precision=precision)
     ro = Rollout(env, pol, T_p)
-    ro.reset(seed=seed)
+    ro.reset(seed=seed + rank)
     ro.run()
     ppo = PPO(pol, T_p, precision=precision)
-    ppo.update(ro)
+    update = DistributedPPO(ppo).update if world > 1 else ppo.update
+    update(ro)
     torch.cuda.synchronize(dev)
     steps = max(1, min(args.steps, 2))
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -301,18 +308,22 @@ def run_ppo(args, dev, precision, E_p=2048, T_p=128, seed=3000):
         ro.carry_over()
         ro.run()
         ev[1].record()
-        stats = ppo.update(ro)
+        stats = update(ro)
         ev[2].record()
         torch.cuda.synchronize(dev)
         ro_ms += ev[0].elapsed_time(ev[1]) / steps
         ms += ev[1].elapsed_time(ev[2]) / steps
+    if world > 1:   # sums over ranks and minibatches -> means over all rows of the update
+        n_rows = torch.tensor([[E_p * A], [E_p]], dtype=torch.float64, device=stats.device)
+        stats = (stats[:, 2:5] / (n_rows * T_p * ppo.pp.epochs * world)).float()
     st = stats.cpu().numpy()
-    rows = ppo.pp.epochs * T_p * E_p
+    rows = ppo.pp.epochs * T_p * E_p * world
     flops = rows * (A * ppo_flops_per_row(env.D, 128, env.nA) + ppo_flops_per_row(env.G, 128, env.p.nb * env.p.tax_levels))
     out = {"updates_per_s": 1e3 / ms, "ms_per_update": ms, "precision": precision,
-           "rollout_ms": ro_ms, "train_agent_steps_per_s": E_p * A * T_p / ((ro_ms + ms) / 1e3),
+           "rollout_ms": ro_ms, "train_agent_steps_per_s": world * E_p * A * T_p / ((ro_ms + ms) / 1e3),
            "useful_TFLOPs": flops / (ms / 1e3) / 1e12, "useful_TFLOP_per_update": flops / 1e12,
-           "transitions_per_update": E_p * A * T_p, "epochs": ppo.pp.epochs, "minibatches": ppo.pp.minibatches,
+           "transitions_per_update": world * E_p * A * T_p, "epochs": ppo.pp.epochs, "minibatches": ppo.pp.minibatches,
+           "ranks": world,
            "population_loss": {"policy": float(st[0, 0]), "value": float(st[0, 1]), "entropy": float(st[0, 2])}}
     del ppo, ro, pol, env
     torch.cuda.empty_cache()
