@@ -224,6 +224,7 @@ def run_gpu(args):
                            "bf16": run_rollout(args, dev, "bf16"), "fp32": run_rollout(args, dev, "fp32")}
         line["ppo"] = {"workload": "E=2048 x A=100 x 128 steps, GAE, 4 epochs x 8 minibatches, both networks",
                        "bf16": run_ppo(args, dev, "bf16"), "fp32": run_ppo(args, dev, "fp32")}
+        line["batched"] = run_batched(args, dev)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if world > 1:
@@ -326,6 +327,50 @@ def run_ppo(args, dev, precision, E_p=2048, T_p=128, seed=3000):
            "ranks": world,
            "population_loss": {"policy": float(st[0, 0]), "value": float(st[0, 1]), "entropy": float(st[0, 2])}}
     del ppo, ro, pol, env
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batched(args, dev, E_b=2048, T_b=1000, seed=4000):
+    """Config 5: E_b environments with populations drawn uniformly from
+    {10, 50, 100, 250, 500} and price grids from {5, 10, 20} levels (24, 44,
+    84 actions), one network per action-space size; the partition into
+    classes is chosen by the autotuner (8-step probes), then one T_b-step
+    rollout of all classes is one CUDA-graph replay, timed with events."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2410_22165_gb300 import BatchedRollout, VecEnv, autotune, price_grid
+
+    rng = np.random.default_rng(seed)
+    pops = rng.choice([10, 50, 100, 250, 500], E_b).tolist()
+    levels = rng.choice([5, 10, 20], E_b).tolist()
+    weights = {}
+    for P in (5, 10, 20):
+        probe = VecEnv(1, 10, device=dev, **price_grid(P))
+        weights[("pop", P)] = torch.from_numpy(synth.net_weights(seed + P, 0, probe.D, 128, probe.nA))
+        weights[("gov",)] = torch.from_numpy(synth.net_weights(seed, 1, probe.G, 128,
+                                                               probe.p.nb * probe.p.tax_levels))
+        del probe
+    kw = dict(T_ep=T_EP, T_tax=T_TAX)
+    best, rates = autotune(pops, levels, weights, T_probe=8, repeats=2, device=dev,
+                           candidates=("exact", "pow2", "coarse"), **kw)
+    br = BatchedRollout(pops, levels, T_b, weights, granularity=best, device=dev, **kw)
+    br.reset(seed=seed)
+    br.capture()
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    br.run()
+    b.record()
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b)
+    out = {"workload": f"E={E_b} environments, populations from {{10,50,100,250,500}} ({sum(pops)} agents), "
+                       f"price grids from {{5,10,20}} levels, {T_b} steps, BF16 policy, one graph replay",
+           "value": br.agent_steps / (ms / 1e3), "unit": UNIT, "ms_per_rollout": ms, "partition": best,
+           "classes": len(br.classes), "autotune_agent_steps_per_s": rates}
+    del br
     torch.cuda.empty_cache()
     return out
 
