@@ -530,6 +530,267 @@ __global__ void __launch_bounds__(BT, 1) policy_bf16_fast_kernel(PolicyArgs a) {
     if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
 }
 
+// ---------------------------------------------------------------------------
+// Two tile pipelines per CTA.  Actor and critic run in different CTAs (the
+// sampler needs only the actor; the value is only written out), which halves
+// the weights a CTA holds; each of its two warpgroups then runs its own
+// sequence of 128-row tiles with its own observation and activation buffers,
+// its own half of TMEM and its own mbarrier, synchronising only through a
+// named barrier of its 128 threads.  While one warpgroup runs an epilogue or
+// the sampler, the tensor core runs the other's products.
+
+struct PpLayout {
+    uint32_t w1, w2, w3, x[2], h[2], bias, total;
+    int N3;
+};
+
+__host__ __device__ inline PpLayout pp_layout(int H, int O) {
+    PpLayout L;
+    L.N3 = (O + 15) / 16 * 16;
+    uint32_t b = 0;
+    L.w1 = b; b += (uint32_t)H * KX * 2;                         // [H][KX]
+    L.w2 = b; b += (uint32_t)H * H * 2;                          // [H][H]
+    L.w3 = b; b += (uint32_t)(L.N3 > 16 ? L.N3 : 16) * H * 2;    // [N3][H] (actor) or [16][H] (critic)
+    for (int w = 0; w < 2; ++w) { L.x[w] = b; b += BM * KX * 2; }
+    for (int w = 0; w < 2; ++w) { L.h[w] = b; b += (uint32_t)BM * H * 2; }
+    L.bias = b; b += ((2u * H + (uint32_t)O + 4) * 4 + 1023) & ~1023u;
+    L.total = b;
+    return L;
+}
+
+__device__ __forceinline__ void wg_bar(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+
+__device__ __forceinline__ bool wg_and(int id, bool v) {
+    uint32_t out;
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %1, 0;\n barrier.red.and.pred p, %2, 128, p;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(out)
+        : "r"((uint32_t)v), "r"(id)
+        : "memory");
+    return out != 0;
+}
+
+__device__ __forceinline__ void wg_sync_for_mma(int id) {
+    fence_async_shared();
+    tc_fence_before();
+    wg_bar(id);
+    tc_fence_after();
+}
+
+__device__ __forceinline__ bool wg_wait_mma(uint64_t* bar, uint32_t& phase, int id) {
+    const bool ok = mbar_wait(bar, phase);
+    phase ^= 1;
+    const bool all = wg_and(id, ok);
+    tc_fence_after();
+    return all;
+}
+
+template <int KT>
+__global__ void __launch_bounds__(BT, 1) policy_bf16_pp_kernel(PolicyArgs a, int n_actor) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t bars[2];
+    __shared__ uint32_t tmem_slot;
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int wg = warp >> 2, quarter = warp & 3;
+    const int wtid = tid & 127;
+    const int row_in_tile = quarter * 32 + lane;     // TMEM lane of this thread (within its warpgroup)
+    const int bar_id = 1 + wg;
+    const int H = a.H, O = a.O, I = a.in_dim;
+    const PpLayout L = pp_layout(H, O);
+    const NetOffsets off = net_offsets(I, H, O);
+    const float* w = a.weights;
+    const bool actor = (int)blockIdx.x < n_actor;
+    const int role_cta = actor ? (int)blockIdx.x : (int)blockIdx.x - n_actor;
+    const int role_ctas = actor ? n_actor : (int)gridDim.x - n_actor;
+
+    const size_t oW1 = actor ? off.W1 : off.V1, oW2 = actor ? off.W2 : off.V2;
+    pack_operand(smem + L.w1, H, KX, [&](int n, int k) { return k < I ? __ldg(w + oW1 + (size_t)k * H + n) : 0.0f; });
+    pack_operand(smem + L.w2, H, H, [&](int n, int k) { return __ldg(w + oW2 + (size_t)k * H + n); });
+    if (actor)
+        pack_operand(smem + L.w3, L.N3, H, [&](int n, int k) { return n < O ? __ldg(w + off.W3 + (size_t)k * O + n) : 0.0f; });
+    else
+        pack_operand(smem + L.w3, 16, H, [&](int n, int k) { return n == 0 ? __ldg(w + off.V3 + k) : 0.0f; });
+    float* bias = (float*)(smem + L.bias);           // [0,H) first layer, [H,2H) second, [2H, 2H+O) head (critic: 2H = c3)
+    for (int k = tid; k < 2 * H + O; k += BT) {
+        float v = 0.0f;
+        if (k < H) v = w[(actor ? off.b1 : off.c1) + k];
+        else if (k < 2 * H) v = w[(actor ? off.b2 : off.c2) + k - H];
+        else v = actor ? w[off.b3 + k - 2 * H] : (k == 2 * H ? w[off.c3] : 0.0f);
+        bias[k] = v;
+    }
+    for (int k = tid; k < 2 * BM * KX * 2 / 16; k += BT) st_shared_v4(smem + L.x[0] + k * 16, 0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_slot, TMEM_COLS);
+    sync_for_mma();
+    const uint32_t tcol = tmem_slot + (uint32_t)(wg * 256);          // this warpgroup's 256 columns
+    const uint32_t lane_base = tcol + ((uint32_t)(quarter * 32) << 16);
+    uint8_t* xb = smem + L.x[wg];
+    uint8_t* hb = smem + L.h[wg];
+    const uint32_t sx = smem_u32(xb), sh = smem_u32(hb);
+    const uint32_t sw1 = smem_u32(smem + L.w1), sw2 = smem_u32(smem + L.w2), sw3 = smem_u32(smem + L.w3);
+    uint64_t* bar = &bars[wg];
+    const __nv_bfloat162 zero2 = __floats2bfloat162_rn(0.0f, 0.0f);
+
+    // a tile's observations (contiguous rows): 8 float4 slots per thread of the warpgroup
+    constexpr int XS = 8;
+    float4 xr[XS];
+    const int n_tiles = (a.rows + BM - 1) / BM;
+    auto load_obs = [&](int tile) {
+        const int row0 = tile * BM;
+        const int n = tile < n_tiles ? min(BM, a.rows - row0) * I : 0;
+        const float* src = a.x + (size_t)row0 * I;
+#pragma unroll
+        for (int q = 0; q < XS; ++q) {
+            const int f = (wtid + q * 128) * 4;
+            if (f + 3 < n) {
+                xr[q] = __ldg(reinterpret_cast<const float4*>(src + f));
+            } else {
+                xr[q].x = f < n ? __ldg(src + f) : 0.0f;
+                xr[q].y = f + 1 < n ? __ldg(src + f + 1) : 0.0f;
+                xr[q].z = f + 2 < n ? __ldg(src + f + 2) : 0.0f;
+                xr[q].w = f + 3 < n ? __ldg(src + f + 3) : 0.0f;
+            }
+        }
+    };
+    auto store_obs = [&]() {
+#pragma unroll
+        for (int q = 0; q < XS; ++q) {
+            const int f = (wtid + q * 128) * 4;
+            if (f < BM * I) {
+                int r = f / I, c = f - r * I;
+                const float v[4] = {xr[q].x, xr[q].y, xr[q].z, xr[q].w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (r < BM) *reinterpret_cast<__nv_bfloat16*>(xb + sw128_offset(r, c, BM)) = __float2bfloat16_rn(v[j]);
+                    if (++c == I) { c = 0; ++r; }
+                }
+            }
+        }
+    };
+    auto relu_epi = [&](int bias_off) {
+        for (int c = 0; c < H / 32; ++c) {
+            float v[32];
+            tmem_ld32(lane_base + c * 32, v);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t pk[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int k = q * 8 + 2 * j;
+                    const float* bb = bias + bias_off + c * 32 + k;
+                    const __nv_bfloat162 y = __hmax2(__floats2bfloat162_rn(v[k] + bb[0], v[k + 1] + bb[1]), zero2);
+                    pk[j] = *reinterpret_cast<const uint32_t*>(&y);
+                }
+                st_shared_v4(hb + sw128_offset(row_in_tile, c * 32 + q * 8, BM), pk[0], pk[1], pk[2], pk[3]);
+            }
+        }
+    };
+
+    uint32_t phase = 0;
+    bool ok = true;
+    const int first = role_cta * 2 + wg, stride = role_ctas * 2;
+    if (first < n_tiles) load_obs(first);
+    for (int tile = first; tile < n_tiles; tile += stride) {
+        const int row0 = tile * BM;
+        const int nrows = min(BM, a.rows - row0);
+        store_obs();
+        const int grow = row0 + row_in_tile;
+        const bool live = row_in_tile < nrows;
+        uint32_t w0 = 0xFFFFFFFFu, w1 = 0xFFFFFFFFu;
+        float us[EJ_MAX_NB] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (actor && live && a.act) {
+            if (a.W) {
+                const uint32_t* mw = a.mask + (size_t)grow * a.W;
+                w0 = mw[0];
+                w1 = (KT > 32 && a.W > 1) ? mw[1] : 0u;
+            }
+            if (a.u) {
+#pragma unroll
+                for (int h = 0; h < EJ_MAX_NB; ++h)
+                    if (h < a.n_heads) us[h] = a.u[(size_t)grow * a.n_heads + h];
+            } else {
+                const int e = grow / a.per_env, i = grow % a.per_env;
+                const uint4 x = philox4x32_10(make_uint4(a.stream_id == 0 ? (uint32_t)i : 0u, (uint32_t)e, a.gstep[e],
+                                                         (uint32_t)a.stream_id), a.key[0], a.key[1]);
+                if (a.stream_id == 0) us[0] = u01(x.w);
+                else { us[0] = u01(x.x); us[1] = u01(x.y); us[2] = u01(x.z); us[3] = u01(x.w); }
+            }
+        }
+        wg_sync_for_mma(bar_id);
+        if (wtid == 0) {
+            mma_chain(tcol, sx, BM, sw1, H, KX, idesc_bf16(BM, H));
+            mma_commit(bar);
+        }
+        if (tile + stride < n_tiles) load_obs(tile + stride);
+        if (!(ok = wg_wait_mma(bar, phase, bar_id))) break;
+        relu_epi(0);
+        wg_sync_for_mma(bar_id);
+        if (wtid == 0) {
+            mma_chain(tcol, sh, BM, sw2, H, H, idesc_bf16(BM, H));
+            mma_commit(bar);
+        }
+        if (!(ok = wg_wait_mma(bar, phase, bar_id))) break;
+        relu_epi(H);
+        wg_sync_for_mma(bar_id);
+        if (wtid == 0) {
+            if (actor) mma_chain(tcol + 128, sh, BM, sw3, L.N3, H, idesc_bf16(BM, L.N3));
+            else mma_chain(tcol + 128, sh, BM, sw3, 16, H, idesc_bf16(BM, 16));
+            mma_commit(bar);
+        }
+        if (!(ok = wg_wait_mma(bar, phase, bar_id))) break;
+        if (actor) {
+            float l[KT];
+            {
+                float v[32];
+                tmem_ld32(lane_base + 128, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) l[j] = v[j];
+                if constexpr (KT == 64) {
+                    tmem_ld32(lane_base + 160, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) l[32 + j] = v[j];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < KT; ++j) l[j] = j < O ? l[j] + bias[2 * H + j] : 0.0f;
+            if (live) {
+                if (a.logits) {
+#pragma unroll
+                    for (int j = 0; j < KT; ++j)
+                        if (j < O) a.logits[(size_t)grow * O + j] = l[j];
+                }
+                if (a.act) {
+                    float logp = 0.0f, ent = 0.0f;
+                    bool none = false;
+                    for (int h = 0; h < a.n_heads; ++h) {
+                        const float uh = h == 0 ? us[0] : h == 1 ? us[1] : h == 2 ? us[2] : us[3];
+                        int act = sample_head_reg<KT>(l, h * a.head, a.head, w0, w1, uh, logp, ent);
+                        if (act < 0) { act = 0; none = true; }
+                        a.act[(size_t)grow * a.n_heads + h] = act;
+                    }
+                    if (none) { logp = 0.0f; ent = 0.0f; }
+                    a.logp[grow] = logp;
+                    if (a.entropy) a.entropy[grow] = ent;
+                }
+            }
+        } else {
+            float vv[32];
+            tmem_ld32(lane_base + 128, vv);          // warp-collective: every lane loads
+            if (live) a.value[grow] = vv[0] + bias[2 * H];
+        }
+    }
+    if (!ok) mbar_wait(bar, phase, 200000000LL);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem_slot, TMEM_COLS);
+}
+
 }  // namespace
 
 size_t policy_bf16_smem(int H, int O) { return bf_layout(H, O).total + 1024; }
@@ -552,6 +813,37 @@ ej_status launch_policy_bf16(const PolicyArgs& a, cudaStream_t stream) {
     int grid = n_tiles < 152 ? n_tiles : 152;
     if (grid < 1) grid = 1;
     const bool fast = a.O <= 64 && a.in_dim <= 32 && a.W <= 2 && a.n_heads <= EJ_MAX_NB && ((uintptr_t)a.x & 15) == 0;
+    if (fast && a.H == 128) {
+        // two tile pipelines per CTA, actor and critic in separate CTAs
+        const size_t smem_pp = pp_layout(a.H, a.O).total + 1024;
+        static size_t conf_pp[2] = {0, 0};
+        const int kt = a.O <= 32 ? 0 : 1;
+        if (conf_pp[kt] < smem_pp) {
+            cudaError_t err = cudaFuncSetAttribute(kt == 0 ? policy_bf16_pp_kernel<32> : policy_bf16_pp_kernel<64>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pp);
+            if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
+            conf_pp[kt] = smem_pp;
+        }
+        // one CTA per SM; the actor (two layers, head, sampler) gets 3/5 of them, a
+        // split measured on E = 4096 x A = 100 (1/2: 0.274 ms, 3/5: 0.233 ms, 2/3: 0.238 ms)
+        static int sms = 0;
+        if (sms == 0) {
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 2)
+                sms = 2;
+        }
+        const int pairs = (n_tiles + 1) / 2;                 // tiles are taken two at a time per CTA
+        int n_act = sms * 3 / 5, n_cri = sms - sms * 3 / 5;
+        n_act = n_act < pairs ? n_act : pairs;
+        n_cri = n_cri < pairs ? n_cri : pairs;
+        if (n_act < 1) n_act = 1;
+        if (n_cri < 1) n_cri = 1;
+        if (kt == 0) policy_bf16_pp_kernel<32><<<n_act + n_cri, BT, smem_pp, stream>>>(a, n_act);
+        else policy_bf16_pp_kernel<64><<<n_act + n_cri, BT, smem_pp, stream>>>(a, n_act);
+        cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "bf16 policy launch: %s", cudaGetErrorString(err));
+        return EJ_OK;
+    }
     if (fast) {
         static size_t conf_fast[2] = {0, 0};
         const int kt = a.O <= 32 ? 0 : 1;
