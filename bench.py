@@ -376,26 +376,19 @@ def run_batched(args, dev, E_b=2048, T_b=1000, seed=4000):
 
 
 def run_e2e(env, d, out, args, dev, world):
-    """Same metric, through VecEnv.step with host buffers: each step copies its
-    inputs from pinned host memory and all its outputs back, in 100-step chunks."""
+    """Same metric through the host-buffer API (VecEnv.step_host): each step's
+    inputs come from pinned host memory and all its outputs go back to it, in
+    100-step chunks whose copies overlap the kernel of the next chunk."""
     import torch
 
     chunk = 100
     host_in = {k: v.cpu().pin_memory() for k, v in d.items()}
     host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
-    dev_in = {k: torch.empty((chunk,) + tuple(v.shape[1:]), dtype=v.dtype, device=dev) for k, v in d.items()}
-    dev_out = env.alloc_outputs(chunk)
     h2d = sum(v.numel() * v.element_size() for v in host_in.values())
     d2h = sum(v.numel() * v.element_size() for v in host_out.values())
 
     def one():
-        for s in range(0, T_EP, chunk):
-            for k, v in dev_in.items():
-                v.copy_(host_in[k][s:s + chunk], non_blocking=True)
-            env.step(chunk, act=dev_in["act"], gov_act=dev_in["gov_act"], gather_u=dev_in["gather_u"],
-                     tb=dev_in["tb"], out=dev_out)
-            for k, v in dev_out.items():
-                host_out[k][s:s + chunk].copy_(v, non_blocking=True)
+        env.step_host(T_EP, host_in, host_out, chunk=chunk, sync=False)
 
     steps = max(1, min(args.steps, 3))
     one()
@@ -407,7 +400,9 @@ def run_e2e(env, d, out, args, dev, world):
     dt = time.perf_counter() - t0
     return {"value": E * A * T_EP * steps * world / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": steps,
-            "how": "VecEnv.step on 100-step chunks: pinned host inputs copied in, all outputs copied out"}
+            "link_GBps": (h2d + d2h) * steps / dt / 1e9,
+            "how": "VecEnv.step_host, 100-step chunks: pinned host inputs copied in and all outputs copied out, "
+                   "copies of one chunk overlapping the kernel of the next"}
 
 
 # ------------------------------------------------------------- CPU oracle

@@ -1,0 +1,42 @@
+"""VecEnv.step_host (pipelined host-buffer I/O) against the device path: same
+outputs bit for bit, with a ragged last chunk and the state continuing across
+calls."""
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_22165_gb300 import build
+    build.build()
+
+
+def test_step_host_equals_device_steps():
+    import paper_2410_22165_gb300 as P
+    E, A, n = 8, 10, 250
+    kw = dict(T_ep=30, T_tax=6)
+    ref, got = P.VecEnv(E, A, **kw), P.VecEnv(E, A, **kw)
+    ref.reset(seed=3)
+    got.reset(seed=3)
+    d = ref.fill_draws(seed=3, g0=0, n_steps=2 * n)
+    out_ref = ref.step(2 * n, act=d["act"], gov_act=d["gov_act"], gather_u=d["gather_u"], tb=d["tb"])
+    host_in = {k: v.cpu().pin_memory() for k, v in d.items()}
+    host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out_ref.items()}
+    for half in range(2):                       # two calls: the state carries over
+        sl = slice(half * n, (half + 1) * n)
+        got.step_host(n, {k: v[sl] for k, v in host_in.items()}, {k: v[sl] for k, v in host_out.items()},
+                      chunk=64, copy_streams=3)
+    for k, v in out_ref.items():
+        assert torch.equal(host_out[k], v.cpu()), k
+    # state: every field, the order book up to its live length (slots past it are unused)
+    for name in ("coin", "esc", "income", "uprev", "nord", "counts", "sc", "inv", "inve", "sg", "t", "gstep",
+                 "episode", "pop", "rates", "ugprev", "level_count"):
+        assert torch.equal(got.field(name), ref.field(name)), name
+    live = ref.field("level_count").sum(1)
+    for e in range(E):
+        nb = int(live[e])
+        assert torch.equal(got.field("book")[e, :nb], ref.field("book")[e, :nb])
