@@ -90,6 +90,29 @@ class Rollout:
         for k in ("obs", "gobs", "mask"):
             self.buf[k][0].copy_(self.buf[k][self.T])
 
+    def capture(self):
+        """Capture carry_over + run (3T + 2 launches and the slot-0 copies) as
+        one CUDA graph; replay() then runs the next rollout.  Runs one rollout
+        eagerly first (kernel attributes are set outside the capture)."""
+        self.carry_over()
+        self.run()
+        torch.cuda.synchronize(self.env.device)
+        s = torch.cuda.Stream(device=self.env.device)
+        s.wait_stream(torch.cuda.current_stream(self.env.device))
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                self.carry_over()
+                self.run(stream=s)
+        torch.cuda.current_stream(self.env.device).wait_stream(s)
+        self.graph = g
+        return g
+
+    def replay(self):
+        """The next rollout (carry_over + run) as one graph launch."""
+        self.graph.replay()
+        return self.buf
+
     def run(self, stream=None):
         pol = self.policy
         N.check(N.load().rollout(C.byref(self.env.p), _ptr(self.env.state), self.T, pol.hidden,

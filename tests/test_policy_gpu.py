@@ -201,3 +201,29 @@ def test_no_device_fault_recorded():
     f = C.c_int32(-1)
     N.check(N.load().ej_device_status(C.byref(f), 0), "ej_device_status")
     assert f.value == 0
+
+
+def test_rollout_graph_replay_equals_eager():
+    """A rollout captured as a CUDA graph and replayed gives the eager rollout's buffers."""
+    import paper_2410_22165_gb300 as P
+    E, A, T = 4, 10, 12
+    res = []
+    for graph in (False, True):
+        env = P.VecEnv(E, A, T_ep=8, T_tax=4)
+        pw = synth.net_weights(3, 0, env.D, 128, env.nA)
+        gw = synth.net_weights(3, 1, env.G, 128, env.p.nb * env.p.tax_levels)
+        pol = P.Policy(env, torch.from_numpy(pw), torch.from_numpy(gw), hidden=128, precision="bf16")
+        ro = P.Rollout(env, pol, T)
+        ro.reset(seed=5)
+        ro.run()
+        if graph:
+            ro.capture()          # second rollout, eager
+            ro.replay()           # third rollout, from the graph
+        else:
+            for _ in range(2):
+                ro.carry_over()
+                ro.run()
+        torch.cuda.synchronize()
+        res.append({k: v.clone() for k, v in ro.buf.items()})
+    for k in res[0]:
+        assert torch.equal(res[0][k], res[1][k]), k
