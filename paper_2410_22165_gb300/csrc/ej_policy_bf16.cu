@@ -119,7 +119,10 @@ __device__ __forceinline__ void mma_chain(uint32_t d, uint32_t a_base, int a_row
 
 // Waits for the tensor core and agrees across the CTA on success.
 __device__ __forceinline__ bool wait_mma(uint64_t* bar, uint32_t& phase) {
-    const bool ok = mbar_wait(bar, phase);
+    // one warp polls the mbarrier; the others block in the barrier (issuing nothing),
+    // which then carries the completion to them
+    bool ok = true;
+    if (threadIdx.x < 32) ok = mbar_wait(bar, phase);
     phase ^= 1;
     const bool all = __syncthreads_and(ok);
     tc_fence_after();
@@ -578,7 +581,8 @@ __device__ __forceinline__ void wg_sync_for_mma(int id) {
 }
 
 __device__ __forceinline__ bool wg_wait_mma(uint64_t* bar, uint32_t& phase, int id) {
-    const bool ok = mbar_wait(bar, phase);
+    bool ok = true;
+    if ((threadIdx.x & 127) < 32) ok = mbar_wait(bar, phase);   // the warpgroup's first warp polls
     phase ^= 1;
     const bool all = wg_and(id, ok);
     tc_fence_after();

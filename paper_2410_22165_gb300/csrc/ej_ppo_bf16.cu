@@ -133,7 +133,10 @@ __device__ __forceinline__ void sync_for_mma() {
 }
 
 __device__ __forceinline__ bool wait_mma(uint64_t* bar, uint32_t& phase) {
-    const bool ok = mbar_wait(bar, phase);
+    // one warp polls the mbarrier; the others block in the barrier (issuing nothing),
+    // which then carries the completion to them
+    bool ok = true;
+    if (threadIdx.x < 32) ok = mbar_wait(bar, phase);
     phase ^= 1;
     const bool all = __syncthreads_and(ok);
     tc_fence_after();
