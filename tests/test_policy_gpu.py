@@ -227,3 +227,25 @@ def test_rollout_graph_replay_equals_eager():
         res.append({k: v.clone() for k, v in ro.buf.items()})
     for k in res[0]:
         assert torch.equal(res[0][k], res[1][k]), k
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_full_size_forward_sampled_rows(precision):
+    """The rollout workload's size, E = 4096 x A = 100 (409,600 rows, 3,200 tiles: every CTA and both
+    warpgroup pipelines run many tiles): 3,000 sampled rows checked against the float64 forward, and
+    every sampled action against the oracle's float32 sampler on the kernel's logits."""
+    E, A = 4096, 100
+    env, pol, obs, gobs, mask, pw, gw = _setup(E, A, seed=8, steps=5, precision=precision, T_ep=1000, T_tax=100)
+    P, N = _mods()
+    out = pol.forward(N.NET_POP, obs, mask, logits=True, entropy=True)
+    rng = np.random.default_rng(8)
+    rows = np.sort(rng.choice(E * A, 3000, replace=False))
+    rows = np.concatenate([rows, [0, 127, 128, E * A - 1]])
+    lg = out["logits"].cpu().numpy()[rows]
+    val = out["value"].cpu().numpy()[rows]
+    x = obs.cpu().numpy().reshape(E * A, env.D)[rows]
+    _check_forward(lg, val, synth.unpack(pw, env.D, H, env.nA), x, env.D, precision)
+    valid = op.mask_bits(mask.cpu().numpy().view(np.uint32).reshape(E * A, env.W), env.nA)[rows]
+    g = int(env.field("gstep")[0].item())
+    u = synth.pop_draws(8, np.arange(E), A, g, 1, env.nA)[3][0].reshape(E * A)[rows]   # key = the reset seed
+    assert np.array_equal(out["act"].cpu().numpy()[rows, 0], op.sample32(lg, valid, u))

@@ -158,3 +158,15 @@ def test_bf16_update_moves_weights_like_fp32():
     agree = np.mean(np.sign(steps["fp32"][big]) == np.sign(steps["bf16"][big]))
     print("sign agreement of bf16 and fp32 update steps:", agree)
     assert agree > 0.9, agree
+
+
+def test_bf16_gradient_profile_size_minibatch():
+    """The PPO profile case's minibatch: E = 256 x A = 100 x 32 steps, minibatch 3 of 8 (102,400
+    population rows = 800 tiles, several per CTA and role), against the BF16-operand oracle."""
+    E, A, T = 256, 100, 32
+    env, pol, ro, ppo, b, pw, gw = _setup(E, A, T, 7, dict(minibatches=8, seed=11), T_ep=1000, T_tax=100)
+    ppo.advantages(ro)
+    grad, _ = ppo.minibatch_grad(ro, 0, 2, 3)
+    rows = shuffle.minibatch_rows(3, 8, T * E * A, 11, 2)
+    _, gbf, _ = _oracle(env, b, ppo.pp, 0, rows, pw, operand=oppo.bf16_round)
+    _compare(env, 0, grad.cpu().numpy(), gbf, TIGHT, "bf16-operand oracle")
