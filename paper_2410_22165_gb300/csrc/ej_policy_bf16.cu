@@ -70,7 +70,7 @@ __device__ __forceinline__ void st_shared_v4(uint8_t* p, uint32_t a, uint32_t b,
 template <class F>
 __device__ void pack_operand(uint8_t* dst, int rows, int K, F get) {
     const int items = rows * (K / 8);
-    for (int it = threadIdx.x; it < items; it += BT) {
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
         const int n = it % rows, kc = it / rows;
         float v[8];
 #pragma unroll
@@ -542,20 +542,29 @@ __global__ void __launch_bounds__(BT, 1) policy_bf16_fast_kernel(PolicyArgs a) {
 // named barrier of its 128 threads.  While one warpgroup runs an epilogue or
 // the sampler, the tensor core runs the other's products.
 
+constexpr int PP_MAX_WG = 3;
+#ifndef PP_WG32
+#define PP_WG32 3     // tile pipelines per CTA for <= 32 logits
+#endif
+#ifndef PP_ACT_NUM
+#define PP_ACT_NUM 3  // share of the CTAs that run the actor: PP_ACT_NUM / PP_ACT_DEN
+#define PP_ACT_DEN 5
+#endif
+
 struct PpLayout {
-    uint32_t w1, w2, w3, x[2], h[2], bias, total;
+    uint32_t w1, w2, w3, x[PP_MAX_WG], h[PP_MAX_WG], bias, total;
     int N3;
 };
 
-__host__ __device__ inline PpLayout pp_layout(int H, int O) {
+__host__ __device__ inline PpLayout pp_layout(int H, int O, int nwg) {
     PpLayout L;
     L.N3 = (O + 15) / 16 * 16;
     uint32_t b = 0;
     L.w1 = b; b += (uint32_t)H * KX * 2;                         // [H][KX]
     L.w2 = b; b += (uint32_t)H * H * 2;                          // [H][H]
     L.w3 = b; b += (uint32_t)(L.N3 > 16 ? L.N3 : 16) * H * 2;    // [N3][H] (actor) or [16][H] (critic)
-    for (int w = 0; w < 2; ++w) { L.x[w] = b; b += BM * KX * 2; }
-    for (int w = 0; w < 2; ++w) { L.h[w] = b; b += (uint32_t)BM * H * 2; }
+    for (int w = 0; w < nwg; ++w) { L.x[w] = b; b += BM * KX * 2; }
+    for (int w = 0; w < nwg; ++w) { L.h[w] = b; b += (uint32_t)BM * H * 2; }
     L.bias = b; b += ((2u * H + (uint32_t)O + 4) * 4 + 1023) & ~1023u;
     L.total = b;
     return L;
@@ -589,10 +598,17 @@ __device__ __forceinline__ bool wg_wait_mma(uint64_t* bar, uint32_t& phase, int 
     return all;
 }
 
-template <int KT>
-__global__ void __launch_bounds__(BT, 1) policy_bf16_pp_kernel(PolicyArgs a, int n_actor) {
+// NWG warpgroups (tile pipelines) per CTA; TMEM columns per warpgroup: the
+// 128-column product slot and the head (KT logits or the value).
+template <int KT, int NWG>
+__global__ void __launch_bounds__(128 * NWG, 1) policy_bf16_pp_kernel(PolicyArgs a, int n_actor) {
+    constexpr int NTH_PP = 128 * NWG;
+    // TMEM: product slots of 128 columns at wg * 128, heads after them (32-column aligned)
+    constexpr uint32_t HEAD_W = KT == 64 ? 64u : 32u;
+    static_assert(NWG * 128 + NWG * HEAD_W <= TMEM_COLS, "TMEM columns");
+    static_assert(NWG == 2 || KT == 32, "three pipelines fit TMEM only with 32 logit columns");
     extern __shared__ uint8_t smem_raw[];
-    __shared__ uint64_t bars[2];
+    __shared__ uint64_t bars[NWG];
     __shared__ uint32_t tmem_slot;
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -601,7 +617,7 @@ __global__ void __launch_bounds__(BT, 1) policy_bf16_pp_kernel(PolicyArgs a, int
     const int row_in_tile = quarter * 32 + lane;     // TMEM lane of this thread (within its warpgroup)
     const int bar_id = 1 + wg;
     const int H = a.H, O = a.O, I = a.in_dim;
-    const PpLayout L = pp_layout(H, O);
+    const PpLayout L = pp_layout(H, O, NWG);
     const NetOffsets off = net_offsets(I, H, O);
     const float* w = a.weights;
     const bool actor = (int)blockIdx.x < n_actor;
@@ -616,23 +632,24 @@ __global__ void __launch_bounds__(BT, 1) policy_bf16_pp_kernel(PolicyArgs a, int
     else
         pack_operand(smem + L.w3, 16, H, [&](int n, int k) { return n == 0 ? __ldg(w + off.V3 + k) : 0.0f; });
     float* bias = (float*)(smem + L.bias);           // [0,H) first layer, [H,2H) second, [2H, 2H+O) head (critic: 2H = c3)
-    for (int k = tid; k < 2 * H + O; k += BT) {
+    for (int k = tid; k < 2 * H + O; k += NTH_PP) {
         float v = 0.0f;
         if (k < H) v = w[(actor ? off.b1 : off.c1) + k];
         else if (k < 2 * H) v = w[(actor ? off.b2 : off.c2) + k - H];
         else v = actor ? w[off.b3 + k - 2 * H] : (k == 2 * H ? w[off.c3] : 0.0f);
         bias[k] = v;
     }
-    for (int k = tid; k < 2 * BM * KX * 2 / 16; k += BT) st_shared_v4(smem + L.x[0] + k * 16, 0u, 0u, 0u, 0u);
+    for (int k = tid; k < NWG * BM * KX * 2 / 16; k += NTH_PP) st_shared_v4(smem + L.x[0] + k * 16, 0u, 0u, 0u, 0u);
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int q = 0; q < NWG; ++q) mbar_init(&bars[q], 1);
         fence_mbar_init();
     }
     if (warp == 0) tmem_alloc(&tmem_slot, TMEM_COLS);
     sync_for_mma();
-    const uint32_t tcol = tmem_slot + (uint32_t)(wg * 256);          // this warpgroup's 256 columns
+    const uint32_t tcol = tmem_slot + (uint32_t)wg * 128u;                      // product slot
+    const uint32_t thead = tmem_slot + (uint32_t)(NWG * 128) + (uint32_t)wg * HEAD_W;   // head columns
     const uint32_t lane_base = tcol + ((uint32_t)(quarter * 32) << 16);
+    const uint32_t lane_head = thead + ((uint32_t)(quarter * 32) << 16);
     uint8_t* xb = smem + L.x[wg];
     uint8_t* hb = smem + L.h[wg];
     const uint32_t sx = smem_u32(xb), sh = smem_u32(hb);
@@ -697,7 +714,7 @@ __global__ void __launch_bounds__(BT, 1) policy_bf16_pp_kernel(PolicyArgs a, int
 
     uint32_t phase = 0;
     bool ok = true;
-    const int first = role_cta * 2 + wg, stride = role_ctas * 2;
+    const int first = role_cta * NWG + wg, stride = role_ctas * NWG;
     if (first < n_tiles) load_obs(first);
     for (int tile = first; tile < n_tiles; tile += stride) {
         const int row0 = tile * BM;
@@ -742,8 +759,8 @@ __global__ void __launch_bounds__(BT, 1) policy_bf16_pp_kernel(PolicyArgs a, int
         relu_epi(H);
         wg_sync_for_mma(bar_id);
         if (wtid == 0) {
-            if (actor) mma_chain(tcol + 128, sh, BM, sw3, L.N3, H, idesc_bf16(BM, L.N3));
-            else mma_chain(tcol + 128, sh, BM, sw3, 16, H, idesc_bf16(BM, 16));
+            if (actor) mma_chain(thead, sh, BM, sw3, L.N3, H, idesc_bf16(BM, L.N3));
+            else mma_chain(thead, sh, BM, sw3, 16, H, idesc_bf16(BM, 16));
             mma_commit(bar);
         }
         if (!(ok = wg_wait_mma(bar, phase, bar_id))) break;
@@ -751,11 +768,11 @@ __global__ void __launch_bounds__(BT, 1) policy_bf16_pp_kernel(PolicyArgs a, int
             float l[KT];
             {
                 float v[32];
-                tmem_ld32(lane_base + 128, v);
+                tmem_ld32(lane_head, v);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) l[j] = v[j];
                 if constexpr (KT == 64) {
-                    tmem_ld32(lane_base + 160, v);
+                    tmem_ld32(lane_head + 32, v);
 #pragma unroll
                     for (int j = 0; j < 32; ++j) l[32 + j] = v[j];
                 }
@@ -784,7 +801,7 @@ __global__ void __launch_bounds__(BT, 1) policy_bf16_pp_kernel(PolicyArgs a, int
             }
         } else {
             float vv[32];
-            tmem_ld32(lane_base + 128, vv);          // warp-collective: every lane loads
+            tmem_ld32(lane_head, vv);                // warp-collective: every lane loads
             if (live) a.value[grow] = vv[0] + bias[2 * H];
         }
     }
@@ -818,32 +835,34 @@ ej_status launch_policy_bf16(const PolicyArgs& a, cudaStream_t stream) {
     if (grid < 1) grid = 1;
     const bool fast = a.O <= 64 && a.in_dim <= 32 && a.W <= 2 && a.n_heads <= EJ_MAX_NB && ((uintptr_t)a.x & 15) == 0;
     if (fast && a.H == 128) {
-        // two tile pipelines per CTA, actor and critic in separate CTAs
-        const size_t smem_pp = pp_layout(a.H, a.O).total + 1024;
-        static size_t conf_pp[2] = {0, 0};
+        // tile pipelines per CTA (three for up to 32 logits, two otherwise), actor and critic in separate CTAs
         const int kt = a.O <= 32 ? 0 : 1;
+        const int nwg = kt == 0 ? PP_WG32 : 2;
+        const size_t smem_pp = pp_layout(a.H, a.O, nwg).total + 1024;
+        static size_t conf_pp[2] = {0, 0};
         if (conf_pp[kt] < smem_pp) {
-            cudaError_t err = cudaFuncSetAttribute(kt == 0 ? policy_bf16_pp_kernel<32> : policy_bf16_pp_kernel<64>,
+            cudaError_t err = cudaFuncSetAttribute(kt == 0 ? policy_bf16_pp_kernel<32, PP_WG32> : policy_bf16_pp_kernel<64, 2>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pp);
             if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
             conf_pp[kt] = smem_pp;
         }
-        // one CTA per SM; the actor (two layers, head, sampler) gets 3/5 of them, a
-        // split measured on E = 4096 x A = 100 (1/2: 0.274 ms, 3/5: 0.233 ms, 2/3: 0.238 ms)
+        // one CTA per SM; the actor (two layers, head, sampler) gets 3/5 of them, the split
+        // measured best on E = 4096 x A = 100 (three pipelines: 1/2 0.217 ms, 3/5 0.186 ms,
+        // 5/8 0.185 ms, 2/3 0.191 ms)
         static int sms = 0;
         if (sms == 0) {
             int dev = 0;
             if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 2)
                 sms = 2;
         }
-        const int pairs = (n_tiles + 1) / 2;                 // tiles are taken two at a time per CTA
-        int n_act = sms * 3 / 5, n_cri = sms - sms * 3 / 5;
+        const int pairs = (n_tiles + nwg - 1) / nwg;          // tiles are taken nwg at a time per CTA
+        int n_act = sms * PP_ACT_NUM / PP_ACT_DEN, n_cri = sms - sms * PP_ACT_NUM / PP_ACT_DEN;
         n_act = n_act < pairs ? n_act : pairs;
         n_cri = n_cri < pairs ? n_cri : pairs;
         if (n_act < 1) n_act = 1;
         if (n_cri < 1) n_cri = 1;
-        if (kt == 0) policy_bf16_pp_kernel<32><<<n_act + n_cri, BT, smem_pp, stream>>>(a, n_act);
-        else policy_bf16_pp_kernel<64><<<n_act + n_cri, BT, smem_pp, stream>>>(a, n_act);
+        if (kt == 0) policy_bf16_pp_kernel<32, PP_WG32><<<n_act + n_cri, 128 * PP_WG32, smem_pp, stream>>>(a, n_act);
+        else policy_bf16_pp_kernel<64, 2><<<n_act + n_cri, 256, smem_pp, stream>>>(a, n_act);
         cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "bf16 policy launch: %s", cudaGetErrorString(err));
         return EJ_OK;
