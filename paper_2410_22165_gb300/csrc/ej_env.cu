@@ -40,8 +40,11 @@ __global__ void fill_draws_kernel(KParams p, uint32_t k0, uint32_t k1, uint32_t 
 ej_status launch_env(const KParams& kp, const Layout& lay, const DevState& st, const DevIO& io,
                      int n_steps, int mode, uint64_t seed, cudaStream_t stream) {
     using envk::launch_nt;
-    if (kp.R == 2 && kp.P == 5 && lay.sizes.threads <= 512)
-        return launch_env_r2p5(kp, lay, st, io, n_steps, mode, seed, stream);
+    if (kp.R == 2 && lay.sizes.threads <= 512) {
+        if (kp.P == 5) return launch_env_r2p5(kp, lay, st, io, n_steps, mode, seed, stream);
+        if (kp.P == 10) return launch_env_r2p10(kp, lay, st, io, n_steps, mode, seed, stream);
+        if (kp.P == 20) return launch_env_r2p20(kp, lay, st, io, n_steps, mode, seed, stream);
+    }
     switch (lay.sizes.threads) {
         case 32: return launch_nt<32, 0, 0>(kp, lay, st, io, n_steps, mode, seed, stream);
         case 64: return launch_nt<64, 0, 0>(kp, lay, st, io, n_steps, mode, seed, stream);

@@ -1,9 +1,10 @@
 // EconoJax environment step on sm_103a (arxiv 2410.22165, Section 3): the
 // kernel template.  ej_env.cu instantiates it for any resource / price-level
 // count (read from the parameters at run time); ej_env_r2p5.cu for the
-// default market of Table 2 (2 resources, 5 price levels) with those counts
-// known at compile time, so that every per-level loop unrolls and every
-// division by the number of levels becomes a multiply.
+// default market of Table 2 (2 resources, 5 price levels), ej_env_r2p10.cu and
+// ej_env_r2p20.cu for the finer price grids, with those counts known at
+// compile time, so that every per-level loop unrolls and every division by the
+// number of levels becomes a multiply.
 //
 // One CTA runs one environment; thread i is population agent i.  The CTA
 // loads the environment's state from HBM once, runs n_steps steps with the

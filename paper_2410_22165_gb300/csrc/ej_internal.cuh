@@ -48,12 +48,17 @@ DevState state_pointers(const Layout& lay, void* base);
 // Records the error message of the calling thread and returns s.
 ej_status fail(ej_status s, const char* fmt, ...);
 
-// Launchers (ej_env.cu; the 2-resource, 5-level instantiations in ej_env_r2p5.cu).
+// Launchers (ej_env.cu; the 2-resource instantiations with 5, 10 and 20 price levels in
+// ej_env_r2p5.cu, ej_env_r2p10.cu, ej_env_r2p20.cu).
 enum : int { MODE_RESET = 1, MODE_POP_DRAW = 2, MODE_GOV_DRAW = 4, MODE_AUX_DRAW = 8 };
 ej_status launch_env(const KParams& kp, const Layout& lay, const DevState& st, const DevIO& io,
                      int n_steps, int mode, uint64_t seed, cudaStream_t stream);
 ej_status launch_env_r2p5(const KParams& kp, const Layout& lay, const DevState& st, const DevIO& io,
                           int n_steps, int mode, uint64_t seed, cudaStream_t stream);
+ej_status launch_env_r2p10(const KParams& kp, const Layout& lay, const DevState& st, const DevIO& io,
+                           int n_steps, int mode, uint64_t seed, cudaStream_t stream);
+ej_status launch_env_r2p20(const KParams& kp, const Layout& lay, const DevState& st, const DevIO& io,
+                           int n_steps, int mode, uint64_t seed, cudaStream_t stream);
 ej_status launch_fill_draws(const KParams& kp, uint64_t seed, uint32_t g0, int n_steps,
                             int32_t* act, float* gather_u, uint32_t* tb, float* policy_u,
                             int32_t* gov_act, cudaStream_t stream);
