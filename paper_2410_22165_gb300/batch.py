@@ -11,6 +11,19 @@ government policy and env_step per step) on its own stream; the T-step
 rollouts of all classes are captured as parallel branches of one CUDA graph,
 so a whole batched rollout is one graph launch.
 
+With ``merge`` the policy launches of a step are merged across
+classes: every network shape that the segmented BF16 policy kernel takes (the
+government network, and the population networks of up to 64 actions) runs as
+one launch over the rows of all classes that use it (policy_forward_segments;
+one table entry per class), the other population networks per class on the
+class's stream; then each class's env_step runs on its own stream.  Per step
+the graph holds one node per merged network, one per unmerged class policy and
+one env_step per class, instead of three launches per class.  The values,
+actions and states are those of the per-class rollouts, bit for bit.  The
+merged form joins all classes at every step, which costs more than the
+per-class streams save when the classes' policy launches are short, so it is
+off by default and the autotuner can compare both.
+
 The partition is a tuning choice: ``exact`` (one class per distinct
 (P, population)), ``pow2`` (populations rounded up to a power of two: one CTA
 size per class), ``coarse`` (populations up to 64, up to 256, larger) or
@@ -22,9 +35,12 @@ from __future__ import annotations
 import time
 from collections import OrderedDict
 
+import ctypes as C
+
 import torch
 
-from .env import VecEnv
+from . import _native as N
+from .env import VecEnv, _ptr, _stream
 from .policy import Policy, Rollout
 
 
@@ -60,11 +76,12 @@ def plan_classes(pops, levels, granularity):
 
 class BatchedRollout:
     def __init__(self, pops, levels, T, weights, hidden=128, precision="bf16", granularity="pow2",
-                 device="cuda", **env_kw):
+                 device="cuda", merge=False, **env_kw):
         """weights: {("pop", P): tensor, ("gov",): tensor} in the library's layout."""
         self.pops, self.levels, self.T = list(pops), list(levels), T
         self.device = torch.device(device)
         self.granularity = granularity
+        self.merge = merge
         self.classes = []
         for P, A_max, idx in plan_classes(self.pops, self.levels, granularity):
             env = VecEnv(len(idx), A_max, device=self.device, **price_grid(P), **env_kw)
@@ -74,6 +91,33 @@ class BatchedRollout:
             self.classes.append(dict(P=P, A_max=A_max, idx=idx, env=env, policy=pol, ro=ro, pop=pop,
                                      stream=torch.cuda.Stream(device=self.device)))
         self.graph = None
+        self._plan_merge(hidden, precision)
+
+    def _plan_merge(self, hidden, precision):
+        """Groups of classes whose policy launches merge: [(net, classes, stream)]
+        and the classes whose population policy runs on their own stream."""
+        self.groups, self.solo, self.solo_gov = [], [], False
+        if not self.merge:
+            return
+        lib = N.load()
+        ok = C.c_int32()
+        by_P = OrderedDict()
+        for c in self.classes:
+            N.check(lib.policy_segmented(C.byref(c["env"].p), N.NET_POP, hidden, c["policy"].precision,
+                                         C.byref(ok)), "policy_segmented")
+            if ok.value:
+                by_P.setdefault(c["P"], []).append(c)
+            else:
+                self.solo.append(c)
+        for cls in by_P.values():
+            self.groups.append((N.NET_POP, cls, torch.cuda.Stream(device=self.device)))
+        c0 = self.classes[0]
+        N.check(lib.policy_segmented(C.byref(c0["env"].p), N.NET_GOV, hidden, c0["policy"].precision,
+                                     C.byref(ok)), "policy_segmented")
+        if ok.value:
+            self.groups.append((N.NET_GOV, list(self.classes), torch.cuda.Stream(device=self.device)))
+        else:
+            self.solo_gov = True
 
     @property
     def agent_steps(self):
@@ -84,9 +128,77 @@ class BatchedRollout:
             c["ro"].reset(seed=seed + 7919 * k, pop_sizes=c["pop"])
         torch.cuda.synchronize(self.device)
 
+    @staticmethod
+    def _policy(c, net, t, stream):
+        """One class's policy launch for step t (t = T: values only)."""
+        b, env, pol = c["ro"].buf, c["env"], c["policy"]
+        last = t == c["ro"].T
+        pop = net == N.NET_POP
+        N.check(N.load().policy_forward(
+            C.byref(env.p), _ptr(env.state), net, pol.hidden, pol.precision, _ptr(pol.pop_w if pop else pol.gov_w),
+            _ptr(b["obs"][t] if pop else b["gobs"][t]), _ptr(b["mask"][t] if pop else None), None,
+            None if last else _ptr(b["act"][t] if pop else b["gact"][t]),
+            None if last else _ptr(b["logp"][t] if pop else b["glogp"][t]),
+            _ptr(b["value"][t] if pop else b["gvalue"][t]), None, None, _stream(stream)), "policy_forward")
+
+    @staticmethod
+    def _policy_merged(net, cls, t, stream):
+        """The step-t policy launch of every class in cls, merged."""
+        n = len(cls)
+        pop = net == N.NET_POP
+        last = t == cls[0]["ro"].T
+        P_ = C.c_void_p * n
+        bufs = [c["ro"].buf for c in cls]
+        pol = cls[0]["policy"]
+        params = P_(*[C.addressof(c["env"].p) for c in cls])
+        states = P_(*[_ptr(c["env"].state) for c in cls])
+        obs = P_(*[_ptr(b["obs"][t] if pop else b["gobs"][t]) for b in bufs])
+        mask = P_(*[_ptr(b["mask"][t]) for b in bufs]) if pop else None
+        act = None if last else P_(*[_ptr(b["act"][t] if pop else b["gact"][t]) for b in bufs])
+        logp = None if last else P_(*[_ptr(b["logp"][t] if pop else b["glogp"][t]) for b in bufs])
+        value = P_(*[_ptr(b["value"][t] if pop else b["gvalue"][t]) for b in bufs])
+        N.check(N.load().policy_forward_segments(
+            params, states, n, net, pol.hidden, pol.precision, _ptr(pol.pop_w if pop else pol.gov_w),
+            obs, mask, act, logp, value, _stream(stream)), "policy_forward_segments")
+
+    def _issue_merged(self):
+        """T + 1 steps of {merged policies, per-class env_step}, forked and
+        joined per step, then the slot-0 copies."""
+        main = torch.cuda.current_stream(self.device)
+        T = self.T
+        for t in range(T + 1):
+            for _, _, s in self.groups:
+                s.wait_stream(main)
+            for c in self.classes:
+                c["stream"].wait_stream(main)
+            for net, cls, s in self.groups:
+                self._policy_merged(net, cls, t, s)
+            for c in self.solo:
+                self._policy(c, N.NET_POP, t, c["stream"])
+            if self.solo_gov:
+                for c in self.classes:
+                    self._policy(c, N.NET_GOV, t, c["stream"])
+            if t < T:
+                for c in self.classes:
+                    for _, _, s in self.groups:
+                        c["stream"].wait_stream(s)
+                    b, s = c["ro"].buf, c["stream"]
+                    c["env"].step(1, act=b["act"][t], gov_act=b["gact"][t], stream=s,
+                                  out=dict(rew=b["rew"][t:t + 1], grew=b["grew"][t:t + 1],
+                                           done=b["done"][t:t + 1], obs=b["obs"][t + 1:t + 2],
+                                           gobs=b["gobs"][t + 1:t + 2], mask=b["mask"][t + 1:t + 2]))
+            for _, _, s in self.groups:
+                main.wait_stream(s)
+            for c in self.classes:
+                main.wait_stream(c["stream"])
+        for c in self.classes:
+            c["ro"].carry_over()
+
     def _issue(self):
         """Every class's T-step rollout on its own stream, then the copy of its
         last observation into slot 0 for the next rollout."""
+        if self.merge:
+            return self._issue_merged()
         main = torch.cuda.current_stream(self.device)
         for c in self.classes:
             c["stream"].wait_stream(main)

@@ -57,6 +57,28 @@ struct PolicyArgs {
     float* logits;                // [rows][O] (may be NULL)
 };
 
+// Row segments of one policy launch: several buffers (e.g. several
+// environment classes that share the network) processed by one grid.  Each
+// segment's rows are padded to whole 128-row tiles; tile0 = its first tile.
+constexpr int EJ_MAX_SEG = 16;
+struct PolicySeg {
+    const float* x;
+    const uint32_t* mask;
+    const float* u;
+    const uint32_t* gstep;
+    const uint32_t* key;
+    int32_t* act;
+    float* logp;
+    float* value;
+    float* entropy;
+    float* logits;
+    int rows, per_env, tile0, pad;
+};
+struct PolicySegs {
+    int n;
+    PolicySeg s[EJ_MAX_SEG];
+};
+
 // exp on float32 by Cody-Waite reduction (Cody and Waite, "Software Manual for
 // the Elementary Functions", 1980) and the degree-7 Taylor polynomial of e^r
 // on |r| <= ln2/2, Horner's rule, each operation rounded once; 0 below -80.
@@ -223,5 +245,9 @@ size_t policy_fp32_smem(int in_pad, int H, int O);
 ej_status launch_policy_fp32(const PolicyArgs& a, cudaStream_t stream);
 size_t policy_bf16_smem(int H, int O);
 ej_status launch_policy_bf16(const PolicyArgs& a, cudaStream_t stream);
+// One launch over several row segments sharing the network of `a` (a's own
+// row pointers are ignored); false in *handled when the shape has no
+// segmented kernel (the caller then launches per segment).
+ej_status launch_policy_bf16_segments(const PolicyArgs& a, const PolicySegs& segs, cudaStream_t stream, bool* handled);
 
 }  // namespace ej

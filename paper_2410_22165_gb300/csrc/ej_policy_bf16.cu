@@ -69,14 +69,30 @@ __device__ __forceinline__ void st_shared_v4(uint8_t* p, uint32_t a, uint32_t b,
 // get(n, k).  Work items (chunk of 8 k, row n), rows fastest.
 template <class F>
 __device__ void pack_operand(uint8_t* dst, int rows, int K, F get) {
+    // Items (8 consecutive k of row n) four at a time: all their loads are
+    // issued before any conversion and store, so a thread waits for memory
+    // once per four items rather than once per item.
+    constexpr int G = 4;
     const int items = rows * (K / 8);
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int n = it % rows, kc = it / rows;
-        float v[8];
+    const int step = (int)blockDim.x;
+    for (int it0 = threadIdx.x; it0 < items; it0 += G * step) {
+        float v[G][8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = get(n, kc * 8 + q);
-        st_shared_v4(dst + sw128_offset(n, kc * 8, rows), pack2(v[0], v[1]), pack2(v[2], v[3]),
-                     pack2(v[4], v[5]), pack2(v[6], v[7]));
+        for (int g = 0; g < G; ++g) {
+            const int it = it0 + g * step;
+            const int n = it % rows, kc = it / rows;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[g][q] = it < items ? get(n, kc * 8 + q) : 0.0f;
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int it = it0 + g * step;
+            if (it < items) {
+                const int n = it % rows, kc = it / rows;
+                st_shared_v4(dst + sw128_offset(n, kc * 8, rows), pack2(v[g][0], v[g][1]), pack2(v[g][2], v[g][3]),
+                             pack2(v[g][4], v[g][5]), pack2(v[g][6], v[g][7]));
+            }
+        }
     }
 }
 
@@ -601,7 +617,7 @@ __device__ __forceinline__ bool wg_wait_mma(uint64_t* bar, uint32_t& phase, int 
 // NWG warpgroups (tile pipelines) per CTA; TMEM columns per warpgroup: the
 // 128-column product slot and the head (KT logits or the value).
 template <int KT, int NWG>
-__global__ void __launch_bounds__(128 * NWG, 1) policy_bf16_pp_kernel(PolicyArgs a, int n_actor) {
+__global__ void __launch_bounds__(128 * NWG, 1) policy_bf16_pp_kernel(PolicyArgs a, PolicySegs segs, int n_actor) {
     constexpr int NTH_PP = 128 * NWG;
     // TMEM: product slots of 128 columns at wg * 128, heads after them (32-column aligned)
     constexpr uint32_t HEAD_W = KT == 64 ? 64u : 32u;
@@ -609,6 +625,7 @@ __global__ void __launch_bounds__(128 * NWG, 1) policy_bf16_pp_kernel(PolicyArgs
     static_assert(NWG == 2 || KT == 32, "three pipelines fit TMEM only with 32 logit columns");
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bars[NWG];
+    __shared__ PolicySeg seg_tab[EJ_MAX_SEG];
     __shared__ uint32_t tmem_slot;
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -640,6 +657,7 @@ __global__ void __launch_bounds__(128 * NWG, 1) policy_bf16_pp_kernel(PolicyArgs
         bias[k] = v;
     }
     for (int k = tid; k < NWG * BM * KX * 2 / 16; k += NTH_PP) st_shared_v4(smem + L.x[0] + k * 16, 0u, 0u, 0u, 0u);
+    if (tid < segs.n) seg_tab[tid] = segs.s[tid];
     if (tid == 0) {
         for (int q = 0; q < NWG; ++q) mbar_init(&bars[q], 1);
         fence_mbar_init();
@@ -660,11 +678,18 @@ __global__ void __launch_bounds__(128 * NWG, 1) policy_bf16_pp_kernel(PolicyArgs
     // a tile's observations (contiguous rows): 8 float4 slots per thread of the warpgroup
     constexpr int XS = 8;
     float4 xr[XS];
-    const int n_tiles = (a.rows + BM - 1) / BM;
+    const int n_seg = segs.n;
+    const int n_tiles = segs.s[n_seg - 1].tile0 + (segs.s[n_seg - 1].rows + BM - 1) / BM;
+    auto seg_of = [&](int tile) {
+        int q = 0;
+        while (q + 1 < n_seg && tile >= seg_tab[q + 1].tile0) ++q;
+        return q;
+    };
     auto load_obs = [&](int tile) {
-        const int row0 = tile * BM;
-        const int n = tile < n_tiles ? min(BM, a.rows - row0) * I : 0;
-        const float* src = a.x + (size_t)row0 * I;
+        const PolicySeg& sg = seg_tab[tile < n_tiles ? seg_of(tile) : 0];
+        const int row0 = (tile - sg.tile0) * BM;
+        const int n = tile < n_tiles ? min(BM, sg.rows - row0) * I : 0;
+        const float* src = sg.x + (size_t)(n > 0 ? row0 : 0) * I;
 #pragma unroll
         for (int q = 0; q < XS; ++q) {
             const int f = (wtid + q * 128) * 4;
@@ -717,27 +742,28 @@ __global__ void __launch_bounds__(128 * NWG, 1) policy_bf16_pp_kernel(PolicyArgs
     const int first = role_cta * NWG + wg, stride = role_ctas * NWG;
     if (first < n_tiles) load_obs(first);
     for (int tile = first; tile < n_tiles; tile += stride) {
-        const int row0 = tile * BM;
-        const int nrows = min(BM, a.rows - row0);
+        const PolicySeg& sg = seg_tab[seg_of(tile)];
+        const int row0 = (tile - sg.tile0) * BM;
+        const int nrows = min(BM, sg.rows - row0);
         store_obs();
         const int grow = row0 + row_in_tile;
         const bool live = row_in_tile < nrows;
         uint32_t w0 = 0xFFFFFFFFu, w1 = 0xFFFFFFFFu;
         float us[EJ_MAX_NB] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (actor && live && a.act) {
+        if (actor && live && sg.act) {
             if (a.W) {
-                const uint32_t* mw = a.mask + (size_t)grow * a.W;
+                const uint32_t* mw = sg.mask + (size_t)grow * a.W;
                 w0 = mw[0];
                 w1 = (KT > 32 && a.W > 1) ? mw[1] : 0u;
             }
-            if (a.u) {
+            if (sg.u) {
 #pragma unroll
                 for (int h = 0; h < EJ_MAX_NB; ++h)
-                    if (h < a.n_heads) us[h] = a.u[(size_t)grow * a.n_heads + h];
+                    if (h < a.n_heads) us[h] = sg.u[(size_t)grow * a.n_heads + h];
             } else {
-                const int e = grow / a.per_env, i = grow % a.per_env;
-                const uint4 x = philox4x32_10(make_uint4(a.stream_id == 0 ? (uint32_t)i : 0u, (uint32_t)e, a.gstep[e],
-                                                         (uint32_t)a.stream_id), a.key[0], a.key[1]);
+                const int e = grow / sg.per_env, i = grow % sg.per_env;
+                const uint4 x = philox4x32_10(make_uint4(a.stream_id == 0 ? (uint32_t)i : 0u, (uint32_t)e, sg.gstep[e],
+                                                         (uint32_t)a.stream_id), sg.key[0], sg.key[1]);
                 if (a.stream_id == 0) us[0] = u01(x.w);
                 else { us[0] = u01(x.x); us[1] = u01(x.y); us[2] = u01(x.z); us[3] = u01(x.w); }
             }
@@ -780,29 +806,29 @@ __global__ void __launch_bounds__(128 * NWG, 1) policy_bf16_pp_kernel(PolicyArgs
 #pragma unroll
             for (int j = 0; j < KT; ++j) l[j] = j < O ? l[j] + bias[2 * H + j] : 0.0f;
             if (live) {
-                if (a.logits) {
+                if (sg.logits) {
 #pragma unroll
                     for (int j = 0; j < KT; ++j)
-                        if (j < O) a.logits[(size_t)grow * O + j] = l[j];
+                        if (j < O) sg.logits[(size_t)grow * O + j] = l[j];
                 }
-                if (a.act) {
+                if (sg.act) {
                     float logp = 0.0f, ent = 0.0f;
                     bool none = false;
                     for (int h = 0; h < a.n_heads; ++h) {
                         const float uh = h == 0 ? us[0] : h == 1 ? us[1] : h == 2 ? us[2] : us[3];
                         int act = sample_head_reg<KT>(l, h * a.head, a.head, w0, w1, uh, logp, ent);
                         if (act < 0) { act = 0; none = true; }
-                        a.act[(size_t)grow * a.n_heads + h] = act;
+                        sg.act[(size_t)grow * a.n_heads + h] = act;
                     }
                     if (none) { logp = 0.0f; ent = 0.0f; }
-                    a.logp[grow] = logp;
-                    if (a.entropy) a.entropy[grow] = ent;
+                    sg.logp[grow] = logp;
+                    if (sg.entropy) sg.entropy[grow] = ent;
                 }
             }
         } else {
             float vv[32];
             tmem_ld32(lane_head, vv);                // warp-collective: every lane loads
-            if (live) a.value[grow] = vv[0] + bias[2 * H];
+            if (live) sg.value[grow] = vv[0] + bias[2 * H];
         }
     }
     if (!ok) mbar_wait(bar, phase, 200000000LL);
@@ -815,6 +841,58 @@ __global__ void __launch_bounds__(128 * NWG, 1) policy_bf16_pp_kernel(PolicyArgs
 }  // namespace
 
 size_t policy_bf16_smem(int H, int O) { return bf_layout(H, O).total + 1024; }
+
+namespace {
+
+// The segmented two/three-pipeline kernel: tile pipelines per CTA (three for
+// up to 32 logits, two otherwise), actor and critic in separate CTAs.
+ej_status launch_pp(const PolicyArgs& a, const PolicySegs& segs, cudaStream_t stream) {
+    const int kt = a.O <= 32 ? 0 : 1;
+    const int nwg = kt == 0 ? PP_WG32 : 2;
+    const size_t smem_pp = pp_layout(a.H, a.O, nwg).total + 1024;
+    static size_t conf_pp[2] = {0, 0};
+    if (conf_pp[kt] < smem_pp) {
+        cudaError_t err = cudaFuncSetAttribute(kt == 0 ? policy_bf16_pp_kernel<32, PP_WG32> : policy_bf16_pp_kernel<64, 2>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pp);
+        if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
+        conf_pp[kt] = smem_pp;
+    }
+    // one CTA per SM; the actor (two layers, head, sampler) gets 3/5 of them, the split
+    // measured best on E = 4096 x A = 100 (three pipelines: 1/2 0.217 ms, 3/5 0.186 ms,
+    // 5/8 0.185 ms, 2/3 0.191 ms)
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 2)
+            sms = 2;
+    }
+    const PolicySeg& last = segs.s[segs.n - 1];
+    const int n_tiles = last.tile0 + (last.rows + BM - 1) / BM;
+    const int pairs = (n_tiles + nwg - 1) / nwg;          // tiles are taken nwg at a time per CTA
+    int n_act = sms * PP_ACT_NUM / PP_ACT_DEN, n_cri = sms - sms * PP_ACT_NUM / PP_ACT_DEN;
+    n_act = n_act < pairs ? n_act : pairs;
+    n_cri = n_cri < pairs ? n_cri : pairs;
+    if (n_act < 1) n_act = 1;
+    if (n_cri < 1) n_cri = 1;
+    if (kt == 0) policy_bf16_pp_kernel<32, PP_WG32><<<n_act + n_cri, 128 * PP_WG32, smem_pp, stream>>>(a, segs, n_act);
+    else policy_bf16_pp_kernel<64, 2><<<n_act + n_cri, 256, smem_pp, stream>>>(a, segs, n_act);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "bf16 policy launch: %s", cudaGetErrorString(err));
+    return EJ_OK;
+}
+
+}  // namespace
+
+ej_status launch_policy_bf16_segments(const PolicyArgs& a, const PolicySegs& segs, cudaStream_t stream,
+                                      bool* handled) {
+    *handled = false;
+    if (segs.n < 1 || segs.n > EJ_MAX_SEG) return fail(EJ_ERR_ARG, "bf16 policy: 1 to %d segments", EJ_MAX_SEG);
+    if (!(a.H == 128 && a.O <= 64 && a.in_dim <= 32 && a.W <= 2 && a.n_heads <= EJ_MAX_NB)) return EJ_OK;
+    for (int q = 0; q < segs.n; ++q)
+        if (((uintptr_t)segs.s[q].x & 15) != 0) return EJ_OK;
+    *handled = true;
+    return launch_pp(a, segs, stream);
+}
 
 ej_status launch_policy_bf16(const PolicyArgs& a, cudaStream_t stream) {
     if (a.H != 64 && a.H != 128) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: hidden must be 64 or 128");
@@ -835,37 +913,13 @@ ej_status launch_policy_bf16(const PolicyArgs& a, cudaStream_t stream) {
     if (grid < 1) grid = 1;
     const bool fast = a.O <= 64 && a.in_dim <= 32 && a.W <= 2 && a.n_heads <= EJ_MAX_NB && ((uintptr_t)a.x & 15) == 0;
     if (fast && a.H == 128) {
-        // tile pipelines per CTA (three for up to 32 logits, two otherwise), actor and critic in separate CTAs
-        const int kt = a.O <= 32 ? 0 : 1;
-        const int nwg = kt == 0 ? PP_WG32 : 2;
-        const size_t smem_pp = pp_layout(a.H, a.O, nwg).total + 1024;
-        static size_t conf_pp[2] = {0, 0};
-        if (conf_pp[kt] < smem_pp) {
-            cudaError_t err = cudaFuncSetAttribute(kt == 0 ? policy_bf16_pp_kernel<32, PP_WG32> : policy_bf16_pp_kernel<64, 2>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pp);
-            if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
-            conf_pp[kt] = smem_pp;
-        }
-        // one CTA per SM; the actor (two layers, head, sampler) gets 3/5 of them, the split
-        // measured best on E = 4096 x A = 100 (three pipelines: 1/2 0.217 ms, 3/5 0.186 ms,
-        // 5/8 0.185 ms, 2/3 0.191 ms)
-        static int sms = 0;
-        if (sms == 0) {
-            int dev = 0;
-            if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 2)
-                sms = 2;
-        }
-        const int pairs = (n_tiles + nwg - 1) / nwg;          // tiles are taken nwg at a time per CTA
-        int n_act = sms * PP_ACT_NUM / PP_ACT_DEN, n_cri = sms - sms * PP_ACT_NUM / PP_ACT_DEN;
-        n_act = n_act < pairs ? n_act : pairs;
-        n_cri = n_cri < pairs ? n_cri : pairs;
-        if (n_act < 1) n_act = 1;
-        if (n_cri < 1) n_cri = 1;
-        if (kt == 0) policy_bf16_pp_kernel<32, PP_WG32><<<n_act + n_cri, 128 * PP_WG32, smem_pp, stream>>>(a, n_act);
-        else policy_bf16_pp_kernel<64, 2><<<n_act + n_cri, 256, smem_pp, stream>>>(a, n_act);
-        cudaError_t err = cudaGetLastError();
-        if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "bf16 policy launch: %s", cudaGetErrorString(err));
-        return EJ_OK;
+        PolicySegs segs;
+        segs.n = 1;
+        PolicySeg& g = segs.s[0];
+        g.x = a.x; g.mask = a.mask; g.u = a.u; g.gstep = a.gstep; g.key = a.key;
+        g.act = a.act; g.logp = a.logp; g.value = a.value; g.entropy = a.entropy; g.logits = a.logits;
+        g.rows = a.rows; g.per_env = a.per_env; g.tile0 = 0; g.pad = 0;
+        return launch_pp(a, segs, stream);
     }
     if (fast) {
         static size_t conf_fast[2] = {0, 0};

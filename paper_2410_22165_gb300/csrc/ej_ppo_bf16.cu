@@ -146,14 +146,30 @@ __device__ __forceinline__ bool wait_mma(uint64_t* bar, uint32_t& phase) {
 // Packs rows x K of a K-major operand from a float source get(n, k).
 template <class F>
 __device__ void pack_operand(uint8_t* dst, int rows, int K, F get) {
+    // Items (8 consecutive k of row n) four at a time: all their loads are
+    // issued before any conversion and store, so a thread waits for memory
+    // once per four items rather than once per item.
+    constexpr int G = 4;
     const int items = rows * (K / 8);
-    for (int it = threadIdx.x; it < items; it += BT) {
-        const int n = it % rows, kc = it / rows;
-        float v[8];
+    const int step = (int)blockDim.x;
+    for (int it0 = threadIdx.x; it0 < items; it0 += G * step) {
+        float v[G][8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = get(n, kc * 8 + q);
-        st_shared_v4(dst + sw128_offset(n, kc * 8, rows), pack2(v[0], v[1]), pack2(v[2], v[3]),
-                     pack2(v[4], v[5]), pack2(v[6], v[7]));
+        for (int g = 0; g < G; ++g) {
+            const int it = it0 + g * step;
+            const int n = it % rows, kc = it / rows;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[g][q] = it < items ? get(n, kc * 8 + q) : 0.0f;
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int it = it0 + g * step;
+            if (it < items) {
+                const int n = it % rows, kc = it / rows;
+                st_shared_v4(dst + sw128_offset(n, kc * 8, rows), pack2(v[g][0], v[g][1]), pack2(v[g][2], v[g][3]),
+                             pack2(v[g][4], v[g][5]), pack2(v[g][6], v[g][7]));
+            }
+        }
     }
 }
 

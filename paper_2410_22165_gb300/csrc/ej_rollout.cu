@@ -91,6 +91,66 @@ ej_status policy_forward(const EjParams* p, const void* state, int32_t net, int3
     return launch_policy(a, precision, (cudaStream_t)stream);
 }
 
+ej_status policy_segmented(const EjParams* p, int32_t net, int32_t hidden, int32_t precision, int32_t* ok) {
+    if (!ok) return fail(EJ_ERR_ARG, "policy_segmented: NULL argument");
+    *ok = 0;
+    Layout lay;
+    KParams kp;
+    ej_status st = derive(p, &lay, &kp);
+    if (st != EJ_OK) return st;
+    int in_dim, O, heads, head;
+    if ((st = net_shape(p, kp, net, hidden, &in_dim, &O, &heads, &head)) != EJ_OK) return st;
+    const int W = net == EJ_NET_POP ? kp.W : 0;
+    *ok = precision == EJ_BF16 && hidden == 128 && O <= 64 && in_dim <= 32 && W <= 2 && heads <= EJ_MAX_NB;
+    return EJ_OK;
+}
+
+ej_status policy_forward_segments(const EjParams* const* params, const void* const* states, int32_t n_seg,
+                                  int32_t net, int32_t hidden, int32_t precision, const float* weights,
+                                  const float* const* obs, const uint32_t* const* mask, int32_t* const* act,
+                                  float* const* logp, float* const* value, void* stream) {
+    if (n_seg < 1 || !params || !states || !obs || !value) return fail(EJ_ERR_ARG, "policy_forward_segments: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int base = 0; base < n_seg; base += EJ_MAX_SEG) {
+        const int n = n_seg - base < EJ_MAX_SEG ? n_seg - base : EJ_MAX_SEG;
+        PolicyArgs args[EJ_MAX_SEG];
+        PolicySegs segs;
+        segs.n = n;
+        int tile = 0;
+        for (int q = 0; q < n; ++q) {
+            const int k = base + q;
+            Layout lay;
+            KParams kp;
+            ej_status st = derive(params[k], &lay, &kp);
+            if (st != EJ_OK) return st;
+            st = make_args(params[k], kp, lay, states[k], net, hidden, weights, obs[k], mask ? mask[k] : nullptr,
+                           nullptr, act ? act[k] : nullptr, logp ? logp[k] : nullptr, value[k], nullptr, nullptr,
+                           &args[q]);
+            if (st != EJ_OK) return st;
+            const PolicyArgs& a = args[q];
+            if (a.in_dim != args[0].in_dim || a.O != args[0].O || a.n_heads != args[0].n_heads ||
+                a.head != args[0].head || a.W != args[0].W)
+                return fail(EJ_ERR_ARG, "policy_forward_segments: segment %d has another network shape", k);
+            PolicySeg& g = segs.s[q];
+            g.x = a.x; g.mask = a.mask; g.u = nullptr; g.gstep = a.gstep; g.key = a.key;
+            g.act = a.act; g.logp = a.logp; g.value = a.value; g.entropy = nullptr; g.logits = nullptr;
+            g.rows = a.rows; g.per_env = a.per_env; g.tile0 = tile; g.pad = 0;
+            tile += (a.rows + 127) / 128;
+        }
+        bool handled = false;
+        if (precision == EJ_BF16) {
+            ej_status st = launch_policy_bf16_segments(args[0], segs, s, &handled);
+            if (st != EJ_OK) return st;
+        }
+        if (!handled)
+            for (int q = 0; q < n; ++q) {
+                ej_status st = launch_policy(args[q], precision, s);
+                if (st != EJ_OK) return st;
+            }
+    }
+    return EJ_OK;
+}
+
 ej_status rollout(const EjParams* p, void* state, int32_t T, int32_t hidden, int32_t precision,
                   const float* pop_weights, const float* gov_weights, const EjRollout* b,
                   void* stream) {

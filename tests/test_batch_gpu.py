@@ -87,3 +87,29 @@ def test_autotune_returns_a_candidate():
     import paper_2410_22165_gb300 as P
     best, rates = P.autotune(POPS, LEVELS, _weights(5), T_probe=4, repeats=1, T_ep=20, T_tax=5)
     assert best in rates and all(r > 0 for r in rates.values())
+
+
+@pytest.mark.parametrize("granularity", ["exact", "coarse"])
+def test_merged_policy_launches_equal_per_class_rollouts(granularity):
+    """Policy launches merged across classes (one per network shape) give the
+    per-class rollouts' buffers and states bit for bit, eager and captured."""
+    import paper_2410_22165_gb300 as P
+    T = 7
+    kw = dict(T_ep=5, T_tax=3)
+    w = _weights(6)
+    a = P.BatchedRollout(POPS, LEVELS, T, w, granularity=granularity, merge=False, **kw)
+    b = P.BatchedRollout(POPS, LEVELS, T, w, granularity=granularity, merge=True, **kw)
+    assert b.groups and all(len(cls) >= 1 for _, cls, _ in b.groups)
+    a.reset(seed=12)
+    b.reset(seed=12)
+    a.run()
+    b.run()
+    for _ in range(2):
+        a.run()
+    b.capture()                 # one eager run inside, then the graph
+    b.run()
+    torch.cuda.synchronize()
+    for ca, cb in zip(a.classes, b.classes):
+        for n, v in ca["ro"].buf.items():
+            assert torch.equal(v, cb["ro"].buf[n]), n
+        assert torch.equal(ca["env"].state, cb["env"].state)
