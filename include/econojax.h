@@ -255,23 +255,27 @@ ej_status policy_forward(const EjParams* p, const void* state, int32_t net, int3
                          const uint32_t* mask, const float* u, int32_t* act, float* logp,
                          float* value, float* entropy, float* logits, void* stream);
 
-/* policy_forward_segments: policy_forward over n_seg row sets that share one
- * network (same net, hidden, weights and observation / action shapes), e.g.
- * the environment classes of a batch of uneven populations: params[k],
- * states[k], obs[k], mask[k], act[k], logp[k], value[k] as in policy_forward
- * for set k (mask, act, logp arrays may be NULL; entries as there).  Sets are
- * processed 16 at a time by one launch each when the shape has a segmented
- * BF16 kernel (hidden 128, <= 64 logits, <= 32 inputs), else one launch per
- * set.  Results equal separate policy_forward calls. */
-/* policy_segmented: *ok (host) = 1 when policy_forward_segments processes
- * sets of this network shape (params' observation / action sizes, net,
- * hidden, precision) in one launch per 16 sets, else 0. */
-ej_status policy_segmented(const EjParams* p, int32_t net, int32_t hidden, int32_t precision, int32_t* ok);
+/* policy_forward_segments: policy_forward over n_seg row sets in as few
+ * launches as the kernels allow, e.g. the population and government
+ * networks of several environment classes of a batch of uneven populations.
+ * Set k: params[k], states[k] (device), nets[k] (EJ_NET_POP / EJ_NET_GOV),
+ * weights[k] (device), obs[k], mask[k], act[k], logp[k], value[k] as in
+ * policy_forward (the mask, act and logp arrays may be NULL, and so may their
+ * entries; a government set takes no mask).  hidden and precision are common.
+ * In BF16 with hidden 128, sets whose network has <= 96 logits and <= 32
+ * inputs share launches: up to 4 networks (sets with the same weights
+ * pointer, network and shape) and 32 sets per launch, CTAs split between
+ * them by rows; other sets get a launch each.  Results equal separate
+ * policy_forward calls.  Host arrays are read during the call only. */
+ej_status policy_forward_segments(int32_t n_seg, const EjParams* const* params, const void* const* states,
+                                  const int32_t* nets, const float* const* weights, int32_t hidden,
+                                  int32_t precision, const float* const* obs, const uint32_t* const* mask,
+                                  int32_t* const* act, float* const* logp, float* const* value, void* stream);
 
-ej_status policy_forward_segments(const EjParams* const* params, const void* const* states, int32_t n_seg,
-                                  int32_t net, int32_t hidden, int32_t precision, const float* weights,
-                                  const float* const* obs, const uint32_t* const* mask, int32_t* const* act,
-                                  float* const* logp, float* const* value, void* stream);
+/* policy_segmented: *ok (host) = 1 when policy_forward_segments puts sets
+ * of this network shape (params' observation / action sizes, net, hidden,
+ * precision) into shared launches, else 0 (one launch per set). */
+ej_status policy_segmented(const EjParams* p, int32_t net, int32_t hidden, int32_t precision, int32_t* ok);
 
 /* Rollout buffer (device pointers, caller-owned).  Slot 0 of obs, gobs and
  * mask must hold the current observation (from env_reset or the previous

@@ -91,8 +91,9 @@ _PROTOS = {
                                      C.c_int32, C.c_int32, _VP, C.c_void_p, _VP, C.c_uint32, C.c_int32,
                                      _VP, _VP, _VP]),
     "policy_segmented": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
-    "policy_forward_segments": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
-                                          _VP, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, _VP]),
+    "policy_forward_segments": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                          C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          _VP]),
     "ppo_minibatch_moments": (C.c_int, [C.POINTER(EjParams), C.POINTER(EjPpoParams), C.c_int32, C.c_int32,
                                         C.c_void_p, _VP, C.c_uint32, C.c_int32, _VP, _VP]),
     "ppo_minibatch_grad_global": (C.c_int, [C.POINTER(EjParams), C.POINTER(EjPpoParams), C.c_int32, C.c_int32,

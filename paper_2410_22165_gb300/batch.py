@@ -11,18 +11,14 @@ government policy and env_step per step) on its own stream; the T-step
 rollouts of all classes are captured as parallel branches of one CUDA graph,
 so a whole batched rollout is one graph launch.
 
-With ``merge`` the policy launches of a step are merged across
-classes: every network shape that the segmented BF16 policy kernel takes (the
-government network, and the population networks of up to 64 actions) runs as
-one launch over the rows of all classes that use it (policy_forward_segments;
-one table entry per class), the other population networks per class on the
-class's stream; then each class's env_step runs on its own stream.  Per step
-the graph holds one node per merged network, one per unmerged class policy and
-one env_step per class, instead of three launches per class.  The values,
-actions and states are those of the per-class rollouts, bit for bit.  The
-merged form joins all classes at every step, which costs more than the
-per-class streams save when the classes' policy launches are short, so it is
-off by default and the autotuner can compare both.
+With ``merge`` the policy launches of a step are merged across classes:
+the population networks (one per price grid) and the government network of
+all classes run as one launch of the BF16 kernel, which splits its CTAs
+between the networks by rows (policy_forward_segments, one table entry per
+class and network); then each class's env_step runs on its own stream.  Per
+step the graph holds one policy node and one env_step node per class instead
+of three launches per class.  The values, actions and states are those of the
+per-class rollouts, bit for bit.
 
 The partition is a tuning choice: ``exact`` (one class per distinct
 (P, population)), ``pow2`` (populations rounded up to a power of two: one CTA
@@ -82,6 +78,8 @@ class BatchedRollout:
         self.device = torch.device(device)
         self.granularity = granularity
         self.merge = merge
+        # one device copy per network: classes with the same price grid share it
+        weights = {k: v.to(self.device, torch.float32).contiguous() for k, v in weights.items()}
         self.classes = []
         for P, A_max, idx in plan_classes(self.pops, self.levels, granularity):
             env = VecEnv(len(idx), A_max, device=self.device, **price_grid(P), **env_kw)
@@ -91,33 +89,6 @@ class BatchedRollout:
             self.classes.append(dict(P=P, A_max=A_max, idx=idx, env=env, policy=pol, ro=ro, pop=pop,
                                      stream=torch.cuda.Stream(device=self.device)))
         self.graph = None
-        self._plan_merge(hidden, precision)
-
-    def _plan_merge(self, hidden, precision):
-        """Groups of classes whose policy launches merge: [(net, classes, stream)]
-        and the classes whose population policy runs on their own stream."""
-        self.groups, self.solo, self.solo_gov = [], [], False
-        if not self.merge:
-            return
-        lib = N.load()
-        ok = C.c_int32()
-        by_P = OrderedDict()
-        for c in self.classes:
-            N.check(lib.policy_segmented(C.byref(c["env"].p), N.NET_POP, hidden, c["policy"].precision,
-                                         C.byref(ok)), "policy_segmented")
-            if ok.value:
-                by_P.setdefault(c["P"], []).append(c)
-            else:
-                self.solo.append(c)
-        for cls in by_P.values():
-            self.groups.append((N.NET_POP, cls, torch.cuda.Stream(device=self.device)))
-        c0 = self.classes[0]
-        N.check(lib.policy_segmented(C.byref(c0["env"].p), N.NET_GOV, hidden, c0["policy"].precision,
-                                     C.byref(ok)), "policy_segmented")
-        if ok.value:
-            self.groups.append((N.NET_GOV, list(self.classes), torch.cuda.Stream(device=self.device)))
-        else:
-            self.solo_gov = True
 
     @property
     def agent_steps(self):
@@ -128,67 +99,46 @@ class BatchedRollout:
             c["ro"].reset(seed=seed + 7919 * k, pop_sizes=c["pop"])
         torch.cuda.synchronize(self.device)
 
-    @staticmethod
-    def _policy(c, net, t, stream):
-        """One class's policy launch for step t (t = T: values only)."""
-        b, env, pol = c["ro"].buf, c["env"], c["policy"]
-        last = t == c["ro"].T
-        pop = net == N.NET_POP
-        N.check(N.load().policy_forward(
-            C.byref(env.p), _ptr(env.state), net, pol.hidden, pol.precision, _ptr(pol.pop_w if pop else pol.gov_w),
-            _ptr(b["obs"][t] if pop else b["gobs"][t]), _ptr(b["mask"][t] if pop else None), None,
-            None if last else _ptr(b["act"][t] if pop else b["gact"][t]),
-            None if last else _ptr(b["logp"][t] if pop else b["glogp"][t]),
-            _ptr(b["value"][t] if pop else b["gvalue"][t]), None, None, _stream(stream)), "policy_forward")
+    def _policies(self, t, stream):
+        """Step t's policy launches of every class (population and government
+        networks) in one policy_forward_segments call (t = T: values only)."""
+        n = 2 * len(self.classes)
+        last = t == self.T
+        V = C.c_void_p * n
+        segs = [(c, net) for c in self.classes for net in (N.NET_POP, N.NET_GOV)]
 
-    @staticmethod
-    def _policy_merged(net, cls, t, stream):
-        """The step-t policy launch of every class in cls, merged."""
-        n = len(cls)
-        pop = net == N.NET_POP
-        last = t == cls[0]["ro"].T
-        P_ = C.c_void_p * n
-        bufs = [c["ro"].buf for c in cls]
-        pol = cls[0]["policy"]
-        params = P_(*[C.addressof(c["env"].p) for c in cls])
-        states = P_(*[_ptr(c["env"].state) for c in cls])
-        obs = P_(*[_ptr(b["obs"][t] if pop else b["gobs"][t]) for b in bufs])
-        mask = P_(*[_ptr(b["mask"][t]) for b in bufs]) if pop else None
-        act = None if last else P_(*[_ptr(b["act"][t] if pop else b["gact"][t]) for b in bufs])
-        logp = None if last else P_(*[_ptr(b["logp"][t] if pop else b["glogp"][t]) for b in bufs])
-        value = P_(*[_ptr(b["value"][t] if pop else b["gvalue"][t]) for b in bufs])
+        def buf(c, pop_key, gov_key, net):
+            return _ptr(c["ro"].buf[pop_key if net == N.NET_POP else gov_key][t])
+
+        pol = self.classes[0]["policy"]
         N.check(N.load().policy_forward_segments(
-            params, states, n, net, pol.hidden, pol.precision, _ptr(pol.pop_w if pop else pol.gov_w),
-            obs, mask, act, logp, value, _stream(stream)), "policy_forward_segments")
+            n, V(*[C.addressof(c["env"].p) for c, _ in segs]), V(*[_ptr(c["env"].state) for c, _ in segs]),
+            (C.c_int32 * n)(*[net for _, net in segs]),
+            V(*[_ptr(c["policy"].pop_w if net == N.NET_POP else c["policy"].gov_w) for c, net in segs]),
+            pol.hidden, pol.precision, V(*[buf(c, "obs", "gobs", net) for c, net in segs]),
+            V(*[buf(c, "mask", None, net) if net == N.NET_POP else None for c, net in segs]),
+            None if last else V(*[buf(c, "act", "gact", net) for c, net in segs]),
+            None if last else V(*[buf(c, "logp", "glogp", net) for c, net in segs]),
+            V(*[buf(c, "value", "gvalue", net) for c, net in segs]), _stream(stream)),
+            "policy_forward_segments")
 
     def _issue_merged(self):
-        """T + 1 steps of {merged policies, per-class env_step}, forked and
-        joined per step, then the slot-0 copies."""
+        """T + 1 steps of {every class's policies in one call on the calling
+        stream, then each class's env_step on its own stream}, then the
+        slot-0 copies."""
         main = torch.cuda.current_stream(self.device)
         T = self.T
         for t in range(T + 1):
-            for _, _, s in self.groups:
-                s.wait_stream(main)
+            self._policies(t, main)
+            if t == T:
+                break
             for c in self.classes:
                 c["stream"].wait_stream(main)
-            for net, cls, s in self.groups:
-                self._policy_merged(net, cls, t, s)
-            for c in self.solo:
-                self._policy(c, N.NET_POP, t, c["stream"])
-            if self.solo_gov:
-                for c in self.classes:
-                    self._policy(c, N.NET_GOV, t, c["stream"])
-            if t < T:
-                for c in self.classes:
-                    for _, _, s in self.groups:
-                        c["stream"].wait_stream(s)
-                    b, s = c["ro"].buf, c["stream"]
-                    c["env"].step(1, act=b["act"][t], gov_act=b["gact"][t], stream=s,
-                                  out=dict(rew=b["rew"][t:t + 1], grew=b["grew"][t:t + 1],
-                                           done=b["done"][t:t + 1], obs=b["obs"][t + 1:t + 2],
-                                           gobs=b["gobs"][t + 1:t + 2], mask=b["mask"][t + 1:t + 2]))
-            for _, _, s in self.groups:
-                main.wait_stream(s)
+                b = c["ro"].buf
+                c["env"].step(1, act=b["act"][t], gov_act=b["gact"][t], stream=c["stream"],
+                              out=dict(rew=b["rew"][t:t + 1], grew=b["grew"][t:t + 1],
+                                       done=b["done"][t:t + 1], obs=b["obs"][t + 1:t + 2],
+                                       gobs=b["gobs"][t + 1:t + 2], mask=b["mask"][t + 1:t + 2]))
             for c in self.classes:
                 main.wait_stream(c["stream"])
         for c in self.classes:

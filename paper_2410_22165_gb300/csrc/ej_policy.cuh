@@ -58,9 +58,11 @@ struct PolicyArgs {
 };
 
 // Row segments of one policy launch: several buffers (e.g. several
-// environment classes that share the network) processed by one grid.  Each
-// segment's rows are padded to whole 128-row tiles; tile0 = its first tile.
-constexpr int EJ_MAX_SEG = 16;
+// environment classes that share a network) processed by one grid.  Each
+// segment's rows are padded to whole 128-row tiles; tile0 = its first tile
+// within its network's tiles.
+constexpr int EJ_MAX_SEG = 32;
+constexpr int EJ_MAX_NET = 4;
 struct PolicySeg {
     const float* x;
     const uint32_t* mask;
@@ -74,10 +76,27 @@ struct PolicySeg {
     float* logits;
     int rows, per_env, tile0, pad;
 };
-struct PolicySegs {
-    int n;
-    PolicySeg s[EJ_MAX_SEG];
+// A network of a launch: its weights and shape, its segments
+// [seg_lo, seg_hi) and its CTAs (actors [cta0, cta0 + n_act), critics after).
+struct PolicyNet {
+    const float* weights;
+    int in_dim, O, n_heads, head, W, stream_id;
+    int seg_lo, seg_hi, n_tiles;
+    int cta0, n_act, n_cri;
 };
+struct PolicyLaunch {
+    int H, n3_max, n_net, n_seg;
+    PolicyNet net[EJ_MAX_NET];
+    PolicySeg seg[EJ_MAX_SEG];
+};
+
+// One launch of the pipelined BF16 kernel over segs[0..n) (each a PolicyArgs
+// of its own rows; segments with the same weights and shape form one
+// network, at most EJ_MAX_NET networks and EJ_MAX_SEG segments).  *handled =
+// false (nothing launched) when a shape is outside the kernel's range
+// (hidden 128, <= 96 logits, <= 32 inputs, <= 4 mask words) or an
+// observation buffer is not 16-byte aligned.
+ej_status launch_policy_bf16_multi(const PolicyArgs* segs, int n, cudaStream_t stream, bool* handled);
 
 // exp on float32 by Cody-Waite reduction (Cody and Waite, "Software Manual for
 // the Elementary Functions", 1980) and the degree-7 Taylor polynomial of e^r
@@ -248,6 +267,5 @@ ej_status launch_policy_bf16(const PolicyArgs& a, cudaStream_t stream);
 // One launch over several row segments sharing the network of `a` (a's own
 // row pointers are ignored); false in *handled when the shape has no
 // segmented kernel (the caller then launches per segment).
-ej_status launch_policy_bf16_segments(const PolicyArgs& a, const PolicySegs& segs, cudaStream_t stream, bool* handled);
 
 }  // namespace ej

@@ -550,38 +550,45 @@ __global__ void __launch_bounds__(BT, 1) policy_bf16_fast_kernel(PolicyArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Two tile pipelines per CTA.  Actor and critic run in different CTAs (the
-// sampler needs only the actor; the value is only written out), which halves
-// the weights a CTA holds; each of its two warpgroups then runs its own
+// Several tile pipelines per CTA.  Actor and critic run in different CTAs
+// (the sampler needs only the actor; the value is only written out), which
+// halves the weights a CTA holds; each of its warpgroups then runs its own
 // sequence of 128-row tiles with its own observation and activation buffers,
-// its own half of TMEM and its own mbarrier, synchronising only through a
+// its own TMEM columns and its own mbarrier, synchronising only through a
 // named barrier of its 128 threads.  While one warpgroup runs an epilogue or
-// the sampler, the tensor core runs the other's products.
+// the sampler, the tensor core runs the others' products.
 
-constexpr int PP_MAX_WG = 3;
-#ifndef PP_WG32
-#define PP_WG32 3     // tile pipelines per CTA for <= 32 logits
-#endif
-#ifndef PP_ACT_NUM
-#define PP_ACT_NUM 3  // share of the CTAs that run the actor: PP_ACT_NUM / PP_ACT_DEN
-#define PP_ACT_DEN 5
-#endif
+// ---------------------------------------------------------------------------
+// Pipelined kernel for hidden 128, up to 96 logits and 32 inputs, several
+// networks per launch.  PP_NWG warpgroups per CTA, each an independent tile
+// pipeline with its own observation and hidden operands in shared memory and
+// its own 128 TMEM columns, which hold the layer products and then the head.
+// Each CTA serves one network in one role (actor or critic): it packs that
+// network's weights once and then takes that network's tiles PP_NWG at a time.
+
+constexpr int PP_NWG = 3;       // tile pipelines per CTA
+constexpr int PP_MAX_O = 96;    // logits: the head operand [N3][H] fits beside three pipelines
+constexpr int PP_SCR = 64;      // exp weights a thread keeps in shared memory per head
+// Cost of a tile in thousands of SM cycles, measured with clock64 stamps per
+// phase on GB300 (hidden 128): the critic's tile about 12 (observations,
+// three products, two epilogues); the actor's the same plus about 3 per group
+// of 8 logit columns its heads scan (24 logits: 9.3, 63 logits in three heads
+// of 21: 28, 84 logits: 35).
+constexpr double PP_TILE_BASE = 12.0, PP_TILE_GROUP = 3.0;
 
 struct PpLayout {
-    uint32_t w1, w2, w3, x[PP_MAX_WG], h[PP_MAX_WG], bias, total;
-    int N3;
+    uint32_t w1, w2, w3, x[PP_NWG], h[PP_NWG], bias, total;
 };
 
-__host__ __device__ inline PpLayout pp_layout(int H, int O, int nwg) {
+__host__ __device__ inline PpLayout pp_layout(int H, int n3_max) {
     PpLayout L;
-    L.N3 = (O + 15) / 16 * 16;
     uint32_t b = 0;
-    L.w1 = b; b += (uint32_t)H * KX * 2;                         // [H][KX]
-    L.w2 = b; b += (uint32_t)H * H * 2;                          // [H][H]
-    L.w3 = b; b += (uint32_t)(L.N3 > 16 ? L.N3 : 16) * H * 2;    // [N3][H] (actor) or [16][H] (critic)
-    for (int w = 0; w < nwg; ++w) { L.x[w] = b; b += BM * KX * 2; }
-    for (int w = 0; w < nwg; ++w) { L.h[w] = b; b += (uint32_t)BM * H * 2; }
-    L.bias = b; b += ((2u * H + (uint32_t)O + 4) * 4 + 1023) & ~1023u;
+    L.w1 = b; b += (uint32_t)H * KX * 2;                        // [H][KX]
+    L.w2 = b; b += (uint32_t)H * H * 2;                         // [H][H]
+    L.w3 = b; b += (uint32_t)(n3_max > 16 ? n3_max : 16) * H * 2;   // [N3][H] (actor) or [16][H] (critic)
+    for (int w = 0; w < PP_NWG; ++w) { L.x[w] = b; b += BM * KX * 2; }
+    for (int w = 0; w < PP_NWG; ++w) { L.h[w] = b; b += (uint32_t)BM * H * 2; }
+    L.bias = b; b += ((2u * H + (uint32_t)n3_max + 4) * 4 + 1023) & ~1023u;   // layer 1 | layer 2 | head (to N3)
     L.total = b;
     return L;
 }
@@ -614,18 +621,104 @@ __device__ __forceinline__ bool wg_wait_mma(uint64_t* bar, uint32_t& phase, int 
     return all;
 }
 
-// NWG warpgroups (tile pipelines) per CTA; TMEM columns per warpgroup: the
-// 128-column product slot and the head (KT logits or the value).
-template <int KT, int NWG>
-__global__ void __launch_bounds__(128 * NWG, 1) policy_bf16_pp_kernel(PolicyArgs a, PolicySegs segs, int n_actor) {
-    constexpr int NTH_PP = 128 * NWG;
-    // TMEM: product slots of 128 columns at wg * 128, heads after them (32-column aligned)
-    constexpr uint32_t HEAD_W = KT == 64 ? 64u : 32u;
-    static_assert(NWG * 128 + NWG * HEAD_W <= TMEM_COLS, "TMEM columns");
-    static_assert(NWG == 2 || KT == 32, "three pipelines fit TMEM only with 32 logit columns");
+// The inverse-CDF draw of one head: logits = this lane's TMEM columns
+// [lo, lo + K) + the head bias b3, under the mask words mw.  Same operations
+// in the same order as sample_head, so the draw is the same.  Each pass walks
+// the head in groups of 8 columns (one 8-column TMEM load each) in a loop
+// that is not unrolled: the sampler runs once per row and tile, and a long
+// unrolled body would be fetched from L2 every time.  Every step within a
+// group is a select on the column's valid bit (the lanes' masks differ).  The
+// exp weights of the first PP_SCR columns are kept in scr (this thread's
+// column of a [PP_SCR][128] float array), the others are recomputed.  lo and
+// K are warp-uniform (every lane loads).  Returns the action (-1: nothing
+// allowed) and adds the head's log probability and entropy.
+__device__ __forceinline__ uint32_t group_bits(const uint32_t (&mw)[4], int g, int lo, int hi) {
+    const int c = g >> 5;
+    const uint32_t wd = c == 0 ? mw[0] : c == 1 ? mw[1] : c == 2 ? mw[2] : mw[3];
+    uint32_t b = (wd >> (g & 31)) & 0xFFu;                  // mask bits of columns g .. g + 7
+    if (lo > g) b &= 0xFFu << (lo - g);                     // lo - g < 8: g starts at lo rounded down
+    if (hi - g < 8) b &= (1u << (hi - g)) - 1u;
+    return b;
+}
+
+__device__ __forceinline__ int sample_head_tmem(uint32_t taddr, const float* b3, int lo, int K, const uint32_t (&mw)[4],
+                                             float u, float* scr, float& logp, float& ent) {
+    const int g0 = lo & ~7, hi = lo + K;
+    float m = -FLT_MAX;
+    uint32_t any = 0;
+#pragma unroll 1
+    for (int g = g0; g < hi; g += 8) {
+        float v[8];
+        tmem_ld8(taddr + (uint32_t)g, v);
+        const uint32_t vb = group_bits(mw, g, lo, hi);
+        any |= vb;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) m = ((vb >> j) & 1u) ? fmaxf(m, v[j] + b3[g + j]) : m;
+    }
+    float S = 0.0f, dot = 0.0f;
+#pragma unroll 1
+    for (int g = g0; g < hi; g += 8) {
+        float v[8];
+        tmem_ld8(taddr + (uint32_t)g, v);
+        const uint32_t vb = group_bits(mw, g, lo, hi);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const bool ok = (vb >> j) & 1u;
+            const float d = ok ? __fsub_rn(v[j] + b3[g + j], m) : 0.0f;
+            const float wj = exp32(d);
+            S = ok ? __fadd_rn(S, wj) : S;
+            dot = ok ? fmaf(wj, d, dot) : dot;
+            const int k = g + j - lo;
+            if (ok && k < PP_SCR) scr[k * 128] = wj;
+        }
+    }
+    const float thr = __fmul_rn(u, S);
+    float cum = 0.0f, la = 0.0f, ll = 0.0f;
+    int act = -1, last = -1;
+#pragma unroll 1
+    for (int g = g0; g < hi; g += 8) {
+        float v[8];
+        tmem_ld8(taddr + (uint32_t)g, v);
+        const uint32_t vb = group_bits(mw, g, lo, hi);
+        float wv[8];
+        if (g + 7 - lo < PP_SCR) {            // uniform: the group's weights are in scr
+#pragma unroll
+            for (int j = 0; j < 8; ++j) wv[j] = scr[(((vb >> j) & 1u) ? g + j - lo : 0) * 128];
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int k = g + j - lo;
+                wv[j] = k < PP_SCR ? scr[(k >= 0 ? k : 0) * 128]
+                                   : exp32(((vb >> j) & 1u) ? __fsub_rn(v[j] + b3[g + j], m) : 0.0f);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const bool ok = (vb >> j) & 1u;
+            const float l = v[j] + b3[g + j];
+            const float cn = __fadd_rn(cum, wv[j]);
+            cum = ok ? cn : cum;
+            const bool hit = ok && act < 0 && cn > thr;
+            act = hit ? g + j : act;
+            la = hit ? l : la;
+            last = ok ? g + j : last;
+            ll = ok ? l : ll;
+        }
+    }
+    if (any == 0) return -1;
+    if (act < 0) { act = last; la = ll; }
+    const float logS = logf(S);
+    logp += (la - m) - logS;
+    ent += logS - dot / S;
+    return act - lo;
+}
+
+__global__ void __launch_bounds__(128 * PP_NWG, 1) policy_bf16_pp_kernel(const __grid_constant__ PolicyLaunch pl) {
+    constexpr int NWG = PP_NWG;
+    constexpr int NTH = 128 * NWG;
+    static_assert(NWG * 128 <= (int)TMEM_COLS, "TMEM columns");
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bars[NWG];
-    __shared__ PolicySeg seg_tab[EJ_MAX_SEG];
     __shared__ uint32_t tmem_slot;
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -633,89 +726,114 @@ __global__ void __launch_bounds__(128 * NWG, 1) policy_bf16_pp_kernel(PolicyArgs
     const int wtid = tid & 127;
     const int row_in_tile = quarter * 32 + lane;     // TMEM lane of this thread (within its warpgroup)
     const int bar_id = 1 + wg;
-    const int H = a.H, O = a.O, I = a.in_dim;
-    const PpLayout L = pp_layout(H, O, NWG);
+    const int H = pl.H;
+    const PpLayout L = pp_layout(H, pl.n3_max);
+    // this CTA's network and role
+    int ni = 0;
+    while (ni + 1 < pl.n_net && (int)blockIdx.x >= pl.net[ni + 1].cta0) ++ni;
+    const PolicyNet& nt = pl.net[ni];
+    const int O = nt.O, I = nt.in_dim, N3 = (O + 15) / 16 * 16;
     const NetOffsets off = net_offsets(I, H, O);
-    const float* w = a.weights;
-    const bool actor = (int)blockIdx.x < n_actor;
-    const int role_cta = actor ? (int)blockIdx.x : (int)blockIdx.x - n_actor;
-    const int role_ctas = actor ? n_actor : (int)gridDim.x - n_actor;
+    const float* w = nt.weights;
+    const int local = (int)blockIdx.x - nt.cta0;
+    const bool actor = local < nt.n_act;
+    const int role_cta = actor ? local : local - nt.n_act;
+    const int role_ctas = actor ? nt.n_act : nt.n_cri;
 
     const size_t oW1 = actor ? off.W1 : off.V1, oW2 = actor ? off.W2 : off.V2;
     pack_operand(smem + L.w1, H, KX, [&](int n, int k) { return k < I ? __ldg(w + oW1 + (size_t)k * H + n) : 0.0f; });
     pack_operand(smem + L.w2, H, H, [&](int n, int k) { return __ldg(w + oW2 + (size_t)k * H + n); });
     if (actor)
-        pack_operand(smem + L.w3, L.N3, H, [&](int n, int k) { return n < O ? __ldg(w + off.W3 + (size_t)k * O + n) : 0.0f; });
+        pack_operand(smem + L.w3, N3, H, [&](int n, int k) { return n < O ? __ldg(w + off.W3 + (size_t)k * O + n) : 0.0f; });
     else
         pack_operand(smem + L.w3, 16, H, [&](int n, int k) { return n == 0 ? __ldg(w + off.V3 + k) : 0.0f; });
-    float* bias = (float*)(smem + L.bias);           // [0,H) first layer, [H,2H) second, [2H, 2H+O) head (critic: 2H = c3)
-    for (int k = tid; k < 2 * H + O; k += NTH_PP) {
+    float* bias = (float*)(smem + L.bias);   // [0,H) layer 1, [H,2H) layer 2, [2H, 2H+N3) head (critic: 2H = c3)
+    for (int k = tid; k < 2 * H + pl.n3_max; k += NTH) {
         float v = 0.0f;
         if (k < H) v = w[(actor ? off.b1 : off.c1) + k];
         else if (k < 2 * H) v = w[(actor ? off.b2 : off.c2) + k - H];
-        else v = actor ? w[off.b3 + k - 2 * H] : (k == 2 * H ? w[off.c3] : 0.0f);
+        else if (actor) v = k - 2 * H < O ? w[off.b3 + k - 2 * H] : 0.0f;
+        else v = k == 2 * H ? w[off.c3] : 0.0f;
         bias[k] = v;
     }
-    for (int k = tid; k < NWG * BM * KX * 2 / 16; k += NTH_PP) st_shared_v4(smem + L.x[0] + k * 16, 0u, 0u, 0u, 0u);
-    if (tid < segs.n) seg_tab[tid] = segs.s[tid];
+    for (int k = tid; k < NWG * BM * KX * 2 / 16; k += NTH) st_shared_v4(smem + L.x[0] + k * 16, 0u, 0u, 0u, 0u);
     if (tid == 0) {
         for (int q = 0; q < NWG; ++q) mbar_init(&bars[q], 1);
         fence_mbar_init();
     }
     if (warp == 0) tmem_alloc(&tmem_slot, TMEM_COLS);
     sync_for_mma();
-    const uint32_t tcol = tmem_slot + (uint32_t)wg * 128u;                      // product slot
-    const uint32_t thead = tmem_slot + (uint32_t)(NWG * 128) + (uint32_t)wg * HEAD_W;   // head columns
+    const uint32_t tcol = tmem_slot + (uint32_t)wg * 128u;                   // this pipeline's columns
     const uint32_t lane_base = tcol + ((uint32_t)(quarter * 32) << 16);
-    const uint32_t lane_head = thead + ((uint32_t)(quarter * 32) << 16);
     uint8_t* xb = smem + L.x[wg];
     uint8_t* hb = smem + L.h[wg];
+    float* scr = reinterpret_cast<float*>(hb) + wtid;   // sampler scratch: the hidden operand is free after layer 3
     const uint32_t sx = smem_u32(xb), sh = smem_u32(hb);
     const uint32_t sw1 = smem_u32(smem + L.w1), sw2 = smem_u32(smem + L.w2), sw3 = smem_u32(smem + L.w3);
     uint64_t* bar = &bars[wg];
     const __nv_bfloat162 zero2 = __floats2bfloat162_rn(0.0f, 0.0f);
 
-    // a tile's observations (contiguous rows): 8 float4 slots per thread of the warpgroup
+    // a tile's observations (contiguous rows, n = rows x I floats from src):
+    // 8 float4 slots per thread of the warpgroup, slot q holding the floats
+    // [f - mis, f - mis + 4) of the tile, f = (wtid + 128 q) * 4, where src is
+    // mis floats past a 16-byte boundary; 16-byte loads where the 4 floats are
+    // all in the tile, single loads at its ends (nothing outside it is read)
     constexpr int XS = 8;
     float4 xr[XS];
-    const int n_seg = segs.n;
-    const int n_tiles = segs.s[n_seg - 1].tile0 + (segs.s[n_seg - 1].rows + BM - 1) / BM;
+    int mis = 0;
+    const int n_tiles = nt.n_tiles;
     auto seg_of = [&](int tile) {
-        int q = 0;
-        while (q + 1 < n_seg && tile >= seg_tab[q + 1].tile0) ++q;
+        int q = nt.seg_lo;
+        while (q + 1 < nt.seg_hi && tile >= pl.seg[q + 1].tile0) ++q;
         return q;
     };
     auto load_obs = [&](int tile) {
-        const PolicySeg& sg = seg_tab[tile < n_tiles ? seg_of(tile) : 0];
+        const PolicySeg& sg = pl.seg[tile < n_tiles ? seg_of(tile) : nt.seg_lo];
         const int row0 = (tile - sg.tile0) * BM;
         const int n = tile < n_tiles ? min(BM, sg.rows - row0) * I : 0;
         const float* src = sg.x + (size_t)(n > 0 ? row0 : 0) * I;
+        mis = (int)(((uintptr_t)src & 15) >> 2);
 #pragma unroll
         for (int q = 0; q < XS; ++q) {
-            const int f = (wtid + q * 128) * 4;
-            if (f + 3 < n) {
-                xr[q] = __ldg(reinterpret_cast<const float4*>(src + f));
+            const int r0 = (wtid + q * 128) * 4 - mis;
+            if (r0 >= 0 && r0 + 3 < n) {
+                xr[q] = __ldg(reinterpret_cast<const float4*>(src + r0));
             } else {
-                xr[q].x = f < n ? __ldg(src + f) : 0.0f;
-                xr[q].y = f + 1 < n ? __ldg(src + f + 1) : 0.0f;
-                xr[q].z = f + 2 < n ? __ldg(src + f + 2) : 0.0f;
-                xr[q].w = f + 3 < n ? __ldg(src + f + 3) : 0.0f;
+                xr[q].x = r0 >= 0 && r0 < n ? __ldg(src + r0) : 0.0f;
+                xr[q].y = r0 + 1 >= 0 && r0 + 1 < n ? __ldg(src + r0 + 1) : 0.0f;
+                xr[q].z = r0 + 2 >= 0 && r0 + 2 < n ? __ldg(src + r0 + 2) : 0.0f;
+                xr[q].w = r0 + 3 < n ? __ldg(src + r0 + 3) : 0.0f;
             }
         }
     };
+    // observations -> BF16 operand: the prefetched floats go row-major into the
+    // hidden operand's buffer (free at the start of a tile), then each thread
+    // converts its own row in 16-byte chunks (columns I.. of the last chunk
+    // are zero; the chunks after it stay zero from the start)
     auto store_obs = [&]() {
+        float* stage = reinterpret_cast<float*>(hb);
+        wg_bar(bar_id);                        // every warp is done with the last tile's sampler scratch
 #pragma unroll
         for (int q = 0; q < XS; ++q) {
-            const int f = (wtid + q * 128) * 4;
-            if (f < BM * I) {
-                int r = f / I, c = f - r * I;
-                const float v[4] = {xr[q].x, xr[q].y, xr[q].z, xr[q].w};
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (r < BM) *reinterpret_cast<__nv_bfloat16*>(xb + sw128_offset(r, c, BM)) = __float2bfloat16_rn(v[j]);
-                    if (++c == I) { c = 0; ++r; }
-                }
+            const int r0 = (wtid + q * 128) * 4 - mis;
+            if (mis == 0) {
+                if (r0 < BM * I) *reinterpret_cast<float4*>(stage + r0) = xr[q];
+            } else {
+                if (r0 >= 0 && r0 < BM * I) stage[r0] = xr[q].x;
+                if (r0 + 1 >= 0 && r0 + 1 < BM * I) stage[r0 + 1] = xr[q].y;
+                if (r0 + 2 >= 0 && r0 + 2 < BM * I) stage[r0 + 2] = xr[q].z;
+                if (r0 + 3 < BM * I) stage[r0 + 3] = xr[q].w;
             }
+        }
+        wg_bar(bar_id);
+        const float* srow = stage + row_in_tile * I;
+#pragma unroll 1
+        for (int c8 = 0; c8 < I; c8 += 8) {
+            float f8[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) f8[j] = c8 + j < I ? srow[c8 + j] : 0.0f;
+            st_shared_v4(xb + sw128_offset(row_in_tile, c8, BM), pack2(f8[0], f8[1]), pack2(f8[2], f8[3]),
+                         pack2(f8[4], f8[5]), pack2(f8[6], f8[7]));
         }
     };
     auto relu_epi = [&](int bias_off) {
@@ -742,36 +860,39 @@ __global__ void __launch_bounds__(128 * NWG, 1) policy_bf16_pp_kernel(PolicyArgs
     const int first = role_cta * NWG + wg, stride = role_ctas * NWG;
     if (first < n_tiles) load_obs(first);
     for (int tile = first; tile < n_tiles; tile += stride) {
-        const PolicySeg& sg = seg_tab[seg_of(tile)];
+        const PolicySeg& sg = pl.seg[seg_of(tile)];
         const int row0 = (tile - sg.tile0) * BM;
         const int nrows = min(BM, sg.rows - row0);
         store_obs();
         const int grow = row0 + row_in_tile;
         const bool live = row_in_tile < nrows;
-        uint32_t w0 = 0xFFFFFFFFu, w1 = 0xFFFFFFFFu;
-        float us[EJ_MAX_NB] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (actor && live && sg.act) {
-            if (a.W) {
-                const uint32_t* mw = sg.mask + (size_t)grow * a.W;
-                w0 = mw[0];
-                w1 = (KT > 32 && a.W > 1) ? mw[1] : 0u;
-            }
-            if (sg.u) {
-#pragma unroll
-                for (int h = 0; h < EJ_MAX_NB; ++h)
-                    if (h < a.n_heads) us[h] = sg.u[(size_t)grow * a.n_heads + h];
-            } else {
-                const int e = grow / sg.per_env, i = grow % sg.per_env;
-                const uint4 x = philox4x32_10(make_uint4(a.stream_id == 0 ? (uint32_t)i : 0u, (uint32_t)e, sg.gstep[e],
-                                                         (uint32_t)a.stream_id), sg.key[0], sg.key[1]);
-                if (a.stream_id == 0) us[0] = u01(x.w);
-                else { us[0] = u01(x.x); us[1] = u01(x.y); us[2] = u01(x.z); us[3] = u01(x.w); }
-            }
-        }
         wg_sync_for_mma(bar_id);
         if (wtid == 0) {
             mma_chain(tcol, sx, BM, sw1, H, KX, idesc_bf16(BM, H));
             mma_commit(bar);
+        }
+        // the sampler's mask words and uniforms: their loads overlap the products
+        uint32_t mw[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+        float us[EJ_MAX_NB] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (actor && live && sg.act) {
+            if (nt.W) {
+                const uint32_t* m = sg.mask + (size_t)grow * nt.W;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k < nt.W) mw[k] = m[k];
+            }
+            if (sg.u) {
+#pragma unroll
+                for (int h = 0; h < EJ_MAX_NB; ++h)
+                    if (h < nt.n_heads) us[h] = sg.u[(size_t)grow * nt.n_heads + h];
+            } else {
+                const int e = grow / sg.per_env, i = grow % sg.per_env;
+                const uint4 x = philox4x32_10(make_uint4(nt.stream_id == 0 ? (uint32_t)i : 0u, (uint32_t)e,
+                                                         sg.gstep[e], (uint32_t)nt.stream_id),
+                                              sg.key[0], sg.key[1]);
+                if (nt.stream_id == 0) us[0] = u01(x.w);
+                else { us[0] = u01(x.x); us[1] = u01(x.y); us[2] = u01(x.z); us[3] = u01(x.w); }
+            }
         }
         if (tile + stride < n_tiles) load_obs(tile + stride);
         if (!(ok = wg_wait_mma(bar, phase, bar_id))) break;
@@ -783,51 +904,44 @@ __global__ void __launch_bounds__(128 * NWG, 1) policy_bf16_pp_kernel(PolicyArgs
         }
         if (!(ok = wg_wait_mma(bar, phase, bar_id))) break;
         relu_epi(H);
-        wg_sync_for_mma(bar_id);
+        wg_sync_for_mma(bar_id);   // the layer-2 product has been read: the head goes to the same columns
         if (wtid == 0) {
-            if (actor) mma_chain(thead, sh, BM, sw3, L.N3, H, idesc_bf16(BM, L.N3));
-            else mma_chain(thead, sh, BM, sw3, 16, H, idesc_bf16(BM, 16));
+            if (actor) mma_chain(tcol, sh, BM, sw3, N3, H, idesc_bf16(BM, N3));
+            else mma_chain(tcol, sh, BM, sw3, 16, H, idesc_bf16(BM, 16));
             mma_commit(bar);
         }
         if (!(ok = wg_wait_mma(bar, phase, bar_id))) break;
         if (actor) {
-            float l[KT];
-            {
-                float v[32];
-                tmem_ld32(lane_head, v);
+            const float* b3 = bias + 2 * H;
+            if (sg.logits) {
+                for (int c = 0; c < (O + 31) / 32; ++c) {
+                    float v[32];
+                    tmem_ld32(lane_base + c * 32, v);       // warp-collective: every lane loads
+                    if (live) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) l[j] = v[j];
-                if constexpr (KT == 64) {
-                    tmem_ld32(lane_head + 32, v);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) l[32 + j] = v[j];
+                        for (int j = 0; j < 32; ++j)
+                            if (c * 32 + j < O) sg.logits[(size_t)grow * O + c * 32 + j] = v[j] + b3[c * 32 + j];
+                    }
                 }
             }
-#pragma unroll
-            for (int j = 0; j < KT; ++j) l[j] = j < O ? l[j] + bias[2 * H + j] : 0.0f;
-            if (live) {
-                if (sg.logits) {
-#pragma unroll
-                    for (int j = 0; j < KT; ++j)
-                        if (j < O) sg.logits[(size_t)grow * O + j] = l[j];
+            if (sg.act) {
+                float logp = 0.0f, ent = 0.0f;
+                bool none = false;
+                for (int h = 0; h < nt.n_heads; ++h) {
+                    const float uh = h == 0 ? us[0] : h == 1 ? us[1] : h == 2 ? us[2] : us[3];
+                    int act = sample_head_tmem(lane_base, b3, h * nt.head, nt.head, mw, uh, scr, logp, ent);
+                    if (act < 0) { act = 0; none = true; }
+                    if (live) sg.act[(size_t)grow * nt.n_heads + h] = act;
                 }
-                if (sg.act) {
-                    float logp = 0.0f, ent = 0.0f;
-                    bool none = false;
-                    for (int h = 0; h < a.n_heads; ++h) {
-                        const float uh = h == 0 ? us[0] : h == 1 ? us[1] : h == 2 ? us[2] : us[3];
-                        int act = sample_head_reg<KT>(l, h * a.head, a.head, w0, w1, uh, logp, ent);
-                        if (act < 0) { act = 0; none = true; }
-                        sg.act[(size_t)grow * a.n_heads + h] = act;
-                    }
-                    if (none) { logp = 0.0f; ent = 0.0f; }
+                if (none) { logp = 0.0f; ent = 0.0f; }
+                if (live) {
                     sg.logp[grow] = logp;
                     if (sg.entropy) sg.entropy[grow] = ent;
                 }
             }
         } else {
             float vv[32];
-            tmem_ld32(lane_head, vv);                // warp-collective: every lane loads
+            tmem_ld32(lane_base, vv);                // warp-collective: every lane loads
             if (live) sg.value[grow] = vv[0] + bias[2 * H];
         }
     }
@@ -844,54 +958,130 @@ size_t policy_bf16_smem(int H, int O) { return bf_layout(H, O).total + 1024; }
 
 namespace {
 
-// The segmented two/three-pipeline kernel: tile pipelines per CTA (three for
-// up to 32 logits, two otherwise), actor and critic in separate CTAs.
-ej_status launch_pp(const PolicyArgs& a, const PolicySegs& segs, cudaStream_t stream) {
-    const int kt = a.O <= 32 ? 0 : 1;
-    const int nwg = kt == 0 ? PP_WG32 : 2;
-    const size_t smem_pp = pp_layout(a.H, a.O, nwg).total + 1024;
-    static size_t conf_pp[2] = {0, 0};
-    if (conf_pp[kt] < smem_pp) {
-        cudaError_t err = cudaFuncSetAttribute(kt == 0 ? policy_bf16_pp_kernel<32, PP_WG32> : policy_bf16_pp_kernel<64, 2>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pp);
-        if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
-        conf_pp[kt] = smem_pp;
-    }
-    // one CTA per SM; the actor (two layers, head, sampler) gets 3/5 of them, the split
-    // measured best on E = 4096 x A = 100 (three pipelines: 1/2 0.217 ms, 3/5 0.186 ms,
-    // 5/8 0.185 ms, 2/3 0.191 ms)
+bool pp_takes(const PolicyArgs& a) {
+    // observations: 4-byte aligned (16-byte when a row is 32 floats: a tile's
+    // 4096 floats then fill the eight 16-byte slots of every thread exactly)
+    return a.H == 128 && a.O >= 1 && a.O <= PP_MAX_O && a.in_dim <= 32 && a.W <= 4 && a.n_heads >= 1 &&
+           a.n_heads <= EJ_MAX_NB && a.head >= 1 && a.n_heads * a.head == a.O && a.rows >= 1 &&
+           ((uintptr_t)a.x & 3) == 0 && (a.in_dim < 32 || ((uintptr_t)a.x & 15) == 0);
+}
+
+bool same_net(const PolicyArgs& a, const PolicyArgs& b) {
+    return a.weights == b.weights && a.in_dim == b.in_dim && a.O == b.O && a.n_heads == b.n_heads &&
+           a.head == b.head && a.W == b.W && a.stream_id == b.stream_id;
+}
+
+int sm_count() {
     static int sms = 0;
     if (sms == 0) {
         int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 2)
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 2)
             sms = 2;
     }
-    const PolicySeg& last = segs.s[segs.n - 1];
-    const int n_tiles = last.tile0 + (last.rows + BM - 1) / BM;
-    const int pairs = (n_tiles + nwg - 1) / nwg;          // tiles are taken nwg at a time per CTA
-    int n_act = sms * PP_ACT_NUM / PP_ACT_DEN, n_cri = sms - sms * PP_ACT_NUM / PP_ACT_DEN;
-    n_act = n_act < pairs ? n_act : pairs;
-    n_cri = n_cri < pairs ? n_cri : pairs;
-    if (n_act < 1) n_act = 1;
-    if (n_cri < 1) n_cri = 1;
-    if (kt == 0) policy_bf16_pp_kernel<32, PP_WG32><<<n_act + n_cri, 128 * PP_WG32, smem_pp, stream>>>(a, segs, n_act);
-    else policy_bf16_pp_kernel<64, 2><<<n_act + n_cri, 256, smem_pp, stream>>>(a, segs, n_act);
-    cudaError_t err = cudaGetLastError();
-    if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "bf16 policy launch: %s", cudaGetErrorString(err));
-    return EJ_OK;
+    return sms;
 }
 
 }  // namespace
 
-ej_status launch_policy_bf16_segments(const PolicyArgs& a, const PolicySegs& segs, cudaStream_t stream,
-                                      bool* handled) {
+ej_status launch_policy_bf16_multi(const PolicyArgs* segs, int n, cudaStream_t stream, bool* handled) {
     *handled = false;
-    if (segs.n < 1 || segs.n > EJ_MAX_SEG) return fail(EJ_ERR_ARG, "bf16 policy: 1 to %d segments", EJ_MAX_SEG);
-    if (!(a.H == 128 && a.O <= 64 && a.in_dim <= 32 && a.W <= 2 && a.n_heads <= EJ_MAX_NB)) return EJ_OK;
-    for (int q = 0; q < segs.n; ++q)
-        if (((uintptr_t)segs.s[q].x & 15) != 0) return EJ_OK;
+    if (n < 1 || n > EJ_MAX_SEG) return fail(EJ_ERR_ARG, "bf16 policy: 1 to %d segments", EJ_MAX_SEG);
+    for (int q = 0; q < n; ++q)
+        if (!pp_takes(segs[q]) || segs[q].H != segs[0].H) return EJ_OK;
+    // networks in order of first appearance; their segments contiguous
+    PolicyLaunch pl;
+    memset(&pl, 0, sizeof pl);
+    pl.H = segs[0].H;
+    int rep[EJ_MAX_NET], net_of[EJ_MAX_SEG];
+    int n_net = 0;
+    for (int q = 0; q < n; ++q) {
+        int k = 0;
+        while (k < n_net && !same_net(segs[rep[k]], segs[q])) ++k;
+        if (k == n_net) {
+            if (n_net == EJ_MAX_NET) return EJ_OK;
+            rep[n_net++] = q;
+        }
+        net_of[q] = k;
+    }
+    pl.n_net = n_net;
+    pl.n_seg = n;
+    int total_tiles = 0, q_out = 0;
+    for (int k = 0; k < n_net; ++k) {
+        const PolicyArgs& r = segs[rep[k]];
+        PolicyNet& nt = pl.net[k];
+        nt.weights = r.weights; nt.in_dim = r.in_dim; nt.O = r.O; nt.n_heads = r.n_heads; nt.head = r.head;
+        nt.W = r.W; nt.stream_id = r.stream_id;
+        nt.seg_lo = q_out;
+        int tiles = 0;
+        for (int q = 0; q < n; ++q) {
+            if (net_of[q] != k) continue;
+            const PolicyArgs& a = segs[q];
+            PolicySeg& g = pl.seg[q_out++];
+            g.x = a.x; g.mask = a.mask; g.u = a.u; g.gstep = a.gstep; g.key = a.key;
+            g.act = a.act; g.logp = a.logp; g.value = a.value; g.entropy = a.entropy; g.logits = a.logits;
+            g.rows = a.rows; g.per_env = a.per_env; g.tile0 = tiles; g.pad = 0;
+            tiles += (a.rows + BM - 1) / BM;
+        }
+        nt.seg_hi = q_out;
+        nt.n_tiles = tiles;
+        total_tiles += tiles;
+        const int n3 = (r.O + 15) / 16 * 16;
+        if (n3 > pl.n3_max) pl.n3_max = n3;
+    }
+    // CTAs: one per SM, split over the networks and roles by their work
+    // (tiles x cost per tile): each role first gets one CTA, then each
+    // further CTA goes to the role with the most work per CTA, at most one
+    // CTA per PP_NWG tiles of the role.
+    const int sms = sm_count();
+    double cost[EJ_MAX_NET][2];
+    int used = 0;
+    for (int k = 0; k < n_net; ++k) {
+        PolicyNet& nt = pl.net[k];
+        int groups = 0;
+        for (int h = 0; h < nt.n_heads; ++h) {
+            const int lo = h * nt.head, hi = lo + nt.head;
+            groups += (hi + 7) / 8 - lo / 8;
+        }
+        cost[k][0] = nt.n_tiles * (PP_TILE_BASE + PP_TILE_GROUP * groups);
+        cost[k][1] = nt.n_tiles * PP_TILE_BASE;
+        nt.n_act = 1;
+        nt.n_cri = 1;
+        used += 2;
+    }
+    while (used < sms) {
+        int best = -1, best_role = 0;
+        double load = 0.0;
+        for (int k = 0; k < n_net; ++k) {
+            const PolicyNet& nt = pl.net[k];
+            const int pairs = (nt.n_tiles + PP_NWG - 1) / PP_NWG;
+            const double la = cost[k][0] / nt.n_act, lc = cost[k][1] / nt.n_cri;
+            if (nt.n_act < pairs && la > load) { load = la; best = k; best_role = 0; }
+            if (nt.n_cri < pairs && lc > load) { load = lc; best = k; best_role = 1; }
+        }
+        if (best < 0) break;
+        if (best_role == 0) ++pl.net[best].n_act;
+        else ++pl.net[best].n_cri;
+        ++used;
+    }
+    int cta = 0;
+    for (int k = 0; k < n_net; ++k) {
+        pl.net[k].cta0 = cta;
+        cta += pl.net[k].n_act + pl.net[k].n_cri;
+    }
+    const size_t smem = pp_layout(pl.H, pl.n3_max).total + 1024;
+    static size_t configured = 0;
+    if (configured < smem) {
+        cudaError_t err = cudaFuncSetAttribute(policy_bf16_pp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+        if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
+        configured = smem;
+    }
     *handled = true;
-    return launch_pp(a, segs, stream);
+    policy_bf16_pp_kernel<<<cta, 128 * PP_NWG, smem, stream>>>(pl);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "bf16 policy launch: %s", cudaGetErrorString(err));
+    return EJ_OK;
 }
 
 ej_status launch_policy_bf16(const PolicyArgs& a, cudaStream_t stream) {
@@ -911,16 +1101,12 @@ ej_status launch_policy_bf16(const PolicyArgs& a, cudaStream_t stream) {
     const int n_tiles = (a.rows + BM - 1) / BM;
     int grid = n_tiles < 152 ? n_tiles : 152;
     if (grid < 1) grid = 1;
-    const bool fast = a.O <= 64 && a.in_dim <= 32 && a.W <= 2 && a.n_heads <= EJ_MAX_NB && ((uintptr_t)a.x & 15) == 0;
-    if (fast && a.H == 128) {
-        PolicySegs segs;
-        segs.n = 1;
-        PolicySeg& g = segs.s[0];
-        g.x = a.x; g.mask = a.mask; g.u = a.u; g.gstep = a.gstep; g.key = a.key;
-        g.act = a.act; g.logp = a.logp; g.value = a.value; g.entropy = a.entropy; g.logits = a.logits;
-        g.rows = a.rows; g.per_env = a.per_env; g.tile0 = 0; g.pad = 0;
-        return launch_pp(a, segs, stream);
+    if (a.H == 128) {
+        bool handled = false;
+        ej_status st = launch_policy_bf16_multi(&a, 1, stream, &handled);
+        if (st != EJ_OK || handled) return st;
     }
+    const bool fast = a.O <= 64 && a.in_dim <= 32 && a.W <= 2 && a.n_heads <= EJ_MAX_NB && ((uintptr_t)a.x & 15) == 0;
     if (fast) {
         static size_t conf_fast[2] = {0, 0};
         const int kt = a.O <= 32 ? 0 : 1;

@@ -101,54 +101,59 @@ ej_status policy_segmented(const EjParams* p, int32_t net, int32_t hidden, int32
     int in_dim, O, heads, head;
     if ((st = net_shape(p, kp, net, hidden, &in_dim, &O, &heads, &head)) != EJ_OK) return st;
     const int W = net == EJ_NET_POP ? kp.W : 0;
-    *ok = precision == EJ_BF16 && hidden == 128 && O <= 64 && in_dim <= 32 && W <= 2 && heads <= EJ_MAX_NB;
+    *ok = precision == EJ_BF16 && hidden == 128 && O <= 96 && in_dim <= 32 && W <= 4 && heads <= EJ_MAX_NB;
     return EJ_OK;
 }
 
-ej_status policy_forward_segments(const EjParams* const* params, const void* const* states, int32_t n_seg,
-                                  int32_t net, int32_t hidden, int32_t precision, const float* weights,
-                                  const float* const* obs, const uint32_t* const* mask, int32_t* const* act,
-                                  float* const* logp, float* const* value, void* stream) {
-    if (n_seg < 1 || !params || !states || !obs || !value) return fail(EJ_ERR_ARG, "policy_forward_segments: NULL argument");
+ej_status policy_forward_segments(int32_t n_seg, const EjParams* const* params, const void* const* states,
+                                  const int32_t* nets, const float* const* weights, int32_t hidden,
+                                  int32_t precision, const float* const* obs, const uint32_t* const* mask,
+                                  int32_t* const* act, float* const* logp, float* const* value, void* stream) {
+    if (n_seg < 1 || !params || !states || !nets || !weights || !obs || !value)
+        return fail(EJ_ERR_ARG, "policy_forward_segments: NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
-    for (int base = 0; base < n_seg; base += EJ_MAX_SEG) {
-        const int n = n_seg - base < EJ_MAX_SEG ? n_seg - base : EJ_MAX_SEG;
-        PolicyArgs args[EJ_MAX_SEG];
-        PolicySegs segs;
-        segs.n = n;
-        int tile = 0;
-        for (int q = 0; q < n; ++q) {
-            const int k = base + q;
-            Layout lay;
-            KParams kp;
-            ej_status st = derive(params[k], &lay, &kp);
-            if (st != EJ_OK) return st;
-            st = make_args(params[k], kp, lay, states[k], net, hidden, weights, obs[k], mask ? mask[k] : nullptr,
-                           nullptr, act ? act[k] : nullptr, logp ? logp[k] : nullptr, value[k], nullptr, nullptr,
-                           &args[q]);
-            if (st != EJ_OK) return st;
-            const PolicyArgs& a = args[q];
-            if (a.in_dim != args[0].in_dim || a.O != args[0].O || a.n_heads != args[0].n_heads ||
-                a.head != args[0].head || a.W != args[0].W)
-                return fail(EJ_ERR_ARG, "policy_forward_segments: segment %d has another network shape", k);
-            PolicySeg& g = segs.s[q];
-            g.x = a.x; g.mask = a.mask; g.u = nullptr; g.gstep = a.gstep; g.key = a.key;
-            g.act = a.act; g.logp = a.logp; g.value = a.value; g.entropy = nullptr; g.logits = nullptr;
-            g.rows = a.rows; g.per_env = a.per_env; g.tile0 = tile; g.pad = 0;
-            tile += (a.rows + 127) / 128;
-        }
+    PolicyArgs args[EJ_MAX_SEG];
+    int n = 0;
+    auto flush = [&]() -> ej_status {
+        if (n == 0) return EJ_OK;
         bool handled = false;
         if (precision == EJ_BF16) {
-            ej_status st = launch_policy_bf16_segments(args[0], segs, s, &handled);
+            ej_status st = launch_policy_bf16_multi(args, n, s, &handled);
             if (st != EJ_OK) return st;
         }
-        if (!handled)
-            for (int q = 0; q < n; ++q) {
-                ej_status st = launch_policy(args[q], precision, s);
-                if (st != EJ_OK) return st;
-            }
+        for (int q = 0; q < n && !handled; ++q) {
+            ej_status st = launch_policy(args[q], precision, s);
+            if (st != EJ_OK) return st;
+        }
+        n = 0;
+        return EJ_OK;
+    };
+    for (int k = 0; k < n_seg; ++k) {
+        Layout lay;
+        KParams kp;
+        ej_status st = derive(params[k], &lay, &kp);
+        if (st != EJ_OK) return st;
+        if (nets[k] == EJ_NET_GOV && mask && mask[k]) return fail(EJ_ERR_ARG, "policy_forward_segments: the government takes no mask");
+        PolicyArgs a;
+        st = make_args(params[k], kp, lay, states[k], nets[k], hidden, weights[k], obs[k],
+                       mask && nets[k] == EJ_NET_POP ? mask[k] : nullptr, nullptr, act ? act[k] : nullptr,
+                       logp ? logp[k] : nullptr, value[k], nullptr, nullptr, &a);
+        if (st != EJ_OK) return st;
+        // a launch takes at most EJ_MAX_SEG segments of at most EJ_MAX_NET networks
+        int nets_in = 0;
+        bool known = false;
+        for (int q = 0; q < n; ++q) {
+            bool first = true;
+            for (int r = 0; r < q; ++r)
+                if (args[r].weights == args[q].weights && args[r].stream_id == args[q].stream_id) first = false;
+            nets_in += first;
+            if (args[q].weights == a.weights && args[q].stream_id == a.stream_id) known = true;
+        }
+        if (n == EJ_MAX_SEG || (!known && nets_in == EJ_MAX_NET))
+            if ((st = flush()) != EJ_OK) return st;
+        args[n++] = a;
     }
-    return EJ_OK;
+    return flush();
 }
 
 ej_status rollout(const EjParams* p, void* state, int32_t T, int32_t hidden, int32_t precision,
@@ -174,13 +179,21 @@ ej_status rollout(const EjParams* p, void* state, int32_t T, int32_t hidden, int
                        b->mask + t * EA * kp.W, nullptr, last ? nullptr : b->act + t * EA,
                        last ? nullptr : b->logp + t * EA, b->value + t * EA, nullptr, nullptr, &pa);
         if (st != EJ_OK) return st;
-        if ((st = launch_policy(pa, precision, s)) != EJ_OK) return st;
         st = make_args(p, kp, lay, state, EJ_NET_GOV, hidden, gov_weights, b->gobs + (size_t)t * kp.E * kp.G,
                        nullptr, nullptr, last ? nullptr : b->gact + (size_t)t * kp.E * kp.nb,
                        last ? nullptr : b->glogp + (size_t)t * kp.E, b->gvalue + (size_t)t * kp.E,
                        nullptr, nullptr, &ga);
         if (st != EJ_OK) return st;
-        if ((st = launch_policy(ga, precision, s)) != EJ_OK) return st;
+        // BF16: population and government networks in one launch where the kernel takes both
+        bool handled = false;
+        if (precision == EJ_BF16) {
+            const PolicyArgs both[2] = {pa, ga};
+            if ((st = launch_policy_bf16_multi(both, 2, s, &handled)) != EJ_OK) return st;
+        }
+        if (!handled) {
+            if ((st = launch_policy(pa, precision, s)) != EJ_OK) return st;
+            if ((st = launch_policy(ga, precision, s)) != EJ_OK) return st;
+        }
         if (last) break;
         DevIO io;
         memset(&io, 0, sizeof io);

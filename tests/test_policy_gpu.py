@@ -103,6 +103,88 @@ def test_population_forward_and_sampling(precision):
     assert np.allclose(out["entropy"].cpu().numpy(), ent, rtol=0, atol=1e-5 * (1 + np.abs(ent)).max())
 
 
+@pytest.mark.parametrize("levels", [5, 10, 20])
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_population_forward_price_grids(precision, levels):
+    """24, 44 and 84 actions (1, 2 and 3 mask words), 7 x 100 rows: several
+    tiles and a ragged one."""
+    P, N = _mods()
+    E, A = 7, 100
+    env, pol, obs, gobs, mask, pw, gw = _setup(E, A, seed=5, precision=precision, T_ep=60, T_tax=10,
+                                               **P.price_grid(levels))
+    assert env.W == (env.nA + 31) // 32
+    out = pol.forward(N.NET_POP, obs, mask, logits=True, entropy=True)
+    lg = out["logits"].cpu().numpy()
+    x = obs.cpu().numpy().reshape(E * A, env.D)
+    _check_forward(lg, out["value"].cpu().numpy(), synth.unpack(pw, env.D, H, env.nA), x, env.D, precision)
+    valid = op.mask_bits(mask.cpu().numpy().view(np.uint32).reshape(E * A, env.W), env.nA)
+    g = int(env.field("gstep")[0].item())
+    u = synth.pop_draws(5, np.arange(E), A, g, 1, env.nA)[3][0].reshape(E * A)
+    got = out["act"].cpu().numpy()[:, 0]
+    assert np.array_equal(got, op.sample32(lg, valid, u))
+    lp, ent = op.logp_entropy64(lg, valid, got)
+    assert np.allclose(out["logp"].cpu().numpy(), lp, rtol=0, atol=1e-5 * (1 + np.abs(lp)).max())
+    assert np.allclose(out["entropy"].cpu().numpy(), ent, rtol=0, atol=1e-5 * (1 + np.abs(ent)).max())
+
+
+def test_segments_equal_separate_calls():
+    """policy_forward_segments over several environments sets and both
+    networks (one launch of up to 4 networks) equals one policy_forward per
+    set, bit for bit."""
+    import ctypes as C
+    P, N = _mods()
+    from paper_2410_22165_gb300.env import _ptr, _stream
+    sets = []
+    for k, (levels, E, A) in enumerate([(5, 3, 50), (10, 2, 37), (20, 4, 10), (5, 5, 20)]):
+        env, pol, obs, gobs, mask, pw, gw = _setup(E, A, seed=20 + k, precision="bf16", T_ep=30, T_tax=7,
+                                                   **P.price_grid(levels))
+        if k == 3:    # same population weights as set 0: one network
+            pol = P.Policy(env, sets[0][1].pop_w.cpu(), sets[0][1].gov_w.cpu(), hidden=H, precision="bf16")
+            pol.pop_w, pol.gov_w = sets[0][1].pop_w, sets[0][1].gov_w
+        sets.append((env, pol, obs, gobs, mask))
+    segs = []
+    for env, pol, obs, gobs, mask in sets:
+        for net in (N.NET_POP, N.NET_GOV):
+            rows = env.E * env.A if net == N.NET_POP else env.E
+            heads = 1 if net == N.NET_POP else env.p.nb
+            segs.append(dict(env=env, net=net, w=pol.pop_w if net == N.NET_POP else pol.gov_w,
+                             x=obs if net == N.NET_POP else gobs, mask=mask if net == N.NET_POP else None,
+                             act=torch.empty((rows, heads), dtype=torch.int32, device="cuda"),
+                             logp=torch.empty(rows, device="cuda"), value=torch.empty(rows, device="cuda"),
+                             pol=pol))
+    n = len(segs)
+    V = C.c_void_p * n
+    N.check(N.load().policy_forward_segments(
+        n, V(*[C.addressof(s["env"].p) for s in segs]), V(*[_ptr(s["env"].state) for s in segs]),
+        (C.c_int32 * n)(*[s["net"] for s in segs]), V(*[_ptr(s["w"]) for s in segs]), H, N.BF16,
+        V(*[_ptr(s["x"]) for s in segs]), V(*[_ptr(s["mask"]) for s in segs]), V(*[_ptr(s["act"]) for s in segs]),
+        V(*[_ptr(s["logp"]) for s in segs]), V(*[_ptr(s["value"]) for s in segs]), _stream()),
+        "policy_forward_segments")
+    for s in segs:
+        ref = s["pol"].forward(s["net"], s["x"], s["mask"])
+        assert torch.equal(ref["act"], s["act"]) and torch.equal(ref["logp"], s["logp"])
+        assert torch.equal(ref["value"], s["value"])
+
+
+@pytest.mark.parametrize("net", [0, 1])
+def test_unaligned_observations(net):
+    """Observation buffers 1, 2 and 3 floats past a 16-byte boundary (e.g.
+    rollout slots of E x A x D floats) give the aligned buffer's results."""
+    P, N = _mods()
+    E, A = 5, 77
+    env, pol, obs, gobs, mask, pw, gw = _setup(E, A, seed=6, precision="bf16", T_ep=40, T_tax=9)
+    x = obs if net == 0 else gobs
+    ref = pol.forward(net, x, mask if net == 0 else None, logits=True, entropy=True)
+    for off in (1, 2, 3):
+        big = torch.zeros(x.numel() + 4, device="cuda")
+        xs = big[off:off + x.numel()].view(x.shape)
+        xs.copy_(x)
+        assert xs.data_ptr() % 16 == 4 * off
+        got = pol.forward(net, xs, mask if net == 0 else None, logits=True, entropy=True)
+        for k in ref:
+            assert torch.equal(ref[k], got[k]), (off, k)
+
+
 def test_given_uniforms_and_values_only():
     E, A = 2, 64
     env, pol, obs, gobs, mask, pw, gw = _setup(E, A, seed=4)
