@@ -570,11 +570,11 @@ constexpr int PP_NWG = 3;       // tile pipelines per CTA
 constexpr int PP_MAX_O = 96;    // logits: the head operand [N3][H] fits beside three pipelines
 constexpr int PP_SCR = 64;      // exp weights a thread keeps in shared memory per head
 // Cost of a tile in thousands of SM cycles, measured with clock64 stamps per
-// phase on GB300 (hidden 128): the critic's tile about 12 (observations,
-// three products, two epilogues); the actor's the same plus about 3 per group
-// of 8 logit columns its heads scan (24 logits: 9.3, 63 logits in three heads
-// of 21: 28, 84 logits: 35).
-constexpr double PP_TILE_BASE = 12.0, PP_TILE_GROUP = 3.0;
+// phase on GB300 (hidden 128, three pipelines per CTA): the critic's tile
+// about 12 (observations, three products, two epilogues, value); the actor's
+// about 13 plus 3.1 per group of 8 logit columns its heads scan (24 logits:
+// 9.3, 63 logits in three heads of 21: 28-31, 84 logits: 35).
+constexpr double PP_CRITIC_TILE = 12.0, PP_ACTOR_TILE = 13.0, PP_ACTOR_GROUP = 3.1;
 
 struct PpLayout {
     uint32_t w1, w2, w3, x[PP_NWG], h[PP_NWG], bias, total;
@@ -1029,40 +1029,58 @@ ej_status launch_policy_bf16_multi(const PolicyArgs* segs, int n, cudaStream_t s
         const int n3 = (r.O + 15) / 16 * 16;
         if (n3 > pl.n3_max) pl.n3_max = n3;
     }
-    // CTAs: one per SM, split over the networks and roles by their work
-    // (tiles x cost per tile): each role first gets one CTA, then each
-    // further CTA goes to the role with the most work per CTA, at most one
-    // CTA per PP_NWG tiles of the role.
+    // CTAs: at most one per SM, split over the networks and roles.  A role
+    // with n CTAs runs its tiles in ceil(tiles / (n PP_NWG)) rounds of its
+    // tile cost; the split is the one with the smallest longest role time
+    // (binary search over the candidate times cost x rounds).
     const int sms = sm_count();
-    double cost[EJ_MAX_NET][2];
-    int used = 0;
+    const int n_role = 2 * n_net;
+    double cost[2 * EJ_MAX_NET];
+    int tiles[2 * EJ_MAX_NET];
     for (int k = 0; k < n_net; ++k) {
-        PolicyNet& nt = pl.net[k];
+        const PolicyNet& nt = pl.net[k];
         int groups = 0;
         for (int h = 0; h < nt.n_heads; ++h) {
             const int lo = h * nt.head, hi = lo + nt.head;
             groups += (hi + 7) / 8 - lo / 8;
         }
-        cost[k][0] = nt.n_tiles * (PP_TILE_BASE + PP_TILE_GROUP * groups);
-        cost[k][1] = nt.n_tiles * PP_TILE_BASE;
-        nt.n_act = 1;
-        nt.n_cri = 1;
-        used += 2;
+        cost[2 * k] = PP_ACTOR_TILE + PP_ACTOR_GROUP * groups;
+        cost[2 * k + 1] = PP_CRITIC_TILE;
+        tiles[2 * k] = tiles[2 * k + 1] = nt.n_tiles;
     }
-    while (used < sms) {
-        int best = -1, best_role = 0;
-        double load = 0.0;
-        for (int k = 0; k < n_net; ++k) {
-            const PolicyNet& nt = pl.net[k];
-            const int pairs = (nt.n_tiles + PP_NWG - 1) / PP_NWG;
-            const double la = cost[k][0] / nt.n_act, lc = cost[k][1] / nt.n_cri;
-            if (nt.n_act < pairs && la > load) { load = la; best = k; best_role = 0; }
-            if (nt.n_cri < pairs && lc > load) { load = lc; best = k; best_role = 1; }
+    auto ctas_for = [&](int r, double T) {        // fewest CTAs of role r finishing within T (0: impossible)
+        const int rounds = (int)(T / cost[r] + 1e-9);
+        if (rounds < 1) return 0;
+        const int per = rounds * PP_NWG;
+        return (tiles[r] + per - 1) / per;
+    };
+    auto fits = [&](double T, int* n) {
+        int sum = 0;
+        for (int r = 0; r < n_role; ++r) {
+            const int c = ctas_for(r, T);
+            if (c == 0) return false;
+            if (n) n[r] = c;
+            sum += c;
         }
-        if (best < 0) break;
-        if (best_role == 0) ++pl.net[best].n_act;
-        else ++pl.net[best].n_cri;
-        ++used;
+        return sum <= sms;
+    };
+    double lo_T = 0.0, hi_T = 0.0;
+    for (int r = 0; r < n_role; ++r) {
+        const double t1 = cost[r] * ((tiles[r] + PP_NWG - 1) / PP_NWG);   // one CTA per role
+        if (t1 > hi_T) hi_T = t1;
+    }
+    int n_ctas[2 * EJ_MAX_NET];
+    if (!fits(hi_T, n_ctas)) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: more roles than SMs");
+    // the smallest feasible time is cost[r] x q for some role r and rounds q: bisect on the value, then snap
+    for (int it = 0; it < 60; ++it) {
+        const double mid = 0.5 * (lo_T + hi_T);
+        if (fits(mid, nullptr)) hi_T = mid;
+        else lo_T = mid;
+    }
+    fits(hi_T, n_ctas);
+    for (int k = 0; k < n_net; ++k) {
+        pl.net[k].n_act = n_ctas[2 * k];
+        pl.net[k].n_cri = n_ctas[2 * k + 1];
     }
     int cta = 0;
     for (int k = 0; k < n_net; ++k) {

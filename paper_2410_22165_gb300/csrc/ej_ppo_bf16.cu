@@ -51,6 +51,12 @@ constexpr int KX = 64;         // input operand width: inputs, then a ones colum
 constexpr int KO = 64;         // logit operand width
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int PC = 352;        // accumulator columns written per TMEM lane
+// Cost of a tile in thousands of SM cycles, measured with clock64 stamps per
+// phase on GB300: about 13.8 for the critic (inputs, three forward products
+// and two epilogues, value loss, backward products and masks) and the same
+// plus the loss epilogue for the actor, about 1.9 per group of 8 logit
+// columns its heads span (24 logits: 5.9; three heads of 21: 18.4).
+constexpr double PPO_TILE = 13.8, PPO_LOSS_GROUP = 1.9;
 
 // TMEM columns.  Actor: dW1^T [h][in] 0..63, dW2 [h_in][h_out] 64..191,
 // dW3 [h][o] 192..255, db2 (column 256), db3 [o] 272..335 (every lane).
@@ -256,17 +262,13 @@ struct Head4 {
 
 struct ActorRow { float pg, ent, clip, kl; };
 
-// Section 4, actor part of one minibatch row: per-head masked log-softmax of
-// the logits l[0, O) (O <= KT), the clipped surrogate on the normalised
-// advantage and the entropy bonus; l is overwritten with d loss / d logits
-// (0 beyond O and at masked actions).  One exp per logit: e[k] = exp(l_k - max)
-// serves the normaliser, the entropy and the gradient.
 // Per-row inputs of the actor's loss, loaded at the start of a tile so that
 // their latency overlaps the forward products.
 struct RowIn {
-    uint32_t w0, w1;      // action-mask words (all ones without a mask)
-    int act0;             // action of head 0
-    float lpo, adv;       // log-probability at sampling time, raw advantage
+    uint32_t w0, w1;           // action-mask words (all ones without a mask)
+    int act0, act1, act2, act3;   // actions of heads 0..3
+    float lpo, adv;            // log-probability at sampling time, raw advantage
+    __device__ __forceinline__ int act(int h) const { return h == 0 ? act0 : h == 1 ? act1 : h == 2 ? act2 : act3; }
 };
 
 __device__ __forceinline__ RowIn load_row_in(const FbArgs& a, uint32_t row, bool two_words) {
@@ -278,42 +280,72 @@ __device__ __forceinline__ RowIn load_row_in(const FbArgs& a, uint32_t row, bool
         q.w0 = mw[0];
         q.w1 = (two_words && a.W > 1) ? mw[1] : 0u;
     }
-    q.act0 = a.act[(size_t)row * a.n_heads];
+    const int32_t* ac = a.act + (size_t)row * a.n_heads;
+    q.act0 = ac[0];
+    q.act1 = a.n_heads > 1 ? ac[1] : 0;
+    q.act2 = a.n_heads > 2 ? ac[2] : 0;
+    q.act3 = a.n_heads > 3 ? ac[3] : 0;
     q.lpo = a.logp_old[row];
     q.adv = a.adv[row];
     return q;
 }
 
-template <int KT>
-__device__ __forceinline__ ActorRow actor_row(const FbArgs& a, uint32_t row, const RowIn& in, float (&l)[KT],
-                                              float mean, float inv_std, float inv_n) {
-    const uint32_t w0 = in.w0, w1 = in.w1;
-    auto valid = [&](int k) { return (((k < 32 ? w0 : w1) >> (k & 31)) & 1u) != 0; };
-    float e[KT];
+// Bits of columns g .. g + 7 that lie in the head window [lo, hi) (g = lo
+// rounded down to 8, then steps of 8), and of those the ones the mask allows.
+__device__ __forceinline__ uint32_t window8(int g, int lo, int hi) {
+    uint32_t b = 0xFFu;
+    if (lo > g) b &= 0xFFu << (lo - g);
+    if (hi - g < 8) b &= (1u << (hi - g)) - 1u;
+    return b;
+}
+__device__ __forceinline__ uint32_t mask8(uint32_t w0, uint32_t w1, int g) {
+    return ((g < 32 ? w0 : w1) >> (g & 31)) & 0xFFu;
+}
+
+// Section 4, actor part of one minibatch row, from its logits in TMEM (this
+// lane's columns from taddr, plus the head bias b3).  Per head, two passes
+// over 8-column groups (loops not unrolled: the code runs once per row and
+// tile): the maximum of the allowed logits, then the exp weights e_k (kept in
+// scr, this thread's column of a [64][128] float array), their sum S and
+// sum e_k (l_k - max), which gives the head's entropy log S - that / S.  Then
+// the clipped surrogate on the normalised advantage and the entropy bonus,
+// and d loss / d logits (0 at masked actions, beyond O and, when !live, in
+// the whole row) written into row `row` of the BF16 operand dl [BM][KO].
+__device__ __forceinline__ ActorRow actor_row_tmem(const FbArgs& a, const RowIn& in, bool live, uint32_t taddr,
+                                                   const float* b3, float* scr, uint8_t* dl, int row, int KT,
+                                                   float mean, float inv_std, float inv_n) {
     Head4 lse, ent_h, rS;
     float logp = 0.0f, ent = 0.0f;
     for (int h = 0; h < a.n_heads; ++h) {
-        const int lo = h * a.head, hi = lo + a.head;
-        const int act = lo + (h == 0 ? in.act0 : a.act[(size_t)row * a.n_heads + h]);
+        const int lo = h * a.head, hi = lo + a.head, act = lo + in.act(h);
         float m = -FLT_MAX;
+#pragma unroll 1
+        for (int g = lo & ~7; g < hi; g += 8) {
+            float v[8];
+            tmem_ld8(taddr + (uint32_t)g, v);
+            const uint32_t vb = window8(g, lo, hi) & mask8(in.w0, in.w1, g);
 #pragma unroll
-        for (int k = 0; k < KT; ++k)
-            if (k >= lo && k < hi && valid(k)) m = fmaxf(m, l[k]);
-        float S = 0.0f, la = 0.0f;
+            for (int j = 0; j < 8; ++j) m = ((vb >> j) & 1u) ? fmaxf(m, v[j] + b3[g + j]) : m;
+        }
+        float S = 0.0f, T = 0.0f, la = 0.0f;
+#pragma unroll 1
+        for (int g = lo & ~7; g < hi; g += 8) {
+            float v[8];
+            tmem_ld8(taddr + (uint32_t)g, v);
+            const uint32_t wb = window8(g, lo, hi), vb = wb & mask8(in.w0, in.w1, g);
 #pragma unroll
-        for (int k = 0; k < KT; ++k) {
-            if (k >= lo && k < hi) {
-                e[k] = valid(k) ? expf(l[k] - m) : 0.0f;
-                S += e[k];
+            for (int j = 0; j < 8; ++j) {
+                const float d = v[j] + b3[g + j] - m;
+                const float e = ((vb >> j) & 1u) ? expf(d) : 0.0f;
+                S += e;
+                T += e * d;
+                la = g + j == act ? d : la;
+                if ((wb >> j) & 1u) scr[(g + j) * 128] = e;
             }
-            if (k == act) la = l[k];
         }
         const float logS = logf(S), inv_S = 1.0f / S;
-        logp += la - m - logS;
-        float Hh = 0.0f;
-#pragma unroll
-        for (int k = 0; k < KT; ++k)
-            if (k >= lo && k < hi && valid(k)) Hh -= (e[k] * inv_S) * (l[k] - m - logS);
+        logp += la - logS;
+        const float Hh = logS - T * inv_S;
         ent += Hh;
         lse.set(h, m + logS);
         ent_h.set(h, Hh);
@@ -328,27 +360,38 @@ __device__ __forceinline__ ActorRow actor_row(const FbArgs& a, uint32_t row, con
     st.pg = -fminf(s1, s2);
     const bool inside = ratio > 1.0f - a.clip && ratio < 1.0f + a.clip;
     const float dratio = (s1 <= s2 || inside) ? -an : 0.0f;
-    const float dlogp = dratio * ratio * inv_n;
+    const float dlogp = live ? dratio * ratio * inv_n : 0.0f;
     st.clip = fabsf(ratio - 1.0f) > a.clip ? 1.0f : 0.0f;
     st.kl = lpo - logp;
     st.ent = ent;
-    const float ec = a.ent_coef * inv_n;
+    const float ec = live ? a.ent_coef * inv_n : 0.0f;
     for (int h = 0; h < a.n_heads; ++h) {
-        const int lo = h * a.head, hi = lo + a.head;
-        const int act = lo + (h == 0 ? in.act0 : a.act[(size_t)row * a.n_heads + h]);
+        const int lo = h * a.head, hi = lo + a.head, act = lo + in.act(h);
         const float o = lse.get(h), Hh = ent_h.get(h), inv_S = rS.get(h);
+#pragma unroll 1
+        for (int g = lo & ~7; g < hi; g += 8) {
+            float v[8];
+            tmem_ld8(taddr + (uint32_t)g, v);
+            const uint32_t wb = window8(g, lo, hi), vb = wb & mask8(in.w0, in.w1, g);
 #pragma unroll
-        for (int k = 0; k < KT; ++k) {
-            if (k >= lo && k < hi) {
-                float g = 0.0f;
-                if (valid(k)) {
-                    const float lp = l[k] - o;
-                    const float pk = e[k] * inv_S;
-                    g = dlogp * ((k == act ? 1.0f : 0.0f) - pk) + ec * pk * (lp + Hh);
-                }
-                l[k] = g;
+            for (int j = 0; j < 8; ++j) {
+                const int k = g + j;
+                const float pk = scr[(((wb >> j) & 1u) ? k : 0) * 128] * inv_S;
+                const float lp = v[j] + b3[k] - o;
+                const float gk = dlogp * ((k == act ? 1.0f : 0.0f) - pk) + ec * pk * (lp + Hh);
+                if ((wb >> j) & 1u) scr[k * 128] = ((vb >> j) & 1u) ? gk : 0.0f;
             }
         }
+    }
+    // gradient row -> BF16 operand (columns O .. KT - 1 zero)
+    const int O = a.O;
+#pragma unroll 1
+    for (int c8 = 0; c8 < KT; c8 += 8) {
+        float f[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) f[j] = c8 + j < O ? scr[(c8 + j) * 128] : 0.0f;
+        st_shared_v4(dl + sw128_offset(row, c8, BM), pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]),
+                     pack2(f[6], f[7]));
     }
     return st;
 }
@@ -498,7 +541,7 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
         // this thread's row's loss inputs (used after the forward pass)
         const uint32_t my_src = rows_cur[row];
         const bool my_live = half == 0 && row < nrows;
-        RowIn rin;
+        RowIn rin{0xFFFFFFFFu, 0xFFFFFFFFu, 0, 0, 0, 0, 0.0f, 0.0f};
         float v_old = 0.0f, ret = 0.0f;
         if (my_live) {
             if (actor) rin = load_row_in(a, my_src, KT > 32);
@@ -535,26 +578,14 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
             }
             if (!(ok = wait_mma(&bar, phase))) break;
             if (half == 0) {
-                float l[KT];
-                if constexpr (KT == 64) {
-                    tmem_ld64(lane_base + C_SLOT, l);
-                } else {
-                    tmem_ld32(lane_base + C_SLOT, l);
-                }
-#pragma unroll
-                for (int k = 0; k < KT; ++k) l[k] = k < O ? l[k] + bias[2 * HID + k] : 0.0f;
-                if (row < nrows) {
-                    const ActorRow s = actor_row<KT>(a, my_src, rin, l, mean, inv_std, inv_n);
-                    acc_st[0] += s.pg; acc_st[2] += s.ent; acc_st[3] += s.clip; acc_st[4] += s.kl;
-                } else {
-#pragma unroll
-                    for (int k = 0; k < KT; ++k) l[k] = 0.0f;
-                }
-#pragma unroll
-                for (int q = 0; q < KT / 8; ++q)
-                    st_shared_v4(smem + L.dl + sw128_offset(row, q * 8, BM), pack2(l[q * 8], l[q * 8 + 1]),
-                                 pack2(l[q * 8 + 2], l[q * 8 + 3]), pack2(l[q * 8 + 4], l[q * 8 + 5]),
-                                 pack2(l[q * 8 + 6], l[q * 8 + 7]));
+                // the loss and d loss / d logits of this thread's row; scratch: the dZ2
+                // buffer, free from the last tile's second backward product to this
+                // tile's first mask epilogue
+                const bool live = row < nrows;
+                const ActorRow s = actor_row_tmem(a, rin, live, lane_base + C_SLOT, bias + 2 * HID,
+                                                  reinterpret_cast<float*>(smem + L.dz2) + row, smem + L.dl, row,
+                                                  KT, mean, inv_std, inv_n);
+                if (live) { acc_st[0] += s.pg; acc_st[2] += s.ent; acc_st[3] += s.clip; acc_st[4] += s.kl; }
             }
             sync_for_mma();
             if (tid == 0) {
@@ -739,14 +770,26 @@ ej_status launch_ppo_bf16(const FbArgs& fa, float* partial, size_t partial_bytes
     if (!fa.rows && (st = launch_adv_stats(fa.mb, fa.adv, fa.stats, s)) != EJ_OK) return st;
     const NetOffsets off = net_offsets(fa.in_dim, HID, fa.O);
     const int n_tiles = (fa.mb.count + BM - 1) / BM;
-    int per_role = sm_count() / 2;
-    if (per_role > n_tiles) per_role = n_tiles;
-    if (per_role < 1) {
+    if (n_tiles < 1) {
         if (cudaMemsetAsync(grad, 0, sizeof(float) * off.total, s) != cudaSuccess) return fail(EJ_ERR_CUDA, "memset failed");
         return EJ_OK;
     }
-    if ((size_t)2 * per_role * BM * PC * sizeof(float) > partial_bytes)
-        return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: workspace too small for %d CTAs", 2 * per_role);
+    // actor and critic CTAs (one per SM in all): the split with the shortest
+    // longer role, a role with n CTAs taking ceil(tiles / n) rounds of its
+    // tile cost
+    const int sms = sm_count();
+    int groups = 0;
+    for (int h = 0; h < fa.n_heads; ++h) groups += (h * fa.head + fa.head + 7) / 8 - (h * fa.head) / 8;
+    const double c_act = PPO_TILE + PPO_LOSS_GROUP * groups, c_cri = PPO_TILE;
+    int n_act = 1, n_cri = 1;
+    double best = 1e300;
+    for (int na = 1; na < sms && na <= n_tiles; ++na) {
+        const int nc = sms - na < n_tiles ? sms - na : n_tiles;
+        const double t = fmax(c_act * ((n_tiles + na - 1) / na), c_cri * ((n_tiles + nc - 1) / nc));
+        if (t < best) { best = t; n_act = na; n_cri = nc; }
+    }
+    if ((size_t)(n_act + n_cri) * BM * PC * sizeof(float) > partial_bytes)
+        return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: workspace too small for %d CTAs", n_act + n_cri);
     const size_t smem = ppo_smem().total + 1024;
     static size_t configured[2] = {0, 0};
     const int kt = fa.O <= 32 ? 0 : 1;
@@ -759,16 +802,16 @@ ej_status launch_ppo_bf16(const FbArgs& fa, float* partial, size_t partial_bytes
     BfPpoArgs P;
     P.f = fa;
     P.partial = partial;
-    P.n_actor = per_role;
+    P.n_actor = n_act;
     if (fa.rows) {
         st = launch_mb_rows_stats(fa.mb, fa.adv, fa.rows, fa.stats, s);
         if (st != EJ_OK) return st;
     }
-    if (kt == 0) ppo_bf16_kernel<32><<<2 * per_role, BT, smem, s>>>(P);
-    else ppo_bf16_kernel<64><<<2 * per_role, BT, smem, s>>>(P);
+    if (kt == 0) ppo_bf16_kernel<32><<<n_act + n_cri, BT, smem, s>>>(P);
+    else ppo_bf16_kernel<64><<<n_act + n_cri, BT, smem, s>>>(P);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "bf16 PPO launch: %s", cudaGetErrorString(err));
-    ppo_bf16_reduce_kernel<<<128, 256, 0, s>>>(partial, per_role, per_role, fa.in_dim, fa.O, grad);
+    ppo_bf16_reduce_kernel<<<128, 256, 0, s>>>(partial, n_act, n_cri, fa.in_dim, fa.O, grad);
     err = cudaGetLastError();
     if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "bf16 PPO reduce launch: %s", cudaGetErrorString(err));
     return EJ_OK;
