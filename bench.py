@@ -234,7 +234,8 @@ def run_gpu(args):
 
 def run_rollout(args, dev, precision, E_r=4096, T_r=1000, seed=2000):
     """Full rollout: E_r x A policy forward + masked sampling + government
-    policy + env_step per step (3 launches per step), T_r steps."""
+    policy + env_step per step, T_r steps (BF16: the two networks share one
+    launch, 2 launches per step; FP32: 3)."""
     import torch
 
     import synth
@@ -259,7 +260,7 @@ def run_rollout(args, dev, precision, E_r=4096, T_r=1000, seed=2000):
     ms = a.elapsed_time(b) / steps
     mean_rew = float(ro.buf["rew"].double().mean().item())
     out = {"value": E_r * A * T_r / (ms / 1e3), "unit": UNIT, "ms_per_rollout": ms,
-           "mean_population_reward": mean_rew, "launches_per_rollout": 3 * T_r + 2,
+           "mean_population_reward": mean_rew, "launches_per_rollout": 2 * T_r + 1 if precision == "bf16" else 3 * T_r + 2,
            "graph": "one CUDA graph per rollout (carry-over copies + all launches)"}
     del ro, pol, env
     torch.cuda.empty_cache()
@@ -356,8 +357,9 @@ def run_batched(args, dev, E_b=2048, T_b=1000, seed=4000):
         del probe
     kw = dict(T_ep=T_EP, T_tax=T_TAX)
     best, rates = autotune(pops, levels, weights, T_probe=8, repeats=2, device=dev,
-                           candidates=("exact", "pow2", "coarse"), **kw)
-    br = BatchedRollout(pops, levels, T_b, weights, granularity=best, device=dev, **kw)
+                           candidates=("exact", "pow2", "coarse", "exact+merge", "coarse+merge"), **kw)
+    gran, _, merged = best.partition("+")
+    br = BatchedRollout(pops, levels, T_b, weights, granularity=gran, merge=bool(merged), device=dev, **kw)
     br.reset(seed=seed)
     br.capture()
     torch.cuda.synchronize(dev)

@@ -178,13 +178,17 @@ class BatchedRollout:
 
 def autotune(pops, levels, weights, T_probe=8, hidden=128, precision="bf16", candidates=None,
              device="cuda", repeats=3, **env_kw):
-    """Times a captured T_probe-step batched rollout per partition; returns
-    (best granularity, {granularity: agent-steps/s})."""
-    candidates = candidates or ("exact", "pow2", "coarse", "by_actions")
+    """Times a captured T_probe-step batched rollout per candidate; returns
+    (best candidate, {candidate: agent-steps/s}).  A candidate is a partition
+    granularity, with "+merge" for merged policy launches ("exact+merge")."""
+    candidates = candidates or ("exact", "pow2", "coarse", "by_actions", "exact+merge", "coarse+merge")
     rates = {}
-    for gran in candidates:
+    for cand in candidates:
+        gran, _, merged = cand.partition("+")
+        if merged not in ("", "merge"):
+            raise ValueError(cand)
         br = BatchedRollout(pops, levels, T_probe, weights, hidden=hidden, precision=precision,
-                            granularity=gran, device=device, **env_kw)
+                            granularity=gran, merge=bool(merged), device=device, **env_kw)
         br.reset(seed=1)
         br.capture()
         torch.cuda.synchronize(device)
@@ -192,7 +196,7 @@ def autotune(pops, levels, weights, T_probe=8, hidden=128, precision="bf16", can
         for _ in range(repeats):
             br.run()
         torch.cuda.synchronize(device)
-        rates[gran] = br.agent_steps * repeats / (time.perf_counter() - t0)
+        rates[cand] = br.agent_steps * repeats / (time.perf_counter() - t0)
         del br
         torch.cuda.empty_cache()
     best = max(rates, key=rates.get)
