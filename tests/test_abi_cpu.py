@@ -127,3 +127,36 @@ def test_policy_argument_checks(lib):
                               fake, None, fake, None, None, None) == 1   # act without logp
     assert lib.policy_forward(C.byref(p), fake, 7, 128, 0, fake, fake, None, None,
                               None, None, fake, None, None, None) == 1   # unknown network
+
+
+def test_policy_segmented_shapes(lib):
+    """Which network shapes share launches in policy_forward_segments: BF16,
+    hidden 128, <= 96 logits, <= 32 inputs (every benchmark network)."""
+    from paper_2410_22165_gb300.batch import price_grid
+    ok = C.c_int32()
+    for levels, n_actions in ((5, 24), (10, 44), (20, 84)):
+        p = N.make_params(E=2, A=10, **price_grid(levels))
+        assert N.sizes(p).n_actions == n_actions
+        for net in (N.NET_POP, N.NET_GOV):
+            assert lib.policy_segmented(C.byref(p), net, 128, N.BF16, C.byref(ok)) == 0 and ok.value == 1
+            assert lib.policy_segmented(C.byref(p), net, 128, N.FP32, C.byref(ok)) == 0 and ok.value == 0
+            assert lib.policy_segmented(C.byref(p), net, 64, N.BF16, C.byref(ok)) == 0 and ok.value == 0
+    p = N.make_params(E=2, A=10, **price_grid(30))           # 2 + 2 + 120 = 124 actions: one launch per set
+    assert lib.policy_segmented(C.byref(p), N.NET_POP, 128, N.BF16, C.byref(ok)) == 0 and ok.value == 0
+    assert lib.policy_segmented(C.byref(p), 7, 128, N.BF16, C.byref(ok)) == 1     # unknown network
+    assert lib.policy_segmented(C.byref(p), N.NET_POP, 128, N.BF16, None) == 1    # NULL result
+
+
+def test_policy_segments_argument_checks(lib):
+    p = N.make_params(E=2, A=10)
+    fake = C.c_void_p(4096)
+    V = C.c_void_p * 1
+    one = lambda x: V(x)
+    nets = (C.c_int32 * 1)(N.NET_GOV)
+    # no sets, NULL arrays, and a mask given for a government set are rejected on the host
+    assert lib.policy_forward_segments(0, one(C.addressof(p)), one(fake), nets, one(fake), 128, N.BF16,
+                                       one(fake), None, None, None, one(fake), None) == 1
+    assert lib.policy_forward_segments(1, None, one(fake), nets, one(fake), 128, N.BF16,
+                                       one(fake), None, None, None, one(fake), None) == 1
+    assert lib.policy_forward_segments(1, one(C.addressof(p)), one(fake), nets, one(fake), 128, N.BF16,
+                                       one(fake), one(fake), None, None, one(fake), None) == 1

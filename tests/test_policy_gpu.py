@@ -185,6 +185,45 @@ def test_unaligned_observations(net):
             assert torch.equal(ref[k], got[k]), (off, k)
 
 
+def test_more_sets_than_one_launch_takes():
+    """40 sets of two networks (20 small environments, shared weights): the
+    call splits them into launches of at most 32 sets; results equal one
+    policy_forward per set."""
+    import ctypes as C
+    P, N = _mods()
+    from paper_2410_22165_gb300.env import _ptr, _stream
+    rng = np.random.default_rng(3)
+    base = None
+    segs = []
+    for k in range(20):
+        E, A = int(rng.integers(1, 4)), int(rng.integers(5, 40))
+        env, pol, obs, gobs, mask, pw, gw = _setup(E, A, seed=40 + k, precision="bf16", T_ep=30, T_tax=7)
+        if base is None:
+            base = pol
+        pol = P.Policy(env, base.pop_w.cpu(), base.gov_w.cpu(), hidden=H, precision="bf16")
+        pol.pop_w, pol.gov_w = base.pop_w, base.gov_w
+        for net in (N.NET_POP, N.NET_GOV):
+            rows = E * A if net == N.NET_POP else E
+            heads = 1 if net == N.NET_POP else env.p.nb
+            segs.append(dict(env=env, pol=pol, net=net, x=obs if net == N.NET_POP else gobs,
+                             mask=mask if net == N.NET_POP else None,
+                             act=torch.empty((rows, heads), dtype=torch.int32, device="cuda"),
+                             logp=torch.empty(rows, device="cuda"), value=torch.empty(rows, device="cuda")))
+    n = len(segs)
+    V = C.c_void_p * n
+    N.check(N.load().policy_forward_segments(
+        n, V(*[C.addressof(s["env"].p) for s in segs]), V(*[_ptr(s["env"].state) for s in segs]),
+        (C.c_int32 * n)(*[s["net"] for s in segs]),
+        V(*[_ptr(s["pol"].pop_w if s["net"] == N.NET_POP else s["pol"].gov_w) for s in segs]), H, N.BF16,
+        V(*[_ptr(s["x"]) for s in segs]), V(*[_ptr(s["mask"]) for s in segs]), V(*[_ptr(s["act"]) for s in segs]),
+        V(*[_ptr(s["logp"]) for s in segs]), V(*[_ptr(s["value"]) for s in segs]), _stream()),
+        "policy_forward_segments")
+    for s in segs:
+        ref = s["pol"].forward(s["net"], s["x"], s["mask"])
+        assert torch.equal(ref["act"], s["act"]) and torch.equal(ref["logp"], s["logp"])
+        assert torch.equal(ref["value"], s["value"])
+
+
 def test_given_uniforms_and_values_only():
     E, A = 2, 64
     env, pol, obs, gobs, mask, pw, gw = _setup(E, A, seed=4)
