@@ -593,6 +593,22 @@ __host__ __device__ inline PpLayout pp_layout(int H, int n3_max) {
     return L;
 }
 
+// Two float32 additions in one instruction (add.rn.f32x2: each rounded once,
+// as two scalar additions), and two floats -> BF16 pair with negatives set
+// to 0 (cvt.rn.relu: ReLU then round, the same values as round then ReLU).
+__device__ __forceinline__ void add2_rn(float& a, float& b, float c, float d) {
+    unsigned long long x, y, z;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a), "f"(b));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(c), "f"(d));
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(z) : "l"(x), "l"(y));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(z));
+}
+__device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
 __device__ __forceinline__ void wg_bar(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
 
 __device__ __forceinline__ bool wg_and(int id, bool v) {
@@ -771,7 +787,6 @@ __global__ void __launch_bounds__(128 * PP_NWG, 1) policy_bf16_pp_kernel(const _
     const uint32_t sx = smem_u32(xb), sh = smem_u32(hb);
     const uint32_t sw1 = smem_u32(smem + L.w1), sw2 = smem_u32(smem + L.w2), sw3 = smem_u32(smem + L.w3);
     uint64_t* bar = &bars[wg];
-    const __nv_bfloat162 zero2 = __floats2bfloat162_rn(0.0f, 0.0f);
 
     // a tile's observations (contiguous rows, n = rows x I floats from src):
     // 8 float4 slots per thread of the warpgroup, slot q holding the floats
@@ -842,15 +857,15 @@ __global__ void __launch_bounds__(128 * PP_NWG, 1) policy_bf16_pp_kernel(const _
             tmem_ld32(lane_base + c * 32, v);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                uint32_t pk[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int k = q * 8 + 2 * j;
-                    const float* bb = bias + bias_off + c * 32 + k;
-                    const __nv_bfloat162 y = __hmax2(__floats2bfloat162_rn(v[k] + bb[0], v[k + 1] + bb[1]), zero2);
-                    pk[j] = *reinterpret_cast<const uint32_t*>(&y);
-                }
-                st_shared_v4(hb + sw128_offset(row_in_tile, c * 32 + q * 8, BM), pk[0], pk[1], pk[2], pk[3]);
+                const float4 b0 = *reinterpret_cast<const float4*>(bias + bias_off + c * 32 + q * 8);
+                const float4 b1 = *reinterpret_cast<const float4*>(bias + bias_off + c * 32 + q * 8 + 4);
+                float* y = v + q * 8;
+                add2_rn(y[0], y[1], b0.x, b0.y);
+                add2_rn(y[2], y[3], b0.z, b0.w);
+                add2_rn(y[4], y[5], b1.x, b1.y);
+                add2_rn(y[6], y[7], b1.z, b1.w);
+                st_shared_v4(hb + sw128_offset(row_in_tile, c * 32 + q * 8, BM), relu_bf16x2(y[0], y[1]),
+                             relu_bf16x2(y[2], y[3]), relu_bf16x2(y[4], y[5]), relu_bf16x2(y[6], y[7]));
             }
         }
     };
