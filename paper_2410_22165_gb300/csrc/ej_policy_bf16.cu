@@ -572,9 +572,9 @@ constexpr int PP_SCR = 64;      // exp weights a thread keeps in shared memory p
 // Cost of a tile in thousands of SM cycles, measured with clock64 stamps per
 // phase on GB300 (hidden 128, three pipelines per CTA): the critic's tile
 // about 12 (observations, three products, two epilogues, value); the actor's
-// about 13 plus 3.1 per group of 8 logit columns its heads scan (24 logits:
-// 9.3, 63 logits in three heads of 21: 28-31, 84 logits: 35).
-constexpr double PP_CRITIC_TILE = 12.0, PP_ACTOR_TILE = 13.0, PP_ACTOR_GROUP = 3.1;
+// about 13 plus 2.2 per group of 8 logit columns its heads scan (24 logits:
+// 7.1, 84 logits: 23.5).
+constexpr double PP_CRITIC_TILE = 12.0, PP_ACTOR_TILE = 13.0, PP_ACTOR_GROUP = 2.2;
 
 struct PpLayout {
     uint32_t w1, w2, w3, x[PP_NWG], h[PP_NWG], bias, total;
@@ -607,6 +607,57 @@ __device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
     uint32_t r;
     asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
     return r;
+}
+
+__device__ __forceinline__ unsigned long long f2(float a, float b) {
+    unsigned long long x;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a), "f"(b));
+    return x;
+}
+__device__ __forceinline__ void f2_split(unsigned long long x, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
+}
+__device__ __forceinline__ unsigned long long mul2_rn(unsigned long long x, unsigned long long y) {
+    unsigned long long z;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(z) : "l"(x), "l"(y));
+    return z;
+}
+__device__ __forceinline__ unsigned long long sub2_rn(unsigned long long x, unsigned long long y) {
+    unsigned long long z;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(z) : "l"(x), "l"(y));
+    return z;
+}
+__device__ __forceinline__ unsigned long long fadd2_rn(unsigned long long x, unsigned long long y) {
+    unsigned long long z;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(z) : "l"(x), "l"(y));
+    return z;
+}
+
+// exp32 of two arguments at once: exp32's operations in exp32's order, the
+// float32 ones on pairs (f32x2 arithmetic rounds each element once, as the
+// scalar operation does), so each result equals exp32 of its argument.
+__device__ __forceinline__ void exp32x2(float xa, float xb, float& ea, float& eb) {
+    auto c2 = [](float c) { return f2(c, c); };
+    const unsigned long long X = f2(xa, xb);
+    float na, nb;
+    f2_split(mul2_rn(X, c2(0x1.715476p+0f)), na, nb);
+    na = rintf(na);
+    nb = rintf(nb);
+    const unsigned long long N = f2(na, nb);
+    unsigned long long R = sub2_rn(X, mul2_rn(N, c2(0x1.62e4p-1f)));
+    R = sub2_rn(R, mul2_rn(N, c2(0x1.7f7d1cp-20f)));
+    unsigned long long P = c2(0x1.a01a02p-13f);
+    P = fadd2_rn(mul2_rn(P, R), c2(0x1.6c16c2p-10f));
+    P = fadd2_rn(mul2_rn(P, R), c2(0x1.111112p-7f));
+    P = fadd2_rn(mul2_rn(P, R), c2(0x1.555556p-5f));
+    P = fadd2_rn(mul2_rn(P, R), c2(0x1.555556p-3f));
+    P = fadd2_rn(mul2_rn(P, R), c2(0.5f));
+    P = fadd2_rn(mul2_rn(P, R), c2(1.0f));
+    P = fadd2_rn(mul2_rn(P, R), c2(1.0f));
+    const unsigned long long S = f2(__int_as_float(((int)na + 127) << 23), __int_as_float(((int)nb + 127) << 23));
+    f2_split(mul2_rn(P, S), ea, eb);
+    ea = xa < -80.0f ? 0.0f : ea;
+    eb = xb < -80.0f ? 0.0f : eb;
 }
 
 __device__ __forceinline__ void wg_bar(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
@@ -677,15 +728,18 @@ __device__ __forceinline__ int sample_head_tmem(uint32_t taddr, const float* b3,
         float v[8];
         tmem_ld8(taddr + (uint32_t)g, v);
         const uint32_t vb = group_bits(mw, g, lo, hi);
+        float d[8], wv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) d[j] = ((vb >> j) & 1u) ? __fsub_rn(v[j] + b3[g + j], m) : 0.0f;
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) exp32x2(d[j], d[j + 1], wv[j], wv[j + 1]);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const bool ok = (vb >> j) & 1u;
-            const float d = ok ? __fsub_rn(v[j] + b3[g + j], m) : 0.0f;
-            const float wj = exp32(d);
-            S = ok ? __fadd_rn(S, wj) : S;
-            dot = ok ? fmaf(wj, d, dot) : dot;
+            S = ok ? __fadd_rn(S, wv[j]) : S;
+            dot = ok ? fmaf(wv[j], d[j], dot) : dot;
             const int k = g + j - lo;
-            if (ok && k < PP_SCR) scr[k * 128] = wj;
+            if (ok && k < PP_SCR) scr[k * 128] = wv[j];
         }
     }
     const float thr = __fmul_rn(u, S);
@@ -701,11 +755,15 @@ __device__ __forceinline__ int sample_head_tmem(uint32_t taddr, const float* b3,
 #pragma unroll
             for (int j = 0; j < 8; ++j) wv[j] = scr[(((vb >> j) & 1u) ? g + j - lo : 0) * 128];
         } else {
+            float d[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) d[j] = ((vb >> j) & 1u) ? __fsub_rn(v[j] + b3[g + j], m) : 0.0f;
+#pragma unroll
+            for (int j = 0; j < 8; j += 2) exp32x2(d[j], d[j + 1], wv[j], wv[j + 1]);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int k = g + j - lo;
-                wv[j] = k < PP_SCR ? scr[(k >= 0 ? k : 0) * 128]
-                                   : exp32(((vb >> j) & 1u) ? __fsub_rn(v[j] + b3[g + j], m) : 0.0f);
+                if (k < PP_SCR) wv[j] = scr[(k >= 0 ? k : 0) * 128];
             }
         }
 #pragma unroll
