@@ -513,11 +513,17 @@ __device__ void observe(const KParams& p, const Sm& s, const Agent& g, const Dev
             }
         }
     }
-    if (io.obs) {
+    // observations: each warp stages its 32 rows in shared memory and copies
+    // them out with 16-byte stores; in CTAs of 256 and 512 threads half of the
+    // warps at a time share the staging slots (two rounds), which halves the
+    // buffer so that 4 and 2 such CTAs fit an SM
+    constexpr int NW = NT / 32, ROUNDS = NT >= 256 ? 2 : 1, HALF = NW / ROUNDS;
+    for (int round = 0; round < ROUNDS; ++round) {
+    if (io.obs && warp / HALF == round) {
         const int first = warp * 32;
         if (first < p.A) {
             if (i < p.A) {
-                float* o = s.obs + (size_t)i * D;
+                float* o = s.obs + (size_t)(i - round * HALF * 32) * D;
                 if (i < Ae) {
                     int k = 0;
                     o[k++] = g.coin;
@@ -549,7 +555,7 @@ __device__ void observe(const KParams& p, const Sm& s, const Agent& g, const Dev
             __syncwarp();
             const int rows = min(32, p.A - first);
             const int n = rows * D;
-            const float* src = s.obs + (size_t)first * D;
+            const float* src = s.obs + (size_t)(first - round * HALF * 32) * D;
             float* dst = io.obs + (row * p.A + first) * (size_t)D;
             if ((n & 3) == 0 && (((uintptr_t)dst) & 15) == 0) {
                 const float4* src4 = (const float4*)src;
@@ -561,12 +567,17 @@ __device__ void observe(const KParams& p, const Sm& s, const Agent& g, const Dev
         }
     }
     __syncthreads();
+    }
 }
 
-// CTAs per SM each instantiation must fit (registers), so that a batch of
-// environments runs in one wave: e.g. 1024 environments of 100 agents need 7
-// CTAs of 128 threads on each of 152 SMs.
-template <int NT> struct MinCtas { static constexpr int value = NT <= 32 ? 16 : NT <= 64 ? 12 : NT <= 128 ? 7 : NT <= 256 ? 3 : 1; };
+// CTAs per SM each instantiation must fit (registers: 72 per thread at 7
+// CTAs of 128 threads, 64 at 4 of 256 and 2 of 512, none spilled; the shared
+// memory of 100-, 250- and 500-agent environments fits the same counts), so
+// that a batch of environments runs in as few waves as possible: e.g. 1024
+// environments of 100 agents in one wave of 7 x 152 CTAs.  (8 CTAs of 128
+// threads fit at 64 registers, but were slower: 12.2 against 10.6 ms per
+// 1000-step episode of 1024 x 100.)
+template <int NT> struct MinCtas { static constexpr int value = NT <= 32 ? 16 : NT <= 64 ? 12 : NT <= 128 ? 7 : NT <= 256 ? 4 : 2; };
 
 template <int NT, int RC, int PC>
 __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, DevState st, DevIO io, int n_steps,

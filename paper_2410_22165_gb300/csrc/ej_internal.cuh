@@ -93,7 +93,8 @@ __host__ __device__ inline SmemLayout smem_layout(int NT, int R, int P, int L, i
     uint32_t a = align16(8u * NT) + align16(4u * NT) + 4u * align16(4u * NT) +
                  2u * align16(4u * R * NT) + align16(4u * NT);
     uint32_t bsz = 4u * M * NT;              // phase B: statistics being sorted
-    uint32_t c = 4u * NT * D;                // phase C: observation staging
+    const uint32_t stage_nt = NT >= 256 ? NT / 2 : NT;
+    uint32_t c = 4u * stage_nt * D;          // phase C: observation staging (half of the warps at a time from 256 threads)
     uint32_t m = a > bsz ? a : bsz;
     m = m > c ? m : c;
     b = align16(b + m);
