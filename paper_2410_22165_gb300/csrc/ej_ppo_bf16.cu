@@ -211,14 +211,24 @@ __device__ __forceinline__ __nv_bfloat162 bits_bf2(uint32_t u) { return *reinter
 __device__ __forceinline__ void relu_epilogue64(uint32_t taddr, const float* bias, uint8_t* dst, int row, int col) {
     float v[64];
     tmem_ld64(taddr, v);
-    const __nv_bfloat162 zero = __floats2bfloat162_rn(0.0f, 0.0f);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
+        // bias on float32 pairs (add.rn.f32x2: each element rounded once), then
+        // ReLU and BF16 in one conversion (the values of round-then-ReLU)
+        const float4 b0 = *reinterpret_cast<const float4*>(bias + q * 8);
+        const float4 b1 = *reinterpret_cast<const float4*>(bias + q * 8 + 4);
+        float* y = v + q * 8;
         uint32_t w[4];
+        const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int k = q * 8 + 2 * j;
-            w[j] = bf2_bits(__hmax2(__floats2bfloat162_rn(v[k] + bias[k], v[k + 1] + bias[k + 1]), zero));
+            unsigned long long x, c, z;
+            asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(y[2 * j]), "f"(y[2 * j + 1]));
+            asm("mov.b64 %0, {%1, %2};" : "=l"(c) : "f"(bb[2 * j]), "f"(bb[2 * j + 1]));
+            asm("add.rn.f32x2 %0, %1, %2;" : "=l"(z) : "l"(x), "l"(c));
+            float lo, hi;
+            asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(z));
+            asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(w[j]) : "f"(hi), "f"(lo));
         }
         st_shared_v4(dst + sw128_offset(row, col + q * 8, BM), w[0], w[1], w[2], w[3]);
     }
