@@ -235,7 +235,8 @@ def run_gpu(args):
 def run_rollout(args, dev, precision, E_r=4096, T_r=1000, seed=2000):
     """Full rollout: E_r x A policy forward + masked sampling + government
     policy + env_step per step, T_r steps (BF16: the two networks share one
-    launch, 2 launches per step; FP32: 3)."""
+    launch, 2 launches per step; FP32: 3), from 2048 environments in two
+    independent chains of environments on two streams."""
     import torch
 
     import synth
@@ -260,7 +261,8 @@ def run_rollout(args, dev, precision, E_r=4096, T_r=1000, seed=2000):
     ms = a.elapsed_time(b) / steps
     mean_rew = float(ro.buf["rew"].double().mean().item())
     out = {"value": E_r * A * T_r / (ms / 1e3), "unit": UNIT, "ms_per_rollout": ms,
-           "mean_population_reward": mean_rew, "launches_per_rollout": 2 * T_r + 1 if precision == "bf16" else 3 * T_r + 2,
+           "mean_population_reward": mean_rew, "launches_per_rollout": (2 if E_r >= 2048 else 1) * (2 * T_r + 1 if precision == "bf16" else 3 * T_r + 2),
+           "chains": 2 if E_r >= 2048 else 1,
            "graph": "one CUDA graph per rollout (carry-over copies + all launches)"}
     del ro, pol, env
     torch.cuda.empty_cache()

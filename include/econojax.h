@@ -296,12 +296,24 @@ typedef struct {
 } EjRollout;
 
 /* rollout: T steps of {population policy, government policy, env_step},
- * then the critics on slot T.  3T + 2 launches on `stream` (capture them in
- * a CUDA graph to replay).  Gather draws and tie-break keys come from the
- * kernel's Philox streams. */
+ * then the critics on slot T, on `stream` (capture them in a CUDA graph to
+ * replay): 3T + 2 launches, or 2T + 1 in BF16 where one launch serves both
+ * networks (per chain: from E = 2048 on, rollout_split with 2 chains).
+ * Gather draws and tie-break keys come from the kernel's Philox streams. */
 ej_status rollout(const EjParams* p, void* state, int32_t T, int32_t hidden, int32_t precision,
                   const float* pop_weights, const float* gov_weights, const EjRollout* buf,
                   void* stream);
+
+/* rollout_split: rollout with the environments split into n_chains (1..4)
+ * contiguous ranges whose T-step chains are independent (environments do
+ * not interact), issued on as many streams: the caller's stream and library-
+ * owned ones that fork from it and join back into it before the call
+ * returns (so the result is ordered on `stream`, and a capture of `stream`
+ * holds all chains).  One chain's env_step runs while another's policy
+ * does.  Results equal rollout's bit for bit (draws are per environment). */
+ej_status rollout_split(const EjParams* p, void* state, int32_t T, int32_t hidden, int32_t precision,
+                        const float* pop_weights, const float* gov_weights, const EjRollout* b, int32_t n_chains,
+                        void* stream);
 
 /* --------------------------------------------------------------------- PPO
  * Clipped PPO (Section 4; Table 2) for the population and the government

@@ -81,6 +81,8 @@ _PROTOS = {
                                  _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "rollout": (C.c_int, [C.POINTER(EjParams), _VP, C.c_int32, C.c_int32, C.c_int32, _VP, _VP,
                           C.c_void_p, _VP]),
+    "rollout_split": (C.c_int, [C.POINTER(EjParams), _VP, C.c_int32, C.c_int32, C.c_int32, _VP, _VP,
+                                C.c_void_p, C.c_int32, _VP]),
     "ej_ppo_params_default": (C.c_int, [C.POINTER(EjPpoParams)]),
     "ej_ppo_workspace_bytes": (C.c_int, [C.POINTER(EjParams), C.POINTER(EjPpoParams), C.c_int32, C.c_int32,
                                          C.POINTER(C.c_uint64)]),

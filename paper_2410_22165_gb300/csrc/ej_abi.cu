@@ -92,7 +92,7 @@ ej_status derive(const EjParams* p, Layout* lay, KParams* kp) {
     if (kp) {
         KParams k;
         memset(&k, 0, sizeof k);
-        k.E = p->E; k.A = p->A; k.A_s = A_s; k.R = p->R; k.P = p->P; k.nb = p->nb; k.L = L;
+        k.E = p->E; k.e0 = 0; k.ne = p->E; k.A = p->A; k.A_s = A_s; k.R = p->R; k.P = p->P; k.nb = p->nb; k.L = L;
         k.nA = nA; k.D = D; k.G = G; k.W = W; k.M = M; k.cap = cap;
         k.T_ep = p->T_ep; k.T_tax = p->T_tax; k.expire = p->expire; k.max_orders = p->max_orders;
         k.Rk = p->Rk; k.Rd = p->Rd; k.allow_noop = p->allow_noop != 0; k.gov_enabled = p->gov_enabled != 0;

@@ -584,7 +584,7 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
                                                                      int mode, uint32_t seed_lo, uint32_t seed_hi) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Sm s = carve<NT>(smem_raw, p);
-    const int e = blockIdx.x;
+    const int e = p.e0 + (int)blockIdx.x;
     const int i = threadIdx.x;
     const int lane = i & 31, warp = i >> 5;
     constexpr int NW = NT / 32;
@@ -951,7 +951,7 @@ ej_status launch_nt(const KParams& kp, const Layout& lay, const DevState& st, co
         if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
         configured = smem;
     }
-    env_kernel<NT, RC, PC><<<kp.E, NT, smem, stream>>>(kp, st, io, n_steps, mode, (uint32_t)seed,
+    env_kernel<NT, RC, PC><<<kp.ne, NT, smem, stream>>>(kp, st, io, n_steps, mode, (uint32_t)seed,
                                                         (uint32_t)(seed >> 32));
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "env kernel launch: %s", cudaGetErrorString(err));

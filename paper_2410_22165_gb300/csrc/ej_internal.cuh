@@ -13,6 +13,7 @@ namespace ej {
 // Kernel-side copy of the parameters, with the derived sizes.
 struct KParams {
     int E, A, A_s, R, P, nb, L, nA, D, G, W, M, cap;
+    int e0, ne;                 // environments [e0, e0 + ne) of a launch (default: all)
     int T_ep, T_tax, expire, max_orders, Rk, Rd, allow_noop, gov_enabled, tax_levels;
     float start_coin, ome, omega, lg, lc, lt, craft_coin, gather_rho, tick;
     float price[EJ_MAX_P];      // tick * ticks[p], rounded once to float

@@ -44,6 +44,7 @@ struct PolicyArgs {
     int n_heads, head;   // population: 1 head of nA (masked); government: nb heads of tax_levels
     int W;               // mask words per row (0: every action allowed)
     int stream_id;       // Philox stream of the sampling uniforms (0 population, 1 government)
+    int env0;            // global index of the first environment of x's rows (Philox counters)
     const float* weights;
     const float* x;
     const uint32_t* mask;
@@ -74,7 +75,8 @@ struct PolicySeg {
     float* value;
     float* entropy;
     float* logits;
-    int rows, per_env, tile0, pad;
+    int rows, per_env, tile0;
+    int env0;         // global index of the segment's first environment (its Philox counters)
 };
 // A network of a launch: its weights and shape, its segments
 // [seg_lo, seg_hi) and its CTAs (actors [cta0, cta0 + n_act), critics after).
@@ -95,7 +97,7 @@ struct PolicyLaunch {
 // network, at most EJ_MAX_NET networks and EJ_MAX_SEG segments).  *handled =
 // false (nothing launched) when a shape is outside the kernel's range
 // (hidden 128, <= 96 logits, <= 32 inputs, <= 4 mask words) or an
-// observation buffer is not 16-byte aligned.
+// observation buffer is not 4-byte aligned.
 ej_status launch_policy_bf16_multi(const PolicyArgs* segs, int n, cudaStream_t stream, bool* handled);
 
 // exp on float32 by Cody-Waite reduction (Cody and Waite, "Software Manual for
@@ -172,7 +174,7 @@ __device__ __forceinline__ void sample_row(const PolicyArgs& a, int row, const f
     if (a.logits)
         for (int j = 0; j < a.O; ++j) a.logits[(size_t)row * a.O + j] = l[j];
     if (!a.act) return;
-    const int e = row / a.per_env, i = row % a.per_env;
+    const int e = a.env0 + row / a.per_env, i = row % a.per_env;
     float us[EJ_MAX_NB];
     if (a.u) {
         for (int h = 0; h < a.n_heads; ++h) us[h] = a.u[(size_t)row * a.n_heads + h];

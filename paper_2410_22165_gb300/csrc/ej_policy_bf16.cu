@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(BT, 1) policy_bf16_fast_kernel(PolicyArgs a) {
                 for (int h = 0; h < EJ_MAX_NB; ++h)
                     if (h < a.n_heads) us[h] = a.u[(size_t)grow * a.n_heads + h];
             } else {
-                const int e = grow / a.per_env, i = grow % a.per_env;
+                const int e = a.env0 + grow / a.per_env, i = grow % a.per_env;
                 const uint4 x = philox4x32_10(make_uint4(a.stream_id == 0 ? (uint32_t)i : 0u, (uint32_t)e, a.gstep[e],
                                                          (uint32_t)a.stream_id), a.key[0], a.key[1]);
                 if (a.stream_id == 0) us[0] = u01(x.w);
@@ -959,7 +959,7 @@ __global__ void __launch_bounds__(128 * PP_NWG, 1) policy_bf16_pp_kernel(const _
                 for (int h = 0; h < EJ_MAX_NB; ++h)
                     if (h < nt.n_heads) us[h] = sg.u[(size_t)grow * nt.n_heads + h];
             } else {
-                const int e = grow / sg.per_env, i = grow % sg.per_env;
+                const int e = sg.env0 + grow / sg.per_env, i = grow % sg.per_env;
                 const uint4 x = philox4x32_10(make_uint4(nt.stream_id == 0 ? (uint32_t)i : 0u, (uint32_t)e,
                                                          sg.gstep[e], (uint32_t)nt.stream_id),
                                               sg.key[0], sg.key[1]);
@@ -1093,7 +1093,7 @@ ej_status launch_policy_bf16_multi(const PolicyArgs* segs, int n, cudaStream_t s
             PolicySeg& g = pl.seg[q_out++];
             g.x = a.x; g.mask = a.mask; g.u = a.u; g.gstep = a.gstep; g.key = a.key;
             g.act = a.act; g.logp = a.logp; g.value = a.value; g.entropy = a.entropy; g.logits = a.logits;
-            g.rows = a.rows; g.per_env = a.per_env; g.tile0 = tiles; g.pad = 0;
+            g.rows = a.rows; g.per_env = a.per_env; g.tile0 = tiles; g.env0 = a.env0;
             tiles += (a.rows + BM - 1) / BM;
         }
         nt.seg_hi = q_out;

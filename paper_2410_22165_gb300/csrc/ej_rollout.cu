@@ -156,34 +156,39 @@ ej_status policy_forward_segments(int32_t n_seg, const EjParams* const* params, 
     return flush();
 }
 
-ej_status rollout(const EjParams* p, void* state, int32_t T, int32_t hidden, int32_t precision,
-                  const float* pop_weights, const float* gov_weights, const EjRollout* b,
-                  void* stream) {
-    Layout lay;
-    KParams kp;
-    ej_status st = derive(p, &lay, &kp);
-    if (st != EJ_OK) return st;
-    if (!b || !state || !pop_weights || !gov_weights) return fail(EJ_ERR_ARG, "rollout: NULL argument");
-    if (T < 1) return fail(EJ_ERR_ARG, "rollout: T must be >= 1");
-    if (!b->obs || !b->gobs || !b->mask || !b->act || !b->gact || !b->logp || !b->glogp ||
-        !b->value || !b->gvalue || !b->rew || !b->grew || !b->done)
-        return fail(EJ_ERR_ARG, "rollout: every buffer is required");
-    if ((uintptr_t)state % 256) return fail(EJ_ERR_ARG, "state must be 256-byte aligned");
-    cudaStream_t s = (cudaStream_t)stream;
-    const size_t EA = (size_t)kp.E * kp.A;
+}  // extern "C"
+
+namespace {
+
+// T steps of {population policy, government policy, env_step} for the
+// environments [e0, e0 + ne) into the rollout buffer's rows of those
+// environments, then their bootstrap values, on one stream.
+ej_status rollout_range(const EjParams* p, const KParams& kp, const Layout& lay, void* state, int T, int hidden,
+                        int precision, const float* pop_weights, const float* gov_weights, const EjRollout* b,
+                        int e0, int ne, cudaStream_t s) {
+    const size_t EA = (size_t)kp.E * kp.A, A = kp.A;
     const DevState ds = state_pointers(lay, state);
+    KParams kr = kp;
+    kr.e0 = e0;
+    kr.ne = ne;
+    ej_status st;
     for (int t = 0; t <= T; ++t) {
         const bool last = t == T;
         PolicyArgs pa, ga;
-        st = make_args(p, kp, lay, state, EJ_NET_POP, hidden, pop_weights, b->obs + t * EA * kp.D,
-                       b->mask + t * EA * kp.W, nullptr, last ? nullptr : b->act + t * EA,
-                       last ? nullptr : b->logp + t * EA, b->value + t * EA, nullptr, nullptr, &pa);
+        const size_t r0 = (size_t)e0 * A;          // first population row of the range
+        st = make_args(p, kp, lay, state, EJ_NET_POP, hidden, pop_weights, b->obs + (t * EA + r0) * kp.D,
+                       b->mask + (t * EA + r0) * kp.W, nullptr, last ? nullptr : b->act + t * EA + r0,
+                       last ? nullptr : b->logp + t * EA + r0, b->value + t * EA + r0, nullptr, nullptr, &pa);
         if (st != EJ_OK) return st;
-        st = make_args(p, kp, lay, state, EJ_NET_GOV, hidden, gov_weights, b->gobs + (size_t)t * kp.E * kp.G,
-                       nullptr, nullptr, last ? nullptr : b->gact + (size_t)t * kp.E * kp.nb,
-                       last ? nullptr : b->glogp + (size_t)t * kp.E, b->gvalue + (size_t)t * kp.E,
+        pa.rows = ne * kp.A;
+        pa.env0 = e0;
+        const size_t g0 = (size_t)t * kp.E + e0;    // first government row of the range
+        st = make_args(p, kp, lay, state, EJ_NET_GOV, hidden, gov_weights, b->gobs + g0 * kp.G, nullptr, nullptr,
+                       last ? nullptr : b->gact + g0 * kp.nb, last ? nullptr : b->glogp + g0, b->gvalue + g0,
                        nullptr, nullptr, &ga);
         if (st != EJ_OK) return st;
+        ga.rows = ne;
+        ga.env0 = e0;
         // BF16: population and government networks in one launch where the kernel takes both
         bool handled = false;
         if (precision == EJ_BF16) {
@@ -205,9 +210,85 @@ ej_status rollout(const EjParams* p, void* state, int32_t T, int32_t hidden, int
         io.obs = b->obs + (t + 1) * EA * kp.D;
         io.gobs = b->gobs + (size_t)(t + 1) * kp.E * kp.G;
         io.mask = b->mask + (t + 1) * EA * kp.W;
-        if ((st = launch_env(kp, lay, ds, io, 1, MODE_AUX_DRAW, 0, s)) != EJ_OK) return st;
+        if ((st = launch_env(kr, lay, ds, io, 1, MODE_AUX_DRAW, 0, s)) != EJ_OK) return st;
     }
     return EJ_OK;
+}
+
+// Streams and events for the chains of a split rollout (per device, created
+// once; the chains fork from and join back to the caller's stream).
+constexpr int EJ_MAX_CHAINS = 4;
+struct ChainRes {
+    cudaStream_t s[EJ_MAX_CHAINS] = {};
+    cudaEvent_t ev[EJ_MAX_CHAINS] = {};
+    bool ready = false;
+};
+
+ej_status chain_resources(ChainRes** out) {
+    static ChainRes res[16];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return fail(EJ_ERR_CUDA, "rollout: no device");
+    ChainRes& r = res[dev];
+    if (!r.ready) {
+        for (int c = 0; c < EJ_MAX_CHAINS; ++c) {
+            if (c > 0 && cudaStreamCreateWithFlags(&r.s[c], cudaStreamNonBlocking) != cudaSuccess)
+                return fail(EJ_ERR_CUDA, "rollout: stream creation failed");
+            if (cudaEventCreateWithFlags(&r.ev[c], cudaEventDisableTiming) != cudaSuccess)
+                return fail(EJ_ERR_CUDA, "rollout: event creation failed");
+        }
+        r.ready = true;
+    }
+    *out = &r;
+    return EJ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ej_status rollout_split(const EjParams* p, void* state, int32_t T, int32_t hidden, int32_t precision,
+                        const float* pop_weights, const float* gov_weights, const EjRollout* b, int32_t n_chains,
+                        void* stream) {
+    Layout lay;
+    KParams kp;
+    ej_status st = derive(p, &lay, &kp);
+    if (st != EJ_OK) return st;
+    if (!b || !state || !pop_weights || !gov_weights) return fail(EJ_ERR_ARG, "rollout: NULL argument");
+    if (T < 1) return fail(EJ_ERR_ARG, "rollout: T must be >= 1");
+    if (!b->obs || !b->gobs || !b->mask || !b->act || !b->gact || !b->logp || !b->glogp ||
+        !b->value || !b->gvalue || !b->rew || !b->grew || !b->done)
+        return fail(EJ_ERR_ARG, "rollout: every buffer is required");
+    if ((uintptr_t)state % 256) return fail(EJ_ERR_ARG, "state must be 256-byte aligned");
+    if (n_chains < 1 || n_chains > EJ_MAX_CHAINS) return fail(EJ_ERR_ARG, "rollout: 1 to %d chains", EJ_MAX_CHAINS);
+    if (n_chains > kp.E) n_chains = kp.E;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_chains == 1) return rollout_range(p, kp, lay, state, T, hidden, precision, pop_weights, gov_weights, b, 0,
+                                            kp.E, s);
+    ChainRes* r = nullptr;
+    if ((st = chain_resources(&r)) != EJ_OK) return st;
+    if (cudaEventRecord(r->ev[0], s) != cudaSuccess) return fail(EJ_ERR_CUDA, "rollout: event record failed");
+    for (int c = 1; c < n_chains; ++c)
+        if (cudaStreamWaitEvent(r->s[c], r->ev[0], 0) != cudaSuccess) return fail(EJ_ERR_CUDA, "rollout: fork failed");
+    for (int c = 0; c < n_chains; ++c) {
+        const int e0 = (int)((int64_t)kp.E * c / n_chains), e1 = (int)((int64_t)kp.E * (c + 1) / n_chains);
+        st = rollout_range(p, kp, lay, state, T, hidden, precision, pop_weights, gov_weights, b, e0, e1 - e0,
+                           c == 0 ? s : r->s[c]);
+        if (st != EJ_OK) return st;
+    }
+    for (int c = 1; c < n_chains; ++c) {
+        if (cudaEventRecord(r->ev[c], r->s[c]) != cudaSuccess || cudaStreamWaitEvent(s, r->ev[c], 0) != cudaSuccess)
+            return fail(EJ_ERR_CUDA, "rollout: join failed");
+    }
+    return EJ_OK;
+}
+
+ej_status rollout(const EjParams* p, void* state, int32_t T, int32_t hidden, int32_t precision,
+                  const float* pop_weights, const float* gov_weights, const EjRollout* b, void* stream) {
+    // two chains from 2048 environments: one chain's env_step fills the SMs that the
+    // other's policy launch leaves idle at its start and end (E = 4096 x A = 100, BF16:
+    // 211.8 -> 203.4 us per step; three or four chains: 219-221 us)
+    const int chains = p && p->E >= 2048 ? 2 : 1;
+    return rollout_split(p, state, T, hidden, precision, pop_weights, gov_weights, b, chains, stream);
 }
 
 }  // extern "C"

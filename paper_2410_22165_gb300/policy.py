@@ -80,6 +80,7 @@ class Rollout:
             done=torch.empty((T, E), dtype=torch.uint8, device=dev),
         )
         self._c = N.EjRollout(**{k: v.data_ptr() for k, v in self.buf.items()})
+        self.chains = None
 
     def reset(self, seed=0, pop_sizes=None):
         b = self.buf
@@ -113,9 +114,18 @@ class Rollout:
         self.graph.replay()
         return self.buf
 
-    def run(self, stream=None):
+    def run(self, stream=None, chains=None):
+        """One T-step rollout.  `chains` (1..4, default self.chains) splits
+        the environments into independent chains on as many streams; None:
+        the library's choice (2 chains from 2048 environments).  The result
+        is the same for every choice."""
         pol = self.policy
-        N.check(N.load().rollout(C.byref(self.env.p), _ptr(self.env.state), self.T, pol.hidden,
-                                 pol.precision, _ptr(pol.pop_w), _ptr(pol.gov_w), C.byref(self._c),
-                                 _stream(stream)), "rollout")
+        n = self.chains if chains is None else chains
+        lib = N.load()
+        args = (C.byref(self.env.p), _ptr(self.env.state), self.T, pol.hidden, pol.precision, _ptr(pol.pop_w),
+                _ptr(pol.gov_w), C.byref(self._c))
+        if n is None:
+            N.check(lib.rollout(*args, _stream(stream)), "rollout")
+        else:
+            N.check(lib.rollout_split(*args, int(n), _stream(stream)), "rollout_split")
         return self.buf

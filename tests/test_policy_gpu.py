@@ -224,6 +224,33 @@ def test_more_sets_than_one_launch_takes():
         assert torch.equal(ref["value"], s["value"])
 
 
+@pytest.mark.parametrize("precision", ["bf16", "fp32"])
+def test_split_rollout_equals_one_chain(precision):
+    """rollout_split: 2 and 3 chains of environments (ranges of 6 and 4/4/5
+    of 13) on their own streams give the single chain's buffers and state bit
+    for bit, eager and from a captured graph."""
+    P, N = _mods()
+    E, A, T = 13, 20, 6
+    out = {}
+    for chains in (1, 2, 3):
+        env = P.VecEnv(E, A, T_ep=5, T_tax=3)
+        pw = synth.net_weights(12, 0, env.D, H, env.nA)
+        gw = synth.net_weights(12, 1, env.G, H, env.p.nb * env.p.tax_levels)
+        pol = P.Policy(env, torch.from_numpy(pw), torch.from_numpy(gw), hidden=H, precision=precision)
+        ro = P.Rollout(env, pol, T)
+        ro.chains = chains
+        ro.reset(seed=12)
+        ro.run()
+        ro.capture()            # carry-over + one more rollout eagerly, then the graph
+        ro.replay()
+        torch.cuda.synchronize()
+        out[chains] = ({k: v.clone() for k, v in ro.buf.items()}, env.state.clone())
+    for chains in (2, 3):
+        for k, v in out[1][0].items():
+            assert torch.equal(v, out[chains][0][k]), (chains, k)
+        assert torch.equal(out[1][1], out[chains][1])
+
+
 def test_given_uniforms_and_values_only():
     E, A = 2, 64
     env, pol, obs, gobs, mask, pw, gw = _setup(E, A, seed=4)
