@@ -160,3 +160,16 @@ def test_policy_segments_argument_checks(lib):
                                        one(fake), None, None, None, one(fake), None) == 1
     assert lib.policy_forward_segments(1, one(C.addressof(p)), one(fake), nets, one(fake), 128, N.BF16,
                                        one(fake), one(fake), None, None, one(fake), None) == 1
+
+
+def test_rollout_split_argument_checks(lib):
+    """Chain counts outside 1..4 and missing buffers are rejected on the host."""
+    p = N.make_params(E=4, A=10)
+    fake = C.c_void_p(4096)
+    buf = N.EjRollout(**{f: 4096 for f, _ in N.EjRollout._fields_})
+    for chains in (0, 5, -1):
+        assert lib.rollout_split(C.byref(p), fake, 3, 128, N.BF16, fake, fake, C.byref(buf), chains, None) == 1
+    assert "chains" in N.load().ej_last_error().decode()
+    missing = N.EjRollout(**{f: (0 if f == "rew" else 4096) for f, _ in N.EjRollout._fields_})
+    assert lib.rollout_split(C.byref(p), fake, 3, 128, N.BF16, fake, fake, C.byref(missing), 2, None) == 1
+    assert lib.rollout_split(C.byref(p), fake, 0, 128, N.BF16, fake, fake, C.byref(buf), 2, None) == 1   # T = 0
