@@ -36,7 +36,7 @@ UNIT = "agent-steps/s"
 # and small), so a launch of n steps is reported as n/100 times this.  It
 # belongs to the kernel version it was taken on (env_kernel<128, 2, 5>, 6.69 k
 # warp instructions per environment-step) and is re-taken when that changes.
-ENV_DRAM_BYTES_PER_100_STEPS = 129450752 + 1059778816
+ENV_DRAM_BYTES_PER_100_STEPS = 130012928 + 1059629312
 E, A, T_EP, T_TAX = 1024, 100, 1000, 100
 CONFIG = {"workload": "env_step E=1024 x A=100 (+1 government), R=2, P=5, 1000-step episode, "
                       "tax period 100, uniform random seeded actions; one benchmark step = one episode "

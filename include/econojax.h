@@ -249,7 +249,10 @@ ej_status ej_net_floats(const EjParams* p, int32_t net, int32_t hidden, uint64_t
  * act     (device) int32[E][A] or int32[E][nb]; NULL: no sampling (values only).
  * logp, entropy (device) float[rows] (sum over heads); value float[rows];
  * logits  (device) float[rows][O] (may be NULL).  Rows with no allowed action
- * get action 0, logp 0, entropy 0. */
+ * get action 0, logp 0, entropy 0.
+ * BF16 takes hidden 64 or 128, at most 64 inputs and at most 128 logits with
+ * (logits | 1) <= hidden (so <= 63 logits at hidden 64); other shapes return
+ * EJ_ERR_UNSUPPORTED (FP32 takes them). */
 ej_status policy_forward(const EjParams* p, const void* state, int32_t net, int32_t hidden,
                          int32_t precision, const float* weights, const float* obs,
                          const uint32_t* mask, const float* u, int32_t* act, float* logp,

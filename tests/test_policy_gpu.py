@@ -251,6 +251,64 @@ def test_split_rollout_equals_one_chain(precision):
         assert torch.equal(out[1][1], out[chains][1])
 
 
+@pytest.mark.parametrize("hidden,levels", [(64, 5), (64, 10), (128, 30)])
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_forward_outside_the_pipelined_kernel(precision, hidden, levels):
+    """Shapes the pipelined BF16 kernel does not take: hidden 64 (24 and 44
+    actions) and 124 actions at hidden 128 (P = 30 levels, 4 mask words);
+    population and government networks against the oracle."""
+    P, N = _mods()
+    E, A = 5, 60
+    env = P.VecEnv(E, A, T_ep=40, T_tax=9, **P.price_grid(levels))
+    env.reset(seed=31)
+    o = env.step(11)
+    obs, gobs, mask = o["obs"][-1].contiguous(), o["gobs"][-1].contiguous(), o["mask"][-1].contiguous()
+    O_gov = env.p.nb * env.p.tax_levels
+    pw = synth.net_weights(31, 0, env.D, hidden, env.nA)
+    gw = synth.net_weights(31, 1, env.G, hidden, O_gov)
+    pol = P.Policy(env, torch.from_numpy(pw), torch.from_numpy(gw), hidden=hidden, precision=precision)
+    g = int(env.field("gstep")[0].item())
+    bound = (env.D + 2 * hidden) * 2.0 ** -24 if precision == "fp32" else 8 * 2.0 ** -9
+    # population
+    out = pol.forward(N.NET_POP, obs, mask, logits=True)
+    lg, val = out["logits"].cpu().numpy(), out["value"].cpu().numpy()
+    x = obs.cpu().numpy().reshape(E * A, env.D)
+    w = synth.unpack(pw, env.D, hidden, env.nA)
+    lg64, v64 = op.mlp64(w, x)
+    mlg, mv = magnitude(w, x)
+    assert np.all(np.abs(lg - lg64) <= bound * mlg + 1e-30) and np.all(np.abs(val - v64) <= bound * mv + 1e-30)
+    valid = op.mask_bits(mask.cpu().numpy().view(np.uint32).reshape(E * A, env.W), env.nA)
+    u = synth.pop_draws(31, np.arange(E), A, g, 1, env.nA)[3][0].reshape(E * A)
+    assert np.array_equal(out["act"].cpu().numpy()[:, 0], op.sample32(lg, valid, u))
+    # government
+    out = pol.forward(N.NET_GOV, gobs, logits=True)
+    lg = out["logits"].cpu().numpy()
+    wg = synth.unpack(gw, env.G, hidden, O_gov)
+    lg64, v64 = op.mlp64(wg, gobs.cpu().numpy())
+    mlg, mv = magnitude(wg, gobs.cpu().numpy())
+    assert np.all(np.abs(lg - lg64) <= bound * mlg + 1e-30)
+    _, gu = synth.gov_draws(31, np.arange(E), g, 1, env.p.nb, env.p.tax_levels)
+    L = env.p.tax_levels
+    for b in range(env.p.nb):
+        head = lg[:, b * L:(b + 1) * L]
+        assert np.array_equal(out["act"].cpu().numpy()[:, b], op.sample32(head, np.ones_like(head, bool), gu[0, :, b]))
+
+
+def test_bf16_shape_limits_are_reported():
+    """BF16 at hidden 64 takes at most 63 logits: 84 actions are refused with
+    EJ_ERR_UNSUPPORTED (nothing launched); FP32 takes the shape."""
+    P, N = _mods()
+    env = P.VecEnv(2, 10, **P.price_grid(20))
+    env.reset(seed=1)
+    pw = torch.from_numpy(synth.net_weights(1, 0, env.D, 64, env.nA))
+    gw = torch.from_numpy(synth.net_weights(1, 1, env.G, 64, env.p.nb * env.p.tax_levels))
+    obs = torch.zeros((2, 10, env.D), device="cuda")
+    with pytest.raises(N.EjError, match="UNSUPPORTED"):
+        P.Policy(env, pw, gw, hidden=64, precision="bf16").forward(N.NET_POP, obs)
+    out = P.Policy(env, pw, gw, hidden=64, precision="fp32").forward(N.NET_POP, obs)
+    assert torch.isfinite(out["value"]).all()
+
+
 def test_given_uniforms_and_values_only():
     E, A = 2, 64
     env, pol, obs, gobs, mask, pw, gw = _setup(E, A, seed=4)
