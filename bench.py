@@ -225,6 +225,7 @@ def run_gpu(args):
         line["ppo"] = {"workload": "E=2048 x A=100 x 128 steps, GAE, 4 epochs x 8 minibatches, both networks",
                        "bf16": run_ppo(args, dev, "bf16"), "fp32": run_ppo(args, dev, "fp32")}
         line["batched"] = run_batched(args, dev)
+        line["section5"] = run_section5(args, dev)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if world > 1:
@@ -332,6 +333,41 @@ def run_ppo(args, dev, precision, E_p=2048, T_p=128, seed=3000):
            "population_loss": {"policy": float(st[0, 0]), "value": float(st[0, 1]), "entropy": float(st[0, 2])}}
     del ppo, ro, pol, env
     torch.cuda.empty_cache()
+    return out
+
+
+def run_section5(args, dev, E_s=1024, T_s=1000, seed=5000):
+    """Section 5's multi-resource environments (no taxes, prices 3, 6, 9,
+    skills around 1 that grow by 0.5 % per gather / craft, R_d = log2 R):
+    env_step of E_s x A agents over one T_s-step episode in one launch, with
+    the draws made in the kernel, at 4 and 12 resources."""
+    import torch
+
+    from paper_2410_22165_gb300 import VecEnv
+
+    out = {}
+    for R, Rd in ((4, 2), (12, 3)):
+        env = VecEnv(E_s, A, device=dev, T_ep=T_s, T_tax=T_TAX, R=R, P=3, price_tick=3.0, price_ticks=[1, 2, 3],
+                     Rd=Rd, gov_enabled=0, skill_gain=0.005, skill_init=1)
+        env.reset(seed=seed)
+        o = env.alloc_outputs(T_s)
+        env.step(T_s, out=o)                      # warm-up episode
+        torch.cuda.synchronize(dev)
+        ms = []
+        for _ in range(max(1, min(args.steps, 3))):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            env.step(T_s, out=o)
+            b.record()
+            torch.cuda.synchronize(dev)
+            ms.append(a.elapsed_time(b))
+        m = statistics.median(ms)
+        out[f"R{R}"] = {"value": E_s * A * T_s / (m / 1e3), "unit": UNIT, "ms_per_episode": m,
+                        "actions": env.nA, "mean_skill_end": float(env.field("sg")[:, :, :A].float().mean().item())}
+        del env, o
+        torch.cuda.empty_cache()
+    out["workload"] = (f"E={E_s} x A={A}, {T_s}-step episode in one launch, draws in the kernel; R resources, "
+                       "prices 3/6/9, no taxes, skill growth 0.5 % to a maximum of 5, skills around 1")
     return out
 
 

@@ -120,6 +120,19 @@ typedef struct {
     float price_tick;        /* prices are whole multiples of this (2) */
     int32_t price_ticks[EJ_MAX_P];      /* level p costs price_tick*price_ticks[p]; ascending ({1..5}) */
     float thresholds[EJ_MAX_NB - 1];    /* bracket edges, ascending ({50, 100}) */
+    /* Skill improvement (Section 5's multi-resource experiments; off in Table 2):
+     * a gather raises that resource's gather skill, a craft the craft skill, by
+     * s <- min(skill_max, s + s * skill_gain * (1 - s / skill_max)) in float32
+     * (relative gain skill_gain, shrinking to 0 at skill_max).  READING of "increased
+     * by 0.5 %, a bonus that shrinks as the agent approaches the maximum skill". */
+    float skill_gain;        /* 0: skills fixed (Table 2); Section 5: 0.005 */
+    float skill_max;         /* 5 */
+    /* Skills at each episode start: 0 = U[0, 1) (Table 2); 1 = "a normal distribution
+     * around 1.0 with a standard deviation of 1.0" (Section 5), READ as the
+     * Irwin-Hall sum of 12 uniforms - 5 (mean 1, variance exactly 1), clamped to
+     * [0, skill_max]; uniform k of skill j is word k % 4 of the Philox draw
+     * (i, e, episode, 2 | (3j + k / 4) << 8), summed in order in float32. */
+    int32_t skill_init;
 } EjParams;
 
 /* Sizes implied by a parameter set. */

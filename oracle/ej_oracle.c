@@ -249,6 +249,19 @@ static float price32(const orc_params* p, int level) {
     return (float)p->price_tick * (float)p->price_ticks[level];
 }
 
+/* Section 5: the skill after a gather or craft.  The relative bonus is
+ * skill_gain at skill 0 and falls linearly to 0 at skill_max (READING of
+ * "increased by 0.5 %, a bonus that shrinks as the agent approaches the
+ * maximum skill level of 5"); float32, every operation rounded once. */
+static float skill_up(const orc_params* p, float s) {
+    if (!(p->skill_gain > 0.0)) return s;
+    const float smax = (float)p->skill_max;
+    const float room = 1.0f - s / smax;
+    const float gain = (float)p->skill_gain * room;
+    const float up = s + s * gain;
+    return up < smax ? up : smax;
+}
+
 /* Section 3, "Crafting": can the agent craft?  It needs R_k units of each of
  * R_d different resources. */
 static int can_craft(const orc_env* env, int i) {
@@ -501,6 +514,7 @@ void orc_env_step(orc_env* env, const int32_t* act, const int32_t* gov_act,
             float s = env->sg[i * R + r] + rho;
             env->inv[i * R + r] += (int)floorf(s);
             env->n_gather[i] += 1;
+            env->sg[i * R + r] = skill_up(p, env->sg[i * R + r]);
         } else if (a == R + 1) {                              /* craft */
             int used[ORC_MAX_R] = {0};
             for (int k = 0; k < p->Rd; ++k) {                 /* richest first, lower index on ties */
@@ -517,6 +531,7 @@ void orc_env_step(orc_env* env, const int32_t* act, const int32_t* gov_act,
             env->coin64[i] += gain64;
             env->income64[i] += gain64;
             env->n_craft[i] += 1;
+            env->sc[i] = skill_up(p, env->sc[i]);
         } else {                                              /* place one order */
             int j = a - (R + 2);
             int side = j >= R * P;

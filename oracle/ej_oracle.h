@@ -47,6 +47,10 @@ typedef struct {
     double price_tick;      /* all prices are integer multiples of this */
     int price_ticks[ORC_MAX_P];          /* level p costs price_tick * price_ticks[p], ascending */
     double thresholds[ORC_MAX_NB - 1];   /* bracket edges, ascending */
+    /* Section 5's multi-resource experiments: a gather raises that gather
+     * skill, a craft the craft skill, by 0.5 % shrinking to 0 at the maximum
+     * skill 5 (READING: s + s * (gain * (1 - s / max)), capped; 0 = off). */
+    double skill_gain, skill_max;
 } orc_params;
 
 typedef struct orc_env orc_env;

@@ -26,6 +26,7 @@ class _Params(C.Structure):
         ("labor_trade", C.c_double), ("craft_coin", C.c_double),
         ("gather_rho", C.c_double), ("price_tick", C.c_double),
         ("price_ticks", C.c_int * MAX_P), ("thresholds", C.c_double * (MAX_NB - 1)),
+        ("skill_gain", C.c_double), ("skill_max", C.c_double),
     ]
 
 
@@ -46,7 +47,7 @@ def default_params(**over):
         allow_noop=1, gov_enabled=1, tax_levels=21, start_coin=15.0, eta=0.27,
         omega=1.0, labor_gather=1.0, labor_craft=1.0, labor_trade=0.05,
         craft_coin=10.0, gather_rho=1.1, price_tick=2.0, price_ticks=[1, 2, 3, 4, 5],
-        thresholds=[50.0, 100.0],
+        thresholds=[50.0, 100.0], skill_gain=0.0, skill_max=5.0, skill_init=0,
     )
     p.update(over)
     return p

@@ -31,6 +31,7 @@ class EjParams(C.Structure):
         ("labor_gather", C.c_float), ("labor_craft", C.c_float), ("labor_trade", C.c_float),
         ("craft_coin", C.c_float), ("gather_rho", C.c_float), ("price_tick", C.c_float),
         ("price_ticks", C.c_int32 * EJ_MAX_P), ("thresholds", C.c_float * (EJ_MAX_NB - 1)),
+        ("skill_gain", C.c_float), ("skill_max", C.c_float), ("skill_init", C.c_int32),
     ]
 
 

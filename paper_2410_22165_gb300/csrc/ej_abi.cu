@@ -49,6 +49,8 @@ ej_status derive(const EjParams* p, Layout* lay, KParams* kp) {
     }
     for (int b = 1; b + 1 < p->nb; ++b)
         if (!(p->thresholds[b] > p->thresholds[b - 1])) return fail(EJ_ERR_ARG, "thresholds must ascend");
+    if (!(p->skill_gain >= 0.0f) || !(p->skill_max > 0.0f)) return fail(EJ_ERR_ARG, "need skill_gain >= 0 and skill_max > 0");
+    if (p->skill_init != 0 && p->skill_init != 1) return fail(EJ_ERR_ARG, "skill_init must be 0 or 1");
 
     const int A_s = (p->A + 3) & ~3;
     const int D = 8 + 7 * p->R + p->nb;
@@ -100,6 +102,7 @@ ej_status derive(const EjParams* p, Layout* lay, KParams* kp) {
         k.start_coin = p->start_coin; k.ome = 1.0f - p->eta; k.omega = p->omega;
         k.lg = p->labor_gather; k.lc = p->labor_craft; k.lt = p->labor_trade;
         k.craft_coin = p->craft_coin; k.gather_rho = p->gather_rho; k.tick = p->price_tick;
+        k.skill_gain = p->skill_gain; k.skill_max = p->skill_max; k.skill_init = p->skill_init;
         for (int q = 0; q < p->P; ++q) {
             k.ticks[q] = p->price_ticks[q];
             volatile float prod = p->price_tick * (float)p->price_ticks[q];   // one float rounding
@@ -155,6 +158,7 @@ ej_status ej_params_default(EjParams* p) {
     p->craft_coin = 10.0f; p->gather_rho = 1.1f; p->price_tick = 2.0f;
     for (int q = 0; q < 5; ++q) p->price_ticks[q] = q + 1;
     p->thresholds[0] = 50.0f; p->thresholds[1] = 100.0f;
+    p->skill_gain = 0.0f; p->skill_max = 5.0f; p->skill_init = 0;
     return EJ_OK;
 }
 

@@ -195,6 +195,15 @@ __device__ __forceinline__ bool craftable(const KParams& p, const Sm& s, int i) 
 }
 
 // Section 3 "Action masking".
+// Skill improvement after a gather or a craft (Section 5): relative gain
+// skill_gain shrinking linearly to 0 at skill_max, every operation rounded
+// once: s + s * (gain * (1 - s / max)), capped at max.
+__device__ __forceinline__ float skill_up(const KParams& p, float sk) {
+    const float room = __fsub_rn(1.0f, __fdiv_rn(sk, p.skill_max));
+    const float up = __fadd_rn(sk, __fmul_rn(sk, __fmul_rn(p.skill_gain, room)));
+    return fminf(up, p.skill_max);
+}
+
 template <int NT, int RC, int PC>
 __device__ __forceinline__ bool action_valid(const KParams& p, const Sm& s, const Agent& g, int i, int a) {
     const int R = nR<RC>(p), P = nP<PC>(p);
@@ -232,15 +241,35 @@ __device__ void start_agent(const KParams& p, const Sm& s, Agent& g, int i, int 
         s.sg[r * NT + i] = 0.0f;
     }
     if (live) {
-        const int n_chunks = (R + 1 + 3) / 4;
-        for (int c = 0; c < n_chunks; ++c) {
-            const uint4 x = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)e, ep, 2u | ((uint32_t)c << 8)), k0, k1);
-            const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+        if (p.skill_init == 0) {
+            // U[0, 1): the uniforms of consecutive chunks give SG[0..R-1], then SC
+            const int n_chunks = (R + 1 + 3) / 4;
+            for (int c = 0; c < n_chunks; ++c) {
+                const uint4 x = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)e, ep, 2u | ((uint32_t)c << 8)), k0, k1);
+                const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int idx = 4 * c + j;
-                if (idx < R) s.sg[idx * NT + i] = u01(xs[j]);
-                else if (idx == R) g.sc = u01(xs[j]);
+                for (int j = 0; j < 4; ++j) {
+                    const int idx = 4 * c + j;
+                    if (idx < R) s.sg[idx * NT + i] = u01(xs[j]);
+                    else if (idx == R) g.sc = u01(xs[j]);
+                }
+            }
+        } else {
+            // around 1 with standard deviation 1 (Section 5): 12 uniforms (chunks 3j..3j+2)
+            // summed in order, minus 5, clamped to [0, skill_max]; skill j < R gathers r = j
+            for (int j = 0; j <= R; ++j) {
+                float sum = 0.0f;
+                for (int c = 0; c < 3; ++c) {
+                    const uint4 x = philox4x32_10(
+                        make_uint4((uint32_t)i, (uint32_t)e, ep, 2u | ((uint32_t)(3 * j + c) << 8)), k0, k1);
+                    sum = __fadd_rn(sum, u01(x.x));
+                    sum = __fadd_rn(sum, u01(x.y));
+                    sum = __fadd_rn(sum, u01(x.z));
+                    sum = __fadd_rn(sum, u01(x.w));
+                }
+                const float v = fminf(fmaxf(__fsub_rn(sum, 5.0f), 0.0f), p.skill_max);
+                if (j < R) s.sg[j * NT + i] = v;
+                else g.sc = v;
             }
         }
         g.uprev = utility(p, g.coin, 0.0f);
@@ -697,6 +726,7 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
                 const float sum = __fadd_rn(s.sg[r * NT + i], rho);
                 s.inv[r * NT + i] += (int)floorf(sum);
                 g.ng += 1;
+                if (p.skill_gain > 0.0f) s.sg[r * NT + i] = skill_up(p, s.sg[r * NT + i]);
             } else if (a == R + 1) {                        // craft
                 uint32_t used = 0;
                 for (int k = 0; k < p.Rd; ++k) {
@@ -713,6 +743,7 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
                 g.coin = __fadd_rn(g.coin, gain);
                 g.income = __fadd_rn(g.income, gain);
                 g.nc += 1;
+                if (p.skill_gain > 0.0f) g.sc = skill_up(p, g.sc);
             } else {                                        // one order into escrow
                 int j = a - (R + 2);
                 const int side = j >= R * P;

@@ -16,6 +16,8 @@ struct KParams {
     int e0, ne;                 // environments [e0, e0 + ne) of a launch (default: all)
     int T_ep, T_tax, expire, max_orders, Rk, Rd, allow_noop, gov_enabled, tax_levels;
     float start_coin, ome, omega, lg, lc, lt, craft_coin, gather_rho, tick;
+    float skill_gain, skill_max;   // skill improvement (0: off)
+    int skill_init;                // 0 U[0,1); 1 Irwin-Hall around 1
     float price[EJ_MAX_P];      // tick * ticks[p], rounded once to float
     int ticks[EJ_MAX_P];
     float th[EJ_MAX_NB];        // bracket edges (nb - 1 used)

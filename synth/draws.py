@@ -11,7 +11,11 @@ Key = the 64-bit seed (low word first).  Counters (c0, c1, c2, c3):
   policy-sampling uniform of bracket b.
 * skills of agent i in environment e for episode k:
   ``(i, e, k, STREAM_SKILL | chunk << 8)``; the uniforms of consecutive
-  chunks, in order, give SG[0..R-1] then SC.
+  chunks, in order, give SG[0..R-1] then SC (init 0, U[0, 1)); with init 1
+  skill j (SG[0..R-1], then SC) is the float32 sum, in order, of the 12
+  uniforms of chunks 3j, 3j+1, 3j+2, minus 5, clamped to [0, skill_max]
+  (mean 1, variance 1: the distribution around 1.0 with standard deviation
+  1.0 of Section 5, as an Irwin-Hall sum).
 
 Uniforms are the top 24 bits of a word times 2**-24 (exact float32).
 """
@@ -60,11 +64,24 @@ def gov_draws(seed, env_ids, g0, n_steps, nb, levels):
     return below(x, levels), u01(x)
 
 
-def skill_draws(seed, env_ids, n_agents, episode, R):
+def skill_draws(seed, env_ids, n_agents, episode, R, init=0, skill_max=5.0):
     """Skills for one episode: sg [E, A, R] float32, sc [E, A] float32."""
     k0, k1 = seed_key(seed)
     env_ids = np.asarray(env_ids, dtype=np.uint32)
     i = np.arange(n_agents, dtype=np.uint32)
+    if init == 1:
+        out = []
+        for j in range(R + 1):
+            acc = np.zeros((len(env_ids), n_agents), np.float32)
+            for c in range(3):
+                xs = philox4x32_10(i[None, :], env_ids[:, None], np.uint32(episode),
+                                   np.uint32(STREAM_SKILL | ((3 * j + c) << 8)), k0, k1)
+                for x in xs:
+                    acc = (acc + u01(x).astype(np.float32)).astype(np.float32)
+            out.append(np.clip((acc - np.float32(5.0)).astype(np.float32), np.float32(0.0),
+                               np.float32(skill_max)).astype(np.float32))
+        u = np.stack(out, axis=-1)
+        return u[..., :R], u[..., R]
     n_chunks = (R + 1 + 3) // 4
     us = []
     for ch in range(n_chunks):
@@ -75,7 +92,8 @@ def skill_draws(seed, env_ids, n_agents, episode, R):
     return u[..., :R].astype(np.float32), u[..., R].astype(np.float32)
 
 
-def episode_inputs(seed, env_ids, A, R, nb, n_actions, levels, n_steps, T_ep, g0=0):
+def episode_inputs(seed, env_ids, A, R, nb, n_actions, levels, n_steps, T_ep, g0=0, skill_init=0,
+                   skill_max=5.0):
     """Everything one oracle run needs for envs ``env_ids`` from global step g0.
 
     Returns a dict with act/gather_u/tb [n, E, A], gov_act [n, E, nb],
@@ -85,9 +103,9 @@ def episode_inputs(seed, env_ids, A, R, nb, n_actions, levels, n_steps, T_ep, g0
     act, gu, tb, pu = pop_draws(seed, env_ids, A, g0, n_steps, n_actions)
     gov, gov_u = gov_draws(seed, env_ids, g0, n_steps, nb, levels)
     ep0 = g0 // T_ep
-    sg0, sc0 = skill_draws(seed, env_ids, A, ep0, R)
+    sg0, sc0 = skill_draws(seed, env_ids, A, ep0, R, skill_init, skill_max)
     n_later = (g0 + n_steps) // T_ep - ep0
-    later = [skill_draws(seed, env_ids, A, ep0 + 1 + k, R) for k in range(max(n_later, 0))]
+    later = [skill_draws(seed, env_ids, A, ep0 + 1 + k, R, skill_init, skill_max) for k in range(max(n_later, 0))]
     if later:
         later_sg = np.stack([s for s, _ in later])
         later_sc = np.stack([c for _, c in later])

@@ -28,7 +28,8 @@ REL = 1e-5
 def oracle_run(params, A_e, e, seed, T, g0=0):
     o = OracleEnv(params, A_e)
     inp = synth.episode_inputs(seed, [e], A_e, params["R"], params["nb"], o.nA,
-                               params["tax_levels"], T, params["T_ep"], g0=g0)
+                               params["tax_levels"], T, params["T_ep"], g0=g0,
+                               skill_init=params.get("skill_init", 0), skill_max=params.get("skill_max", 5.0))
     o.reset(inp["sg0"][0], inp["sc0"][0])
     out = o.run(inp["act"][:, 0], inp["gov_act"][:, 0], inp["gather_u"][:, 0], inp["tb"][:, 0],
                 inp["later_sg"][:, 0], inp["later_sc"][:, 0])

@@ -169,6 +169,11 @@ def test_other_cta_sizes(A):
     dict(R=4, P=3, price_ticks=[1, 2, 3], price_tick=3.0, Rd=2, nb=2, thresholds=[40.0]),
     dict(max_orders=0),
     dict(expire=1),
+    # Section 5's multi-resource experiments: skills around 1 that grow by 0.5 % (shrinking
+    # to 0 at 5) with every gather / craft, prices 3, 6, 9, no taxes, 4 and 12 resources
+    dict(R=4, P=3, price_ticks=[1, 2, 3], price_tick=3.0, Rd=2, gov_enabled=0, skill_gain=0.005, skill_init=1),
+    dict(R=12, P=3, price_ticks=[1, 2, 3], price_tick=3.0, Rd=3, gov_enabled=0, skill_gain=0.005, skill_init=1),
+    dict(skill_gain=0.2, skill_max=1.5, skill_init=1),         # fast growth: skills reach the cap
 ])
 def test_parameter_variants(variant):
     kw = dict(T_ep=45, T_tax=8, **variant)
@@ -176,10 +181,17 @@ def test_parameter_variants(variant):
     T = 100
     out = _run_gpu(env, T, seed=21)
     p = default_params(**kw)
+    R = p["R"]
     for e in range(2):
         o, ref = oracle_run(p, 30, e, 21, T)
-        compare_env(_np(out, e), ref, env.params, 30)
+        g = _np(out, e)
+        compare_env(g, ref, env.params, 30)
         _check_state(env, o, e, 30)
+        # the skills (observation columns SG[0..R-1], SC: copied, not computed) bit for bit
+        sk = slice(3 + 2 * R, 4 + 3 * R)
+        assert np.array_equal(g["obs"][:, :30, sk].astype(np.float64), ref["obs"][:, :, sk])
+        if p["skill_gain"] > 0:
+            assert (g["obs"][:, :30, sk] <= p["skill_max"]).all()
 
 
 def test_full_size_sampled_environments():

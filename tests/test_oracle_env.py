@@ -390,3 +390,76 @@ def test_float_mirror_tracks_double():
     a = env.agents()
     err = np.abs(a["coin32"].astype(np.float64) - a["coin64"]) / np.maximum(np.abs(a["coin64"]), 1.0)
     assert err.max() < 1e-5
+
+
+# ---- Section 5: skill improvement and the skill distribution around 1 ----
+
+def _one_agent(s_gather, s_craft, acts, **kw):
+    """One agent (R = 2, no taxes) taking the given actions with gather draws
+    u = 0 (rho = 0); returns the observations [n, D] and the oracle."""
+    p = default_params(T_ep=5000, T_tax=5000, gov_enabled=0, **kw)
+    o = OracleEnv(p, 1)
+    o.reset(np.array(s_gather, np.float32).reshape(1, 2), np.array([s_craft], np.float32))
+    n = len(acts)
+    out = o.run(np.array(acts, np.int32).reshape(n, 1), np.zeros((n, p["nb"]), np.int32),
+                np.zeros((n, 1), np.float32), np.arange(n, dtype=np.uint32).reshape(n, 1))
+    return out["obs"][:, 0, :], p
+
+
+def test_skill_growth_is_logistic_and_uses_the_skill_before_the_step():
+    """1200 gathers of resource 0 from skill 0.2 at gain 0.005, max 5: the
+    skill follows K / (1 + (K/s0 - 1) (1 + g)^-n) (the logistic curve whose
+    rate matches the 0.5 % gain at small skill) within 0.5 %; it never exceeds
+    5; the other skills do not move; each gather brings floor(skill before the
+    step) units (rho = 0)."""
+    n, g, K, s0 = 1200, 0.005, 5.0, 0.2
+    obs, p = _one_agent([s0, 0.7], 0.4, [1] * n, skill_gain=g, skill_max=K)
+    R = 2
+    sg0, sg1, sc = obs[:, 3 + 2 * R], obs[:, 3 + 2 * R + 1], obs[:, 3 + 3 * R]
+    k = np.arange(1, n + 1)
+    logistic = K / (1 + (K / s0 - 1) * (1 + g) ** (-k))
+    assert np.max(np.abs(sg0 / logistic - 1)) < 5e-3
+    assert (np.diff(sg0) >= 0).all() and sg0.max() <= K and sg0[-1] > 4.5
+    assert (sg1 == np.float32(0.7)).all() and (sc == np.float32(0.4)).all()
+    inv0 = obs[:, 3]
+    before = np.concatenate([[np.float32(s0)], sg0[:-1]])
+    assert np.array_equal(np.diff(np.concatenate([[0.0], inv0])), np.floor(before))
+
+
+def test_skill_growth_fixed_points_and_cap():
+    """Skill 0 stays 0; skill at the maximum stays there; a fast gain (0.6,
+    maximum 2) reaches the maximum and never passes it."""
+    R = 2
+    obs, _ = _one_agent([0.0, 1.0], 0.0, [1] * 50, skill_gain=0.005)
+    assert (obs[:, 3 + 2 * R] == 0).all()
+    obs, _ = _one_agent([5.0, 1.0], 1.0, [1] * 50, skill_gain=0.005, skill_max=5.0)
+    assert (obs[:, 3 + 2 * R] == np.float32(5.0)).all()
+    obs, _ = _one_agent([1.9, 1.0], 1.0, [1] * 200, skill_gain=0.6, skill_max=2.0)
+    assert obs[:, 3 + 2 * R].max() <= 2.0 and obs[-1, 3 + 2 * R] == np.float32(2.0)
+
+
+def test_craft_skill_grows_by_the_same_rule():
+    """With R_k = 0 crafting is always allowed: n crafts move the craft skill
+    along exactly the trajectory n gathers give a gather skill from the same
+    start (the same rule for both skills)."""
+    R, n = 2, 300
+    g_obs, _ = _one_agent([0.3, 1.0], 2.0, [1] * n, skill_gain=0.005, Rk=0)
+    c_obs, _ = _one_agent([1.0, 1.0], 0.3, [R + 1] * n, skill_gain=0.005, Rk=0)
+    assert np.array_equal(g_obs[:, 3 + 2 * R], c_obs[:, 3 + 3 * R])
+    assert c_obs[-1, 3 + 3 * R] > 0.3
+
+
+def test_skill_init_around_one():
+    """Skill init 1: 12 uniforms summed minus 5, clamped to [0, 5]: median 1,
+    interquartile range 1.349 (that of a unit normal), Phi(-1) of the skills
+    clamped to 0, none above 5; init 0 stays U[0, 1)."""
+    sg, sc = synth.skill_draws(7, np.arange(200), 100, 3, 4, init=1)
+    v = np.concatenate([sg.ravel(), sc.ravel()]).astype(np.float64)
+    assert v.min() >= 0.0 and v.max() <= 5.0
+    assert abs(np.median(v) - 1.0) < 0.02
+    q1, q3 = np.quantile(v, [0.25, 0.75])
+    assert abs((q3 - q1) - 1.349) < 0.03
+    assert abs((v == 0).mean() - 0.1587) < 0.006
+    sg, sc = synth.skill_draws(7, np.arange(200), 100, 3, 4, init=0)
+    u = np.concatenate([sg.ravel(), sc.ravel()])
+    assert u.min() >= 0.0 and u.max() < 1.0 and abs(u.mean() - 0.5) < 0.01

@@ -257,9 +257,22 @@ def test_forward_outside_the_pipelined_kernel(precision, hidden, levels):
     """Shapes the pipelined BF16 kernel does not take: hidden 64 (24 and 44
     actions) and 124 actions at hidden 128 (P = 30 levels, 4 mask words);
     population and government networks against the oracle."""
+    P, _ = _mods()
+    _forward_vs_oracle(precision, hidden, P.price_grid(levels))
+
+
+@pytest.mark.parametrize("R,Rd", [(4, 2), (12, 3)])
+def test_section5_networks_of_256_units_fp32(R, Rd):
+    """Section 5's networks of 256 units per layer on its multi-resource
+    environments (30 and 86 actions), FP32 forward against the oracle."""
+    _forward_vs_oracle("fp32", 256, dict(R=R, P=3, price_tick=3.0, price_ticks=[1, 2, 3], Rd=Rd,
+                                         gov_enabled=0, skill_gain=0.005, skill_init=1))
+
+
+def _forward_vs_oracle(precision, hidden, env_kw):
     P, N = _mods()
     E, A = 5, 60
-    env = P.VecEnv(E, A, T_ep=40, T_tax=9, **P.price_grid(levels))
+    env = P.VecEnv(E, A, T_ep=40, T_tax=9, **env_kw)
     env.reset(seed=31)
     o = env.step(11)
     obs, gobs, mask = o["obs"][-1].contiguous(), o["gobs"][-1].contiguous(), o["mask"][-1].contiguous()
