@@ -1,5 +1,7 @@
-// C ABI of the policy side: network sizes, policy_forward and rollout.
+// C ABI of the policy side: network sizes, policy_forward (single and
+// segmented launches), rollout and split rollouts.
 #include <cstring>
+#include <mutex>
 
 #include "ej_internal.cuh"
 #include "ej_policy.cuh"
@@ -226,8 +228,10 @@ struct ChainRes {
 
 ej_status chain_resources(ChainRes** out) {
     static ChainRes res[16];
+    static std::mutex mu;                      // first calls from several host threads
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return fail(EJ_ERR_CUDA, "rollout: no device");
+    std::lock_guard<std::mutex> lock(mu);
     ChainRes& r = res[dev];
     if (!r.ready) {
         for (int c = 0; c < EJ_MAX_CHAINS; ++c) {

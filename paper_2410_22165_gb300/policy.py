@@ -92,9 +92,10 @@ class Rollout:
             self.buf[k][0].copy_(self.buf[k][self.T])
 
     def capture(self):
-        """Capture carry_over + run (3T + 2 launches and the slot-0 copies) as
-        one CUDA graph; replay() then runs the next rollout.  Runs one rollout
-        eagerly first (kernel attributes are set outside the capture)."""
+        """Capture carry_over + run (the slot-0 copies and 2T + 1 launches per
+        chain in BF16, 3T + 2 in FP32) as one CUDA graph; replay() then runs
+        the next rollout.  Runs one rollout eagerly first (kernel attributes
+        and the chains' streams are set up outside the capture)."""
         self.carry_over()
         self.run()
         torch.cuda.synchronize(self.env.device)
