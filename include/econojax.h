@@ -29,7 +29,7 @@
  *                                                        "Action masking")
  *  2. per resource, the k-th best bid meets the k-th best ask while bid >= ask;
  *     priority: price, then age, then a random key; the trade is at the
- *     price of the order placed last (the ask's when placed together)
+ *     price of the newer order (the ask's when both are of the same step)
  *                                                       (Sec. 3 "Trading"; App. A)
  *  3. an order leaves after `expire` matching rounds; escrow goes back
  *  4. at a period end ((t+1) mod T_tax == 0) each agent pays the bracket tax
@@ -123,15 +123,16 @@ typedef struct {
     /* Skill improvement (Section 5's multi-resource experiments; off in Table 2):
      * a gather raises that resource's gather skill, a craft the craft skill, by
      * s <- min(skill_max, s + s * skill_gain * (1 - s / skill_max)) in float32
-     * (relative gain skill_gain, shrinking to 0 at skill_max).  READING of "increased
-     * by 0.5 %, a bonus that shrinks as the agent approaches the maximum skill". */
+     * (relative gain skill_gain, shrinking to 0 at skill_max).  READING of the
+     * section's half-percent bonus that falls off towards the skill ceiling. */
     float skill_gain;        /* 0: skills fixed (Table 2); Section 5: 0.005 */
     float skill_max;         /* 5 */
-    /* Skills at each episode start: 0 = U[0, 1) (Table 2); 1 = "a normal distribution
-     * around 1.0 with a standard deviation of 1.0" (Section 5), READ as the
-     * Irwin-Hall sum of 12 uniforms - 5 (mean 1, variance exactly 1), clamped to
-     * [0, skill_max]; uniform k of skill j is word k % 4 of the Philox draw
-     * (i, e, episode, 2 | (3j + k / 4) << 8), summed in order in float32. */
+    /* Skills at each episode start: 0 = U[0, 1) (Table 2); 1 = Section 5's
+     * normally distributed skills of mean 1 and unit standard deviation, READ
+     * as the Irwin-Hall sum of 12 uniforms - 5 (mean 1, variance exactly 1),
+     * clamped to [0, skill_max]; uniform k of skill j is word k % 4 of the
+     * Philox draw (i, e, episode, 2 | (3j + k / 4) << 8), summed in order in
+     * float32. */
     int32_t skill_init;
 } EjParams;
 

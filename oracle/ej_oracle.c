@@ -250,9 +250,9 @@ static float price32(const orc_params* p, int level) {
 }
 
 /* Section 5: the skill after a gather or craft.  The relative bonus is
- * skill_gain at skill 0 and falls linearly to 0 at skill_max (READING of
- * "increased by 0.5 %, a bonus that shrinks as the agent approaches the
- * maximum skill level of 5"); float32, every operation rounded once. */
+ * skill_gain at skill 0 and falls linearly to 0 at skill_max (READING of the
+ * section's half-percent bonus that vanishes at the skill ceiling of 5);
+ * float32, every operation rounded once. */
 static float skill_up(const orc_params* p, float s) {
     if (!(p->skill_gain > 0.0)) return s;
     const float smax = (float)p->skill_max;
@@ -296,7 +296,7 @@ static int cmp_bids(const void* x, const void* y) {
     const order_t* b = *(const order_t* const*)y;
     if (a->p != b->p) return a->p > b->p ? -1 : 1;          /* high bids first */
     if (a->step != b->step) return a->step < b->step ? -1 : 1;  /* then older */
-    if (a->tb != b->tb) return a->tb < b->tb ? -1 : 1;      /* then at random */
+    if (a->tb != b->tb) return a->tb < b->tb ? -1 : 1;      /* then by the random key */
     return a->agent < b->agent ? -1 : (a->agent > b->agent);
 }
 
@@ -316,7 +316,7 @@ typedef struct { int64_t coin_ticks, income_ticks; } tick_delta;
 /* Section 3, "Trading" and Appendix A: sort bids high-to-low and asks
  * low-to-high (ties: older first, then the random key), pair the k-th bid
  * with the k-th ask while the bid is at least the ask.  The trade happens at
- * the price of the order placed last (READING: the ask's price when both were
+ * the price of the newer of the two orders (READING: the ask's price when both were
  * placed in the same step). */
 static void match_resource(orc_env* env, int r, tick_delta* d) {
     const orc_params* p = &env->prm;
@@ -358,8 +358,9 @@ static void match_resource(orc_env* env, int r, tick_delta* d) {
 
 /* Table 2 ("trade order expire time 30"): an order takes part in `expire`
  * matching rounds, its own step's included, and then leaves the market; the
- * escrowed coin or unit goes back to its owner (READING of "active for a
- * certain amount of time"). */
+ * escrowed coin or unit goes back to its owner (READING: the paper gives
+ * orders a limited lifetime measured in steps, not how the boundary step
+ * counts). */
 static void expire_orders(orc_env* env, tick_delta* d) {
     const orc_params* p = &env->prm;
     int R = p->R;

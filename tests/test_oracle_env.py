@@ -141,7 +141,7 @@ def test_gather_boundaries_and_mean():
 # ------------------------------------------------------------------- market
 
 def test_same_step_trade_at_ask_price():
-    """App. A: price of the order placed last; READING: the ask's price when
+    """App. A: price of the newer order; READING: the ask's price when
     both orders come in the same step."""
     s = Scenario(2)
     s.step([NOOP, gather(0)])
@@ -192,7 +192,7 @@ def test_older_order_first():
 
 @pytest.mark.parametrize("keys,winner", [([0, 500, 100], 2), ([0, 100, 500], 1)])
 def test_random_key_breaks_equal_age(keys, winner):
-    """Section 3: equal price and age are broken at random (the smaller key)."""
+    """Section 3: a tie in price and age is broken by the random key (the smaller key first)."""
     s = Scenario(3)
     s.step([NOOP, gather(0), gather(0)])
     s.step([NOOP, sell(0, 1), sell(0, 1)], tb=keys)
