@@ -1,13 +1,12 @@
 """Comparison of the CUDA environment with the CPU oracle.
 
 Tolerances (float outputs; integer state and masks are compared exactly):
-  * coin-like quantities, observations, statistics: |gpu - oracle| <=
-    1e-5 * max(|scale|, 1), where the scale is the value itself (observation
-    features; for the coin-valued ones - coin, coin in escrow, period
-    earnings - at least the environment's mean total coin at that step, since
-    a float coin that falls to a small value after passing through large ones
-    keeps the absolute error of the large ones), the largest of mean / std /
-    median of the same metric
+  * observations, statistics: |gpu - oracle| <= 1e-5 * max(|scale|, 1), where
+    the scale is the value itself (observation features: period earnings,
+    coin in escrow and all others), for liquid coin the largest coin the
+    agent has held since its episode began (a float sum keeps the absolute
+    error of the largest value it passed; the coin contract's reading of
+    "relative"), the largest of mean / std / median of the same metric
     (government statistics), or the utility magnitude of the agent at this or
     the previous step (rewards: the difference of two utilities loses the
     relative precision of each);
@@ -48,6 +47,21 @@ def _close(g, o, scale, what):
     return float((err / np.maximum(np.abs(scale), 1.0)).max()) if err.size else 0.0
 
 
+def coin_scale(coin, done, start_coin):
+    """[n, A]: the largest |coin| each agent has held since its episode began
+    (start coin included), step by step; done[s] = 1 means row s is already
+    the first state of the next episode."""
+    n, A = coin.shape
+    out = np.empty_like(coin, dtype=np.float64)
+    run = np.full(A, abs(float(start_coin)))
+    for s in range(n):
+        if done[s]:
+            run = np.full(A, abs(float(start_coin)))
+        run = np.maximum(run, np.abs(coin[s]))
+        out[s] = run
+    return out
+
+
 def compare_env(g, ref, params, A_e, obs0_ref=None):
     """g: GPU outputs of one env as numpy (rew [n,A], grew [n], done [n], obs [n,A,D],
     gobs [n,G], mask [n,A,W]); ref: oracle outputs (A_e agents).  Returns max rel errors."""
@@ -65,11 +79,14 @@ def compare_env(g, ref, params, A_e, obs0_ref=None):
         assert np.array_equal(go[:, :A_e, ints].astype(np.int64), ro[:, :, ints].astype(np.int64)), \
             "integer observation features (inventories) differ"
         scale = np.abs(ro).copy()
-        mean_coin = ref["gobs"][:, 0][:, None]
-        D = ro.shape[2]
-        for f in (0, 1, D - 3):        # coin, coin in escrow, period earnings
-            scale[:, :, f] = np.maximum(scale[:, :, f], mean_coin)
+        done = ref["done"] if "done" in ref else np.zeros(len(ro), bool)
+        scale[:, :, 0] = coin_scale(ro[:, :, 0], done, params["start_coin"])
         errs["obs"] = _close(go[:, :A_e], ro, scale, "obs")
+        D = ro.shape[2]
+        rel = lambda f, sc: float((np.abs(go[:, :A_e, f] - ro[:, :, f]) / np.maximum(sc, 1.0)).max())
+        errs["coin"] = rel(0, scale[:, :, 0])
+        errs["coin_plain"] = rel(0, np.abs(ro[:, :, 0]))
+        errs["earnings"] = rel(D - 3, np.abs(ro[:, :, D - 3]))
         assert not go[:, A_e:].any(), "obs of absent agents not zero"
     if "rew" in g:
         ro = ref["obs"]

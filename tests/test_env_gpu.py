@@ -207,7 +207,14 @@ def test_full_size_sampled_environments():
     torch.cuda.synchronize()
     assert out["done"][-1].all() and not out["done"][:-1].any()
     p = default_params()
+    worst = {}
     for e in (0, 1, 511, 1023):
         o, ref = oracle_run(p, A, e, seed, T)
-        compare_env(_np(out, e), ref, env.params, A)
+        errs = compare_env(_np(out, e), ref, env.params, A)
         _check_state(env, o, e, A)
+        worst = {k: max(v, worst.get(k, 0.0)) for k, v in errs.items()}
+    # the coin contract (1e-5 relative to the largest coin the agent has held
+    # this episode) is asserted inside compare_env; the plain per-value error
+    # of liquid coin (floor 1 coin) is reported
+    print("worst relative errors at full size:", {k: f"{v:.2e}" for k, v in worst.items()})
+    assert worst["coin"] < 1e-5 and worst["earnings"] < 1e-5
