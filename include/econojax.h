@@ -312,16 +312,21 @@ typedef struct {
     uint8_t* done;       /* [T][E] */
 } EjRollout;
 
-/* rollout: T steps of {population policy, government policy, env_step},
- * then the critics on slot T, on `stream` (capture them in a CUDA graph to
- * replay): 3T + 2 launches, or 2T + 1 in BF16 where one launch serves both
- * networks (per chain: from E = 2048 on, rollout_split with 2 chains).
- * Gather draws and tie-break keys come from the kernel's Philox streams. */
+/* rollout: the data collection of PPO training (Section 4: the agents act
+ * in E parallel environments for T steps with the current shared networks,
+ * Table 2's rollout length; Section 3 "Overall design": the environment is
+ * stepped as a pure function of state and actions).  T steps of {population
+ * policy, government policy, env_step}, then the critics on slot T, on
+ * `stream` (capture them in a CUDA graph to replay): 3T + 2 launches, or
+ * 2T + 1 in BF16 where one launch serves both networks (per chain: from
+ * E = 2048 on, rollout_split with 2 chains).  Gather draws and tie-break keys
+ * come from the kernel's Philox streams.  Every member of buf is required
+ * (EJ_ERR_ARG otherwise). */
 ej_status rollout(const EjParams* p, void* state, int32_t T, int32_t hidden, int32_t precision,
                   const float* pop_weights, const float* gov_weights, const EjRollout* buf,
                   void* stream);
 
-/* rollout_split: rollout with the environments split into n_chains (1..4)
+/* rollout_split (Section 4, as rollout): rollout with the environments split into n_chains (1..4)
  * contiguous ranges whose T-step chains are independent (environments do
  * not interact), issued on as many streams: the caller's stream and library-
  * owned ones that fork from it and join back into it before the call
@@ -382,7 +387,11 @@ ej_status ppo_advantages(const EjParams* p, const EjPpoParams* pp, int32_t T, co
  * EJ_NET_GOV) into grad (device float[ej_net_floats], padding zeroed), after
  * ppo_advantages.  stats_out (device double[8], may be NULL): sums over the
  * minibatch of {advantage, advantage^2, policy loss, value loss, entropy,
- * clipped indicator, logp_old - logp}. */
+ * clipped indicator, logp_old - logp}, then [7] the minibatch's loss itself,
+ * (policy loss + vf_coef value loss - ent_coef entropy) / rows.
+ * The rollout-buffer arrays read: obs, mask, act, logp, value (population) or
+ * gobs, gact, glogp, gvalue (government); ppo_advantages reads rew, value,
+ * grew, gvalue, done.  A NULL one of these returns EJ_ERR_ARG (nothing runs). */
 ej_status ppo_minibatch_grad(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_t hidden,
                              int32_t precision, int32_t net, const float* weights,
                              const EjRollout* buf, void* workspace, uint32_t shuffle_ctr,
@@ -401,7 +410,8 @@ ej_status ppo_minibatch_grad(const EjParams* p, const EjPpoParams* pp, int32_t T
  *     all-reduce) it is the gradient of the union minibatch; with one rank and
  *     its own moments it equals ppo_minibatch_grad.
  * Arguments and errors otherwise as ppo_minibatch_grad; stats_out holds this
- * rank's sums. */
+ * rank's sums, and [7] this rank's part of the union minibatch's loss (the
+ * sums divided by moments[0]; the ranks' parts add up to the loss). */
 ej_status ppo_minibatch_moments(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_t net,
                                 const EjRollout* buf, void* workspace, uint32_t shuffle_ctr,
                                 int32_t minibatch, double* moments, void* stream);
@@ -428,9 +438,10 @@ ej_status ppo_update(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_
                      float* stats_out, void* stream);
 
 /* ppo_minibatch_grad_static: ppo_minibatch_grad for callers that cannot
- * allocate device memory (code running inside a CUDA stream capture, where
- * cudaMalloc is not allowed; hosts whose device memory belongs to another
- * runtime's pool; C programs without an allocator of their own).  It needs no
+ * allocate device memory: hosts whose device memory belongs to another
+ * runtime's pool allocator, which hands out no extra buffers; C programs that
+ * embed the library without a device allocator of their own; service loops
+ * that must not allocate once they are running.  It needs no
  * workspace: the advantages of `net`, the activations and the split-K partial
  * sums live in a static device array of 48 MiB that the library holds on every
  * GPU that loads it, until the process exits.  It computes the advantages of
@@ -438,6 +449,8 @@ ej_status ppo_update(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_
  * gradient are those of ppo_minibatch_grad (the partial sums are reduced in
  * 16 chunks instead of 96, so results agree to rounding).  The paper has no
  * counterpart: this is a convenience of this library.
+ * precision must be EJ_FP32 (EJ_BF16 returns EJ_ERR_UNSUPPORTED: the tensor-
+ * core gradient keeps per-CTA accumulators that do not fit the array).
  * Limits: the rollout's advantages and one minibatch of activations must fit
  * 48 MiB (about 8 thousand minibatch rows at hidden 128); larger sizes return
  * EJ_ERR_UNSUPPORTED with the bytes needed, before anything is enqueued.

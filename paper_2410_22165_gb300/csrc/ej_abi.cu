@@ -19,6 +19,20 @@ ej_status fail(ej_status s, const char* fmt, ...) {
     return s;
 }
 
+int device_sms() {
+    static std::mutex mu;
+    static int sms[kMaxDevices] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 1;
+    std::lock_guard<std::mutex> lock(mu);
+    if (sms[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+        sms[dev] = n;
+    }
+    return sms[dev];
+}
+
 static uint64_t align256(uint64_t x) { return (x + 255u) & ~uint64_t(255u); }
 
 ej_status derive(const EjParams* p, Layout* lay, KParams* kp) {

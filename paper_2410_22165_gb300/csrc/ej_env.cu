@@ -61,7 +61,7 @@ ej_status launch_fill_draws(const KParams& kp, uint64_t seed, uint32_t g0, int n
                             int32_t* gov_act, cudaStream_t stream) {
     const size_t total = (size_t)n_steps * kp.E * (kp.A + 1);
     int blocks = (int)((total + 255) / 256);
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > device_sms() * 16) blocks = device_sms() * 16;
     if (blocks < 1) blocks = 1;
     fill_draws_kernel<<<blocks, 256, 0, stream>>>(kp, (uint32_t)seed, (uint32_t)(seed >> 32), g0, n_steps,
                                                   act, gather_u, tb, policy_u, gov_act);

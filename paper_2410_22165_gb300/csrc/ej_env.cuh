@@ -976,12 +976,9 @@ template <int NT, int RC, int PC>
 ej_status launch_nt(const KParams& kp, const Layout& lay, const DevState& st, const DevIO& io,
                     int n_steps, int mode, uint64_t seed, cudaStream_t stream) {
     const int smem = lay.sizes.smem_bytes;
-    static int configured = 0;   // max dynamic smem set once per instantiation
-    if (configured < smem) {
-        cudaError_t err = cudaFuncSetAttribute(env_kernel<NT, RC, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
-        configured = smem;
-    }
+    static SmemOptIn opt_in;     // per instantiation, per device
+    ej_status st_opt = opt_in.ensure((const void*)env_kernel<NT, RC, PC>, (size_t)smem);
+    if (st_opt != EJ_OK) return st_opt;
     env_kernel<NT, RC, PC><<<kp.ne, NT, smem, stream>>>(kp, st, io, n_steps, mode, (uint32_t)seed,
                                                         (uint32_t)(seed >> 32));
     cudaError_t err = cudaGetLastError();

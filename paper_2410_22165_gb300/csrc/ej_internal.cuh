@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -50,6 +51,38 @@ DevState state_pointers(const Layout& lay, void* base);
 
 // Records the error message of the calling thread and returns s.
 ej_status fail(ej_status s, const char* fmt, ...);
+
+// Per-device launch configuration.  cudaFuncSetAttribute acts on the device
+// that is current when it is called, so the dynamic shared-memory size a
+// kernel has been opened up to is remembered per device (under a lock: host
+// threads may launch concurrently).
+constexpr int kMaxDevices = 64;
+
+class SmemOptIn {
+ public:
+    // Raises `kernel`'s dynamic shared-memory limit on the current device to
+    // at least `bytes` (once per device and size).
+    ej_status ensure(const void* kernel, size_t bytes) {
+        int dev = 0;
+        cudaError_t err = cudaGetDevice(&dev);
+        if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(err));
+        if (dev < 0 || dev >= kMaxDevices) return fail(EJ_ERR_UNSUPPORTED, "device %d: at most %d devices", dev, kMaxDevices);
+        std::lock_guard<std::mutex> lock(mu_);
+        if (bytes_[dev] >= bytes) return EJ_OK;
+        err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
+        bytes_[dev] = bytes;
+        return EJ_OK;
+    }
+
+ private:
+    std::mutex mu_;
+    size_t bytes_[kMaxDevices] = {};
+};
+
+// Streaming multiprocessors of the current device (queried once per device;
+// at least 1).  Grids are sized in multiples of it.
+int device_sms();
 
 // Launchers (ej_env.cu; the 2-resource instantiations with 5, 10 and 20 price levels in
 // ej_env_r2p5.cu, ej_env_r2p10.cu, ej_env_r2p20.cu).

@@ -2,11 +2,11 @@
 // memory in a fixed array that the library itself holds, for callers that
 // cannot allocate device memory.
 //
-// Such callers exist: code running inside a CUDA stream capture (where
-// cudaMalloc is not allowed), hosts whose device memory is owned by another
-// runtime's pool allocator that does not hand out extra buffers, and plain C
-// programs embedding this library with no allocator of their own.  They can
-// pass their inputs and outputs but not a workspace.
+// Such callers exist: hosts whose device memory is owned by another runtime's
+// pool allocator that does not hand out extra buffers, plain C programs
+// embedding this library with no device allocator of their own, and service
+// loops that must not allocate once running.  They can pass their inputs and
+// outputs but not a workspace.
 //
 // The scratch is one file-scope __device__ array of SCRATCH_BYTES (48 MiB),
 // which every GPU that loads the library holds until the process exits.  All
@@ -114,6 +114,7 @@ extern "C" ej_status ppo_minibatch_grad_static(const EjParams* p, const EjPpoPar
                     "with a caller-allocated workspace",
                     (unsigned long long)o, (unsigned long long)SCRATCH_BYTES, (unsigned long long)N,
                     (unsigned long long)count_max);
+    if ((st = check_rollout(b, net, true, true)) != EJ_OK) return st;
     unsigned char* sc = nullptr;
     if ((st = scratch_for_current_device(&sc)) != EJ_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -172,6 +173,8 @@ extern "C" ej_status ppo_minibatch_grad_static(const EjParams* p, const EjPpoPar
         return fail(EJ_ERR_CUDA, "memset of the gradient failed");
     st = launch_minibatch_grad(fa, jobs, 6, (float*)(sc + o_part), STATIC_CHUNKS, weights + off.W2,
                                weights + off.W3, weights + off.V2, grad, s);
+    if (st != EJ_OK) return st;
+    st = launch_minibatch_loss(fa.stats, fa.mb.count, nullptr, pp->vf_coef, pp->ent_coef, s);
     if (st != EJ_OK) return st;
     if (stats_out &&
         cudaMemcpyAsync(stats_out, fa.stats, sizeof(double) * ST_COUNT_, cudaMemcpyDeviceToDevice, s) != cudaSuccess)

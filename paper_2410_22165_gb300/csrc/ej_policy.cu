@@ -69,14 +69,12 @@ size_t policy_fp32_smem(int in_pad, int H, int O) {
 
 ej_status launch_policy_fp32(const PolicyArgs& a, cudaStream_t stream) {
     const size_t smem = policy_fp32_smem(a.in_pad, a.H, a.O);
-    static size_t configured = 0;
-    if (configured < smem) {
-        cudaError_t err = cudaFuncSetAttribute(policy_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
-        configured = smem;
-    }
+    static SmemOptIn opt_in;
+    ej_status st = opt_in.ensure((const void*)policy_fp32_kernel, smem);
+    if (st != EJ_OK) return st;
     const int n_tiles = (a.rows + TILE - 1) / TILE;
-    int grid = n_tiles < 2 * 152 ? n_tiles : 2 * 152;
+    const int cap = 2 * device_sms();
+    int grid = n_tiles < cap ? n_tiles : cap;
     if (grid < 1) grid = 1;
     policy_fp32_kernel<<<grid, NTH, smem, stream>>>(a);
     cudaError_t err = cudaGetLastError();

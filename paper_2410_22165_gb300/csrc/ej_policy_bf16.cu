@@ -1045,14 +1045,8 @@ bool same_net(const PolicyArgs& a, const PolicyArgs& b) {
 }
 
 int sm_count() {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 2)
-            sms = 2;
-    }
-    return sms;
+    const int n = device_sms();
+    return n < 2 ? 2 : n;
 }
 
 }  // namespace
@@ -1161,13 +1155,9 @@ ej_status launch_policy_bf16_multi(const PolicyArgs* segs, int n, cudaStream_t s
         cta += pl.net[k].n_act + pl.net[k].n_cri;
     }
     const size_t smem = pp_layout(pl.H, pl.n3_max).total + 1024;
-    static size_t configured = 0;
-    if (configured < smem) {
-        cudaError_t err = cudaFuncSetAttribute(policy_bf16_pp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem);
-        if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
-        configured = smem;
-    }
+    static SmemOptIn opt_in;
+    ej_status st = opt_in.ensure((const void*)policy_bf16_pp_kernel, smem);
+    if (st != EJ_OK) return st;
     *handled = true;
     policy_bf16_pp_kernel<<<cta, 128 * PP_NWG, smem, stream>>>(pl);
     cudaError_t err = cudaGetLastError();
@@ -1182,15 +1172,11 @@ ej_status launch_policy_bf16(const PolicyArgs& a, cudaStream_t stream) {
     if ((a.O | 1) > a.H) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: logits do not fit the staging area");
     const size_t smem = policy_bf16_smem(a.H, a.O);
     if (smem > 227 * 1024) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: %zu bytes of shared memory", smem);
-    static size_t configured = 0;
-    if (configured < smem) {
-        cudaError_t err = cudaFuncSetAttribute(policy_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem);
-        if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
-        configured = smem;
-    }
+    static SmemOptIn opt_in;
+    ej_status st_opt = opt_in.ensure((const void*)policy_bf16_kernel, smem);
+    if (st_opt != EJ_OK) return st_opt;
     const int n_tiles = (a.rows + BM - 1) / BM;
-    int grid = n_tiles < 152 ? n_tiles : 152;
+    int grid = n_tiles < device_sms() ? n_tiles : device_sms();
     if (grid < 1) grid = 1;
     if (a.H == 128) {
         bool handled = false;
@@ -1199,14 +1185,11 @@ ej_status launch_policy_bf16(const PolicyArgs& a, cudaStream_t stream) {
     }
     const bool fast = a.O <= 64 && a.in_dim <= 32 && a.W <= 2 && a.n_heads <= EJ_MAX_NB && ((uintptr_t)a.x & 15) == 0;
     if (fast) {
-        static size_t conf_fast[2] = {0, 0};
+        static SmemOptIn opt_fast[2];
         const int kt = a.O <= 32 ? 0 : 1;
-        if (conf_fast[kt] < smem) {
-            cudaError_t err = cudaFuncSetAttribute(kt == 0 ? policy_bf16_fast_kernel<32> : policy_bf16_fast_kernel<64>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
-            conf_fast[kt] = smem;
-        }
+        ej_status st_fast = opt_fast[kt].ensure(
+            kt == 0 ? (const void*)policy_bf16_fast_kernel<32> : (const void*)policy_bf16_fast_kernel<64>, smem);
+        if (st_fast != EJ_OK) return st_fast;
         if (kt == 0) policy_bf16_fast_kernel<32><<<grid, BT, smem, stream>>>(a);
         else policy_bf16_fast_kernel<64><<<grid, BT, smem, stream>>>(a);
         cudaError_t err = cudaGetLastError();

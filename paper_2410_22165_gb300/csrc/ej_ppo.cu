@@ -370,7 +370,7 @@ size_t fwd_bwd_smem(int in_pad, int H, int O) {
 ej_status launch_gae(const float* rew, const float* value, const uint8_t* done, int T, int rows,
                      int per_env, float gamma, float lam, float* adv, float* ret, cudaStream_t s) {
     int grid = (rows + 255) / 256;
-    if (grid > 152 * 8) grid = 152 * 8;
+    if (grid > device_sms() * 8) grid = device_sms() * 8;
     gae_kernel<<<grid, 256, 0, s>>>(rew, value, done, T, rows, per_env, gamma, lam, adv, ret);
     return cudaGetLastError() == cudaSuccess ? EJ_OK : fail(EJ_ERR_CUDA, "gae launch failed");
 }
@@ -378,7 +378,7 @@ ej_status launch_gae(const float* rew, const float* value, const uint8_t* done, 
 ej_status launch_adv_stats(const MbDesc& mb, const float* adv, double* stats, cudaStream_t s) {
     zero_kernel<<<1, 32, 0, s>>>(stats, ST_COUNT_);
     int grid = (mb.count + 255) / 256;
-    if (grid > 152 * 4) grid = 152 * 4;
+    if (grid > device_sms() * 4) grid = device_sms() * 4;
     if (grid < 1) grid = 1;
     adv_stats_kernel<<<grid, 256, 0, s>>>(mb, adv, stats);
     return cudaGetLastError() == cudaSuccess ? EJ_OK : fail(EJ_ERR_CUDA, "advantage statistics launch failed");
@@ -387,7 +387,7 @@ ej_status launch_adv_stats(const MbDesc& mb, const float* adv, double* stats, cu
 ej_status launch_mb_rows_stats(const MbDesc& mb, const float* adv, uint32_t* rows, double* stats, cudaStream_t s) {
     zero_kernel<<<1, 32, 0, s>>>(stats, ST_COUNT_);
     int grid = (mb.count + 255) / 256;
-    if (grid > 152 * 8) grid = 152 * 8;
+    if (grid > device_sms() * 8) grid = device_sms() * 8;
     if (grid < 1) grid = 1;
     mb_rows_stats_kernel<<<grid, 256, 0, s>>>(mb, adv, rows, stats);
     return cudaGetLastError() == cudaSuccess ? EJ_OK : fail(EJ_ERR_CUDA, "minibatch rows launch failed");
@@ -402,28 +402,41 @@ ej_status launch_minibatch_grad(const FbArgs& fa, const WgJobs& jobs, int n_jobs
     transpose_kernel<<<64, 256, 0, s>>>(v2, fa.H, fa.H, fa.v2t);
     zero_kernel<<<1, 32, 0, s>>>(fa.stats, ST_COUNT_);
     int grid = (fa.mb.count + 255) / 256;
-    if (grid > 152 * 4) grid = 152 * 4;
+    if (grid > device_sms() * 4) grid = device_sms() * 4;
     adv_stats_kernel<<<grid, 256, 0, s>>>(fa.mb, fa.adv, fa.stats);
     const size_t smem = fwd_bwd_smem(fa.in_pad, fa.H, fa.O);
-    static size_t configured = 0;
-    if (configured < smem) {
-        if (cudaFuncSetAttribute(fwd_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute failed");
-        configured = smem;
-    }
+    static SmemOptIn opt_in;
+    ej_status st = opt_in.ensure((const void*)fwd_bwd_kernel, smem);
+    if (st != EJ_OK) return st;
     const int n_tiles = (fa.mb.count + TILE - 1) / TILE;
-    int g2 = n_tiles < 152 ? n_tiles : 152;
+    int g2 = n_tiles < device_sms() ? n_tiles : device_sms();
     fwd_bwd_kernel<<<g2, NTH, smem, s>>>(fa);
     wgrad_kernel<<<dim3(chunks, n_jobs), NTH, 0, s>>>(jobs, fa.mb.count, chunks, partial);
-    wgrad_reduce_kernel<<<152, 256, 0, s>>>(jobs, n_jobs, chunks, partial, grad);
+    wgrad_reduce_kernel<<<device_sms(), 256, 0, s>>>(jobs, n_jobs, chunks, partial, grad);
     return cudaGetLastError() == cudaSuccess ? EJ_OK : fail(EJ_ERR_CUDA, "minibatch gradient launch failed");
+}
+
+namespace {
+__global__ void minibatch_loss_kernel(double* stats, int count, const double* moments, float vf_coef, float ent_coef) {
+    if (threadIdx.x == 0) {
+        const double n = moments ? moments[0] : (double)count;
+        const double sum = stats[ST_PG] + (double)vf_coef * stats[ST_VF] - (double)ent_coef * stats[ST_ENT];
+        stats[ST_LOSS] = n > 0.0 ? sum / n : 0.0;
+    }
+}
+}  // namespace
+
+ej_status launch_minibatch_loss(double* stats, int count, const double* moments, float vf_coef, float ent_coef,
+                                cudaStream_t s) {
+    minibatch_loss_kernel<<<1, 32, 0, s>>>(stats, count, moments, vf_coef, ent_coef);
+    return cudaGetLastError() == cudaSuccess ? EJ_OK : fail(EJ_ERR_CUDA, "minibatch loss launch failed");
 }
 
 ej_status launch_adam(float* p, const float* g, float* m, float* v, size_t n, float lr, float b1, float b2,
                       float eps, int step, cudaStream_t s) {
     const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
     int grid = (int)((n + 255) / 256);
-    if (grid > 152 * 4) grid = 152 * 4;
+    if (grid > device_sms() * 4) grid = device_sms() * 4;
     adam_kernel<<<grid, 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
     return cudaGetLastError() == cudaSuccess ? EJ_OK : fail(EJ_ERR_CUDA, "adam launch failed");
 }

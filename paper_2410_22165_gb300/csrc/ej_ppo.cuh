@@ -6,7 +6,7 @@
 namespace ej {
 
 // Statistics accumulated per minibatch (doubles).
-enum { ST_ADV_SUM = 0, ST_ADV_SQ = 1, ST_PG = 2, ST_VF = 3, ST_ENT = 4, ST_CLIP = 5, ST_KL = 6, ST_COUNT_ = 8 };
+enum { ST_ADV_SUM = 0, ST_ADV_SQ = 1, ST_PG = 2, ST_VF = 3, ST_ENT = 4, ST_CLIP = 5, ST_KL = 6, ST_LOSS = 7, ST_COUNT_ = 8 };
 
 // Minibatch m of an epoch: positions [lo, lo + count) of the Feistel
 // permutation of [0, N) keyed by (k0, k1, ctr).
@@ -92,6 +92,16 @@ ej_status launch_minibatch_grad(const FbArgs& fa, const WgJobs& jobs, int n_jobs
 // partial_bytes for the per-CTA accumulators.
 ej_status launch_ppo_bf16(const FbArgs& fa, float* partial, size_t partial_bytes, float* grad, cudaStream_t s);
 int ppo_bf16_fault(int clear);
+// The minibatch loss of Section 4 from the gradient launch's sums, into
+// stats[ST_LOSS]: (policy loss + vf_coef value loss - ent_coef entropy) / n,
+// n = the minibatch's rows, or moments[0] (device) for the union of the
+// ranks' minibatches of a data-parallel update.
+ej_status launch_minibatch_loss(double* stats, int count, const double* moments, float vf_coef, float ent_coef,
+                                cudaStream_t s);
+// EJ_ERR_ARG unless every rollout-buffer array the call reads is present
+// (net: EJ_NET_POP, EJ_NET_GOV or -1 for both; gae: GAE inputs; grad:
+// minibatch-gradient inputs).
+ej_status check_rollout(const EjRollout* b, int net, bool gae, bool grad);
 ej_status launch_adv_stats(const MbDesc& mb, const float* adv, double* stats, cudaStream_t s);
 // Writes the minibatch's rollout rows (the permutation, once) and their advantage sums.
 ej_status launch_mb_rows_stats(const MbDesc& mb, const float* adv, uint32_t* rows, double* stats, cudaStream_t s);

@@ -88,6 +88,29 @@ ej_status check_common(const EjParams* p, const EjPpoParams* pp, int T, int H, L
     return EJ_OK;
 }
 
+}  // namespace
+
+// Every rollout-buffer array a PPO call reads is present: for GAE (`gae`)
+// the rewards, values and done flags, for a minibatch gradient the inputs,
+// mask, actions, old log-probabilities and values of the network (net =
+// EJ_NET_POP, EJ_NET_GOV, or -1 for both).
+ej_status check_rollout(const EjRollout* b, int net, bool gae, bool grad) {
+    if (!b) return fail(EJ_ERR_ARG, "rollout buffer is NULL");
+    const bool pop = net != EJ_NET_GOV, gov = net != EJ_NET_POP;
+    struct { const void* p; bool need; const char* name; } f[] = {
+        {b->rew, gae && pop, "rew"}, {b->value, (gae || grad) && pop, "value"}, {b->done, gae, "done"},
+        {b->grew, gae && gov, "grew"}, {b->gvalue, (gae || grad) && gov, "gvalue"},
+        {b->obs, grad && pop, "obs"}, {b->mask, grad && pop, "mask"}, {b->act, grad && pop, "act"},
+        {b->logp, grad && pop, "logp"}, {b->gobs, grad && gov, "gobs"}, {b->gact, grad && gov, "gact"},
+        {b->glogp, grad && gov, "glogp"},
+    };
+    for (const auto& x : f)
+        if (x.need && !x.p) return fail(EJ_ERR_ARG, "rollout buffer member %s is NULL", x.name);
+    return EJ_OK;
+}
+
+namespace {
+
 // Minibatch m of the permutation keyed by (seed, ctr) over the T x rows-per-step rows of `net`.
 MbDesc mb_desc(const KParams& kp, const EjPpoParams* pp, int T, int net, uint32_t ctr, int m) {
     const NetDims d = dims(kp, net);
@@ -133,9 +156,12 @@ ej_status minibatch_grad(const KParams& kp, const EjPpoParams* pp, int T, int H,
     fa.ret = (const float*)(ws + W.ret[net]);
     fa.w3t = (float*)(ws + W.wt3); fa.w2t = (float*)(ws + W.wt2); fa.v2t = (float*)(ws + W.wv2);
     fa.stats = stats;
+    ej_status st;
     if (precision == EJ_BF16) {
         fa.rows = (uint32_t*)(ws + W.rows);      // the float32 path's per-row region holds >= count entries
-        return launch_ppo_bf16(fa, (float*)(ws + W.partial), 4ull * 6 * WG_CHUNKS * WG_STRIDE, grad, s);
+        st = launch_ppo_bf16(fa, (float*)(ws + W.partial), 4ull * 6 * WG_CHUNKS * WG_STRIDE, grad, s);
+        if (st != EJ_OK) return st;
+        return launch_minibatch_loss(stats, fa.mb.count, moments, pp->vf_coef, pp->ent_coef, s);
     }
     const uint64_t R = (uint64_t)fa.mb.count;
     float* rb = (float*)(ws + W.rows);
@@ -164,8 +190,10 @@ ej_status minibatch_grad(const KParams& kp, const EjPpoParams* pp, int T, int H,
     job(5, fa.ws_g2, H, fa.ws_dv, 1, off.V3, off.c3);
     if (cudaMemsetAsync(grad, 0, sizeof(float) * off.total, s) != cudaSuccess)
         return fail(EJ_ERR_CUDA, "memset of the gradient failed");
-    return launch_minibatch_grad(fa, jobs, 6, (float*)(ws + W.partial), WG_CHUNKS, weights + off.W2,
-                                 weights + off.W3, weights + off.V2, grad, s);
+    st = launch_minibatch_grad(fa, jobs, 6, (float*)(ws + W.partial), WG_CHUNKS, weights + off.W2,
+                               weights + off.W3, weights + off.V2, grad, s);
+    if (st != EJ_OK) return st;
+    return launch_minibatch_loss(stats, fa.mb.count, moments, pp->vf_coef, pp->ent_coef, s);
 }
 
 __global__ void accumulate_stats_kernel(const double* st, double* totals) {
@@ -228,6 +256,7 @@ ej_status ppo_advantages(const EjParams* p, const EjPpoParams* pp, int32_t T, co
     ej_status st = check_common(p, pp, T, 128, &lay, &kp);
     if (st != EJ_OK) return st;
     if (!b || !workspace) return fail(EJ_ERR_ARG, "NULL rollout or workspace");
+    if ((st = check_rollout(b, -1, true, false)) != EJ_OK) return st;
     if ((uintptr_t)workspace % 256) return fail(EJ_ERR_ARG, "workspace must be 256-byte aligned");
     const Ws W = ws_layout(kp, pp, T, 128);
     char* ws = (char*)workspace;
@@ -250,6 +279,7 @@ ej_status ppo_minibatch_grad(const EjParams* p, const EjPpoParams* pp, int32_t T
     if (precision != EJ_FP32 && precision != EJ_BF16) return fail(EJ_ERR_ARG, "unknown precision %d", precision);
     if (net != EJ_NET_POP && net != EJ_NET_GOV) return fail(EJ_ERR_ARG, "unknown network %d", net);
     if (!b || !workspace || !weights || !grad) return fail(EJ_ERR_ARG, "NULL argument");
+    if ((st = check_rollout(b, net, false, true)) != EJ_OK) return st;
     if ((uintptr_t)workspace % 256 || (uintptr_t)weights % 16) return fail(EJ_ERR_ARG, "misaligned buffer");
     if (minibatch < 0 || minibatch >= pp->minibatches) return fail(EJ_ERR_ARG, "minibatch out of range");
     const Ws W = ws_layout(kp, pp, T, hidden);
@@ -297,6 +327,7 @@ ej_status ppo_minibatch_grad_global(const EjParams* p, const EjPpoParams* pp, in
     if (precision != EJ_FP32 && precision != EJ_BF16) return fail(EJ_ERR_ARG, "unknown precision %d", precision);
     if (net != EJ_NET_POP && net != EJ_NET_GOV) return fail(EJ_ERR_ARG, "unknown network %d", net);
     if (!b || !workspace || !weights || !grad || !moments) return fail(EJ_ERR_ARG, "NULL argument");
+    if ((st = check_rollout(b, net, false, true)) != EJ_OK) return st;
     if ((uintptr_t)workspace % 256 || (uintptr_t)weights % 16) return fail(EJ_ERR_ARG, "misaligned buffer");
     if (minibatch < 0 || minibatch >= pp->minibatches) return fail(EJ_ERR_ARG, "minibatch out of range");
     const Ws W = ws_layout(kp, pp, T, hidden);
@@ -331,6 +362,7 @@ ej_status ppo_update(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_
     if (precision != EJ_FP32 && precision != EJ_BF16) return fail(EJ_ERR_ARG, "unknown precision %d", precision);
     if (!pop_w || !gov_w || !pop_m || !pop_v || !gov_m || !gov_v || !b || !workspace)
         return fail(EJ_ERR_ARG, "NULL argument");
+    if ((st = check_rollout(b, -1, true, true)) != EJ_OK) return st;
     if ((uintptr_t)workspace % 256 || (uintptr_t)pop_w % 16 || (uintptr_t)gov_w % 16)
         return fail(EJ_ERR_ARG, "misaligned buffer");
     const Ws W = ws_layout(kp, pp, T, hidden);

@@ -762,10 +762,8 @@ __global__ void ppo_bf16_reduce_kernel(const float* __restrict__ partial, int n_
 }
 
 int sm_count() {
-    int dev = 0, n = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 2)
-        return 2;
-    return n;
+    const int n = device_sms();
+    return n < 2 ? 2 : n;
 }
 
 }  // namespace
@@ -801,14 +799,10 @@ ej_status launch_ppo_bf16(const FbArgs& fa, float* partial, size_t partial_bytes
     if ((size_t)(n_act + n_cri) * BM * PC * sizeof(float) > partial_bytes)
         return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: workspace too small for %d CTAs", n_act + n_cri);
     const size_t smem = ppo_smem().total + 1024;
-    static size_t configured[2] = {0, 0};
+    static SmemOptIn opt_in[2];
     const int kt = fa.O <= 32 ? 0 : 1;
-    if (configured[kt] < smem) {
-        cudaError_t err = cudaFuncSetAttribute(kt == 0 ? ppo_bf16_kernel<32> : ppo_bf16_kernel<64>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(err));
-        configured[kt] = smem;
-    }
+    st = opt_in[kt].ensure(kt == 0 ? (const void*)ppo_bf16_kernel<32> : (const void*)ppo_bf16_kernel<64>, smem);
+    if (st != EJ_OK) return st;
     BfPpoArgs P;
     P.f = fa;
     P.partial = partial;

@@ -120,21 +120,17 @@ class PPOLoss(torch.autograd.Function):
     """Clipped PPO loss of one minibatch (Section 4) as a torch autograd node.
 
     forward: one ppo_minibatch_grad call, which runs actor and critic forward,
-    the loss and the hand-written backward in the library's kernels; the loss
-    is (sum policy loss + vf_coef sum value loss - ent_coef sum entropy) / n
-    over the n minibatch rows, from the call's float64 sums.  backward: the
-    saved gradient scaled by the incoming gradient.  The advantages come from
+    the loss and the hand-written backward in the library's kernels and
+    returns the minibatch's loss (float64, entry 7 of its statistics).
+    backward: the saved gradient scaled by the incoming gradient.  The advantages come from
     the last PPO.advantages call, as for ppo_minibatch_grad.
     """
 
     @staticmethod
     def forward(ctx, weights, ppo, rollout, net, shuffle_ctr, minibatch):
         grad, stats = ppo.minibatch_grad(rollout, net, shuffle_ctr, minibatch, weights=weights.detach())
-        n = ppo.minibatch_rows(net, minibatch)
-        pp = ppo.pp
-        loss = (stats[2] + pp.vf_coef * stats[3] - pp.ent_coef * stats[4]) / n
         ctx.save_for_backward(grad)
-        return loss.to(weights.dtype)
+        return stats[7].to(weights.dtype)
 
     @staticmethod
     def backward(ctx, g):

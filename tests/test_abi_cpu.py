@@ -173,3 +173,42 @@ def test_rollout_split_argument_checks(lib):
     missing = N.EjRollout(**{f: (0 if f == "rew" else 4096) for f, _ in N.EjRollout._fields_})
     assert lib.rollout_split(C.byref(p), fake, 3, 128, N.BF16, fake, fake, C.byref(missing), 2, None) == 1
     assert lib.rollout_split(C.byref(p), fake, 0, 128, N.BF16, fake, fake, C.byref(buf), 2, None) == 1   # T = 0
+
+
+@pytest.mark.parametrize("member", [f for f, _ in N.EjRollout._fields_])
+def test_ppo_calls_reject_missing_rollout_arrays(lib, member):
+    """Every PPO entry point checks the rollout-buffer arrays it reads before
+    it enqueues anything: a NULL one returns EJ_ERR_ARG (no GPU is touched)."""
+    p = N.make_params(E=2, A=4)
+    pp = N.EjPpoParams()
+    lib.ej_ppo_params_default(C.byref(pp))
+    fake = C.c_void_p(4096)
+    T, H = 8, 128
+    b = N.EjRollout(**{f: (0 if f == member else 4096) for f, _ in N.EjRollout._fields_})
+    gae = member in ("rew", "value", "grew", "gvalue", "done")
+    pop_grad = member in ("obs", "mask", "act", "logp", "value")
+    gov_grad = member in ("gobs", "gact", "glogp", "gvalue")
+    reads = {
+        "ppo_advantages": gae,
+        "ppo_minibatch_grad pop": pop_grad, "ppo_minibatch_grad gov": gov_grad,
+        "ppo_minibatch_grad_global pop": pop_grad, "ppo_minibatch_grad_global gov": gov_grad,
+        "ppo_update": gae or pop_grad or gov_grad,
+        "ppo_minibatch_grad_static pop": pop_grad or member in ("rew", "value", "done"),
+        "ppo_minibatch_grad_static gov": gov_grad or member in ("grew", "gvalue", "done"),
+    }
+    calls = {
+        "ppo_advantages": lambda: lib.ppo_advantages(C.byref(p), C.byref(pp), T, C.byref(b), fake, None),
+        "ppo_update": lambda: lib.ppo_update(C.byref(p), C.byref(pp), T, H, N.FP32, fake, fake, fake, fake,
+                                             fake, fake, 0, 0, C.byref(b), fake, None, None),
+    }
+    for net, tag in ((N.NET_POP, "pop"), (N.NET_GOV, "gov")):
+        calls[f"ppo_minibatch_grad {tag}"] = lambda net=net: lib.ppo_minibatch_grad(
+            C.byref(p), C.byref(pp), T, H, N.FP32, net, fake, C.byref(b), fake, 0, 0, fake, None, None)
+        calls[f"ppo_minibatch_grad_global {tag}"] = lambda net=net: lib.ppo_minibatch_grad_global(
+            C.byref(p), C.byref(pp), T, H, N.FP32, net, fake, C.byref(b), fake, 0, 0, fake, fake, None, None)
+        calls[f"ppo_minibatch_grad_static {tag}"] = lambda net=net: lib.ppo_minibatch_grad_static(
+            C.byref(p), C.byref(pp), T, H, N.FP32, net, fake, C.byref(b), 0, 0, fake, None, None)
+    for name, call in calls.items():
+        if reads[name]:
+            assert call() == 1, name
+            assert member in lib.ej_last_error().decode(), name

@@ -84,3 +84,26 @@ def test_gradient_matches_finite_differences(net):
         lm = float(ppo.loss((w0.double() - h * d).float(), ro, net, 5, 2))
         fd = (lp - lm) / (2 * h)
         assert fd == pytest.approx(slope, rel=2e-2, abs=2e-3 * float(g.norm())), (fd, slope)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_library_loss_entry(precision):
+    """Entry 7 of the minibatch statistics is the loss of Section 4 assembled
+    in the library: (policy loss + vf_coef value loss - ent_coef entropy) / n;
+    the data-parallel form divides by the union's rows (moments[0])."""
+    import paper_2410_22165_gb300 as P
+    env, pol, ro, _, _ = _setup(E=4)
+    ppo = P.PPO(pol, ro.T, precision=precision, minibatches=4, seed=77)
+    ppo.advantages(ro)
+    pp = ppo.pp
+    for net in (0, 1):
+        _, st = ppo.minibatch_grad(ro, net, 3, 1)
+        n = ppo.minibatch_rows(net, 1)
+        s = st.cpu().numpy()
+        assert s[7] == pytest.approx((s[2] + pp.vf_coef * s[3] - pp.ent_coef * s[4]) / n, rel=1e-12)
+        mom = ppo.minibatch_moments(ro, net, 3, 1)
+        mom2 = mom.clone()
+        mom2[0] *= 2                                   # as if a second rank held as many rows
+        _, sg = ppo.minibatch_grad(ro, net, 3, 1, moments=mom2)
+        g = sg.cpu().numpy()
+        assert g[7] == pytest.approx((g[2] + pp.vf_coef * g[3] - pp.ent_coef * g[4]) / (2 * n), rel=1e-12)

@@ -1,9 +1,9 @@
 """The PPO minibatch gradient without a workspace (ppo_minibatch_grad_static).
 
-Some callers of this library cannot allocate device memory: code that runs
-inside a CUDA stream capture (cudaMalloc is not allowed there), hosts whose
-device memory belongs to another runtime's pool allocator, and C programs
-without an allocator of their own.  For them the library offers an entry point
+Some callers of this library cannot allocate device memory: hosts whose
+device memory belongs to another runtime's pool allocator, C programs without
+a device allocator of their own, and service loops that must not allocate
+once running.  For them the library offers an entry point
 whose scratch is a static device array it holds itself.  This file checks,
 through the C ABI, that two calls in a row give the gradient of the
 workspace-based entry point, within the gradient tolerance the other PPO tests
@@ -66,7 +66,11 @@ def test_static_scratch_gradient_equals_workspace_gradient(net):
     in_dim = env.D if net == 0 else env.G
     O = env.nA if net == 0 else env.p.nb * env.p.tax_levels
     for ctr, mb in ((3, 1), (4, 2)):                     # two calls in a row
+        torch.cuda.synchronize()
+        before = torch.cuda.memory_allocated()
         g_static, s_static = _static_grad(env, pol, ro, ppo, net, ctr, mb)
+        torch.cuda.synchronize()
+        assert torch.cuda.memory_allocated() == before    # the call itself allocates nothing
         g_ws, s_ws = ppo.minibatch_grad(ro, net, ctr, mb)
         torch.cuda.synchronize()
         a = synth.unpack(g_static.cpu().numpy(), in_dim, H, O)
@@ -88,3 +92,15 @@ def test_sizes_beyond_the_static_array_are_refused():
                                             C.byref(rollout), 0, 0, C.c_void_p(4096), None, None)
     assert st == 3
     assert "static" in N.load().ej_last_error().decode()
+
+
+def test_bf16_is_refused():
+    """The static entry point computes in FP32 only."""
+    from paper_2410_22165_gb300 import _native as N
+    p = N.make_params(E=2, A=4)
+    pp = N.EjPpoParams()
+    N.load().ej_ppo_params_default(C.byref(pp))
+    rollout = N.EjRollout(**{f: 4096 for f, _ in N.EjRollout._fields_})
+    st = N.load().ppo_minibatch_grad_static(C.byref(p), C.byref(pp), 16, H, N.BF16, 0, C.c_void_p(4096),
+                                            C.byref(rollout), 0, 0, C.c_void_p(4096), None, None)
+    assert st == 3
