@@ -417,9 +417,10 @@ def run_batched(args, dev, E_b=2048, T_b=1000, seed=4000):
 
 
 def run_e2e(env, d, out, args, dev, world):
-    """Same metric through the host-buffer API (VecEnv.step_host): each step's
-    inputs come from pinned host memory and all its outputs go back to it, in
-    100-step chunks whose copies overlap the kernel of the next chunk."""
+    """Same metric through the C ABI's host-buffer call env_step_host (via
+    VecEnv.step_host, argument marshalling only): each step's inputs come
+    from pinned host memory and all its outputs go back to it, in 100-step
+    chunks whose copies the library overlaps with the kernel of the next."""
     import torch
 
     chunk = 100
@@ -442,8 +443,8 @@ def run_e2e(env, d, out, args, dev, world):
     return {"value": E * A * T_EP * steps * world / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": steps,
             "link_GBps": (h2d + d2h) * steps / dt / 1e9,
-            "how": "VecEnv.step_host, 100-step chunks: pinned host inputs copied in and all outputs copied out, "
-                   "copies of one chunk overlapping the kernel of the next"}
+            "how": "C ABI env_step_host, 100-step chunks: pinned host inputs copied in and all outputs copied "
+                   "out by the library, copies of one chunk overlapping the kernel of the next"}
 
 
 # ------------------------------------------------------------- CPU oracle

@@ -220,6 +220,30 @@ ej_status env_step(const EjParams* p, void* state, int32_t n_steps,
                    float* rew, float* grew, uint8_t* done,
                    float* obs, float* gobs, uint32_t* mask, void* stream);
 
+/* env_step_host: env_step (Sec. 3 "Overall design") with every input and
+ * output in HOST memory, for callers whose data lives on the host.
+ * act, gov_act, gather_u, tb (host): as in env_step ([n][E][A] / [n][E][nb]),
+ * each may be NULL under env_step's rules (in-kernel draws).
+ * rew, grew, done, obs, gobs, mask (host): as in env_step, each may be NULL.
+ * The steps run in chunks of `chunk` steps through two sets of staging
+ * buffers in `workspace` (device, 256-byte aligned, at least
+ * ej_step_host_workspace_bytes(p, chunk) bytes, caller-owned, no
+ * initialisation needed): chunk k+1's inputs are copied in while chunk k
+ * runs and chunk k-1's outputs are copied out, on three library-owned
+ * streams that fork from `stream` and join back into it.  The call returns
+ * after enqueueing; the host outputs are complete once `stream` has reached
+ * this point (e.g. cudaStreamSynchronize).  Host arrays should be page-
+ * locked (cudaHostAlloc, pinned tensors) for the copies to overlap the
+ * kernel; pageable memory works but serialises them.  Results equal
+ * env_step's bit for bit.  Calls on one device are enqueued one at a time
+ * (internal lock).  Errors as env_step; EJ_ERR_ARG also for a NULL or too
+ * small workspace, chunk < 1. */
+ej_status ej_step_host_workspace_bytes(const EjParams* p, int32_t chunk, uint64_t* bytes);
+ej_status env_step_host(const EjParams* p, void* state, int32_t n_steps, int32_t chunk,
+                        const int32_t* act, const int32_t* gov_act, const float* gather_u, const uint32_t* tb,
+                        float* rew, float* grew, uint8_t* done, float* obs, float* gobs, uint32_t* mask,
+                        void* workspace, uint64_t workspace_bytes, void* stream);
+
 /* ej_fill_draws: the draws env_step would make itself, written out (device),
  * for global steps g0 .. g0+n-1: act int32[n][E][A], gather_u float[n][E][A],
  * tb uint32[n][E][A], policy_u float[n][E][A], gov_act int32[n][E][nb];

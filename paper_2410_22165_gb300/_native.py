@@ -75,6 +75,9 @@ _PROTOS = {
     "env_reset": (C.c_int, [C.POINTER(EjParams), _VP, _VP, C.c_uint64, _VP, _VP, _VP, _VP]),
     "env_step": (C.c_int, [C.POINTER(EjParams), _VP, C.c_int32, _VP, _VP, _VP, _VP,
                            _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "ej_step_host_workspace_bytes": (C.c_int, [C.POINTER(EjParams), C.c_int32, C.POINTER(C.c_uint64)]),
+    "env_step_host": (C.c_int, [C.POINTER(EjParams), _VP, C.c_int32, C.c_int32, _VP, _VP, _VP, _VP, _VP, _VP,
+                                _VP, _VP, _VP, _VP, _VP, C.c_uint64, _VP]),
     "ej_fill_draws": (C.c_int, [C.POINTER(EjParams), C.c_uint64, C.c_uint32, C.c_int32,
                                 _VP, _VP, _VP, _VP, _VP, _VP]),
     "ej_net_floats": (C.c_int, [C.POINTER(EjParams), C.c_int32, C.c_int32, C.POINTER(C.c_uint64)]),

@@ -32,6 +32,14 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _host_ptr(t):
+    if t.is_cuda:
+        raise ValueError("expected a host tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
 def _stream(stream=None):
     s = torch.cuda.current_stream() if stream is None else stream
     return C.c_void_p(s.cuda_stream)
@@ -100,73 +108,32 @@ class VecEnv:
         return out
 
     def step_host(self, n_steps: int, host_in: dict, host_out: dict, chunk: int = 100, sync: bool = True,
-                  copy_streams: int = 1):
-        """env_step over n_steps with inputs and outputs in (pinned) host memory.
-
-        host_in: act [n,E,A], gov_act [n,E,nb], gather_u [n,E,A], tb [n,E,A];
-        host_out: any of rew, grew, done, obs, gobs, mask (shapes of step's outputs).
-        The steps run in chunks through two sets of device buffers, so that
-        chunk k's outputs copy out while chunk k+1 runs and chunk k+2's inputs
-        copy in; each chunk's output copies are split over `copy_streams`
-        streams (several copy engines on the host link).  With sync, returns
-        when host_out is filled; otherwise the caller synchronises the device."""
-        dev = self.device
-        keys_in = ("act", "gov_act", "gather_u", "tb")
+                  stream=None):
+        """env_step_host: env_step over n_steps with inputs and outputs in
+        (pinned) host memory.  host_in: act [n,E,A], gov_act [n,E,nb],
+        gather_u [n,E,A], tb [n,E,A] (any may be missing: in-kernel draws as
+        in step); host_out: any of rew, grew, done, obs, gobs, mask (shapes of
+        step's outputs).  The library runs the steps in chunks, copying chunk
+        k+1's inputs in and chunk k-1's outputs out while chunk k runs; the
+        staging workspace is allocated here (caller-owned).  With sync,
+        returns when host_out is filled; otherwise the caller synchronises
+        the stream."""
         chunk = max(1, min(chunk, n_steps))
-        st = getattr(self, "_host_io", None)
-        ncs = max(1, int(copy_streams))
-        if (st is None or st["chunk"] != chunk or set(st["out"][0]) != set(host_out)
-                or len(st["outs"]) != ncs):
-            bufs_in = [{k: torch.empty((chunk,) + tuple(host_in[k].shape[1:]), dtype=host_in[k].dtype, device=dev)
-                        for k in keys_in} for _ in range(2)]
-            names = set(host_out)
-            bufs_out = [self.alloc_outputs(chunk, obs="obs" in names, gobs="gobs" in names, mask="mask" in names,
-                                           rew=bool({"rew", "grew"} & names), done="done" in names)
-                        for _ in range(2)]
-            st = dict(chunk=chunk, inp=bufs_in, out=bufs_out,
-                      streams=[torch.cuda.Stream(device=dev) for _ in range(2)],
-                      outs=[torch.cuda.Stream(device=dev) for _ in range(ncs)],
-                      ev=[[torch.cuda.Event() for _ in range(2)] for _ in range(2)],
-                      ev_out=[[torch.cuda.Event() for _ in range(2)] for _ in range(ncs)])
-            self._host_io = st
-        s_in, s_comp = st["streams"]
-        ev_in, ev_comp = st["ev"]
-        main = torch.cuda.current_stream(dev)
-        for s in (s_in, s_comp, *st["outs"]):
-            s.wait_stream(main)
-        n_chunks = (n_steps + chunk - 1) // chunk
-        for c in range(n_chunks):
-            b, lo = c % 2, c * chunk
-            n = min(chunk, n_steps - lo)
-            bi, bo = st["inp"][b], st["out"][b]
-            with torch.cuda.stream(s_in):
-                if c >= 2:
-                    s_in.wait_event(ev_comp[b])          # chunk c-2 has finished reading these inputs
-                for k in keys_in:
-                    bi[k][:n].copy_(host_in[k][lo:lo + n], non_blocking=True)
-                ev_in[b].record(s_in)
-            with torch.cuda.stream(s_comp):
-                s_comp.wait_event(ev_in[b])
-                if c >= 2:
-                    for ev_out in st["ev_out"]:
-                        s_comp.wait_event(ev_out[b])     # chunk c-2's outputs have left these buffers
-                out = {k: v[:n] for k, v in bo.items()}
-                self.step(n, act=bi["act"][:n], gov_act=bi["gov_act"][:n], gather_u=bi["gather_u"][:n],
-                          tb=bi["tb"][:n], out=out, stream=s_comp)
-                ev_comp[b].record(s_comp)
-            # output copies: each tensor's steps split evenly over the copy streams
-            for j, so in enumerate(st["outs"]):
-                with torch.cuda.stream(so):
-                    so.wait_event(ev_comp[b])
-                    a0, a1 = (n * j) // ncs, (n * (j + 1)) // ncs
-                    if a1 > a0:
-                        for k, v in host_out.items():
-                            v[lo + a0:lo + a1].copy_(bo[k][a0:a1], non_blocking=True)
-                    st["ev_out"][j][b].record(so)
-        for s in (s_in, s_comp, *st["outs"]):
-            main.wait_stream(s)
+        ws = getattr(self, "_host_ws", None)
+        if ws is None or ws[0] != chunk:
+            nbytes = C.c_uint64()
+            N.check(N.load().ej_step_host_workspace_bytes(C.byref(self.p), chunk, C.byref(nbytes)),
+                    "ej_step_host_workspace_bytes")
+            ws = (chunk, torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device))
+            self._host_ws = ws
+        hp = lambda d, k: None if d.get(k) is None else C.c_void_p(_host_ptr(d[k]))
+        N.check(N.load().env_step_host(
+            C.byref(self.p), _ptr(self.state), int(n_steps), int(chunk), hp(host_in, "act"),
+            hp(host_in, "gov_act"), hp(host_in, "gather_u"), hp(host_in, "tb"), hp(host_out, "rew"),
+            hp(host_out, "grew"), hp(host_out, "done"), hp(host_out, "obs"), hp(host_out, "gobs"),
+            hp(host_out, "mask"), _ptr(ws[1]), ws[1].numel(), _stream(stream)), "env_step_host")
         if sync:
-            torch.cuda.synchronize(dev)
+            (torch.cuda.current_stream(self.device) if stream is None else stream).synchronize()
         return host_out
 
     def fill_draws(self, seed: int, g0: int, n_steps: int, stream=None, policy=False):

@@ -212,3 +212,23 @@ def test_ppo_calls_reject_missing_rollout_arrays(lib, member):
         if reads[name]:
             assert call() == 1, name
             assert member in lib.ej_last_error().decode(), name
+
+
+def test_step_host_argument_checks(lib):
+    """env_step_host validates on the host: NULL or misaligned workspace, a
+    workspace below ej_step_host_workspace_bytes, chunk < 1, draws without
+    actions (no GPU is touched)."""
+    p = N.make_params(E=2, A=10)
+    fake = C.c_void_p(4096)
+    need = C.c_uint64()
+    assert lib.ej_step_host_workspace_bytes(C.byref(p), 8, C.byref(need)) == 0 and need.value > 0
+    assert lib.ej_step_host_workspace_bytes(C.byref(p), 0, C.byref(need)) == 1
+    args = lambda ws, nbytes, chunk=8, act=None, gu=None: (
+        C.byref(p), fake, 16, chunk, act, None, gu, gu, None, None, None, None, None, None, ws, nbytes, None)
+    assert lib.env_step_host(*args(None, 1 << 40)) == 1
+    assert lib.env_step_host(*args(C.c_void_p(4100), 1 << 40)) == 1
+    lib.ej_step_host_workspace_bytes(C.byref(p), 8, C.byref(need))
+    assert lib.env_step_host(*args(fake, need.value - 1)) == 1
+    assert "workspace" in lib.ej_last_error().decode()
+    assert lib.env_step_host(*args(fake, 1 << 40, chunk=0)) == 1
+    assert lib.env_step_host(*args(fake, 1 << 40, gu=fake)) == 1
