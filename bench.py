@@ -52,6 +52,16 @@ def _dist():
     return rank, world, local
 
 
+def _bf16_peaks():
+    """(burst, sustained) dense BF16 TFLOP/s of MEASURED_PEAKS.json, else the fallback figures."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), float(d.get("bf16_tflops_sustained", d["bf16_tflops"]))
+    except Exception:
+        return 1900.0, 1700.0
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -226,6 +236,8 @@ def run_gpu(args):
                        "bf16": run_ppo(args, dev, "bf16"), "fp32": run_ppo(args, dev, "fp32")}
         line["batched"] = run_batched(args, dev)
         line["section5"] = run_section5(args, dev)
+        if args.train_updates > 0 and world == 1:
+            line["training"] = run_training(args, dev)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if world > 1:
@@ -328,11 +340,90 @@ def run_ppo(args, dev, precision, E_p=2048, T_p=128, seed=3000):
     out = {"updates_per_s": 1e3 / ms, "ms_per_update": ms, "precision": precision,
            "rollout_ms": ro_ms, "train_agent_steps_per_s": world * E_p * A * T_p / ((ro_ms + ms) / 1e3),
            "useful_TFLOPs": flops / (ms / 1e3) / 1e12, "useful_TFLOP_per_update": flops / 1e12,
+           "peak_TFLOPs": (_bf16_peaks()[1] if precision == "bf16" else FP32_FMA_TFLOPS),
+           "peak_source": ("measured bf16_tflops_sustained" if precision == "bf16" else
+                           "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz"),
            "transitions_per_update": world * E_p * A * T_p, "epochs": ppo.pp.epochs, "minibatches": ppo.pp.minibatches,
            "ranks": world,
            "population_loss": {"policy": float(st[0, 0]), "value": float(st[0, 1]), "entropy": float(st[0, 2])}}
+    out["frac_of_peak"] = out["useful_TFLOPs"] / out["peak_TFLOPs"]
     del ppo, ro, pol, env
     torch.cuda.empty_cache()
+    return out
+
+
+FP32_FMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # derived: SMs x FP32 lanes x 2 FLOP x max SM clock
+
+
+def run_training(args, dev, E_t=2048, T_t=128, seed=3000):
+    """Learning behaviour of the two precisions (Section 4's simultaneous
+    training of the population and government networks): `--train-updates`
+    iterations of {T_t-step rollout, PPO update} of E_t x A agents, in BF16
+    and in FP32, from the same initial weights and environment seed.
+    Returns per iteration the mean population reward per agent-step and the
+    mean government reward per environment-step, and the mean episodic
+    returns (sum over an episode's steps; population: averaged over the
+    agents) of the episodes completed in the last third of the run, with the
+    standard error over environments.  The two runs sample different actions
+    as soon as their policies differ, so they agree statistically, not bit
+    for bit."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2410_22165_gb300 import PPO, Policy, Rollout, VecEnv
+
+    n_up = args.train_updates
+    out = {"workload": f"E={E_t} x A={A}, {n_up} iterations of a {T_t}-step rollout + PPO update "
+                       "(4 epochs x 8 minibatches), both networks, same seed for both precisions"}
+    for precision in ("bf16", "fp32"):
+        env = VecEnv(E_t, A, device=dev, T_ep=T_EP, T_tax=T_TAX)
+        pw = torch.from_numpy(synth.net_weights(seed, 0, env.D, 128, env.nA))
+        gw = torch.from_numpy(synth.net_weights(seed, 1, env.G, 128, env.p.nb * env.p.tax_levels))
+        pol = Policy(env, pw, gw, hidden=128, precision=precision)
+        ro = Rollout(env, pol, T_t)
+        ro.reset(seed=seed)
+        ppo = PPO(pol, T_t, precision=precision)
+        ep_pop = np.zeros(E_t)
+        ep_gov = np.zeros(E_t)
+        finished = []                    # (iteration, population return, government return) per episode
+        curve_pop, curve_gov = [], []
+        t0 = time.perf_counter()
+        for it in range(n_up):
+            if it:
+                ro.carry_over()
+            ro.run()
+            rew = ro.buf["rew"].double().mean(dim=2).cpu().numpy()      # [T, E]
+            grew = ro.buf["grew"].double().cpu().numpy()
+            done = ro.buf["done"].cpu().numpy()
+            curve_pop.append(float(rew.mean()))
+            curve_gov.append(float(grew.mean()))
+            for t in range(T_t):
+                ep_pop += rew[t]
+                ep_gov += grew[t]
+                for e in np.nonzero(done[t])[0]:
+                    finished.append((it, ep_pop[e], ep_gov[e]))
+                ep_pop[done[t] != 0] = 0.0
+                ep_gov[done[t] != 0] = 0.0
+            ppo.update(ro)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        late = [f for f in finished if f[0] >= (2 * n_up) // 3] or finished
+        rp = np.array([f[1] for f in late]) if late else np.zeros(1)
+        rg = np.array([f[2] for f in late]) if late else np.zeros(1)
+        out[precision] = {
+            "mean_population_reward_per_iteration": curve_pop, "mean_government_reward_per_iteration": curve_gov,
+            "episodes_completed": len(finished), "late_episodes": len(late),
+            "late_population_return": float(rp.mean()), "late_population_return_se": float(rp.std() / np.sqrt(len(rp))),
+            "late_government_return": float(rg.mean()), "late_government_return_se": float(rg.std() / np.sqrt(len(rg))),
+            "wall_s": wall}
+        del ppo, ro, pol, env
+        torch.cuda.empty_cache()
+    b, f = out["bf16"], out["fp32"]
+    out["population_return_difference"] = b["late_population_return"] - f["late_population_return"]
+    out["population_return_difference_se"] = float(np.hypot(b["late_population_return_se"], f["late_population_return_se"]))
+    out["government_return_difference"] = b["late_government_return"] - f["late_government_return"]
+    out["government_return_difference_se"] = float(np.hypot(b["late_government_return_se"], f["late_government_return_se"]))
     return out
 
 
@@ -601,6 +692,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-train", action="store_true", help="skip the rollout and PPO measurements")
+    ap.add_argument("--train-updates", type=int, default=20,
+                    help="iterations of the BF16 / FP32 training comparison (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     args = ap.parse_args()

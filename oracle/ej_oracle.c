@@ -153,6 +153,26 @@ static float bracket_tax32(float income, const float* rates, const double* th, i
     return tax;
 }
 
+/* Float mirror of the tax pool (READING R15; the paper fixes no order of
+ * summation): the agents in blocks of 32 in agent order, zero-padded; within
+ * a block a butterfly sum, which at offsets 16, 8, 4, 2, 1 replaces every
+ * entry t[j] by t[j] + t[j ^ offset] (each addition rounded once), the block
+ * sum being entry 0 at the end; the block sums added one after another in
+ * agent order, starting from 0. */
+static float pool_sum32(const float* tax, int A) {
+    float pool = 0.0f;
+    for (int b0 = 0; b0 < A; b0 += 32) {
+        float t[32], u[32];
+        for (int j = 0; j < 32; ++j) t[j] = (b0 + j < A) ? tax[b0 + j] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) {
+            for (int j = 0; j < 32; ++j) u[j] = t[j] + t[j ^ o];
+            memcpy(t, u, sizeof t);
+        }
+        pool = pool + t[0];
+    }
+    return pool;
+}
+
 /* --------------------------------------------------------- life cycle */
 
 orc_env* orc_env_new(const orc_params* p, int A) {
@@ -575,16 +595,15 @@ void orc_env_step(orc_env* env, const int32_t* act, const int32_t* gov_act,
         if (p->gov_enabled) {
             float* tax32 = (float*)malloc(sizeof(float) * (A > 0 ? A : 1));
             double* tax64 = (double*)malloc(sizeof(double) * (A > 0 ? A : 1));
-            float pool32 = 0.0f;
             double pool64 = 0.0;
             for (int i = 0; i < A; ++i) {
                 tax32[i] = bracket_tax32(env->income32[i], env->rates32, p->thresholds, nb);
                 if (tax32[i] > env->coin32[i]) tax32[i] = env->coin32[i];
-                pool32 = pool32 + tax32[i];
                 tax64[i] = orc_bracket_tax(env->income64[i], env->rates64, p->thresholds, nb);
                 if (tax64[i] > env->coin64[i]) tax64[i] = env->coin64[i];
                 pool64 += tax64[i];
             }
+            float pool32 = pool_sum32(tax32, A);
             float share32 = pool32 / (float)A;
             double share64 = pool64 / (double)A;
             for (int i = 0; i < A; ++i) {

@@ -118,7 +118,7 @@ __device__ __forceinline__ Sm carve(unsigned char* base, const KParams& p) {
     m.d_inv = (int*)a;                  a += align16(4u * p.R * NT);
     m.d_inve = (int*)a;                 a += align16(4u * p.R * NT);
     m.tax = (float*)a;
-    m.stat = (float*)(base + s.alias);
+    m.stat = (float*)(base + s.stat);
     m.obs = (float*)(base + s.alias);
     return m;
 }
@@ -399,8 +399,10 @@ __device__ void block_bitonic(float* a, int M) {
 }
 
 // Population statistics (Sec. 3; App. A: the government sees mean, std and
-// median) from s.stat, which fill_stats wrote before a barrier.  Ends with
-// a barrier; results in s.gstat and s.misc.
+// median) from s.stat, which fill_stats wrote before a barrier.  Results in
+// s.gstat and s.misc, for readers after the next barrier (CTAs of up to 128
+// threads sort one metric per warp with no barrier, so the sorting warps can
+// run into the next step's first phase while the others start it).
 template <int NT>
 __device__ void population_stats(const KParams& p, const Sm& s, int i, int Ae) {
     constexpr int NW = NT / 32;
@@ -440,7 +442,6 @@ __device__ void population_stats(const KParams& p, const Sm& s, int i, int Ae) {
             }
         }
     }
-    __syncthreads();
 }
 
 __device__ __forceinline__ float social_welfare(const KParams& p, const Sm& s) {
@@ -478,27 +479,32 @@ __device__ __forceinline__ void time_features(const KParams& p, const Sm& s, int
     s.misc[MISC_TFRAC] = __fdiv_rn((float)t, (float)p.T_ep);
 }
 
-// Observation, government observation and action mask of the current state
-// (Sec. 3; App. A), written for output row `row`.  Needs s.mkt, s.gstat,
-// s.rates and the time features in s.misc; each warp stages the observations
-// of its own 32 agents and writes them as one contiguous block.  Ends with a
-// barrier.
-template <int NT, int RC, int PC>
-__device__ void observe(const KParams& p, const Sm& s, const Agent& g, const DevIO& io, size_t row, int i,
-                        int Ae) {
-    const int R = nR<RC>(p), P = nP<PC>(p), D = p.D, W = nW<RC, PC>(p);
-    const int lane = i & 31, warp = i >> 5;
-    const float period_left = s.misc[MISC_PLEFT];
-    const float time_frac = s.misc[MISC_TFRAC];
+// Government observation of output row `row` (thread i writes entry i):
+// statistics, rates, time features.
+__device__ __forceinline__ void write_gobs(const KParams& p, const Sm& s, const DevIO& io, size_t row, int i) {
     if (io.gobs && i < p.G) {
         const int nst = 3 * p.M;
         float v;
         if (i < nst) v = s.gstat[i];
         else if (i < nst + p.nb) v = s.rates[i - nst];
-        else if (i == nst + p.nb) v = period_left;
-        else v = time_frac;
+        else if (i == nst + p.nb) v = s.misc[MISC_PLEFT];
+        else v = s.misc[MISC_TFRAC];
         io.gobs[row * p.G + i] = v;
     }
+}
+
+// Population observations and action masks of the current state for output
+// row `row` (each warp stages and writes its own agents' rows; no barrier at
+// the end: every warp has finished reading its staging slots when it leaves,
+// except in CTAs of 256 and more threads, whose two staging rounds end with
+// a barrier each).
+template <int NT, int RC, int PC>
+__device__ void observe_rows(const KParams& p, const Sm& s, const Agent& g, const DevIO& io, size_t row, int i,
+                             int Ae) {
+    const int R = nR<RC>(p), P = nP<PC>(p), D = p.D, W = nW<RC, PC>(p);
+    const int lane = i & 31, warp = i >> 5;
+    const float period_left = s.misc[MISC_PLEFT];
+    const float time_frac = s.misc[MISC_TFRAC];
     if (io.mask && i < p.A) {
         const bool live = i < Ae;
         const bool room = g.nord < p.max_orders;
@@ -595,8 +601,19 @@ __device__ void observe(const KParams& p, const Sm& s, const Agent& g, const Dev
             }
         }
     }
-    __syncthreads();
+    if (ROUNDS > 1) __syncthreads();
     }
+}
+
+// Observation, government observation and action mask of the current state
+// (Sec. 3; App. A), written for output row `row`.  Needs s.mkt, s.gstat,
+// s.rates and the time features in s.misc.  Ends with a barrier.
+template <int NT, int RC, int PC>
+__device__ void observe(const KParams& p, const Sm& s, const Agent& g, const DevIO& io, size_t row, int i,
+                        int Ae) {
+    write_gobs(p, s, io, row, i);
+    observe_rows<NT, RC, PC>(p, s, g, io, row, i, Ae);
+    __syncthreads();
 }
 
 // CTAs per SM each instantiation must fit (registers: 72 per thread at 7
@@ -642,6 +659,7 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
         __syncthreads();
         market_stats<RC, PC>(p, s, s.lvl_old, i, Ae);
         population_stats<NT>(p, s, i, Ae);
+        __syncthreads();
         if (i == 0) s.misc[MISC_UGPREV] = social_welfare(p, s);
         observe<NT, RC, PC>(p, s, g, io, (size_t)e, i, Ae);
     } else {
@@ -674,11 +692,20 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
     }
     // per-step scratch starts at zero (later steps clear it after use)
     for (int l = i; l < L; l += NT) s.lvl_new[l] = 0;
-    s.d_coin[i] = 0; s.d_esc[i] = 0; s.d_inc[i] = 0; s.d_nord[i] = 0;
-#pragma unroll
-    for (int r = 0; r < R; ++r) { s.d_inv[r * NT + i] = 0; s.d_inve[r * NT + i] = 0; }
     __syncthreads();
 
+    // Per step, six barriers: (1) after the own action, (2) after the new
+    // orders' keys, (3) after their ranking, (4) after matching and expiry,
+    // (5) after the survivors' compaction and the market deltas, (6) after
+    // the rewards, statistics inputs and observations.  The 20-level prefix
+    // sums are computed by every warp in registers (no barrier of their own),
+    // and the statistics sorts of step k run after barrier (6) without a
+    // barrier behind them: their results (the government reward and
+    // observation of row k) are written in step k+1's second phase, or after
+    // the loop for the last step.
+    const bool reg_scan = L <= 32;
+    bool pending = false;                     // government outputs of the previous row not yet written
+    size_t prev_row = 0;
     for (int step = 0; step < n_steps; ++step) {
         const size_t row = (size_t)step * p.E + e;
         const bool live = i < Ae;
@@ -699,18 +726,6 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
                 gu = io.gather_u[k];
                 tbk = io.tb[k];
             }
-        }
-        // 0. period start: the government's rate levels take effect
-        if (p.gov_enabled && t % p.T_tax == 0 && i < p.nb) {
-            int lev;
-            if (mode & MODE_GOV_DRAW) {
-                const uint4 x = philox4x32_10(make_uint4(0u, (uint32_t)e, gs, 1u), k0, k1);
-                lev = below(i == 0 ? x.x : i == 1 ? x.y : i == 2 ? x.z : x.w, p.tax_levels);
-            } else {
-                lev = io.gov_act[row * p.nb + i];
-            }
-            lev = lev < 0 ? 0 : (lev > p.tax_levels - 1 ? p.tax_levels - 1 : lev);
-            s.rates[i] = __fdiv_rn((float)lev, (float)(p.tax_levels - 1));
         }
         // this agent's market deltas start at zero (only this thread touched them before the barrier)
         s.d_coin[i] = 0; s.d_esc[i] = 0; s.d_inc[i] = 0; s.d_nord[i] = 0;
@@ -762,10 +777,54 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
                 my_slot = atomicAdd(&s.lvl_new[my_l], 1);
             }
         }
-        __syncthreads();
+        __syncthreads();                                                        // (1)
+
+        // the previous row's government reward and observation (its statistics
+        // were sorted after the previous step's last barrier); the rate
+        // entries are written by the threads that own the rates, before 0.
+        if (pending) {
+            if (i == 0) {
+                const float ug = social_welfare(p, s);
+                if (io.grew) io.grew[prev_row] = __fsub_rn(ug, s.misc[MISC_UGPREV]);
+                s.misc[MISC_UGPREV] = ug;
+            }
+            if (io.gobs && i < p.G && (i < 3 * p.M || i >= 3 * p.M + p.nb)) write_gobs(p, s, io, prev_row, i);
+        }
+        if (pending && io.gobs && i < p.nb) io.gobs[prev_row * p.G + 3 * p.M + i] = s.rates[i];
+        // 0. period start: the government's rate levels take effect (read by
+        //    the tax and the observations after later barriers)
+        if (p.gov_enabled && t % p.T_tax == 0 && i < p.nb) {
+            int lev;
+            if (mode & MODE_GOV_DRAW) {
+                const uint4 x = philox4x32_10(make_uint4(0u, (uint32_t)e, gs, 1u), k0, k1);
+                lev = below(i == 0 ? x.x : i == 1 ? x.y : i == 2 ? x.z : x.w, p.tax_levels);
+            } else {
+                lev = io.gov_act[row * p.nb + i];
+            }
+            lev = lev < 0 ? 0 : (lev > p.tax_levels - 1 ? p.tax_levels - 1 : lev);
+            s.rates[i] = __fdiv_rn((float)lev, (float)(p.tax_levels - 1));
+        }
 
         // where this step's orders go; trades per resource K = max_q min(#bids >= q, #asks <= q)
-        if (warp == 0) warp_excl_scan(s.lvl_new, s.lvl_nstart, L, lane);
+        if (reg_scan) {
+            // every warp scans the 20-odd level counts in registers
+            const int v = lane < L ? s.lvl_new[lane] : 0;
+            int x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, x, o);
+                if (lane >= o) x += y;
+            }
+            const int excl = x - v;
+            if (warp == 0) {
+                if (lane < L) s.lvl_nstart[lane] = excl;
+                if (lane == 31) s.lvl_nstart[L] = x;
+            }
+            const int start = __shfl_sync(FULL, excl, my_l < 0 ? 0 : my_l);
+            if (my_l >= 0) s.newkey[start + my_slot] = ((unsigned long long)tbk << 32) | (uint32_t)i;
+        } else if (warp == 0) {
+            warp_excl_scan(s.lvl_new, s.lvl_nstart, L, lane);
+        }
         for (int r = warp; r < R; r += NW) {
             const int q = lane;
             const int lb = (r * 2) * P + q, la = (r * 2 + 1) * P + q;
@@ -790,9 +849,11 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
             }
             if (lane == 0) s.kmatch[r] = m;
         }
-        __syncthreads();
-        if (my_l >= 0) s.newkey[s.lvl_nstart[my_l] + my_slot] = ((unsigned long long)tbk << 32) | (uint32_t)i;
-        __syncthreads();
+        if (!reg_scan) {
+            __syncthreads();
+            if (my_l >= 0) s.newkey[s.lvl_nstart[my_l] + my_slot] = ((unsigned long long)tbk << 32) | (uint32_t)i;
+        }
+        __syncthreads();                                                        // (2)
         // this step's orders in priority order within their level (random key, then agent)
         if (my_l >= 0) {
             const unsigned long long mk = ((unsigned long long)tbk << 32) | (uint32_t)i;
@@ -801,13 +862,15 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
             for (int j = 0; j < cnt; ++j) rank += s.newkey[st0 + j] < mk;
             s.newsorted[st0 + rank] = ((uint32_t)t << 16) | (uint32_t)i;
         }
-        __syncthreads();
+        __syncthreads();                                                        // (3)
 
-        // 2. matching (Sec. 3 "Trading"; App. A): pair k = k-th best bid with k-th best ask
+        // 2. matching (Sec. 3 "Trading"; App. A): pair k = k-th best bid with k-th
+        //    best ask; resource r's trades start on warp r (mod the CTA)
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int K = s.kmatch[r];
-            for (int k = i; k < K; k += NT) {
+            const int base = (r * 32) % NT;
+            for (int k = (i - base + NT) % NT; k < K; k += NT) {
                 int qb = P - 1;
                 while (k >= s.bid_before[r * P + qb] + s.lvl_n[(r * 2) * P + qb]) --qb;
                 int qa = 0;
@@ -853,12 +916,30 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
             s.lvl_rm[l] = idx;                  // removed by matching or expiry
             s.lvl_exp[l] = n - idx;             // survivors
         }
-        __syncthreads();
-        if (warp == 0) warp_excl_scan(s.lvl_exp, s.lvl_cstart, L, lane);
-        __syncthreads();
-        // survivors into the other book buffer, one warp per level
+        __syncthreads();                                                        // (4)
+        // survivors into the other book buffer, one warp per level, at their
+        // compacted start (every warp scans the survivor counts in registers)
+        int cx = 0;
+        if (reg_scan) {
+            const int v = lane < L ? s.lvl_exp[lane] : 0;
+            int x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, x, o);
+                if (lane >= o) x += y;
+            }
+            cx = x - v;
+            if (warp == 0) {
+                if (lane < L) s.lvl_cstart[lane] = cx;
+                if (lane == 31) s.lvl_cstart[L] = x;
+            }
+        } else {
+            if (warp == 0) warp_excl_scan(s.lvl_exp, s.lvl_cstart, L, lane);
+            __syncthreads();
+        }
         for (int l = warp; l < L; l += NW) {
-            const int c = s.lvl_exp[l], src0 = s.lvl_rm[l], dst0 = s.lvl_cstart[l];
+            const int c = s.lvl_exp[l], src0 = s.lvl_rm[l];
+            const int dst0 = reg_scan ? __shfl_sync(FULL, cx, l) : s.lvl_cstart[l];
             const int old = s.lvl_old[l], ostart = s.lvl_start[l], nstart = s.lvl_nstart[l];
             for (int j = lane; j < c; j += 32) {
                 const int k = src0 + j;
@@ -878,7 +959,7 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
             }
         }
         if (i == 0) time_features(p, s, (t + 1) == p.T_ep ? 0 : t + 1);
-        __syncthreads();
+        __syncthreads();                                                        // (5)
         { uint32_t* tmp = s.book; s.book = s.book_alt; s.book_alt = tmp; }
         for (int l = owner; l < L; l += NT) {
             s.lvl_old[l] = s.lvl_exp[l];
@@ -895,20 +976,21 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
                     tax = bracket_tax(p, s.rates, g.income);
                     if (tax > g.coin) tax = g.coin;
                 }
-                s.tax[i] = tax;
+                // pool: each block of 32 agents summed as a butterfly (offsets
+                // 16, 8, 4, 2, 1), the blocks then added in agent order
+                float v = tax;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(FULL, v, o));
+                if (lane == 0) s.red[warp] = v;
                 __syncthreads();
-                if (i == 0) {
-                    float pool = 0.0f;
-                    for (int j = 0; j < Ae; ++j) pool = __fadd_rn(pool, s.tax[j]);
-                    s.misc[MISC_SHARE] = __fdiv_rn(pool, (float)Ae);
-                }
-                __syncthreads();
-                if (live) g.coin = __fadd_rn(__fsub_rn(g.coin, tax), s.misc[MISC_SHARE]);
+                float pool = 0.0f;
+                for (int w = 0; w < NW; ++w) pool = __fadd_rn(pool, s.red[w]);
+                if (live) g.coin = __fadd_rn(__fsub_rn(g.coin, tax), __fdiv_rn(pool, (float)Ae));
             }
             g.income = 0.0f;
         }
 
-        // 5. rewards: Eq. 2 on Eq. 1; the government's on Eq. 3
+        // 5. rewards: Eq. 2 on Eq. 1 (the government's follows from the statistics)
         if (live) {
             const float c = __fadd_rn(g.coin, __fmul_rn(p.tick, (float)g.esc));
             const float u = utility(p, c, labor_of(p, g.ng, g.nc, g.nt));
@@ -918,20 +1000,24 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
             io.rew[row * p.A + i] = 0.0f;
         }
         fill_stats<NT>(p, s, g, i, Ae);
-        __syncthreads();
-        population_stats<NT>(p, s, i, Ae);
-        if (i == 0) {
-            const float ug = social_welfare(p, s);
-            if (io.grew) io.grew[row] = __fsub_rn(ug, s.misc[MISC_UGPREV]);
-            s.misc[MISC_UGPREV] = ug;
-        }
 
         // 6. end of episode: functional reset with the next episode's skills
         t += 1;
         gs += 1;
         const bool ended = t == p.T_ep;
         if (io.done && i == 0) io.done[row] = ended ? 1 : 0;
+        // 7. observation of the new state (at an episode end: of the next episode's first state, below)
+        if (!ended) observe_rows<NT, RC, PC>(p, s, g, io, row, i, Ae);
+        __syncthreads();                                                        // (6)
+        population_stats<NT>(p, s, i, Ae);
+        pending = true;
+        prev_row = row;
         if (ended) {
+            __syncthreads();
+            if (i == 0) {
+                const float ug = social_welfare(p, s);
+                if (io.grew) io.grew[row] = __fsub_rn(ug, s.misc[MISC_UGPREV]);
+            }
             t = 0;
             ep += 1;
             __syncthreads();
@@ -943,12 +1029,26 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
             __syncthreads();
             market_stats<RC, PC>(p, s, s.lvl_old, i, Ae);
             population_stats<NT>(p, s, i, Ae);
-            if (i == 0) s.misc[MISC_UGPREV] = social_welfare(p, s);
             __syncthreads();
+            if (i == 0) s.misc[MISC_UGPREV] = social_welfare(p, s);
+            observe_rows<NT, RC, PC>(p, s, g, io, row, i, Ae);
+            __syncthreads();
+            // the reset state's statistics stand for this row's government observation;
+            // its reward is written
+            if (io.gobs && i < p.G) write_gobs(p, s, io, row, i);
+            pending = false;
         }
-        // 7. observation of the new state
-        observe<NT, RC, PC>(p, s, g, io, row, i, Ae);
     }
+    if (pending) {
+        __syncthreads();
+        if (i == 0) {
+            const float ug = social_welfare(p, s);
+            if (io.grew) io.grew[prev_row] = __fsub_rn(ug, s.misc[MISC_UGPREV]);
+            s.misc[MISC_UGPREV] = ug;
+        }
+        write_gobs(p, s, io, prev_row, i);
+    }
+    __syncthreads();
 
     // ---- store the state
     if (i < p.A_s) {

@@ -108,7 +108,7 @@ inline int env_threads(int A) {
 
 // Shared-memory carve-up of one environment CTA (host and device agree).
 struct SmemLayout {
-    uint32_t inv, inve, sg, book, lvl, kb, fl, alias, total;
+    uint32_t inv, inve, sg, book, lvl, kb, fl, stat, alias, total;
 };
 
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -124,15 +124,15 @@ __host__ __device__ inline SmemLayout smem_layout(int NT, int R, int P, int L, i
     s.kb = b;    b = align16(b + 4u * (R + 2u * R * P));
     const uint32_t nw = NT / 32;
     s.fl = b;    b = align16(b + 4u * (EJ_MAX_NB + 4u * R + nw * (M + 1u) + (M + 1u) + 3u * M + 16u + EJ_MAX_ORDERS + 1u));
+    s.stat = b;  b = align16(b + 4u * M * NT);   // government statistics being sorted (own region: the
+                                                 // sorts overlap the next step's first phase)
     s.alias = b;
     // phase A: new-order keys, sorted new orders, per-agent integer deltas, tax
     uint32_t a = align16(8u * NT) + align16(4u * NT) + 4u * align16(4u * NT) +
                  2u * align16(4u * R * NT) + align16(4u * NT);
-    uint32_t bsz = 4u * M * NT;              // phase B: statistics being sorted
     const uint32_t stage_nt = NT >= 256 ? NT / 2 : NT;
     uint32_t c = 4u * stage_nt * D;          // phase C: observation staging (half of the warps at a time from 256 threads)
-    uint32_t m = a > bsz ? a : bsz;
-    m = m > c ? m : c;
+    uint32_t m = a > c ? a : c;
     b = align16(b + m);
     s.total = b;
     return s;

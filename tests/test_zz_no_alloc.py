@@ -46,16 +46,22 @@ def _setup(E, A, T, seed, **kw):
 
 
 def _static_grad(env, pol, ro, ppo, net, ctr, mb):
+    """One call through the C ABI; returns the gradient, the statistics and
+    the device memory torch holds after the call minus before it (the
+    outputs are allocated before the measurement)."""
     from paper_2410_22165_gb300 import _native as N
     w = pol.pop_w if net == 0 else pol.gov_w
     grad = torch.full_like(w, float("nan"))
     stats = torch.empty(8, dtype=torch.float64, device=w.device)
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
     st = N.load().ppo_minibatch_grad_static(
         C.byref(env.p), C.byref(ppo.pp), ppo.T, H, N.FP32, net, C.c_void_p(w.data_ptr()), C.byref(ro._c),
         ctr, mb, C.c_void_p(grad.data_ptr()), C.c_void_p(stats.data_ptr()),
         C.c_void_p(torch.cuda.current_stream().cuda_stream))
     N.check(st, "ppo_minibatch_grad_static")
-    return grad, stats
+    torch.cuda.synchronize()
+    return grad, stats, torch.cuda.memory_allocated() - before
 
 
 @pytest.mark.parametrize("net", [0, 1])
@@ -66,11 +72,8 @@ def test_static_scratch_gradient_equals_workspace_gradient(net):
     in_dim = env.D if net == 0 else env.G
     O = env.nA if net == 0 else env.p.nb * env.p.tax_levels
     for ctr, mb in ((3, 1), (4, 2)):                     # two calls in a row
-        torch.cuda.synchronize()
-        before = torch.cuda.memory_allocated()
-        g_static, s_static = _static_grad(env, pol, ro, ppo, net, ctr, mb)
-        torch.cuda.synchronize()
-        assert torch.cuda.memory_allocated() == before    # the call itself allocates nothing
+        g_static, s_static, grown = _static_grad(env, pol, ro, ppo, net, ctr, mb)
+        assert grown == 0                                  # the call itself allocates nothing
         g_ws, s_ws = ppo.minibatch_grad(ro, net, ctr, mb)
         torch.cuda.synchronize()
         a = synth.unpack(g_static.cpu().numpy(), in_dim, H, O)
