@@ -392,7 +392,12 @@ typedef struct {
 ej_status ej_ppo_params_default(EjPpoParams* pp);
 
 /* Bytes of the workspace the PPO calls need (caller-allocated, 256-byte
- * aligned, contents need no initialisation).  hidden in {32, 64, 96, 128}. */
+ * aligned, contents need no initialisation).  hidden: a multiple of 32 in
+ * [32, 256] (Section 5's networks have 256 units).  The BF16 gradient takes
+ * hidden 128; the FP32 gradient any of these widths whose 64-row tile (inputs,
+ * three hidden-width buffers, logits) fits 227 KB of shared memory, e.g. hidden
+ * 256 with Section 5's 4-resource market (39 inputs, 30 logits); larger shapes
+ * return EJ_ERR_UNSUPPORTED from the gradient calls before anything runs. */
 ej_status ej_ppo_workspace_bytes(const EjParams* p, const EjPpoParams* pp, int32_t T,
                                  int32_t hidden, uint64_t* bytes);
 

@@ -157,9 +157,11 @@ __device__ __forceinline__ float labor_of(const KParams& p, int ng, int nc, int 
                      __fmul_rn(p.lt, (float)nt));
 }
 
-// Eq. 1, in float.
+// Eq. 1, in float.  C^(1-eta) by the hardware exp2 / log2 (__powf: relative
+// error about 2e-6 for coin up to 1e5, inside the 1e-5 utility tolerance;
+// no integer state depends on it).  4 % of the step at E = 1024 x A = 100.
 __device__ __forceinline__ float utility(const KParams& p, float coin, float labor) {
-    return __fsub_rn(__fdiv_rn(__fsub_rn(powf(coin, p.ome), 1.0f), p.ome), labor);
+    return __fsub_rn(__fdiv_rn(__fsub_rn(__powf(coin, p.ome), 1.0f), p.ome), labor);
 }
 
 // Section 3 "Setting tax rates": marginal tax bracket by bracket, each

@@ -106,7 +106,8 @@ extern "C" ej_status ppo_minibatch_grad_static(const EjParams* p, const EjPpoPar
     const uint64_t o_wt2 = o;   o = up256(o + 4ull * H * H);
     const uint64_t o_wv2 = o;   o = up256(o + 4ull * H * H);
     const uint64_t o_rows = o;  o = up256(o + 4ull * row_floats * count_max);
-    const uint64_t o_part = o;  o = up256(o + 4ull * 6 * STATIC_CHUNKS * WG_STRIDE);
+    const size_t stride = wg_stride(in, H, O);
+    const uint64_t o_part = o;  o = up256(o + 4ull * 6 * STATIC_CHUNKS * stride);
     if (o > SCRATCH_BYTES)
         return fail(EJ_ERR_UNSUPPORTED,
                     "ppo_minibatch_grad_static: this minibatch needs %llu bytes of scratch but the static "
@@ -171,7 +172,7 @@ extern "C" ej_status ppo_minibatch_grad_static(const EjParams* p, const EjPpoPar
     }
     if (cudaMemsetAsync(grad, 0, sizeof(float) * off.total, s) != cudaSuccess)
         return fail(EJ_ERR_CUDA, "memset of the gradient failed");
-    st = launch_minibatch_grad(fa, jobs, 6, (float*)(sc + o_part), STATIC_CHUNKS, weights + off.W2,
+    st = launch_minibatch_grad(fa, jobs, 6, (float*)(sc + o_part), stride, STATIC_CHUNKS, weights + off.W2,
                                weights + off.W3, weights + off.V2, grad, s);
     if (st != EJ_OK) return st;
     st = launch_minibatch_loss(fa.stats, fa.mb.count, nullptr, pp->vf_coef, pp->ent_coef, s);

@@ -281,18 +281,23 @@ __global__ void __launch_bounds__(NTH, 1) fwd_bwd_kernel(FbArgs a) {
 
 // --------------------------------------- split-K weight gradients
 // Job q: G[m][n] = sum over minibatch rows of A[row][i] B[row][j], and the
-// bias gradient sum of B[row][j]; rows split in chunks over blockIdx.x.
+// bias gradient sum of B[row][j]; rows split in chunks over blockIdx.x, the
+// output in 128 x 128 tiles over blockIdx.z (hidden widths above 128).
 constexpr int WG_ROWS = 32;
 
-__global__ void __launch_bounds__(NTH) wgrad_kernel(WgJobs jobs, int rows, int chunks, float* __restrict__ partial) {
+__global__ void __launch_bounds__(NTH) wgrad_kernel(WgJobs jobs, int rows, int chunks, size_t stride,
+                                                    float* __restrict__ partial) {
     const WgJob jb = jobs.job[blockIdx.y];
-    __shared__ __align__(16) float As[WG_ROWS][128 + 4];
-    __shared__ __align__(16) float Bs[WG_ROWS][128 + 4];
+    const int tiles_n = (jb.n + WG_TILE - 1) / WG_TILE, tiles_m = (jb.m + WG_TILE - 1) / WG_TILE;
+    if ((int)blockIdx.z >= tiles_m * tiles_n) return;
+    const int m0 = ((int)blockIdx.z / tiles_n) * WG_TILE, n0 = ((int)blockIdx.z % tiles_n) * WG_TILE;
+    __shared__ __align__(16) float As[WG_ROWS][WG_TILE + 4];
+    __shared__ __align__(16) float Bs[WG_ROWS][WG_TILE + 4];
     const int c = blockIdx.x;
     const int r0 = (int)(((long long)rows * c) / chunks), r1 = (int)(((long long)rows * (c + 1)) / chunks);
     const int ib = threadIdx.x / 16, jbk = threadIdx.x % 16;    // 16 x 16 blocks of 8 x 8
     const int i0 = ib * 8, j0 = jbk * 8;
-    const bool active = i0 < jb.m && j0 < jb.n;
+    const bool active = m0 + i0 < jb.m && n0 + j0 < jb.n;
     float acc[8][8];
 #pragma unroll
     for (int a = 0; a < 8; ++a)
@@ -301,10 +306,10 @@ __global__ void __launch_bounds__(NTH) wgrad_kernel(WgJobs jobs, int rows, int c
     float bsum = 0.0f;
     for (int base = r0; base < r1; base += WG_ROWS) {
         const int nr = min(WG_ROWS, r1 - base);
-        for (int k = threadIdx.x; k < WG_ROWS * 128; k += NTH) {
-            const int r = k / 128, col = k % 128;
-            As[r][col] = (r < nr && col < jb.m) ? jb.A[(size_t)(base + r) * jb.lda + col] : 0.0f;
-            Bs[r][col] = (r < nr && col < jb.n) ? jb.B[(size_t)(base + r) * jb.ldb + col] : 0.0f;
+        for (int k = threadIdx.x; k < WG_ROWS * WG_TILE; k += NTH) {
+            const int r = k / WG_TILE, col = k % WG_TILE;
+            As[r][col] = (r < nr && m0 + col < jb.m) ? jb.A[(size_t)(base + r) * jb.lda + m0 + col] : 0.0f;
+            Bs[r][col] = (r < nr && n0 + col < jb.n) ? jb.B[(size_t)(base + r) * jb.ldb + n0 + col] : 0.0f;
         }
         __syncthreads();
         if (active) {
@@ -318,29 +323,30 @@ __global__ void __launch_bounds__(NTH) wgrad_kernel(WgJobs jobs, int rows, int c
                     for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
             }
         }
-        if (threadIdx.x < jb.n)
+        if (m0 == 0 && threadIdx.x < WG_TILE && n0 + (int)threadIdx.x < jb.n)
             for (int r = 0; r < nr; ++r) bsum += Bs[r][threadIdx.x];
         __syncthreads();
     }
-    float* out = partial + ((size_t)blockIdx.y * chunks + c) * WG_STRIDE;
+    float* out = partial + ((size_t)blockIdx.y * chunks + c) * stride;
     if (active) {
 #pragma unroll
         for (int x = 0; x < 8; ++x)
 #pragma unroll
             for (int y = 0; y < 8; ++y)
-                if (i0 + x < jb.m && j0 + y < jb.n) out[(i0 + x) * jb.n + (j0 + y)] = acc[x][y];
+                if (m0 + i0 + x < jb.m && n0 + j0 + y < jb.n) out[(size_t)(m0 + i0 + x) * jb.n + (n0 + j0 + y)] = acc[x][y];
     }
-    if (threadIdx.x < jb.n) out[jb.m * jb.n + threadIdx.x] = bsum;
+    if (m0 == 0 && threadIdx.x < WG_TILE && n0 + (int)threadIdx.x < jb.n)
+        out[(size_t)jb.m * jb.n + n0 + threadIdx.x] = bsum;
 }
 
-__global__ void wgrad_reduce_kernel(WgJobs jobs, int n_jobs, int chunks, const float* __restrict__ partial,
-                                    float* __restrict__ grad) {
+__global__ void wgrad_reduce_kernel(WgJobs jobs, int n_jobs, int chunks, size_t stride,
+                                    const float* __restrict__ partial, float* __restrict__ grad) {
     for (int q = 0; q < n_jobs; ++q) {
         const WgJob jb = jobs.job[q];
         const int total = jb.m * jb.n + jb.n;
         for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
             float s = 0.0f;
-            for (int c = 0; c < chunks; ++c) s += partial[((size_t)q * chunks + c) * WG_STRIDE + k];
+            for (int c = 0; c < chunks; ++c) s += partial[((size_t)q * chunks + c) * stride + k];
             if (k < jb.m * jb.n) grad[jb.w_off + k] = s;
             else if (jb.b_off >= 0) grad[jb.b_off + (k - jb.m * jb.n)] = s;
         }
@@ -394,8 +400,11 @@ ej_status launch_mb_rows_stats(const MbDesc& mb, const float* adv, uint32_t* row
 }
 
 ej_status launch_minibatch_grad(const FbArgs& fa, const WgJobs& jobs, int n_jobs, float* partial,
-                                int chunks, const float* w2, const float* w3, const float* v2,
+                                size_t stride, int chunks, const float* w2, const float* w3, const float* v2,
                                 float* grad, cudaStream_t s) {
+    if (fwd_bwd_smem(fa.in_pad, fa.H, fa.O) > 227u * 1024u)
+        return fail(EJ_ERR_UNSUPPORTED, "float32 PPO: %d inputs, hidden %d and %d logits need %zu bytes of shared memory "
+                    "per 64-row tile (at most %u)", fa.in_dim, fa.H, fa.O, fwd_bwd_smem(fa.in_pad, fa.H, fa.O), 227u * 1024u);
     // transposed copies of the weights the backward pass multiplies by
     transpose_kernel<<<64, 256, 0, s>>>(w3, fa.H, fa.O, fa.w3t);
     transpose_kernel<<<64, 256, 0, s>>>(w2, fa.H, fa.H, fa.w2t);
@@ -411,8 +420,13 @@ ej_status launch_minibatch_grad(const FbArgs& fa, const WgJobs& jobs, int n_jobs
     const int n_tiles = (fa.mb.count + TILE - 1) / TILE;
     int g2 = n_tiles < device_sms() ? n_tiles : device_sms();
     fwd_bwd_kernel<<<g2, NTH, smem, s>>>(fa);
-    wgrad_kernel<<<dim3(chunks, n_jobs), NTH, 0, s>>>(jobs, fa.mb.count, chunks, partial);
-    wgrad_reduce_kernel<<<device_sms(), 256, 0, s>>>(jobs, n_jobs, chunks, partial, grad);
+    int zt = 1;
+    for (int q = 0; q < n_jobs; ++q) {
+        const int t = ((jobs.job[q].m + WG_TILE - 1) / WG_TILE) * ((jobs.job[q].n + WG_TILE - 1) / WG_TILE);
+        zt = t > zt ? t : zt;
+    }
+    wgrad_kernel<<<dim3(chunks, n_jobs, zt), NTH, 0, s>>>(jobs, fa.mb.count, chunks, stride, partial);
+    wgrad_reduce_kernel<<<device_sms(), 256, 0, s>>>(jobs, n_jobs, chunks, stride, partial, grad);
     return cudaGetLastError() == cudaSuccess ? EJ_OK : fail(EJ_ERR_CUDA, "minibatch gradient launch failed");
 }
 

@@ -73,7 +73,17 @@ __device__ inline void mask_tile(float* out, int ld, const float* ref, int ncols
     }
 }
 
-constexpr int WG_STRIDE = 128 * 128 + 128;   // floats of one job's partial
+constexpr int WG_STRIDE = 128 * 128 + 128;   // floats of one job's partial up to hidden 128
+// Floats of one job's partial sums (weights m x n, then the n bias sums) for
+// the six gradient jobs of a network with `in` inputs, H hidden units and O
+// logits: the largest m n + n of the jobs.
+__host__ __device__ inline size_t wg_stride(int in, int H, int O) {
+    size_t s = (size_t)in * H + H, t = (size_t)H * H + H, u = (size_t)H * O + O;
+    s = s > t ? s : t;
+    s = s > u ? s : u;
+    return s > (size_t)WG_STRIDE ? s : (size_t)WG_STRIDE;
+}
+constexpr int WG_TILE = 128;                  // output rows / columns of one weight-gradient block
 struct WgJob {
     const float* A; const float* B;
     int lda, ldb, m, n;
@@ -85,7 +95,7 @@ size_t fwd_bwd_smem(int in_pad, int H, int O);
 ej_status launch_gae(const float* rew, const float* value, const uint8_t* done, int T, int rows,
                      int per_env, float gamma, float lam, float* adv, float* ret, cudaStream_t s);
 ej_status launch_minibatch_grad(const FbArgs& fa, const WgJobs& jobs, int n_jobs, float* partial,
-                                int chunks, const float* w2, const float* w3, const float* v2,
+                                size_t stride, int chunks, const float* w2, const float* w3, const float* v2,
                                 float* grad, cudaStream_t s);
 // BF16 tensor-core minibatch gradient (ej_ppo_bf16.cu): advantage statistics,
 // the fused kernel and the reduction into grad; partial: scratch of
@@ -102,6 +112,8 @@ ej_status launch_minibatch_loss(double* stats, int count, const double* moments,
 // (net: EJ_NET_POP, EJ_NET_GOV or -1 for both; gae: GAE inputs; grad:
 // minibatch-gradient inputs).
 ej_status check_rollout(const EjRollout* b, int net, bool gae, bool grad);
+// EJ_ERR_UNSUPPORTED when the float32 gradient's tile of network net (-1: both) exceeds shared memory.
+ej_status check_fp32_shape(const KParams& kp, int H, int precision, int net);
 ej_status launch_adv_stats(const MbDesc& mb, const float* adv, double* stats, cudaStream_t s);
 // Writes the minibatch's rollout rows (the permutation, once) and their advantage sums.
 ej_status launch_mb_rows_stats(const MbDesc& mb, const float* adv, uint32_t* rows, double* stats, cudaStream_t s);

@@ -29,6 +29,7 @@ struct Ws {
     uint64_t adv[2], ret[2], stats[2], totals, wt3, wt2, wv2, rows, partial, grad[2], total;
     uint64_t row_floats;   // floats of the per-row buffers (largest minibatch of either network)
     uint64_t max_mb;       // rows of the largest minibatch
+    uint64_t wg_stride;    // floats of one weight-gradient job's partial sums
 };
 
 Ws ws_layout(const KParams& kp, const EjPpoParams* pp, int T, int H) {
@@ -59,7 +60,13 @@ Ws ws_layout(const KParams& kp, const EjPpoParams* pp, int T, int H) {
     w.row_floats = region;
     w.max_mb = mb;
     w.rows = o; o = a256(o + 4ull * region);
-    w.partial = o; o = a256(o + 4ull * 6 * WG_CHUNKS * WG_STRIDE);
+    size_t stride = 0;
+    for (int n = 0; n < 2; ++n) {
+        const size_t s = wg_stride(dd[n].in, H, dd[n].O);
+        stride = s > stride ? s : stride;
+    }
+    w.wg_stride = stride;
+    w.partial = o; o = a256(o + 4ull * 6 * WG_CHUNKS * stride);
     for (int n = 0; n < 2; ++n) {
         w.grad[n] = o;
         o = a256(o + 4ull * net_offsets(dd[n].in, H, dd[n].O).total);
@@ -81,7 +88,7 @@ ej_status check_common(const EjParams* p, const EjPpoParams* pp, int T, int H, L
     if (!pp) return fail(EJ_ERR_ARG, "ppo params is NULL");
     if (T < 1) return fail(EJ_ERR_ARG, "T must be >= 1");
     if (pp->minibatches < 1 || pp->epochs < 1) return fail(EJ_ERR_ARG, "epochs and minibatches must be >= 1");
-    if (H < 32 || H > 128 || H % 32) return fail(EJ_ERR_UNSUPPORTED, "PPO update supports hidden in {32, 64, 96, 128}");
+    if (H < 32 || H > 256 || H % 32) return fail(EJ_ERR_UNSUPPORTED, "PPO update supports hidden 32 .. 256 in steps of 32");
     if (kp->nb * p->tax_levels > 128 || kp->nA > 128 || kp->D > 128 || kp->G > 128)
         return fail(EJ_ERR_UNSUPPORTED, "PPO update needs inputs and logits <= 128");
     if ((uint64_t)T * kp->E * kp->A >= (1ull << 31)) return fail(EJ_ERR_UNSUPPORTED, "too many rows");
@@ -89,6 +96,21 @@ ej_status check_common(const EjParams* p, const EjPpoParams* pp, int T, int H, L
 }
 
 }  // namespace
+
+// The float32 gradient's 64-row tile of network `net` (-1: both) fits shared memory.
+ej_status check_fp32_shape(const KParams& kp, int H, int precision, int net) {
+    if (precision != EJ_FP32) return EJ_OK;
+    for (int n = 0; n < 2; ++n) {
+        if (net >= 0 && n != net) continue;
+        const int in = n == EJ_NET_POP ? kp.D : kp.G;
+        const int O = n == EJ_NET_POP ? kp.nA : kp.nb * kp.tax_levels;
+        const size_t smem = fwd_bwd_smem((in + 3) & ~3, H, O);
+        if (smem > 227u * 1024u)
+            return fail(EJ_ERR_UNSUPPORTED, "float32 PPO: %d inputs, hidden %d and %d logits need %zu bytes of shared "
+                        "memory per 64-row tile (at most %u)", in, H, O, smem, 227u * 1024u);
+    }
+    return EJ_OK;
+}
 
 // Every rollout-buffer array a PPO call reads is present: for GAE (`gae`)
 // the rewards, values and done flags, for a minibatch gradient the inputs,
@@ -159,7 +181,7 @@ ej_status minibatch_grad(const KParams& kp, const EjPpoParams* pp, int T, int H,
     ej_status st;
     if (precision == EJ_BF16) {
         fa.rows = (uint32_t*)(ws + W.rows);      // the float32 path's per-row region holds >= count entries
-        st = launch_ppo_bf16(fa, (float*)(ws + W.partial), 4ull * 6 * WG_CHUNKS * WG_STRIDE, grad, s);
+        st = launch_ppo_bf16(fa, (float*)(ws + W.partial), 4ull * 6 * WG_CHUNKS * W.wg_stride, grad, s);
         if (st != EJ_OK) return st;
         return launch_minibatch_loss(stats, fa.mb.count, moments, pp->vf_coef, pp->ent_coef, s);
     }
@@ -190,7 +212,7 @@ ej_status minibatch_grad(const KParams& kp, const EjPpoParams* pp, int T, int H,
     job(5, fa.ws_g2, H, fa.ws_dv, 1, off.V3, off.c3);
     if (cudaMemsetAsync(grad, 0, sizeof(float) * off.total, s) != cudaSuccess)
         return fail(EJ_ERR_CUDA, "memset of the gradient failed");
-    st = launch_minibatch_grad(fa, jobs, 6, (float*)(ws + W.partial), WG_CHUNKS, weights + off.W2,
+    st = launch_minibatch_grad(fa, jobs, 6, (float*)(ws + W.partial), W.wg_stride, WG_CHUNKS, weights + off.W2,
                                weights + off.W3, weights + off.V2, grad, s);
     if (st != EJ_OK) return st;
     return launch_minibatch_loss(stats, fa.mb.count, moments, pp->vf_coef, pp->ent_coef, s);
@@ -280,6 +302,7 @@ ej_status ppo_minibatch_grad(const EjParams* p, const EjPpoParams* pp, int32_t T
     if (net != EJ_NET_POP && net != EJ_NET_GOV) return fail(EJ_ERR_ARG, "unknown network %d", net);
     if (!b || !workspace || !weights || !grad) return fail(EJ_ERR_ARG, "NULL argument");
     if ((st = check_rollout(b, net, false, true)) != EJ_OK) return st;
+    if ((st = check_fp32_shape(kp, hidden, precision, net)) != EJ_OK) return st;
     if ((uintptr_t)workspace % 256 || (uintptr_t)weights % 16) return fail(EJ_ERR_ARG, "misaligned buffer");
     if (minibatch < 0 || minibatch >= pp->minibatches) return fail(EJ_ERR_ARG, "minibatch out of range");
     const Ws W = ws_layout(kp, pp, T, hidden);
@@ -328,6 +351,7 @@ ej_status ppo_minibatch_grad_global(const EjParams* p, const EjPpoParams* pp, in
     if (net != EJ_NET_POP && net != EJ_NET_GOV) return fail(EJ_ERR_ARG, "unknown network %d", net);
     if (!b || !workspace || !weights || !grad || !moments) return fail(EJ_ERR_ARG, "NULL argument");
     if ((st = check_rollout(b, net, false, true)) != EJ_OK) return st;
+    if ((st = check_fp32_shape(kp, hidden, precision, net)) != EJ_OK) return st;
     if ((uintptr_t)workspace % 256 || (uintptr_t)weights % 16) return fail(EJ_ERR_ARG, "misaligned buffer");
     if (minibatch < 0 || minibatch >= pp->minibatches) return fail(EJ_ERR_ARG, "minibatch out of range");
     const Ws W = ws_layout(kp, pp, T, hidden);
@@ -363,6 +387,7 @@ ej_status ppo_update(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_
     if (!pop_w || !gov_w || !pop_m || !pop_v || !gov_m || !gov_v || !b || !workspace)
         return fail(EJ_ERR_ARG, "NULL argument");
     if ((st = check_rollout(b, -1, true, true)) != EJ_OK) return st;
+    if ((st = check_fp32_shape(kp, hidden, precision, -1)) != EJ_OK) return st;
     if ((uintptr_t)workspace % 256 || (uintptr_t)pop_w % 16 || (uintptr_t)gov_w % 16)
         return fail(EJ_ERR_ARG, "misaligned buffer");
     const Ws W = ws_layout(kp, pp, T, hidden);

@@ -232,3 +232,26 @@ def test_step_host_argument_checks(lib):
     assert "workspace" in lib.ej_last_error().decode()
     assert lib.env_step_host(*args(fake, 1 << 40, chunk=0)) == 1
     assert lib.env_step_host(*args(fake, 1 << 40, gu=fake)) == 1
+
+
+def test_ppo_hidden_limits(lib):
+    """Hidden widths: multiples of 32 up to 256 size a workspace; the
+    12-resource market at hidden 256 exceeds the float32 tile and BF16 takes
+    hidden 128 only: both refused on the host (EJ_ERR_UNSUPPORTED)."""
+    pp = N.EjPpoParams()
+    lib.ej_ppo_params_default(C.byref(pp))
+    p4 = N.make_params(E=2, A=4, R=4, P=3, price_ticks=[1, 2, 3], price_tick=3.0, Rd=2, gov_enabled=0)
+    p12 = N.make_params(E=2, A=4, R=12, P=3, price_ticks=[1, 2, 3], price_tick=3.0, Rd=3, gov_enabled=0)
+    nb = C.c_uint64()
+    for H in (32, 128, 256):
+        assert lib.ej_ppo_workspace_bytes(C.byref(p4), C.byref(pp), 8, H, C.byref(nb)) == 0
+    assert lib.ej_ppo_workspace_bytes(C.byref(p4), C.byref(pp), 8, 288, C.byref(nb)) == 3
+    assert lib.ej_ppo_workspace_bytes(C.byref(p4), C.byref(pp), 8, 100, C.byref(nb)) == 3
+    fake = C.c_void_p(4096)
+    b = N.EjRollout(**{f: 4096 for f, _ in N.EjRollout._fields_})
+    for prec in (N.FP32, N.BF16):
+        st = lib.ppo_minibatch_grad(C.byref(p12), C.byref(pp), 8, 256, prec, 0, fake, C.byref(b), fake,
+                                    0, 0, fake, None, None)
+        assert st == 3, prec
+    assert lib.ppo_update(C.byref(p12), C.byref(pp), 8, 256, N.FP32, fake, fake, fake, fake, fake, fake, 0, 0,
+                          C.byref(b), fake, None, None) == 3

@@ -151,3 +151,72 @@ def test_update_is_one_adam_step_per_minibatch():
             assert np.allclose(d[big], expect[big], rtol=0, atol=2e-7), k
             assert np.all(np.abs(d) <= lr * 1.0001), k
         assert stats[net, 0] == pytest.approx(st["pg"], abs=1e-3 * (1 + abs(st["pg"])))
+
+
+@pytest.mark.parametrize("net", [0, 1])
+def test_section5_hidden256_gradient_matches_float64(net):
+    """Section 5's networks of 256 units on its 4-resource market (prices 3,
+    6, 9, no taxes, skills growing around 1): the float32 minibatch gradient
+    against the float64 oracle, every parameter tensor, within 1e-3 of the
+    tensor's largest entry (the weight-gradient kernel then spans 2 x 2
+    output tiles of 128)."""
+    import paper_2410_22165_gb300 as P
+    H2 = 256
+    kw = dict(R=4, P=3, price_ticks=[1, 2, 3], price_tick=3.0, Rd=2, gov_enabled=0, skill_gain=0.005,
+              skill_init=1, T_ep=12, T_tax=4)
+    E, A, T = (2, 4, 16) if net == 0 else (8, 4, 16)
+    env = P.VecEnv(E, A, **kw)
+    O_gov = env.p.nb * env.p.tax_levels
+    pw = synth.net_weights(4, 0, env.D, H2, env.nA)
+    gw = synth.net_weights(4, 1, env.G, H2, O_gov)
+    pol = P.Policy(env, torch.from_numpy(pw), torch.from_numpy(gw), hidden=H2)
+    ro = P.Rollout(env, pol, T)
+    ro.reset(seed=4)
+    ro.run()
+    ppo = P.PPO(pol, T, minibatches=4, seed=77)
+    b = {k: v.cpu().numpy() for k, v in ro.buf.items()}
+    ppo.advantages(ro)
+    grad = ppo.minibatch_grad(ro, net, 3, 1)[0].cpu().numpy()
+    N = T * (E * A if net == 0 else E)
+    rows = shuffle.minibatch_rows(1, 4, N, 77, 3)
+    adv, ret, gadv, gret = _oracle_gae(env, b, ppo.pp)
+    in_dim = env.D if net == 0 else env.G
+    O = env.nA if net == 0 else O_gov
+    if net == 0:
+        x = b["obs"][:T].reshape(T * E * A, env.D)[rows]
+        valid = op.mask_bits(b["mask"][:T].reshape(T * E * A, env.W).view(np.uint32), env.nA)[rows]
+        act, lpo = b["act"].reshape(-1, 1)[rows], b["logp"].reshape(-1)[rows]
+        vo, a, r = b["value"][:T].reshape(-1)[rows], adv.reshape(-1)[rows], ret.reshape(-1)[rows]
+        heads, head = 1, env.nA
+    else:
+        x = b["gobs"][:T].reshape(T * E, env.G)[rows]
+        valid = np.ones((len(rows), O_gov), bool)
+        act, lpo = b["gact"].reshape(T * E, env.p.nb)[rows], b["glogp"].reshape(-1)[rows]
+        vo, a, r = b["gvalue"][:T].reshape(-1)[rows], gadv.reshape(-1)[rows], gret.reshape(-1)[rows]
+        heads, head = env.p.nb, env.p.tax_levels
+    w = synth.unpack(pw if net == 0 else gw, in_dim, H2, O)
+    _, g64, _ = oppo.ppo_loss_grad64(w, x, act, valid, lpo, vo, a, r, clip=ppo.pp.clip, vf_coef=ppo.pp.vf_coef,
+                                     vclip=ppo.pp.vclip, ent_coef=ppo.pp.ent_coef, heads=heads, head=head)
+    gg = synth.unpack(grad, in_dim, H2, O)
+    for k, ref in g64.items():
+        tol = 1e-3 * np.abs(ref).max() + 1e-7
+        assert np.max(np.abs(gg[k].reshape(ref.shape) - ref)) <= tol, k
+    assert env.nA == 30 and (net == 1 or env.D == 39)
+
+
+def test_hidden256_shapes_beyond_shared_memory_are_refused():
+    """The 12-resource market (95 inputs, 86 logits) at hidden 256 does not
+    fit the float32 tile: refused on the host before anything runs; the BF16
+    gradient takes hidden 128 only."""
+    import ctypes as C
+    import paper_2410_22165_gb300 as P
+    from paper_2410_22165_gb300 import _native as N
+    env = P.VecEnv(2, 4, R=12, P=3, price_ticks=[1, 2, 3], price_tick=3.0, Rd=3, gov_enabled=0)
+    pp = N.EjPpoParams()
+    N.load().ej_ppo_params_default(C.byref(pp))
+    fake = C.c_void_p(4096)
+    b = N.EjRollout(**{f: 4096 for f, _ in N.EjRollout._fields_})
+    for prec in (N.FP32, N.BF16):
+        st = N.load().ppo_minibatch_grad(C.byref(env.p), C.byref(pp), 8, 256, prec, 0, fake, C.byref(b), fake,
+                                         0, 0, fake, None, None)
+        assert st == 3, prec
