@@ -366,7 +366,8 @@ def run_training(args, dev, E_t=2048, T_t=128, seed=3000):
     agents) of the episodes completed in the last third of the run, with the
     standard error over environments.  The two runs sample different actions
     as soon as their policies differ, so they agree statistically, not bit
-    for bit."""
+    for bit; a third run (BF16, the next seed) gives the difference that the
+    seed alone makes, the scale against which the precision's is read."""
     import numpy as np
     import torch
 
@@ -376,13 +377,13 @@ def run_training(args, dev, E_t=2048, T_t=128, seed=3000):
     n_up = args.train_updates
     out = {"workload": f"E={E_t} x A={A}, {n_up} iterations of a {T_t}-step rollout + PPO update "
                        "(4 epochs x 8 minibatches), both networks, same seed for both precisions"}
-    for precision in ("bf16", "fp32"):
+    for run, precision, sd in (("bf16", "bf16", seed), ("fp32", "fp32", seed), ("bf16_seed2", "bf16", seed + 1)):
         env = VecEnv(E_t, A, device=dev, T_ep=T_EP, T_tax=T_TAX)
-        pw = torch.from_numpy(synth.net_weights(seed, 0, env.D, 128, env.nA))
-        gw = torch.from_numpy(synth.net_weights(seed, 1, env.G, 128, env.p.nb * env.p.tax_levels))
+        pw = torch.from_numpy(synth.net_weights(sd, 0, env.D, 128, env.nA))
+        gw = torch.from_numpy(synth.net_weights(sd, 1, env.G, 128, env.p.nb * env.p.tax_levels))
         pol = Policy(env, pw, gw, hidden=128, precision=precision)
         ro = Rollout(env, pol, T_t)
-        ro.reset(seed=seed)
+        ro.reset(seed=sd)
         ppo = PPO(pol, T_t, precision=precision)
         ep_pop = np.zeros(E_t)
         ep_gov = np.zeros(E_t)
@@ -411,7 +412,7 @@ def run_training(args, dev, E_t=2048, T_t=128, seed=3000):
         late = [f for f in finished if f[0] >= (2 * n_up) // 3] or finished
         rp = np.array([f[1] for f in late]) if late else np.zeros(1)
         rg = np.array([f[2] for f in late]) if late else np.zeros(1)
-        out[precision] = {
+        out[run] = {
             "mean_population_reward_per_iteration": curve_pop, "mean_government_reward_per_iteration": curve_gov,
             "episodes_completed": len(finished), "late_episodes": len(late),
             "late_population_return": float(rp.mean()), "late_population_return_se": float(rp.std() / np.sqrt(len(rp))),
@@ -419,11 +420,49 @@ def run_training(args, dev, E_t=2048, T_t=128, seed=3000):
             "wall_s": wall}
         del ppo, ro, pol, env
         torch.cuda.empty_cache()
-    b, f = out["bf16"], out["fp32"]
-    out["population_return_difference"] = b["late_population_return"] - f["late_population_return"]
-    out["population_return_difference_se"] = float(np.hypot(b["late_population_return_se"], f["late_population_return_se"]))
-    out["government_return_difference"] = b["late_government_return"] - f["late_government_return"]
-    out["government_return_difference_se"] = float(np.hypot(b["late_government_return_se"], f["late_government_return_se"]))
+    b, f, b2 = out["bf16"], out["fp32"], out["bf16_seed2"]
+    for who in ("population", "government"):
+        key, se = f"late_{who}_return", f"late_{who}_return_se"
+        # precision effect (same seed) next to the seed effect (same precision)
+        out[f"{who}_return_difference"] = b[key] - f[key]
+        out[f"{who}_return_difference_se"] = float(np.hypot(b[se], f[se]))
+        out[f"{who}_return_seed_difference"] = b[key] - b2[key]
+        out[f"{who}_return_seed_difference_se"] = float(np.hypot(b[se], b2[se]))
+    return out
+
+
+def run_paper_training(args, dev):
+    """Section 4's experiment at Table 2's settings: the population and the
+    government trained simultaneously for 1e7 environment steps (rollouts of
+    150 steps in 10 environments, 6 epochs x 6 minibatches, gamma 0.999,
+    learning rate 5e-4 and entropy coefficient 0.1 annealed), once with taxes
+    and once as a free market (no government), from the same seed.  Prints
+    the episode measurements of the first and the last tenth of the run."""
+    import torch
+
+    import synth
+    from paper_2410_22165_gb300 import Policy, VecEnv
+    from paper_2410_22165_gb300.train import Trainer
+
+    E_t, T_t = args.paper_envs, 150
+    iters = int(round(args.paper_env_steps / (E_t * T_t)))
+    out = {"workload": f"Section 4 training: {E_t} environments x {A} agents, rollouts of {T_t} steps, "
+                       f"{iters} iterations = {iters * E_t * T_t:.3g} environment steps, 6 epochs x 6 minibatches, "
+                       "gamma 0.999, lr 5e-4 and entropy 0.1 annealed (Table 2), BF16",
+           "precision": "bf16"}
+    for label, taxes in (("taxes", True), ("free_market", False)):
+        env = VecEnv(E_t, A, device=dev, T_ep=T_EP, T_tax=T_TAX, gov_enabled=1 if taxes else 0)
+        pw = torch.from_numpy(synth.net_weights(args.paper_seed, 0, env.D, 128, env.nA))
+        gw = torch.from_numpy(synth.net_weights(args.paper_seed, 1, env.G, 128, env.p.nb * env.p.tax_levels))
+        pol = Policy(env, pw, gw, hidden=128, precision="bf16")
+        tr = Trainer(pol, T=T_t, precision="bf16", total_iterations=iters, seed=args.paper_seed, gamma=0.999,
+                     epochs=6, minibatches=6)
+        tr.reset(seed=args.paper_seed)
+        wall = tr.train()
+        out[label] = dict(tr.summary(), wall_s=wall,
+                          agent_steps_per_s=iters * E_t * T_t * A / wall)
+        del tr, pol, env
+        torch.cuda.empty_cache()
     return out
 
 
@@ -694,6 +733,11 @@ def main():
     ap.add_argument("--no-train", action="store_true", help="skip the rollout and PPO measurements")
     ap.add_argument("--train-updates", type=int, default=20,
                     help="iterations of the BF16 / FP32 training comparison (0: skip)")
+    ap.add_argument("--paper-training", action="store_true",
+                    help="run Section 4's training experiment (taxes vs free market) instead of the benchmark")
+    ap.add_argument("--paper-envs", type=int, default=10)
+    ap.add_argument("--paper-env-steps", type=float, default=1e7)
+    ap.add_argument("--paper-seed", type=int, default=7)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     args = ap.parse_args()
@@ -701,6 +745,12 @@ def main():
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.profile_case:
         run_profile_case(args)
+        return
+    if args.paper_training:
+        import torch
+        from paper_2410_22165_gb300 import build as cuda_build
+        cuda_build.build()
+        print(json.dumps(run_paper_training(args, torch.device("cuda", 0))), flush=True)
         return
     line = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if line is not None:

@@ -73,7 +73,8 @@ struct Sm {
     float* obs;                  // [NT][D]
 };
 
-enum { MISC_GINI = 0, MISC_PROD = 1, MISC_SHARE = 2, MISC_UGPREV = 3, MISC_PLEFT = 4, MISC_TFRAC = 5 };
+enum { MISC_GINI = 0, MISC_PROD = 1, MISC_SHARE = 2, MISC_UGPREV = 3, MISC_PLEFT = 4, MISC_TFRAC = 5,
+       MISC_PIVOT = 8 };   // MISC_PIVOT + m: key of metric m's last lower middle value (as float bits)
 
 template <int NT>
 __device__ __forceinline__ Sm carve(unsigned char* base, const KParams& p) {
@@ -339,10 +340,72 @@ __device__ __forceinline__ float sorted_at(const float (&x)[V], int k) {
     return __shfl_sync(FULL, v, k / V);
 }
 
+// Order-preserving unsigned key of a float (not NaN): a < b <=> key(a) < key(b).
+__device__ __forceinline__ uint32_t fkey(float f) {
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+// The k-th smallest (from 0) of the 32 V values of a warp (V per lane), found
+// by walking from `pivot` (a value near the answer) over the distinct values
+// in between: warp-wide counts and minima / maxima per step (redux.sync).
+// Exact; false when the walk would take more than `max_steps` steps.
+template <int V>
+__device__ __forceinline__ bool walk_select(const uint32_t (&key)[V], int k, uint32_t pivot, int max_steps,
+                                            uint32_t& out) {
+    int lt = 0, le = 0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) { lt += key[v] < pivot; le += key[v] <= pivot; }
+    lt = __reduce_add_sync(FULL, lt);
+    le = __reduce_add_sync(FULL, le);
+    if (k >= lt && k < le) { out = pivot; return true; }
+    uint32_t cur = pivot;
+    if (k >= le) {                       // upwards: rank = elements <= cur
+        int rank = le;
+        for (int it = 0; it < max_steps; ++it) {
+            uint32_t mn = 0xFFFFFFFFu;
+#pragma unroll
+            for (int v = 0; v < V; ++v) mn = key[v] > cur ? min(mn, key[v]) : mn;
+            const uint32_t nxt = __reduce_min_sync(FULL, mn);
+            int eq = 0;
+#pragma unroll
+            for (int v = 0; v < V; ++v) eq += key[v] == nxt;
+            eq = __reduce_add_sync(FULL, eq);
+            if (k < rank + eq) { out = nxt; return true; }
+            rank += eq;
+            cur = nxt;
+        }
+    } else {                             // downwards: rank = elements < cur
+        int rank = lt;
+        for (int it = 0; it < max_steps; ++it) {
+            uint32_t mx = 0u;
+#pragma unroll
+            for (int v = 0; v < V; ++v) mx = key[v] < cur ? max(mx, key[v]) : mx;
+            const uint32_t prv = __reduce_max_sync(FULL, mx);
+            int eq = 0;
+#pragma unroll
+            for (int v = 0; v < V; ++v) eq += key[v] == prv;
+            rank -= __reduce_add_sync(FULL, eq);
+            if (k >= rank) { out = prv; return true; }
+            cur = prv;
+        }
+    }
+    return false;
+}
+
 // Statistics of one metric by one warp (mean, population std, median; and
 // for total coin the gini index and the total, Eq. 5-6), from s.stat[m].
+// Total coin is sorted (the gini index weights each value by its rank); the
+// other metrics' medians are the two middle order statistics, walked to from
+// the previous step's lower middle value (the medians move little from step
+// to step), with the sort as the fallback of a long walk.  Same values either
+// way.
 template <int V>
 __device__ void warp_metric_stats(const Sm& s, int m, int lane, int Ae, int NT) {
+    constexpr int MAX_WALK = 12;
     float x[V];
     float sum = 0.0f;
 #pragma unroll
@@ -352,20 +415,50 @@ __device__ void warp_metric_stats(const Sm& s, int m, int lane, int Ae, int NT) 
         if (idx < Ae) sum += x[v];
     }
     sum = warp_sum(sum);
-    warp_bitonic<V>(x, lane);
     const float mean = sum / (float)Ae;
-    float ss = 0.0f, gnum = 0.0f;
+    const int k_lo = (Ae - 1) >> 1, k_hi = Ae >> 1;
+    float ss = 0.0f, gnum = 0.0f, lo = 0.0f, hi = 0.0f;
+    bool walked = false;
+    if (m != 0) {
+        // values in index order (the sum of squares does not need them sorted)
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-        const int idx = lane * V + v;
-        if (idx < Ae) {
-            const float d = x[v] - mean;
-            ss += d * d;
-            gnum += (float)(2 * idx - Ae + 1) * x[v];
+        for (int v = 0; v < V; ++v) {
+            if (lane * V + v < Ae) {
+                const float d = x[v] - mean;
+                ss += d * d;
+            }
+        }
+        uint32_t key[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) key[v] = fkey(x[v]);
+        uint32_t klo, khi;
+        const uint32_t pivot = __float_as_uint(s.misc[MISC_PIVOT + m]);
+        walked = walk_select<V>(key, k_lo, pivot, MAX_WALK, klo) &&
+                 walk_select<V>(key, k_hi, klo, MAX_WALK, khi);
+        if (walked) {
+            lo = fkey_inv(klo);
+            hi = fkey_inv(khi);
+            __syncwarp();
+            if (lane == 0) s.misc[MISC_PIVOT + m] = __uint_as_float(klo);
         }
     }
+    if (!walked) {
+        warp_bitonic<V>(x, lane);
+        ss = 0.0f;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int idx = lane * V + v;
+            if (idx < Ae) {
+                const float d = x[v] - mean;
+                ss += d * d;
+                gnum += (float)(2 * idx - Ae + 1) * x[v];
+            }
+        }
+        lo = sorted_at<V>(x, k_lo);
+        hi = sorted_at<V>(x, k_hi);
+        if (m != 0 && lane == 0) s.misc[MISC_PIVOT + m] = __uint_as_float(fkey(lo));
+    }
     ss = warp_sum(ss);
-    const float lo = sorted_at<V>(x, (Ae - 1) >> 1), hi = sorted_at<V>(x, Ae >> 1);
     if (m == 0) gnum = warp_sum(gnum);
     if (lane == 0) {
         s.gstat[3 * m + 0] = mean;
@@ -641,6 +734,7 @@ __global__ void __launch_bounds__(NT, MinCtas<NT>::value) env_kernel(KParams p, 
     const int owner = NT - 1 - i;          // levels l = owner, owner + NT, ... belong to this thread
 
     if (i <= p.max_orders) s.nord_frac[i] = __fdiv_rn((float)i, (float)(p.max_orders > 0 ? p.max_orders : 1));
+    if (i < 3) s.misc[MISC_PIVOT + i] = __uint_as_float(fkey(0.0f));   // any start works: the walk is exact
     Agent g;
     int t;
     uint32_t gs, ep, k0, k1;
