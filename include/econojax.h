@@ -318,6 +318,31 @@ ej_status policy_forward_segments(int32_t n_seg, const EjParams* const* params, 
  * precision) into shared launches, else 0 (one launch per set). */
 ej_status policy_segmented(const EjParams* p, int32_t net, int32_t hidden, int32_t precision, int32_t* ok);
 
+/* Network layouts of the population (Section 5's three multi-agent methods):
+ *   EJ_NETS_SHARED       one actor and one critic shared by all agents
+ *                        (centralised training; Section 4's setting);
+ *   EJ_NETS_INDEPENDENT  every agent its own actor and critic (iPPO);
+ *   EJ_NETS_CTDE         every agent its own actor, one critic for all (the
+ *                        section's naive CTDE / MAPPO: the critic sees the
+ *                        same per-agent observation as the actor).
+ * A per-agent population network is A consecutive parameter vectors of
+ * ej_net_floats(EJ_NET_POP) floats each (the layout above): agent i's actor
+ * is vector i's actor part; its critic is vector i's critic part
+ * (independent) or vector 0's (CTDE, whose other critic parts are unused and
+ * get zero gradients).  The government network stays one shared vector.
+ * Per-agent networks run in FP32 (EJ_BF16 returns EJ_ERR_UNSUPPORTED). */
+typedef enum { EJ_NETS_SHARED = 0, EJ_NETS_INDEPENDENT = 1, EJ_NETS_CTDE = 2 } ej_net_layout;
+
+/* policy_forward of the population network under `layout` (EJ_NETS_SHARED:
+ * policy_forward).  weights (device) A * ej_net_floats floats for a per-agent
+ * layout; the other arguments as policy_forward's for EJ_NET_POP.  Rows of
+ * agent i use agent i's actor and critic as the layout defines; sampled
+ * actions follow the same counters. */
+ej_status policy_forward_agents(const EjParams* p, const void* state, int32_t layout, int32_t hidden,
+                                int32_t precision, const float* weights, const float* obs, const uint32_t* mask,
+                                const float* u, int32_t* act, float* logp, float* value, float* entropy,
+                                float* logits, void* stream);
+
 /* Rollout buffer (device pointers, caller-owned).  Slot 0 of obs, gobs and
  * mask must hold the current observation (from env_reset or the previous
  * rollout's slot T). */
@@ -349,6 +374,13 @@ typedef struct {
 ej_status rollout(const EjParams* p, void* state, int32_t T, int32_t hidden, int32_t precision,
                   const float* pop_weights, const float* gov_weights, const EjRollout* buf,
                   void* stream);
+
+/* rollout_agents: rollout with the population's networks in `layout`
+ * (EJ_NETS_SHARED: rollout itself); pop_weights as policy_forward_agents'.
+ * One chain of 3T + 2 launches on `stream` (FP32). */
+ej_status rollout_agents(const EjParams* p, void* state, int32_t T, int32_t hidden, int32_t precision,
+                         int32_t layout, const float* pop_weights, const float* gov_weights, const EjRollout* buf,
+                         void* stream);
 
 /* rollout_split (Section 4, as rollout): rollout with the environments split into n_chains (1..4)
  * contiguous ranges whose T-step chains are independent (environments do
@@ -465,6 +497,33 @@ ej_status ppo_update(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_
                      float* pop_v, float* gov_m, float* gov_v, int32_t adam_steps_done,
                      uint32_t update_index, const EjRollout* buf, void* workspace,
                      float* stats_out, void* stream);
+
+/* PPO with the population's networks in a per-agent layout (Section 5:
+ * independent training, iPPO; CTDE / MAPPO), FP32 (EJ_BF16 returns
+ * EJ_ERR_UNSUPPORTED).  EJ_NETS_SHARED makes each call the shared one above
+ * (ej_ppo_workspace_bytes, ppo_minibatch_grad for EJ_NET_POP, ppo_update).
+ * Each agent trains its own actor (and, independent, its own critic) on its
+ * own transitions: minibatch m of an epoch is, for every agent i, the rows
+ * pi(q) * A + i for q in [floor(m N / M), floor((m+1) N / M)), N = T * E,
+ * with pi the Feistel permutation of [0, N) described above (same keys and
+ * counters; one shuffle of the (step, environment) pairs serves all agents).
+ * An actor's loss is the mean over its agent's rows, with advantages
+ * normalised over them; a shared critic's (CTDE) loss is the mean over all
+ * agents' rows.  Gradients, Adam moments and weights of the population are
+ * A vectors (A * ej_net_floats floats; a CTDE critic lives in vector 0 and
+ * the other vectors' critic parts get zero gradients).  stats_out of
+ * ppo_minibatch_grad_agents: sums over all rows (entry 7: their mean loss).
+ * The workspace (ej_ppo_workspace_bytes_agents) also serves ppo_advantages. */
+ej_status ej_ppo_workspace_bytes_agents(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_t hidden,
+                                        int32_t layout, uint64_t* bytes);
+ej_status ppo_minibatch_grad_agents(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_t hidden,
+                                    int32_t precision, int32_t layout, const float* weights, const EjRollout* buf,
+                                    void* workspace, uint32_t shuffle_ctr, int32_t minibatch, float* grad,
+                                    double* stats_out, void* stream);
+ej_status ppo_update_agents(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_t hidden, int32_t precision,
+                            int32_t layout, float* pop_weights, float* gov_weights, float* pop_m, float* pop_v,
+                            float* gov_m, float* gov_v, int32_t adam_steps_done, uint32_t update_index,
+                            const EjRollout* buf, void* workspace, float* stats_out, void* stream);
 
 /* ppo_minibatch_grad_static: ppo_minibatch_grad for callers that cannot
  * allocate device memory: hosts whose device memory belongs to another

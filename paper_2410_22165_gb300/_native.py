@@ -56,6 +56,7 @@ class EjPpoParams(C.Structure):
 
 
 NET_POP, NET_GOV = 0, 1
+NETS_SHARED, NETS_INDEPENDENT, NETS_CTDE = 0, 1, 2
 FP32, BF16 = 0, 1
 
 
@@ -112,6 +113,18 @@ _PROTOS = {
     "ppo_minibatch_grad_static": (C.c_int, [C.POINTER(EjParams), C.POINTER(EjPpoParams), C.c_int32, C.c_int32,
                                             C.c_int32, C.c_int32, _VP, C.c_void_p, C.c_uint32, C.c_int32,
                                             _VP, _VP, _VP]),
+    "policy_forward_agents": (C.c_int, [C.POINTER(EjParams), _VP, C.c_int32, C.c_int32, C.c_int32, _VP, _VP,
+                                        _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "rollout_agents": (C.c_int, [C.POINTER(EjParams), _VP, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _VP, _VP,
+                                 C.c_void_p, _VP]),
+    "ej_ppo_workspace_bytes_agents": (C.c_int, [C.POINTER(EjParams), C.POINTER(EjPpoParams), C.c_int32, C.c_int32,
+                                                C.c_int32, C.POINTER(C.c_uint64)]),
+    "ppo_minibatch_grad_agents": (C.c_int, [C.POINTER(EjParams), C.POINTER(EjPpoParams), C.c_int32, C.c_int32,
+                                            C.c_int32, C.c_int32, _VP, C.c_void_p, _VP, C.c_uint32, C.c_int32,
+                                            _VP, _VP, _VP]),
+    "ppo_update_agents": (C.c_int, [C.POINTER(EjParams), C.POINTER(EjPpoParams), C.c_int32, C.c_int32, C.c_int32,
+                                    C.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, C.c_int32, C.c_uint32, C.c_void_p,
+                                    _VP, _VP, _VP]),
     "ej_device_status": (C.c_int, [C.POINTER(C.c_int32), C.c_int32]),
     "ej_last_error": (C.c_char_p, []),
 }

@@ -27,35 +27,46 @@ __global__ void __launch_bounds__(NTH, 2) policy_fp32_kernel(PolicyArgs a) {
     float* val = lg + TILE * ldo;                    // [TILE]
     float* wsc = val + TILE;                         // [TILE][ldo] sampler scratch
     const NetOffsets off = net_offsets(in_dim, H, O);
-    const float* w = a.weights;
-    const int n_tiles = (a.rows + TILE - 1) / TILE;
+    // shared networks: tiles of TILE consecutive rows; per-agent networks:
+    // tiles of one agent over TILE consecutive environments
+    const int n_env = a.rows / a.per_env;
+    const int tpa = (n_env + TILE - 1) / TILE;
+    const int n_tiles = a.agents ? a.agents * tpa : (a.rows + TILE - 1) / TILE;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int row0 = tile * TILE;
+        const int agent = a.agents ? tile / tpa : 0;
+        const int e0 = a.agents ? (tile % tpa) * TILE : 0;
+        auto row_of = [&](int r) -> int {     // the tile's r-th row, or -1 past the end
+            if (a.agents) return e0 + r < n_env ? (e0 + r) * a.per_env + agent : -1;
+            const int row = tile * TILE + r;
+            return row < a.rows ? row : -1;
+        };
+        const float* wa = a.weights + (size_t)agent * a.actor_stride;
+        const float* wc = a.weights + (size_t)agent * a.critic_stride;
         // observations of the tile (zero rows past the end, zero padding columns)
         for (int idx = threadIdx.x; idx < TILE * ldx; idx += NTH) {
             const int r = idx / ldx, k = idx % ldx;
-            const int row = row0 + r;
-            xs[idx] = (row < a.rows && k < in_dim) ? a.x[(size_t)row * in_dim + k] : 0.0f;
+            const int row = row_of(r);
+            xs[idx] = (row >= 0 && k < in_dim) ? a.x[(size_t)row * in_dim + k] : 0.0f;
         }
         __syncthreads();
         // actor: two hidden layers and the logits
-        dense_tile(xs, ldx, in_dim, w + off.W1, w + off.b1, H, hA, ldh, true);
+        dense_tile(xs, ldx, in_dim, wa + off.W1, wa + off.b1, H, hA, ldh, true);
         __syncthreads();
-        dense_tile(hA, ldh, H, w + off.W2, w + off.b2, H, hB, ldh, true);
+        dense_tile(hA, ldh, H, wa + off.W2, wa + off.b2, H, hB, ldh, true);
         __syncthreads();
-        head_tile(hB, ldh, H, w + off.W3, w + off.b3, O, lg, ldo);
+        head_tile(hB, ldh, H, wa + off.W3, wa + off.b3, O, lg, ldo);
         __syncthreads();
         // critic
-        dense_tile(xs, ldx, in_dim, w + off.V1, w + off.c1, H, hA, ldh, true);
+        dense_tile(xs, ldx, in_dim, wc + off.V1, wc + off.c1, H, hA, ldh, true);
         __syncthreads();
-        dense_tile(hA, ldh, H, w + off.V2, w + off.c2, H, hB, ldh, true);
+        dense_tile(hA, ldh, H, wc + off.V2, wc + off.c2, H, hB, ldh, true);
         __syncthreads();
-        value_tile(hB, ldh, H, w + off.V3, w[off.c3], val);
+        value_tile(hB, ldh, H, wc + off.V3, wc[off.c3], val);
         __syncthreads();
         // sampling, one thread per row
         if (threadIdx.x < TILE) {
-            const int r = threadIdx.x, row = row0 + r;
-            if (row < a.rows) sample_row(a, row, lg + r * ldo, val[r], wsc + r * ldo);
+            const int r = threadIdx.x, row = row_of(r);
+            if (row >= 0) sample_row(a, row, lg + r * ldo, val[r], wsc + r * ldo);
         }
         __syncthreads();
     }
@@ -72,7 +83,7 @@ ej_status launch_policy_fp32(const PolicyArgs& a, cudaStream_t stream) {
     static SmemOptIn opt_in;
     ej_status st = opt_in.ensure((const void*)policy_fp32_kernel, smem);
     if (st != EJ_OK) return st;
-    const int n_tiles = (a.rows + TILE - 1) / TILE;
+    const int n_tiles = a.agents ? a.agents * ((a.rows / a.per_env + TILE - 1) / TILE) : (a.rows + TILE - 1) / TILE;
     const int cap = 2 * device_sms();
     int grid = n_tiles < cap ? n_tiles : cap;
     if (grid < 1) grid = 1;

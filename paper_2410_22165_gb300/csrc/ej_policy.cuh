@@ -56,6 +56,12 @@ struct PolicyArgs {
     float* value;                 // [rows]
     float* entropy;               // [rows] sum over heads (may be NULL)
     float* logits;                // [rows][O] (may be NULL)
+    // Per-agent networks of the population (Section 5): agents > 0 gives each
+    // of the per_env agents its own actor (weights + i * actor_stride) and
+    // critic (weights + i * critic_stride; stride 0: one shared critic), and
+    // the kernel takes agent-major tiles (one agent, TILE environments).
+    int agents;
+    size_t actor_stride, critic_stride;
 };
 
 // Row segments of one policy launch: several buffers (e.g. several

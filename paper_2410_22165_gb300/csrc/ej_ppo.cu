@@ -79,14 +79,6 @@ __global__ void zero_kernel(double* p, int n) {
     for (int k = threadIdx.x; k < n; k += blockDim.x) p[k] = 0.0;
 }
 
-// --------------------------------------------------- transposes
-__global__ void transpose_kernel(const float* __restrict__ src, int rows, int cols, float* __restrict__ dst) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < rows * cols; k += gridDim.x * blockDim.x) {
-        const int r = k / cols, c = k % cols;
-        dst[(size_t)c * rows + r] = src[k];
-    }
-}
-
 // ---------------------------------- fused forward + loss + backward-data
 // Per tile of 64 minibatch rows: gather the rollout rows, run actor and
 // critic, form the gradient of the clipped PPO loss with respect to the
@@ -106,45 +98,65 @@ __global__ void __launch_bounds__(NTH, 1) fwd_bwd_kernel(FbArgs a) {
     float* DV = VAL + TILE;              // [TILE]
     __shared__ float red[8][NTH / 32];
     const NetOffsets off = net_offsets(I, H, O);
-    const float* w = a.weights;
     // advantage moments over the minibatch (or over the union of the ranks'
-    // minibatches, when given: count, sum, sum of squares)
-    const double n = a.moments ? a.moments[0] : (double)a.mb.count;
-    const double m1 = a.moments ? a.moments[1] : a.stats[ST_ADV_SUM];
-    const double m2 = a.moments ? a.moments[2] : a.stats[ST_ADV_SQ];
-    const float mean = (float)(m1 / n);
-    const float var = (float)fmax(m2 / n - (m1 / n) * (m1 / n), 0.0);
-    const float inv_std = 1.0f / (sqrtf(var) + 1e-8f);
-    const float inv_n = 1.0f / (float)n;
-    const int n_tiles = (a.mb.count + TILE - 1) / TILE;
+    // minibatches, when given: count, sum, sum of squares); per agent for
+    // per-agent networks
+    const double n_mb = a.moments ? a.moments[0] : (double)a.mb.count;
+    const int tpa = (a.mb.count + TILE - 1) / TILE;     // tiles per agent (the minibatch's, shared networks)
+    const int n_tiles = a.agents ? a.agents * tpa : tpa;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int j0 = tile * TILE;
+        const int agent = a.agents ? tile / tpa : 0;
+        const int j0 = (a.agents ? tile % tpa : tile) * TILE;   // position in the (agent's) minibatch
+        const int nvalid = min(TILE, a.mb.count - j0);
+        const int base = agent * a.mb.count + j0;               // row of the per-row buffers
+        const float* wa = a.weights + (size_t)agent * a.actor_stride;
+        const float* wc = a.weights + (size_t)agent * a.critic_stride;
+        const float* w3t = a.w3t + (size_t)agent * O * H;
+        const float* w2t = a.w2t + (size_t)agent * H * H;
+        const float* v2t = a.v2t + (a.critic_stride ? (size_t)agent * H * H : 0);
+        double n = n_mb, m1, m2;
+        if (a.agents) {
+            n = (double)a.mb.count;
+            m1 = a.agent_moments[2 * agent];
+            m2 = a.agent_moments[2 * agent + 1];
+        } else {
+            m1 = a.moments ? a.moments[1] : a.stats[ST_ADV_SUM];
+            m2 = a.moments ? a.moments[2] : a.stats[ST_ADV_SQ];
+        }
+        const float mean = (float)(m1 / n);
+        const float var = (float)fmax(m2 / n - (m1 / n) * (m1 / n), 0.0);
+        const float inv_std = 1.0f / (sqrtf(var) + 1e-8f);
+        const float inv_n = 1.0f / (float)n;
+        // the critic's loss: the mean over its own rows (a shared critic of
+        // per-agent actors: over every agent's rows)
+        const float inv_nc = (a.agents && !a.critic_stride) ? 1.0f / (float)(n * a.agents) : inv_n;
         // gather
         __shared__ uint32_t src_row[TILE];
         if (threadIdx.x < TILE) {
             const int j = j0 + threadIdx.x;
-            src_row[threadIdx.x] = j < a.mb.count ? mb_row(a.mb, j) : 0u;
+            src_row[threadIdx.x] = j < a.mb.count ? (a.agents ? mb_row(a.mb, j) * (uint32_t)a.agents + (uint32_t)agent
+                                                              : mb_row(a.mb, j)) : 0u;
         }
         __syncthreads();
         for (int idx = threadIdx.x; idx < TILE * ldx; idx += NTH) {
             const int r = idx / ldx, k = idx % ldx;
-            const bool in = j0 + r < a.mb.count && k < I;
+            const bool in = r < nvalid && k < I;
             xs[idx] = in ? a.x[(size_t)src_row[r] * I + k] : 0.0f;
         }
         __syncthreads();
         // actor forward
-        dense_tile(xs, ldx, I, w + off.W1, w + off.b1, H, B0, ldh, true);
+        dense_tile(xs, ldx, I, wa + off.W1, wa + off.b1, H, B0, ldh, true);
         __syncthreads();
-        dense_tile(B0, ldh, H, w + off.W2, w + off.b2, H, B1, ldh, true);
+        dense_tile(B0, ldh, H, wa + off.W2, wa + off.b2, H, B1, ldh, true);
         __syncthreads();
-        head_tile(B1, ldh, H, w + off.W3, w + off.b3, O, LG, ldo);
+        head_tile(B1, ldh, H, wa + off.W3, wa + off.b3, O, LG, ldo);
         __syncthreads();
-        store_tile(a, xs, ldx, I, a.ws_x, j0);
-        store_tile(a, B0, ldh, H, a.ws_h1, j0);
-        store_tile(a, B1, ldh, H, a.ws_h2, j0);
+        store_tile(xs, ldx, I, a.ws_x, base, nvalid);
+        store_tile(B0, ldh, H, a.ws_h1, base, nvalid);
+        store_tile(B1, ldh, H, a.ws_h2, base, nvalid);
         // loss gradient with respect to the logits, one thread per row
         float pg = 0.0f, ent_sum = 0.0f, clipc = 0.0f, kl = 0.0f;
-        if (threadIdx.x < TILE && j0 + (int)threadIdx.x < a.mb.count) {
+        if ((int)threadIdx.x < nvalid) {
             const int r = threadIdx.x;
             const uint32_t row = src_row[r];
             float* l = LG + r * ldo;
@@ -207,43 +219,43 @@ __global__ void __launch_bounds__(NTH, 1) fwd_bwd_kernel(FbArgs a) {
         __syncthreads();
         for (int idx = threadIdx.x; idx < TILE * O; idx += NTH) {
             const int r = idx / O, c = idx % O;
-            if (j0 + r < a.mb.count) a.ws_dl[(size_t)(j0 + r) * O + c] = LG[r * ldo + c];
+            if (r < nvalid) a.ws_dl[(size_t)(base + r) * O + c] = LG[r * ldo + c];
         }
         // dZ2 = (dL W3^T) * [h2 > 0]
-        dense_tile(LG, ldo, O, a.w3t, nullptr, H, B2, ldh, false);
+        dense_tile(LG, ldo, O, w3t, nullptr, H, B2, ldh, false);
         __syncthreads();
         mask_tile(B2, ldh, B1, H);
         __syncthreads();
-        store_tile(a, B2, ldh, H, a.ws_dz2, j0);
+        store_tile(B2, ldh, H, a.ws_dz2, base, nvalid);
         // dZ1 = (dZ2 W2^T) * [h1 > 0]
-        dense_tile(B2, ldh, H, a.w2t, nullptr, H, B1, ldh, false);
+        dense_tile(B2, ldh, H, w2t, nullptr, H, B1, ldh, false);
         __syncthreads();
         mask_tile(B1, ldh, B0, H);
         __syncthreads();
-        store_tile(a, B1, ldh, H, a.ws_dz1, j0);
+        store_tile(B1, ldh, H, a.ws_dz1, base, nvalid);
         // critic forward
-        dense_tile(xs, ldx, I, w + off.V1, w + off.c1, H, B0, ldh, true);
+        dense_tile(xs, ldx, I, wc + off.V1, wc + off.c1, H, B0, ldh, true);
         __syncthreads();
-        dense_tile(B0, ldh, H, w + off.V2, w + off.c2, H, B1, ldh, true);
+        dense_tile(B0, ldh, H, wc + off.V2, wc + off.c2, H, B1, ldh, true);
         __syncthreads();
-        value_tile(B1, ldh, H, w + off.V3, w[off.c3], VAL);
-        store_tile(a, B0, ldh, H, a.ws_g1, j0);
-        store_tile(a, B1, ldh, H, a.ws_g2, j0);
+        value_tile(B1, ldh, H, wc + off.V3, wc[off.c3], VAL);
+        store_tile(B0, ldh, H, a.ws_g1, base, nvalid);
+        store_tile(B1, ldh, H, a.ws_g2, base, nvalid);
         __syncthreads();
         // value-loss gradient (clipped value loss), one thread per row
         float vf = 0.0f;
         if (threadIdx.x < TILE) {
             const int r = threadIdx.x;
             float dv = 0.0f;
-            if (j0 + r < a.mb.count) {
+            if (r < nvalid) {
                 const uint32_t row = src_row[r];
                 const float v = VAL[r], vo = a.v_old[row], R = a.ret[row];
                 const float dvv = v - vo;
                 const float vc = vo + fminf(fmaxf(dvv, -a.vclip), a.vclip);
                 const float la = (v - R) * (v - R), lb = (vc - R) * (vc - R);
                 vf = 0.5f * fmaxf(la, lb);
-                dv = (la >= lb ? (v - R) : ((vc - R) * (fabsf(dvv) < a.vclip ? 1.0f : 0.0f))) * a.vf_coef * inv_n;
-                a.ws_dv[j0 + r] = dv;
+                dv = (la >= lb ? (v - R) : ((vc - R) * (fabsf(dvv) < a.vclip ? 1.0f : 0.0f))) * a.vf_coef * inv_nc;
+                a.ws_dv[base + r] = dv;
             }
             DV[r] = dv;
         }
@@ -251,15 +263,15 @@ __global__ void __launch_bounds__(NTH, 1) fwd_bwd_kernel(FbArgs a) {
         // dY2 = dv V3^T * [g2 > 0]
         for (int idx = threadIdx.x; idx < TILE * H; idx += NTH) {
             const int r = idx / H, c = idx % H;
-            B2[r * ldh + c] = B1[r * ldh + c] > 0.0f ? DV[r] * __ldg(w + off.V3 + c) : 0.0f;
+            B2[r * ldh + c] = B1[r * ldh + c] > 0.0f ? DV[r] * __ldg(wc + off.V3 + c) : 0.0f;
         }
         __syncthreads();
-        store_tile(a, B2, ldh, H, a.ws_dy2, j0);
-        dense_tile(B2, ldh, H, a.v2t, nullptr, H, B1, ldh, false);
+        store_tile(B2, ldh, H, a.ws_dy2, base, nvalid);
+        dense_tile(B2, ldh, H, v2t, nullptr, H, B1, ldh, false);
         __syncthreads();
         mask_tile(B1, ldh, B0, H);
         __syncthreads();
-        store_tile(a, B1, ldh, H, a.ws_dy1, j0);
+        store_tile(B1, ldh, H, a.ws_dy1, base, nvalid);
         // loss statistics
         float vals[5] = {pg, vf, ent_sum, clipc, kl};
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -285,16 +297,21 @@ __global__ void __launch_bounds__(NTH, 1) fwd_bwd_kernel(FbArgs a) {
 // output in 128 x 128 tiles over blockIdx.z (hidden widths above 128).
 constexpr int WG_ROWS = 32;
 
-__global__ void __launch_bounds__(NTH) wgrad_kernel(WgJobs jobs, int rows, int chunks, size_t stride,
+__global__ void __launch_bounds__(NTH) wgrad_kernel(WgJobs jobs, int rows, int chunks, size_t stride, int gmax,
                                                     float* __restrict__ partial) {
     const WgJob jb = jobs.job[blockIdx.y];
+    const int groups = jb.groups > 0 ? jb.groups : 1;
+    const int grows = jb.groups > 0 ? jb.group_rows : rows;
     const int tiles_n = (jb.n + WG_TILE - 1) / WG_TILE, tiles_m = (jb.m + WG_TILE - 1) / WG_TILE;
-    if ((int)blockIdx.z >= tiles_m * tiles_n) return;
-    const int m0 = ((int)blockIdx.z / tiles_n) * WG_TILE, n0 = ((int)blockIdx.z % tiles_n) * WG_TILE;
+    const int tiles = tiles_m * tiles_n;
+    if ((int)blockIdx.z >= groups * tiles) return;
+    const int g = (int)blockIdx.z / tiles, tz = (int)blockIdx.z % tiles;
+    const int m0 = (tz / tiles_n) * WG_TILE, n0 = (tz % tiles_n) * WG_TILE;
     __shared__ __align__(16) float As[WG_ROWS][WG_TILE + 4];
     __shared__ __align__(16) float Bs[WG_ROWS][WG_TILE + 4];
     const int c = blockIdx.x;
-    const int r0 = (int)(((long long)rows * c) / chunks), r1 = (int)(((long long)rows * (c + 1)) / chunks);
+    const int r0 = g * grows + (int)(((long long)grows * c) / chunks);
+    const int r1 = g * grows + (int)(((long long)grows * (c + 1)) / chunks);
     const int ib = threadIdx.x / 16, jbk = threadIdx.x % 16;    // 16 x 16 blocks of 8 x 8
     const int i0 = ib * 8, j0 = jbk * 8;
     const bool active = m0 + i0 < jb.m && n0 + j0 < jb.n;
@@ -327,7 +344,7 @@ __global__ void __launch_bounds__(NTH) wgrad_kernel(WgJobs jobs, int rows, int c
             for (int r = 0; r < nr; ++r) bsum += Bs[r][threadIdx.x];
         __syncthreads();
     }
-    float* out = partial + ((size_t)blockIdx.y * chunks + c) * stride;
+    float* out = partial + (((size_t)blockIdx.y * gmax + g) * chunks + c) * stride;
     if (active) {
 #pragma unroll
         for (int x = 0; x < 8; ++x)
@@ -339,17 +356,65 @@ __global__ void __launch_bounds__(NTH) wgrad_kernel(WgJobs jobs, int rows, int c
         out[(size_t)jb.m * jb.n + n0 + threadIdx.x] = bsum;
 }
 
-__global__ void wgrad_reduce_kernel(WgJobs jobs, int n_jobs, int chunks, size_t stride,
+__global__ void wgrad_reduce_kernel(WgJobs jobs, int n_jobs, int chunks, size_t stride, int gmax,
                                     const float* __restrict__ partial, float* __restrict__ grad) {
     for (int q = 0; q < n_jobs; ++q) {
         const WgJob jb = jobs.job[q];
-        const int total = jb.m * jb.n + jb.n;
-        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+        const int groups = jb.groups > 0 ? jb.groups : 1;
+        const long long total = (long long)jb.m * jb.n + jb.n;
+        for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total * groups;
+             idx += (long long)gridDim.x * blockDim.x) {
+            const int g = (int)(idx / total);
+            const long long k = idx % total;
             float s = 0.0f;
-            for (int c = 0; c < chunks; ++c) s += partial[((size_t)q * chunks + c) * stride + k];
-            if (k < jb.m * jb.n) grad[jb.w_off + k] = s;
-            else if (jb.b_off >= 0) grad[jb.b_off + (k - jb.m * jb.n)] = s;
+            for (int c = 0; c < chunks; ++c) s += partial[(((size_t)q * gmax + g) * chunks + c) * stride + k];
+            float* dst = grad + (size_t)g * jb.w_gstride;
+            if (k < (long long)jb.m * jb.n) dst[jb.w_off + k] = s;
+            else if (jb.b_off >= 0) dst[jb.b_off + (k - (long long)jb.m * jb.n)] = s;
         }
+    }
+}
+
+// Transposes of `count` row-major [rows][cols] matrices, src + q * src_stride
+// to dst + q * rows * cols.
+__global__ void transpose_batched_kernel(const float* __restrict__ src, size_t src_stride, int rows, int cols,
+                                         int count, float* __restrict__ dst) {
+    const size_t per = (size_t)rows * cols;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < per * count;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const size_t q = k / per, e = k % per;
+        const int r = (int)(e / cols), c = (int)(e % cols);
+        dst[q * per + (size_t)c * rows + r] = src[q * src_stride + e];
+    }
+}
+
+// Per-agent advantage moments of a grouped minibatch (one CTA per agent,
+// fixed-order tree reduction), and their totals into the minibatch sums.
+__global__ void agent_moments_kernel(MbDesc d, int agents, const float* __restrict__ adv, double* moments,
+                                     double* stats) {
+    __shared__ double ss[2][NTH];
+    const int agent = blockIdx.x;
+    double s = 0.0, q = 0.0;
+    for (int j = threadIdx.x; j < d.count; j += NTH) {
+        const double v = adv[(size_t)mb_row(d, j) * agents + agent];
+        s += v;
+        q += v * v;
+    }
+    ss[0][threadIdx.x] = s;
+    ss[1][threadIdx.x] = q;
+    __syncthreads();
+    for (int o = NTH / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            ss[0][threadIdx.x] += ss[0][threadIdx.x + o];
+            ss[1][threadIdx.x] += ss[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        moments[2 * agent] = ss[0][0];
+        moments[2 * agent + 1] = ss[1][0];
+        atomicAdd(&stats[ST_ADV_SUM], ss[0][0]);
+        atomicAdd(&stats[ST_ADV_SQ], ss[1][0]);
     }
 }
 
@@ -405,28 +470,36 @@ ej_status launch_minibatch_grad(const FbArgs& fa, const WgJobs& jobs, int n_jobs
     if (fwd_bwd_smem(fa.in_pad, fa.H, fa.O) > 227u * 1024u)
         return fail(EJ_ERR_UNSUPPORTED, "float32 PPO: %d inputs, hidden %d and %d logits need %zu bytes of shared memory "
                     "per 64-row tile (at most %u)", fa.in_dim, fa.H, fa.O, fwd_bwd_smem(fa.in_pad, fa.H, fa.O), 227u * 1024u);
-    // transposed copies of the weights the backward pass multiplies by
-    transpose_kernel<<<64, 256, 0, s>>>(w3, fa.H, fa.O, fa.w3t);
-    transpose_kernel<<<64, 256, 0, s>>>(w2, fa.H, fa.H, fa.w2t);
-    transpose_kernel<<<64, 256, 0, s>>>(v2, fa.H, fa.H, fa.v2t);
+    // transposed copies of the weights the backward pass multiplies by (per agent)
+    const int na = fa.agents ? fa.agents : 1, nc = fa.agents && fa.critic_stride ? fa.agents : 1;
+    transpose_batched_kernel<<<64 * na, 256, 0, s>>>(w3, fa.actor_stride, fa.H, fa.O, na, fa.w3t);
+    transpose_batched_kernel<<<64 * na, 256, 0, s>>>(w2, fa.actor_stride, fa.H, fa.H, na, fa.w2t);
+    transpose_batched_kernel<<<64 * nc, 256, 0, s>>>(v2, fa.critic_stride, fa.H, fa.H, nc, fa.v2t);
     zero_kernel<<<1, 32, 0, s>>>(fa.stats, ST_COUNT_);
-    int grid = (fa.mb.count + 255) / 256;
-    if (grid > device_sms() * 4) grid = device_sms() * 4;
-    adv_stats_kernel<<<grid, 256, 0, s>>>(fa.mb, fa.adv, fa.stats);
+    if (fa.agents) {
+        agent_moments_kernel<<<fa.agents, NTH, 0, s>>>(fa.mb, fa.agents, fa.adv, const_cast<double*>(fa.agent_moments),
+                                                      fa.stats);
+    } else {
+        int grid = (fa.mb.count + 255) / 256;
+        if (grid > device_sms() * 4) grid = device_sms() * 4;
+        adv_stats_kernel<<<grid, 256, 0, s>>>(fa.mb, fa.adv, fa.stats);
+    }
     const size_t smem = fwd_bwd_smem(fa.in_pad, fa.H, fa.O);
     static SmemOptIn opt_in;
     ej_status st = opt_in.ensure((const void*)fwd_bwd_kernel, smem);
     if (st != EJ_OK) return st;
-    const int n_tiles = (fa.mb.count + TILE - 1) / TILE;
+    const int n_tiles = na * ((fa.mb.count + TILE - 1) / TILE);
     int g2 = n_tiles < device_sms() ? n_tiles : device_sms();
     fwd_bwd_kernel<<<g2, NTH, smem, s>>>(fa);
-    int zt = 1;
+    int zt = 1, gmax = 1;
     for (int q = 0; q < n_jobs; ++q) {
-        const int t = ((jobs.job[q].m + WG_TILE - 1) / WG_TILE) * ((jobs.job[q].n + WG_TILE - 1) / WG_TILE);
+        const int g = jobs.job[q].groups > 0 ? jobs.job[q].groups : 1;
+        const int t = g * ((jobs.job[q].m + WG_TILE - 1) / WG_TILE) * ((jobs.job[q].n + WG_TILE - 1) / WG_TILE);
         zt = t > zt ? t : zt;
+        gmax = g > gmax ? g : gmax;
     }
-    wgrad_kernel<<<dim3(chunks, n_jobs, zt), NTH, 0, s>>>(jobs, fa.mb.count, chunks, stride, partial);
-    wgrad_reduce_kernel<<<device_sms(), 256, 0, s>>>(jobs, n_jobs, chunks, stride, partial, grad);
+    wgrad_kernel<<<dim3(chunks, n_jobs, zt), NTH, 0, s>>>(jobs, na * fa.mb.count, chunks, stride, gmax, partial);
+    wgrad_reduce_kernel<<<device_sms() * 4, 256, 0, s>>>(jobs, n_jobs, chunks, stride, gmax, partial, grad);
     return cudaGetLastError() == cudaSuccess ? EJ_OK : fail(EJ_ERR_CUDA, "minibatch gradient launch failed");
 }
 

@@ -56,12 +56,26 @@ struct FbArgs {
     const double* moments;      // NULL, or {count, sum, sum of squares} of the advantages over all ranks
     float* ws_x; float* ws_h1; float* ws_h2; float* ws_g1; float* ws_g2;
     float* ws_dl; float* ws_dz2; float* ws_dz1; float* ws_dy2; float* ws_dy1; float* ws_dv;
+    // Per-agent population networks (Section 5; float32 path only): agents > 0
+    // makes the minibatch the positions [lo, lo + count) of the permutation of
+    // the T x E (step, environment) pairs, taken for every agent (rollout row
+    // = position * agents + agent), tiles of one agent, per-agent advantage
+    // moments (agent_moments[2 i], [2 i + 1]: sum, sum of squares), agent i's
+    // actor at weights + i * actor_stride, critic at + i * critic_stride
+    // (0: one shared critic, whose loss is the mean over all agents' rows),
+    // transposed weights per agent (w3t + i * O * H, w2t + i * H * H,
+    // v2t + i * H * H when the critic is per agent).  Per-row buffers hold
+    // agent i's rows at [i * count, (i + 1) * count).
+    int agents;
+    size_t actor_stride, critic_stride;
+    const double* agent_moments;
 };
 
-__device__ inline void store_tile(const FbArgs& a, const float* buf, int ld, int ncols, float* dst, int j0) {
+// Rows [0, nvalid) of a tile buffer to rows [base, base + nvalid) of a per-row buffer.
+__device__ inline void store_tile(const float* buf, int ld, int ncols, float* dst, int base, int nvalid) {
     for (int idx = threadIdx.x; idx < TILE * ncols; idx += NTH) {
         const int r = idx / ncols, c = idx % ncols;
-        if (j0 + r < a.mb.count) dst[(size_t)(j0 + r) * ncols + c] = buf[r * ld + c];
+        if (r < nvalid) dst[(size_t)(base + r) * ncols + c] = buf[r * ld + c];
     }
 }
 
@@ -88,6 +102,11 @@ struct WgJob {
     const float* A; const float* B;
     int lda, ldb, m, n;
     long long w_off, b_off;      // where the weight and bias gradients go in the gradient vector
+    // groups of rows with gradients of their own (per-agent networks): group g
+    // is rows [g * group_rows, (g + 1) * group_rows) and adds to the gradient
+    // at + g * w_gstride; groups = 0 means one group of all rows
+    int groups, group_rows;
+    long long w_gstride;
 };
 struct WgJobs { WgJob job[6]; };
 
@@ -97,6 +116,8 @@ ej_status launch_gae(const float* rew, const float* value, const uint8_t* done, 
 ej_status launch_minibatch_grad(const FbArgs& fa, const WgJobs& jobs, int n_jobs, float* partial,
                                 size_t stride, int chunks, const float* w2, const float* w3, const float* v2,
                                 float* grad, cudaStream_t s);
+// Per-agent advantage moments of a grouped minibatch into moments[2 * agents].
+ej_status launch_agent_moments(const MbDesc& mb, int agents, const float* adv, double* moments, cudaStream_t s);
 // BF16 tensor-core minibatch gradient (ej_ppo_bf16.cu): advantage statistics,
 // the fused kernel and the reduction into grad; partial: scratch of
 // partial_bytes for the per-CTA accumulators.

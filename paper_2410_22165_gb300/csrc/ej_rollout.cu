@@ -54,6 +54,23 @@ static ej_status make_args(const EjParams* p, const KParams& kp, const Layout& l
     return EJ_OK;
 }
 
+// Per-agent population networks (Section 5): strides of the actor and the
+// critic between the agents' parameter vectors.
+static ej_status agent_layout(const EjParams* p, const KParams& kp, int layout, int hidden, int precision,
+                              PolicyArgs* a) {
+    if (layout == EJ_NETS_SHARED) return EJ_OK;
+    if (layout != EJ_NETS_INDEPENDENT && layout != EJ_NETS_CTDE) return fail(EJ_ERR_ARG, "unknown network layout %d", layout);
+    if (precision != EJ_FP32) return fail(EJ_ERR_UNSUPPORTED, "per-agent networks run in FP32 (precision %d)", precision);
+    int in, O, heads, head;
+    ej_status st = net_shape(p, kp, EJ_NET_POP, hidden, &in, &O, &heads, &head);
+    if (st != EJ_OK) return st;
+    const size_t n = net_offsets(in, hidden, O).total;
+    a->agents = kp.A;
+    a->actor_stride = n;
+    a->critic_stride = layout == EJ_NETS_INDEPENDENT ? n : 0;
+    return EJ_OK;
+}
+
 static ej_status launch_policy(const PolicyArgs& a, int precision, cudaStream_t stream) {
     if (precision == EJ_FP32) return launch_policy_fp32(a, stream);
     if (precision == EJ_BF16) return launch_policy_bf16(a, stream);
@@ -90,6 +107,22 @@ ej_status policy_forward(const EjParams* p, const void* state, int32_t net, int3
     st = make_args(p, kp, lay, state, net, hidden, weights, obs, mask, u, act, logp, value, entropy,
                    logits, &a);
     if (st != EJ_OK) return st;
+    return launch_policy(a, precision, (cudaStream_t)stream);
+}
+
+ej_status policy_forward_agents(const EjParams* p, const void* state, int32_t layout, int32_t hidden,
+                                int32_t precision, const float* weights, const float* obs, const uint32_t* mask,
+                                const float* u, int32_t* act, float* logp, float* value, float* entropy,
+                                float* logits, void* stream) {
+    Layout lay;
+    KParams kp;
+    ej_status st = derive(p, &lay, &kp);
+    if (st != EJ_OK) return st;
+    PolicyArgs a;
+    st = make_args(p, kp, lay, state, EJ_NET_POP, hidden, weights, obs, mask, u, act, logp, value, entropy,
+                   logits, &a);
+    if (st != EJ_OK) return st;
+    if ((st = agent_layout(p, kp, layout, hidden, precision, &a)) != EJ_OK) return st;
     return launch_policy(a, precision, (cudaStream_t)stream);
 }
 
@@ -167,7 +200,7 @@ namespace {
 // environments, then their bootstrap values, on one stream.
 ej_status rollout_range(const EjParams* p, const KParams& kp, const Layout& lay, void* state, int T, int hidden,
                         int precision, const float* pop_weights, const float* gov_weights, const EjRollout* b,
-                        int e0, int ne, cudaStream_t s) {
+                        int e0, int ne, cudaStream_t s, int layout = EJ_NETS_SHARED) {
     const size_t EA = (size_t)kp.E * kp.A, A = kp.A;
     const DevState ds = state_pointers(lay, state);
     KParams kr = kp;
@@ -182,6 +215,7 @@ ej_status rollout_range(const EjParams* p, const KParams& kp, const Layout& lay,
                        b->mask + (t * EA + r0) * kp.W, nullptr, last ? nullptr : b->act + t * EA + r0,
                        last ? nullptr : b->logp + t * EA + r0, b->value + t * EA + r0, nullptr, nullptr, &pa);
         if (st != EJ_OK) return st;
+        if ((st = agent_layout(p, kp, layout, hidden, precision, &pa)) != EJ_OK) return st;
         pa.rows = ne * kp.A;
         pa.env0 = e0;
         const size_t g0 = (size_t)t * kp.E + e0;    // first government row of the range
@@ -284,6 +318,27 @@ ej_status rollout_split(const EjParams* p, void* state, int32_t T, int32_t hidde
             return fail(EJ_ERR_CUDA, "rollout: join failed");
     }
     return EJ_OK;
+}
+
+ej_status rollout_agents(const EjParams* p, void* state, int32_t T, int32_t hidden, int32_t precision,
+                         int32_t layout, const float* pop_weights, const float* gov_weights, const EjRollout* b,
+                         void* stream) {
+    if (layout == EJ_NETS_SHARED) return rollout(p, state, T, hidden, precision, pop_weights, gov_weights, b, stream);
+    Layout lay;
+    KParams kp;
+    ej_status st = derive(p, &lay, &kp);
+    if (st != EJ_OK) return st;
+    if (!b || !state || !pop_weights || !gov_weights) return fail(EJ_ERR_ARG, "rollout: NULL argument");
+    if (T < 1) return fail(EJ_ERR_ARG, "rollout: T must be >= 1");
+    if (!b->obs || !b->gobs || !b->mask || !b->act || !b->gact || !b->logp || !b->glogp ||
+        !b->value || !b->gvalue || !b->rew || !b->grew || !b->done)
+        return fail(EJ_ERR_ARG, "rollout: every buffer is required");
+    if ((uintptr_t)state % 256) return fail(EJ_ERR_ARG, "state must be 256-byte aligned");
+    PolicyArgs probe;
+    memset(&probe, 0, sizeof probe);
+    if ((st = agent_layout(p, kp, layout, hidden, precision, &probe)) != EJ_OK) return st;
+    return rollout_range(p, kp, lay, state, T, hidden, precision, pop_weights, gov_weights, b, 0, kp.E,
+                         (cudaStream_t)stream, layout);
 }
 
 ej_status rollout(const EjParams* p, void* state, int32_t T, int32_t hidden, int32_t precision,

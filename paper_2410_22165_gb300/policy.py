@@ -9,22 +9,28 @@ from . import _native as N
 from .env import VecEnv, _ptr, _stream
 
 PRECISION = {"fp32": N.FP32, "bf16": N.BF16}
+LAYOUT = {"shared": N.NETS_SHARED, "independent": N.NETS_INDEPENDENT, "ctde": N.NETS_CTDE}
 
 
 class Policy:
     """Population and government actor/critic weights (device, float32 vectors
-    in the documented layout) and their forward pass."""
+    in the documented layout) and their forward pass.  layout (Section 5):
+    "shared" (one population network), "independent" (an actor and a critic
+    per agent) or "ctde" (an actor per agent, one critic); per-agent weights
+    are A vectors, [A * n_pop] floats."""
 
     def __init__(self, env: VecEnv, pop_weights: torch.Tensor, gov_weights: torch.Tensor,
-                 hidden: int = 128, precision: str = "fp32"):
+                 hidden: int = 128, precision: str = "fp32", layout: str = "shared"):
         self.env = env
         self.hidden = hidden
         self.precision = PRECISION[precision]
+        self.layout = LAYOUT[layout]
         self.n_pop = self.net_floats(env, N.NET_POP, hidden)
         self.n_gov = self.net_floats(env, N.NET_GOV, hidden)
         self.pop_w = pop_weights.to(env.device, torch.float32).contiguous()
         self.gov_w = gov_weights.to(env.device, torch.float32).contiguous()
-        assert self.pop_w.numel() == self.n_pop and self.gov_w.numel() == self.n_gov
+        groups = 1 if self.layout == N.NETS_SHARED else env.A
+        assert self.pop_w.numel() == self.n_pop * groups and self.gov_w.numel() == self.n_gov
 
     @staticmethod
     def net_floats(env, net, hidden):
@@ -48,12 +54,15 @@ class Policy:
         if logits:
             out["logits"] = torch.empty((rows, O), dtype=torch.float32, device=dev)
         w = self.pop_w if net == N.NET_POP else self.gov_w
-        N.check(N.load().policy_forward(
-            C.byref(env.p), _ptr(env.state), net, self.hidden, self.precision, _ptr(w),
-            _ptr(obs.contiguous()), _ptr(None if mask is None else mask.contiguous()),
-            _ptr(None if u is None else u.contiguous()), _ptr(out.get("act")), _ptr(out.get("logp")),
-            _ptr(out["value"]), _ptr(out.get("entropy")), _ptr(out.get("logits")), _stream(stream)),
-            "policy_forward")
+        rest = (_ptr(obs.contiguous()), _ptr(None if mask is None else mask.contiguous()),
+                _ptr(None if u is None else u.contiguous()), _ptr(out.get("act")), _ptr(out.get("logp")),
+                _ptr(out["value"]), _ptr(out.get("entropy")), _ptr(out.get("logits")), _stream(stream))
+        if net == N.NET_POP and self.layout != N.NETS_SHARED:
+            N.check(N.load().policy_forward_agents(C.byref(env.p), _ptr(env.state), self.layout, self.hidden,
+                                                   self.precision, _ptr(w), *rest), "policy_forward_agents")
+        else:
+            N.check(N.load().policy_forward(C.byref(env.p), _ptr(env.state), net, self.hidden, self.precision,
+                                            _ptr(w), *rest), "policy_forward")
         return out
 
 
@@ -123,6 +132,11 @@ class Rollout:
         pol = self.policy
         n = self.chains if chains is None else chains
         lib = N.load()
+        if pol.layout != N.NETS_SHARED:
+            N.check(lib.rollout_agents(C.byref(self.env.p), _ptr(self.env.state), self.T, pol.hidden, pol.precision,
+                                       pol.layout, _ptr(pol.pop_w), _ptr(pol.gov_w), C.byref(self._c),
+                                       _stream(stream)), "rollout_agents")
+            return self.buf
         args = (C.byref(self.env.p), _ptr(self.env.state), self.T, pol.hidden, pol.precision, _ptr(pol.pop_w),
                 _ptr(pol.gov_w), C.byref(self._c))
         if n is None:

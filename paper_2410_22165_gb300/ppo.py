@@ -26,8 +26,9 @@ class PPO:
                 raise KeyError(k)
             setattr(self.pp, k, v)
         nbytes = C.c_uint64()
-        N.check(N.load().ej_ppo_workspace_bytes(C.byref(self.env.p), C.byref(self.pp), T, policy.hidden,
-                                                C.byref(nbytes)), "ej_ppo_workspace_bytes")
+        self.layout = policy.layout
+        N.check(N.load().ej_ppo_workspace_bytes_agents(C.byref(self.env.p), C.byref(self.pp), T, policy.hidden,
+                                                       self.layout, C.byref(nbytes)), "ej_ppo_workspace_bytes_agents")
         dev = self.env.device
         self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=dev)
         self.m = [torch.zeros_like(policy.pop_w), torch.zeros_like(policy.gov_w)]
@@ -52,9 +53,14 @@ class PPO:
                     gadv=view(o[2], T * E).view(T, E), gret=view(o[3], T * E).view(T, E))
 
     def minibatch_rows(self, net: int, minibatch: int) -> int:
-        """Rows of minibatch `minibatch` (floor((m+1)N/M) - floor(mN/M))."""
-        n = self.T * (self.env.E * self.env.A if net == N.NET_POP else self.env.E)
+        """Rows of minibatch `minibatch` (floor((m+1)N/M) - floor(mN/M)); for
+        per-agent population networks, A times the positions of the T x E
+        (step, environment) permutation."""
         M = self.pp.minibatches
+        if net == N.NET_POP and self.layout != N.NETS_SHARED:
+            n = self.T * self.env.E
+            return self.env.A * ((minibatch + 1) * n // M - minibatch * n // M)
+        n = self.T * (self.env.E * self.env.A if net == N.NET_POP else self.env.E)
         return (minibatch + 1) * n // M - minibatch * n // M
 
     def minibatch_moments(self, rollout: Rollout, net: int, shuffle_ctr: int, minibatch: int, stream=None):
@@ -77,7 +83,14 @@ class PPO:
         grad = torch.empty_like(w)
         stats = torch.empty(8, dtype=torch.float64, device=w.device)
         lib = N.load()
-        if moments is None:
+        if net == N.NET_POP and self.layout != N.NETS_SHARED:
+            if moments is not None:
+                raise NotImplementedError("data-parallel moments with per-agent networks")
+            N.check(lib.ppo_minibatch_grad_agents(C.byref(self.env.p), C.byref(self.pp), self.T, pol.hidden,
+                                                  self.precision, self.layout, _ptr(w), C.byref(rollout._c),
+                                                  _ptr(self.workspace), shuffle_ctr, minibatch, _ptr(grad),
+                                                  _ptr(stats), _stream(stream)), "ppo_minibatch_grad_agents")
+        elif moments is None:
             N.check(lib.ppo_minibatch_grad(C.byref(self.env.p), C.byref(self.pp), self.T, pol.hidden,
                                            self.precision, net, _ptr(w), C.byref(rollout._c),
                                            _ptr(self.workspace), shuffle_ctr, minibatch, _ptr(grad),
@@ -106,11 +119,11 @@ class PPO:
     def update(self, rollout: Rollout, stream=None):
         pol = self.policy
         stats = torch.empty((2, 8), dtype=torch.float32, device=pol.pop_w.device)
-        N.check(N.load().ppo_update(C.byref(self.env.p), C.byref(self.pp), self.T, pol.hidden, self.precision,
-                                    _ptr(pol.pop_w), _ptr(pol.gov_w), _ptr(self.m[0]), _ptr(self.v[0]),
-                                    _ptr(self.m[1]), _ptr(self.v[1]), self.adam_steps, self.updates,
-                                    C.byref(rollout._c), _ptr(self.workspace), _ptr(stats), _stream(stream)),
-                "ppo_update")
+        N.check(N.load().ppo_update_agents(C.byref(self.env.p), C.byref(self.pp), self.T, pol.hidden, self.precision,
+                                           self.layout, _ptr(pol.pop_w), _ptr(pol.gov_w), _ptr(self.m[0]),
+                                           _ptr(self.v[0]), _ptr(self.m[1]), _ptr(self.v[1]), self.adam_steps,
+                                           self.updates, C.byref(rollout._c), _ptr(self.workspace), _ptr(stats),
+                                           _stream(stream)), "ppo_update_agents")
         self.adam_steps += self.pp.epochs * self.pp.minibatches
         self.updates += 1
         return stats
