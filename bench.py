@@ -238,6 +238,7 @@ def run_gpu(args):
         line["section5"] = run_section5(args, dev)
         if args.train_updates > 0 and world == 1:
             line["training"] = run_training(args, dev)
+        line["multi_agent"] = run_multi_agent(args, dev)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if world > 1:
@@ -445,13 +446,15 @@ def run_paper_training(args, dev):
     from paper_2410_22165_gb300.train import Trainer
 
     E_t, T_t = args.paper_envs, 150
+    skills = {"uniform": 0, "normal": 1}[args.paper_skills]
     iters = int(round(args.paper_env_steps / (E_t * T_t)))
     out = {"workload": f"Section 4 training: {E_t} environments x {A} agents, rollouts of {T_t} steps, "
                        f"{iters} iterations = {iters * E_t * T_t:.3g} environment steps, 6 epochs x 6 minibatches, "
-                       "gamma 0.999, lr 5e-4 and entropy 0.1 annealed (Table 2), BF16",
+                       "gamma 0.999, lr 5e-4 and entropy 0.1 annealed (Table 2), BF16, skills "
+                       + ("U[0,1)" if skills == 0 else "around 1 with sd 1 (Section 5's reading)"),
            "precision": "bf16"}
     for label, taxes in (("taxes", True), ("free_market", False)):
-        env = VecEnv(E_t, A, device=dev, T_ep=T_EP, T_tax=T_TAX, gov_enabled=1 if taxes else 0)
+        env = VecEnv(E_t, A, device=dev, T_ep=T_EP, T_tax=T_TAX, gov_enabled=1 if taxes else 0, skill_init=skills)
         pw = torch.from_numpy(synth.net_weights(args.paper_seed, 0, env.D, 128, env.nA))
         gw = torch.from_numpy(synth.net_weights(args.paper_seed, 1, env.G, 128, env.p.nb * env.p.tax_levels))
         pol = Policy(env, pw, gw, hidden=128, precision="bf16")
@@ -462,6 +465,54 @@ def run_paper_training(args, dev):
         out[label] = dict(tr.summary(), wall_s=wall,
                           agent_steps_per_s=iters * E_t * T_t * A / wall)
         del tr, pol, env
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_multi_agent(args, dev, E_m=256, T_m=32, H_m=256, seed=6000):
+    """Section 5's three multi-agent methods on its 4-resource market (30
+    actions, prices 3, 6, 9, no taxes, skills around 1 growing by 0.5 %,
+    networks of 256 units), float32: one training iteration (a T_m-step
+    rollout of E_m x A agents, then a PPO update, 4 epochs x 8 minibatches)
+    with the population's networks shared, independent (an actor and a critic
+    per agent) and CTDE (an actor per agent, one critic)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2410_22165_gb300 import PPO, Policy, Rollout, VecEnv
+
+    out = {"workload": f"Section 5: E={E_m} x A={A}, R=4 (30 actions), no taxes, skills around 1 growing, "
+                       f"hidden {H_m}, FP32, {T_m}-step rollout + PPO update (4 epochs x 8 minibatches)"}
+    kw = dict(R=4, P=3, price_ticks=[1, 2, 3], price_tick=3.0, Rd=2, gov_enabled=0, skill_gain=0.005,
+              skill_init=1, T_ep=T_EP, T_tax=T_TAX)
+    env = VecEnv(E_m, A, device=dev, **kw)
+    shared = synth.net_weights(seed, 0, env.D, H_m, env.nA)
+    per_agent = np.concatenate([synth.net_weights(seed, 10 + i, env.D, H_m, env.nA) for i in range(A)])
+    gw = torch.from_numpy(synth.net_weights(seed, 1, env.G, H_m, env.p.nb * env.p.tax_levels))
+    del env
+    for layout in ("shared", "independent", "ctde"):
+        env = VecEnv(E_m, A, device=dev, **kw)
+        pw = torch.from_numpy(shared if layout == "shared" else per_agent)
+        pol = Policy(env, pw, gw, hidden=H_m, precision="fp32", layout=layout)
+        ro = Rollout(env, pol, T_m)
+        ro.reset(seed=seed)
+        ro.run()
+        ppo = PPO(pol, T_m, precision="fp32")
+        ppo.update(ro)
+        torch.cuda.synchronize(dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        ro.carry_over()
+        ro.run()
+        ev[1].record()
+        ppo.update(ro)
+        ev[2].record()
+        torch.cuda.synchronize(dev)
+        ro_ms, up_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        out[layout] = {"rollout_ms": ro_ms, "update_ms": up_ms, "population_parameters": int(pw.numel()),
+                       "train_agent_steps_per_s": E_m * A * T_m / ((ro_ms + up_ms) / 1e3)}
+        del ppo, ro, pol, env
         torch.cuda.empty_cache()
     return out
 
@@ -738,6 +789,7 @@ def main():
     ap.add_argument("--paper-envs", type=int, default=10)
     ap.add_argument("--paper-env-steps", type=float, default=1e7)
     ap.add_argument("--paper-seed", type=int, default=7)
+    ap.add_argument("--paper-skills", default="uniform", choices=["uniform", "normal"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     args = ap.parse_args()
