@@ -229,6 +229,7 @@ def run_gpu(args):
     if not args.no_train:
         del d, out
         torch.cuda.empty_cache()
+        line["single_step"] = run_single_step(args, dev)
         line["rollout"] = {"workload": "E=4096 x A=100, 1000 steps: policy + sampling + government policy + "
                                        "env_step per step",
                            "bf16": run_rollout(args, dev, "bf16"), "fp32": run_rollout(args, dev, "fp32")}
@@ -244,6 +245,61 @@ def run_gpu(args):
     if world > 1:
         dist.destroy_process_group()
     return line
+
+
+def run_single_step(args, dev, seed=1000):
+    """env_step in single-step mode: the headline workload (E x A, one
+    1000-step episode, every output) with one launch per step, so that the
+    state goes through HBM every step; the 1000 launches are one CUDA graph.
+    Algorithmic bytes per launch: the step's inputs and outputs plus one load
+    and one store of the state without the order book (whose live part
+    varies; leaving it out keeps the figure a lower bound)."""
+    import torch
+
+    from paper_2410_22165_gb300 import VecEnv
+    from paper_2410_22165_gb300 import _native as N
+
+    env = VecEnv(E, A, device=dev, T_ep=T_EP, T_tax=T_TAX)
+    env.reset(seed=seed)
+    d = env.fill_draws(seed=seed, g0=0, n_steps=T_EP)
+    out = env.alloc_outputs(T_EP)
+
+    def episode(stream=None):
+        for t in range(T_EP):
+            env.step(1, act=d["act"][t:t + 1], gov_act=d["gov_act"][t:t + 1], gather_u=d["gather_u"][t:t + 1],
+                     tb=d["tb"][t:t + 1], out={k: v[t:t + 1] for k, v in out.items()}, stream=stream)
+
+    episode()
+    torch.cuda.synchronize(dev)
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            episode(stream=s)
+    torch.cuda.current_stream(dev).wait_stream(s)
+    g.replay()
+    torch.cuda.synchronize(dev)
+    steps = max(1, min(args.steps, 3))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        g.replay()
+    b.record()
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / steps
+    off, cnt, esz = N.state_field(env.p, "book")
+    state_wo_book = env.sizes.state_bytes - cnt * esz
+    per_launch = algorithmic_bytes_per_launch(env.sizes, 1, state_wo_book)
+    peak, kind = _peaks()
+    achieved = per_launch * T_EP / (ms / 1e3) / 1e9
+    out_d = {"workload": f"env_step E={E} x A={A}, one launch per step over a {T_EP}-step episode (one CUDA graph)",
+             "value": E * A * T_EP / (ms / 1e3), "unit": UNIT, "ms_per_episode": ms, "launches_per_episode": T_EP,
+             "algorithmic_bytes_per_launch": per_launch, "achieved_GBps": achieved, "frac_of_hbm": achieved / peak,
+             "peak_source": f"{kind} hbm_gbs"}
+    del g, out, d, env
+    torch.cuda.empty_cache()
+    return out_d
 
 
 def run_rollout(args, dev, precision, E_r=4096, T_r=1000, seed=2000):
@@ -575,10 +631,12 @@ def run_batched(args, dev, E_b=2048, T_b=1000, seed=4000):
                                                                probe.p.nb * probe.p.tax_levels))
         del probe
     kw = dict(T_ep=T_EP, T_tax=T_TAX)
-    best, rates = autotune(pops, levels, weights, T_probe=8, repeats=2, device=dev,
-                           candidates=("exact", "pow2", "coarse", "exact+merge", "coarse+merge"), **kw)
-    gran, _, merged = best.partition("+")
-    br = BatchedRollout(pops, levels, T_b, weights, granularity=gran, merge=bool(merged), device=dev, **kw)
+    from paper_2410_22165_gb300.batch import parse_candidate
+    best, rates = autotune(pops, levels, weights, T_probe=8, repeats=5, device=dev,
+                           candidates=("exact", "pow2", "coarse", "exact+merge", "coarse+merge", "exact+chains1",
+                                       "exact+chains2", "pow2+chains2"), **kw)
+    gran, merged, chains = parse_candidate(best)
+    br = BatchedRollout(pops, levels, T_b, weights, granularity=gran, merge=merged, chains=chains, device=dev, **kw)
     br.reset(seed=seed)
     br.capture()
     torch.cuda.synchronize(dev)

@@ -72,12 +72,15 @@ def plan_classes(pops, levels, granularity):
 
 class BatchedRollout:
     def __init__(self, pops, levels, T, weights, hidden=128, precision="bf16", granularity="pow2",
-                 device="cuda", merge=False, **env_kw):
-        """weights: {("pop", P): tensor, ("gov",): tensor} in the library's layout."""
+                 device="cuda", merge=False, chains=None, **env_kw):
+        """weights: {("pop", P): tensor, ("gov",): tensor} in the library's layout.
+        chains: independent chains of environments per class rollout (1..4;
+        None: the library's choice), for the per-class (unmerged) rollouts."""
         self.pops, self.levels, self.T = list(pops), list(levels), T
         self.device = torch.device(device)
         self.granularity = granularity
         self.merge = merge
+        self.chains = chains
         # one device copy per network: classes with the same price grid share it
         weights = {k: v.to(self.device, torch.float32).contiguous() for k, v in weights.items()}
         self.classes = []
@@ -85,6 +88,7 @@ class BatchedRollout:
             env = VecEnv(len(idx), A_max, device=self.device, **price_grid(P), **env_kw)
             pol = Policy(env, weights[("pop", P)], weights[("gov",)], hidden=hidden, precision=precision)
             ro = Rollout(env, pol, T)
+            ro.chains = None if chains is None else max(1, min(int(chains), len(idx)))
             pop = torch.tensor([self.pops[e] for e in idx], dtype=torch.int32, device=self.device)
             self.classes.append(dict(P=P, A_max=A_max, idx=idx, env=env, policy=pol, ro=ro, pop=pop,
                                      stream=torch.cuda.Stream(device=self.device)))
@@ -176,27 +180,54 @@ class BatchedRollout:
 
 
 
-def autotune(pops, levels, weights, T_probe=8, hidden=128, precision="bf16", candidates=None,
-             device="cuda", repeats=3, **env_kw):
-    """Times a captured T_probe-step batched rollout per candidate; returns
-    (best candidate, {candidate: agent-steps/s}).  A candidate is a partition
-    granularity, with "+merge" for merged policy launches ("exact+merge")."""
-    candidates = candidates or ("exact", "pow2", "coarse", "by_actions", "exact+merge", "coarse+merge")
-    rates = {}
-    for cand in candidates:
-        gran, _, merged = cand.partition("+")
-        if merged not in ("", "merge"):
+def parse_candidate(cand: str):
+    """"gran[+merge][+chainsN]" -> (granularity, merge, chains)."""
+    parts = cand.split("+")
+    gran, merge, chains = parts[0], False, None
+    plan_classes([1], [5], gran)                       # validates the granularity
+    for p in parts[1:]:
+        if p == "merge":
+            merge = True
+        elif p.startswith("chains") and p[6:].isdigit() and 1 <= int(p[6:]) <= 4:
+            chains = int(p[6:])
+        else:
             raise ValueError(cand)
+    if merge and chains is not None:
+        raise ValueError(f"{cand}: merged launches have no per-class chains")
+    return gran, merge, chains
+
+
+def autotune(pops, levels, weights, T_probe=8, hidden=128, precision="bf16", candidates=None,
+             device="cuda", repeats=5, **env_kw):
+    """Times a captured T_probe-step batched rollout per candidate (CUDA
+    events on the replaying stream, the median of `repeats` replays); returns
+    (best candidate, {candidate: agent-steps/s}).  A candidate is a partition
+    granularity (the environment CTA size of each class follows from it),
+    with "+merge" for merged policy launches ("exact+merge") or "+chainsN"
+    for N independent environment chains per class rollout (policy and
+    env_step of different chains overlapping)."""
+    candidates = candidates or ("exact", "pow2", "coarse", "by_actions", "exact+merge", "coarse+merge",
+                                "exact+chains1", "exact+chains2", "pow2+chains2")
+    rates = {}
+    parsed = {cand: parse_candidate(cand) for cand in candidates}    # every name checked before any work
+    for cand in candidates:
+        gran, merged, chains = parsed[cand]
         br = BatchedRollout(pops, levels, T_probe, weights, hidden=hidden, precision=precision,
-                            granularity=gran, merge=bool(merged), device=device, **env_kw)
+                            granularity=gran, merge=merged, chains=chains, device=device, **env_kw)
         br.reset(seed=1)
         br.capture()
+        br.run()
         torch.cuda.synchronize(device)
-        t0 = time.perf_counter()
+        ms = []
         for _ in range(repeats):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
             br.run()
-        torch.cuda.synchronize(device)
-        rates[cand] = br.agent_steps * repeats / (time.perf_counter() - t0)
+            b.record()
+            torch.cuda.synchronize(device)
+            ms.append(a.elapsed_time(b))
+        ms.sort()
+        rates[cand] = br.agent_steps / (ms[len(ms) // 2] / 1e3)
         del br
         torch.cuda.empty_cache()
     best = max(rates, key=rates.get)

@@ -55,3 +55,15 @@ def test_price_grids():
 def test_autotune_refuses_unknown_candidates_before_any_work():
     with pytest.raises(ValueError):
         autotune(POPS, LEVELS, {}, candidates=("exact+fast",), device="cpu")
+
+
+def test_candidate_names():
+    from paper_2410_22165_gb300.batch import parse_candidate
+    assert parse_candidate("exact") == ("exact", False, None)
+    assert parse_candidate("coarse+merge") == ("coarse", True, None)
+    assert parse_candidate("pow2+chains3") == ("pow2", False, 3)
+    for bad in ("exact+chains5", "exact+chains0", "exact+merge+chains2", "tiny", "exact+fast"):
+        with pytest.raises(ValueError):
+            parse_candidate(bad)
+    with pytest.raises(ValueError):              # a bad name later in the list: refused before any work
+        autotune(POPS, LEVELS, {}, candidates=("exact", "pow2+chains9"), device="cpu")

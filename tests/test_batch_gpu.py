@@ -114,3 +114,24 @@ def test_merged_policy_launches_equal_per_class_rollouts(granularity):
         for n, v in ca["ro"].buf.items():
             assert torch.equal(v, cb["ro"].buf[n]), n
         assert torch.equal(ca["env"].state, cb["env"].state)
+
+
+def test_chains_per_class_equal_one_chain():
+    """Class rollouts split into 2 and 3 chains of environments (the
+    autotuner's "+chainsN" candidates) give the one-chain buffers and states
+    bit for bit (environments do not interact; draws are per environment)."""
+    import paper_2410_22165_gb300 as P
+    T = 6
+    kw = dict(T_ep=5, T_tax=3)
+    w = _weights(7)
+    runs = [P.BatchedRollout(POPS, LEVELS, T, w, granularity="exact", chains=c, **kw) for c in (1, 2, 3)]
+    for r in runs:
+        r.reset(seed=21)
+        r.run()
+        r.run()
+    torch.cuda.synchronize()
+    for other in runs[1:]:
+        for ca, cb in zip(runs[0].classes, other.classes):
+            for n, v in ca["ro"].buf.items():
+                assert torch.equal(v, cb["ro"].buf[n]), n
+            assert torch.equal(ca["env"].state, cb["env"].state)
