@@ -503,14 +503,17 @@ def run_paper_training(args, dev):
 
     E_t, T_t = args.paper_envs, 150
     skills = {"uniform": 0, "normal": 1}[args.paper_skills]
+    th = [float(x) for x in args.paper_thresholds.split(",")]
     iters = int(round(args.paper_env_steps / (E_t * T_t)))
     out = {"workload": f"Section 4 training: {E_t} environments x {A} agents, rollouts of {T_t} steps, "
                        f"{iters} iterations = {iters * E_t * T_t:.3g} environment steps, 6 epochs x 6 minibatches, "
                        "gamma 0.999, lr 5e-4 and entropy 0.1 annealed (Table 2), BF16, skills "
-                       + ("U[0,1)" if skills == 0 else "around 1 with sd 1 (Section 5's reading)"),
+                       + ("U[0,1)" if skills == 0 else "around 1 with sd 1 (Section 5's reading)")
+                       + f", bracket edges {th}",
            "precision": "bf16"}
     for label, taxes in (("taxes", True), ("free_market", False)):
-        env = VecEnv(E_t, A, device=dev, T_ep=T_EP, T_tax=T_TAX, gov_enabled=1 if taxes else 0, skill_init=skills)
+        env = VecEnv(E_t, A, device=dev, T_ep=T_EP, T_tax=T_TAX, gov_enabled=1 if taxes else 0, skill_init=skills,
+                     thresholds=th)
         pw = torch.from_numpy(synth.net_weights(args.paper_seed, 0, env.D, 128, env.nA))
         gw = torch.from_numpy(synth.net_weights(args.paper_seed, 1, env.G, 128, env.p.nb * env.p.tax_levels))
         pol = Policy(env, pw, gw, hidden=128, precision="bf16")
@@ -848,6 +851,9 @@ def main():
     ap.add_argument("--paper-env-steps", type=float, default=1e7)
     ap.add_argument("--paper-seed", type=int, default=7)
     ap.add_argument("--paper-skills", default="uniform", choices=["uniform", "normal"])
+    ap.add_argument("--paper-thresholds", default="50,100",
+                    help="tax bracket edges (default: the worked example's; the paper's Dutch 2025 brackets / 100 "
+                         "are not printed)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     args = ap.parse_args()
