@@ -31,12 +31,13 @@ sys.path.insert(0, ROOT)
 METRIC = "agent-steps/sec (env_step and full rollout) on 1 GB300; PPO updates/sec BF16 vs FP32"
 UNIT = "agent-steps/s"
 # DRAM bytes (read + write) of the environment kernel measured with ncu on the
-# 100-step profile case (E = 1024, A = 100: 129.45 MB read, 1059.78 MB written);
+# 100-step profile case (E = 1024, A = 100: 129.35 MB read, 1059.60 MB written);
 # traffic grows with the steps of a launch (state load/store is once per launch
 # and small), so a launch of n steps is reported as n/100 times this.  It
-# belongs to the kernel version it was taken on (env_kernel<128, 2, 5>, 6.69 k
-# warp instructions per environment-step) and is re-taken when that changes.
-ENV_DRAM_BYTES_PER_100_STEPS = 130012928 + 1059629312
+# belongs to the kernel version it was taken on (env_kernel<128, 2, 5> version
+# 4.1, 6.00 k warp instructions per environment-step) and is re-taken when that
+# changes.
+ENV_DRAM_BYTES_PER_100_STEPS = 129354752 + 1059601664
 E, A, T_EP, T_TAX = 1024, 100, 1000, 100
 CONFIG = {"workload": "env_step E=1024 x A=100 (+1 government), R=2, P=5, 1000-step episode, "
                       "tax period 100, uniform random seeded actions; one benchmark step = one episode "

@@ -330,7 +330,10 @@ ej_status policy_segmented(const EjParams* p, int32_t net, int32_t hidden, int32
  * is vector i's actor part; its critic is vector i's critic part
  * (independent) or vector 0's (CTDE, whose other critic parts are unused and
  * get zero gradients).  The government network stays one shared vector.
- * Per-agent networks run in FP32 (EJ_BF16 returns EJ_ERR_UNSUPPORTED). */
+ * The forward and the rollout take FP32 or BF16 (BF16: hidden 64 or 128; the
+ * tensor-core kernel walks agent-major tiles, a contiguous range per CTA, and
+ * packs an agent's weights when its tiles begin); the PPO gradient and update
+ * of per-agent networks are FP32 (EJ_BF16 returns EJ_ERR_UNSUPPORTED). */
 typedef enum { EJ_NETS_SHARED = 0, EJ_NETS_INDEPENDENT = 1, EJ_NETS_CTDE = 2 } ej_net_layout;
 
 /* policy_forward of the population network under `layout` (EJ_NETS_SHARED:
@@ -377,7 +380,7 @@ ej_status rollout(const EjParams* p, void* state, int32_t T, int32_t hidden, int
 
 /* rollout_agents: rollout with the population's networks in `layout`
  * (EJ_NETS_SHARED: rollout itself); pop_weights as policy_forward_agents'.
- * One chain of 3T + 2 launches on `stream` (FP32). */
+ * One chain of 3T + 2 launches on `stream`. */
 ej_status rollout_agents(const EjParams* p, void* state, int32_t T, int32_t hidden, int32_t precision,
                          int32_t layout, const float* pop_weights, const float* gov_weights, const EjRollout* buf,
                          void* stream);

@@ -156,31 +156,36 @@ __global__ void __launch_bounds__(BT, 1) policy_bf16_kernel(PolicyArgs a) {
     const int H = a.H, O = a.O, I = a.in_dim;
     const BfLayout L = bf_layout(H, O);
     const NetOffsets off = net_offsets(I, H, O);
-    const float* w = a.weights;
     const int ldo = O | 1;
-
-    // weights -> shared memory, BF16, K-major (row n of B = output unit n)
-    pack_operand(smem + L.w1, 2 * H, KX, [&](int n, int k) {
-        if (k >= I) return 0.0f;
-        return n < H ? __ldg(w + off.W1 + (size_t)k * H + n) : __ldg(w + off.V1 + (size_t)k * H + (n - H));
-    });
-    pack_operand(smem + L.w2a, H, H, [&](int n, int k) { return __ldg(w + off.W2 + (size_t)k * H + n); });
-    pack_operand(smem + L.w2c, H, H, [&](int n, int k) { return __ldg(w + off.V2 + (size_t)k * H + n); });
-    pack_operand(smem + L.w3, L.N3, H, [&](int n, int k) {
-        return n < O ? __ldg(w + off.W3 + (size_t)k * O + n) : 0.0f;
-    });
-    pack_operand(smem + L.v3, 16, H, [&](int n, int k) { return n == 0 ? __ldg(w + off.V3 + k) : 0.0f; });
     float* bias = (float*)(smem + L.bias);           // [b1 | c1 | b2 | c2 | b3 | c3]
-    for (int k = tid; k < 4 * H + O + 1; k += BT) {
-        float v;
-        if (k < H) v = w[off.b1 + k];
-        else if (k < 2 * H) v = w[off.c1 + k - H];
-        else if (k < 3 * H) v = w[off.b2 + k - 2 * H];
-        else if (k < 4 * H) v = w[off.c2 + k - 3 * H];
-        else if (k < 4 * H + O) v = w[off.b3 + k - 4 * H];
-        else v = w[off.c3];
-        bias[k] = v;
-    }
+
+    // weights -> shared memory, BF16, K-major (row n of B = output unit n): the
+    // actor of w and the critic of wc (per-agent networks: packed again
+    // whenever a tile's agent differs from the last one's)
+    auto pack_weights = [&](const float* w, const float* wc) {
+        pack_operand(smem + L.w1, 2 * H, KX, [&](int n, int k) {
+            if (k >= I) return 0.0f;
+            return n < H ? __ldg(w + off.W1 + (size_t)k * H + n) : __ldg(wc + off.V1 + (size_t)k * H + (n - H));
+        });
+        pack_operand(smem + L.w2a, H, H, [&](int n, int k) { return __ldg(w + off.W2 + (size_t)k * H + n); });
+        pack_operand(smem + L.w2c, H, H, [&](int n, int k) { return __ldg(wc + off.V2 + (size_t)k * H + n); });
+        pack_operand(smem + L.w3, L.N3, H, [&](int n, int k) {
+            return n < O ? __ldg(w + off.W3 + (size_t)k * O + n) : 0.0f;
+        });
+        pack_operand(smem + L.v3, 16, H, [&](int n, int k) { return n == 0 ? __ldg(wc + off.V3 + k) : 0.0f; });
+        for (int k = tid; k < 4 * H + O + 1; k += BT) {
+            float v;
+            if (k < H) v = w[off.b1 + k];
+            else if (k < 2 * H) v = wc[off.c1 + k - H];
+            else if (k < 3 * H) v = w[off.b2 + k - 2 * H];
+            else if (k < 4 * H) v = wc[off.c2 + k - 3 * H];
+            else if (k < 4 * H + O) v = w[off.b3 + k - 4 * H];
+            else v = wc[off.c3];
+            bias[k] = v;
+        }
+    };
+    pack_weights(a.weights, a.weights);
+    int packed = 0;                                  // agent whose weights are packed
     // padding columns of the observation operand stay zero for every tile
     for (int k = tid; k < BM * KX * 2 / 16; k += BT) st_shared_v4(smem + L.x + k * 16, 0u, 0u, 0u, 0u);
     if (tid == 0) {
@@ -199,18 +204,41 @@ __global__ void __launch_bounds__(BT, 1) policy_bf16_kernel(PolicyArgs a) {
     float* vals = (float*)(smem + L.vals);
     uint32_t phase = 0;
     bool ok = true;
-    const int n_tiles = (a.rows + BM - 1) / BM;
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int row0 = tile * BM;
-        const int nrows = min(BM, a.rows - row0);
-        // observations -> BF16 operand [BM][KX], coalesced over the tile's contiguous rows
-        {
+    // shared networks: tiles of BM consecutive rows, round robin over the CTAs;
+    // per-agent networks: tiles of one agent over BM consecutive environments,
+    // a contiguous range of them per CTA (agent-major, so a CTA meets few agents)
+    const int n_env = a.rows / a.per_env;
+    const int tpa = (n_env + BM - 1) / BM;
+    const int n_tiles = a.agents ? a.agents * tpa : (a.rows + BM - 1) / BM;
+    const int t_lo = a.agents ? (int)((long long)n_tiles * blockIdx.x / gridDim.x) : (int)blockIdx.x;
+    const int t_hi = a.agents ? (int)((long long)n_tiles * (blockIdx.x + 1) / gridDim.x) : n_tiles;
+    const int t_step = a.agents ? 1 : (int)gridDim.x;
+    for (int tile = t_lo; tile < t_hi; tile += t_step) {
+        const int agent = a.agents ? tile / tpa : 0;
+        const int e0 = a.agents ? (tile % tpa) * BM : 0;
+        const int row0 = a.agents ? 0 : tile * BM;
+        const int nrows = a.agents ? min(BM, n_env - e0) : min(BM, a.rows - row0);
+        auto row_of = [&](int r) { return a.agents ? (e0 + r) * a.per_env + agent : row0 + r; };
+        if (a.agents && agent != packed) {
+            __syncthreads();                             // the previous tile's MMAs are complete (waited)
+            pack_weights(a.weights + (size_t)agent * a.actor_stride, a.weights + (size_t)agent * a.critic_stride);
+            packed = agent;
+        }
+        // observations -> BF16 operand [BM][KX]: coalesced over the tile's contiguous rows, or
+        // gathered row by row (per-agent tiles)
+        if (!a.agents) {
             const float* src = a.x + (size_t)row0 * I;
             const int n = nrows * I;
             for (int idx = tid; idx < n; idx += BT) {
                 const int r = idx / I, k = idx - r * I;
                 const __nv_bfloat16 v = __float2bfloat16_rn(__ldg(src + idx));
                 *reinterpret_cast<__nv_bfloat16*>(smem + L.x + sw128_offset(r, k, BM)) = v;
+            }
+        } else {
+            for (int idx = tid; idx < BM * I; idx += BT) {
+                const int r = idx / I, k = idx - r * I;
+                const float f = r < nrows ? __ldg(a.x + (size_t)row_of(r) * I + k) : 0.0f;
+                *reinterpret_cast<__nv_bfloat16*>(smem + L.x + sw128_offset(r, k, BM)) = __float2bfloat16_rn(f);
             }
         }
         sync_for_mma();
@@ -264,7 +292,7 @@ __global__ void __launch_bounds__(BT, 1) policy_bf16_kernel(PolicyArgs a) {
         __syncthreads();
         tc_fence_after();
         if (half == 0 && row_in_tile < nrows)
-            sample_row(a, row0 + row_in_tile, lrow, vals[row_in_tile], wscr ? wscr + row_in_tile * ldo : nullptr);
+            sample_row(a, row_of(row_in_tile), lrow, vals[row_in_tile], wscr ? wscr + row_in_tile * ldo : nullptr);
         __syncthreads();
     }
     if (!ok) {
@@ -1175,9 +1203,16 @@ ej_status launch_policy_bf16(const PolicyArgs& a, cudaStream_t stream) {
     static SmemOptIn opt_in;
     ej_status st_opt = opt_in.ensure((const void*)policy_bf16_kernel, smem);
     if (st_opt != EJ_OK) return st_opt;
-    const int n_tiles = (a.rows + BM - 1) / BM;
+    const int n_tiles = a.agents ? a.agents * ((a.rows / a.per_env + BM - 1) / BM) : (a.rows + BM - 1) / BM;
     int grid = n_tiles < device_sms() ? n_tiles : device_sms();
     if (grid < 1) grid = 1;
+    if (a.agents) {
+        // per-agent networks: the general kernel, agent-major tiles, weights packed per agent
+        policy_bf16_kernel<<<grid, BT, smem, stream>>>(a);
+        cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "bf16 policy launch: %s", cudaGetErrorString(err));
+        return EJ_OK;
+    }
     if (a.H == 128) {
         bool handled = false;
         ej_status st = launch_policy_bf16_multi(&a, 1, stream, &handled);

@@ -60,7 +60,7 @@ static ej_status agent_layout(const EjParams* p, const KParams& kp, int layout, 
                               PolicyArgs* a) {
     if (layout == EJ_NETS_SHARED) return EJ_OK;
     if (layout != EJ_NETS_INDEPENDENT && layout != EJ_NETS_CTDE) return fail(EJ_ERR_ARG, "unknown network layout %d", layout);
-    if (precision != EJ_FP32) return fail(EJ_ERR_UNSUPPORTED, "per-agent networks run in FP32 (precision %d)", precision);
+    if (precision != EJ_FP32 && precision != EJ_BF16) return fail(EJ_ERR_ARG, "unknown precision %d", precision);
     int in, O, heads, head;
     ej_status st = net_shape(p, kp, EJ_NET_POP, hidden, &in, &O, &heads, &head);
     if (st != EJ_OK) return st;
@@ -226,8 +226,9 @@ ej_status rollout_range(const EjParams* p, const KParams& kp, const Layout& lay,
         ga.rows = ne;
         ga.env0 = e0;
         // BF16: population and government networks in one launch where the kernel takes both
+        // (shared networks only)
         bool handled = false;
-        if (precision == EJ_BF16) {
+        if (precision == EJ_BF16 && pa.agents == 0) {
             const PolicyArgs both[2] = {pa, ga};
             if ((st = launch_policy_bf16_multi(both, 2, s, &handled)) != EJ_OK) return st;
         }

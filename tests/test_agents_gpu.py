@@ -171,13 +171,55 @@ def test_update_moves_every_agent(layout):
             assert np.abs(di["V2"]).max() > 0
 
 
-def test_bf16_per_agent_is_refused():
-    import ctypes as C
+@pytest.mark.parametrize("layout", ["independent", "ctde"])
+def test_bf16_forward_per_agent(layout):
+    """The tensor-core forward with per-agent weights: 300 environments x 7
+    agents (3 tiles per agent, the last ragged; CTAs crossing agents repack),
+    each agent's rows within the BF16 bound of test_policy_gpu, sampled
+    actions bit-exact against the oracle's float32 sampler on the kernel's
+    logits; a BF16 rollout runs."""
     import paper_2410_22165_gb300 as P
     from paper_2410_22165_gb300 import _native as N
-    env = P.VecEnv(2, 4)
-    env.reset(seed=0)
-    fake = C.c_void_p(env.state.data_ptr())
-    st = N.load().policy_forward_agents(C.byref(env.p), fake, N.NETS_INDEPENDENT, H, N.BF16, fake, fake, None,
-                                        None, None, None, fake, None, None, None)
+    from tests.test_policy_gpu import _bound, magnitude
+    E, A = 300, 7
+    env = P.VecEnv(E, A)
+    env.reset(seed=3)
+    out = env.step(29)
+    pw = _agent_weights(3, A, env.D, env.nA)
+    gw = synth.net_weights(3, 1, env.G, H, env.p.nb * env.p.tax_levels)
+    pol = P.Policy(env, torch.from_numpy(pw), torch.from_numpy(gw), hidden=H, precision="bf16", layout=layout)
+    obs, mask = out["obs"][-1].contiguous(), out["mask"][-1].contiguous()
+    f = pol.forward(N.NET_POP, obs, mask, logits=True)
+    lg, val = f["logits"].cpu().numpy(), f["value"].cpu().numpy()
+    x = obs.cpu().numpy().reshape(E * A, env.D)
+    for i in range(A):
+        rows = np.arange(E) * A + i
+        w = _net_of(pw, i, layout, env.D, env.nA)
+        lg64, v64 = op.mlp64(w, x[rows])
+        mlg, mv = magnitude(w, x[rows])
+        bound = _bound("bf16", env.D)
+        assert np.all(np.abs(lg[rows] - lg64) <= bound * mlg + 1e-30), i
+        assert np.all(np.abs(val[rows] - v64) <= bound * mv + 1e-30), i
+    valid = op.mask_bits(mask.cpu().numpy().view(np.uint32).reshape(E * A, env.W), env.nA)
+    g = int(env.field("gstep")[0].item())
+    u = synth.pop_draws(3, np.arange(E), A, g, 1, env.nA)[3][0].reshape(E * A)
+    assert np.array_equal(f["act"].cpu().numpy()[:, 0], op.sample32(lg, valid, u))
+    ro = P.Rollout(env, pol, 5)
+    ro.reset(seed=3)
+    ro.run()
+    torch.cuda.synchronize()
+    assert torch.isfinite(ro.buf["value"]).all() and (ro.buf["act"] >= 0).all()
+
+
+def test_bf16_per_agent_update_is_refused():
+    """The per-agent PPO gradient is FP32 only (host check, nothing runs)."""
+    import ctypes as C
+    from paper_2410_22165_gb300 import _native as N
+    p = N.make_params(E=2, A=4)
+    pp = N.EjPpoParams()
+    N.load().ej_ppo_params_default(C.byref(pp))
+    fake = C.c_void_p(4096)
+    b = N.EjRollout(**{f: 4096 for f, _ in N.EjRollout._fields_})
+    st = N.load().ppo_minibatch_grad_agents(C.byref(p), C.byref(pp), 8, H, N.BF16, N.NETS_CTDE, fake, C.byref(b),
+                                            fake, 0, 0, fake, None, None)
     assert st == 3
