@@ -135,3 +135,39 @@ def test_chains_per_class_equal_one_chain():
             for n, v in ca["ro"].buf.items():
                 assert torch.equal(v, cb["ro"].buf[n]), n
             assert torch.equal(ca["env"].state, cb["env"].state)
+
+
+def test_full_size_classes_match_oracle():
+    """The benchmark's largest classes: 500 agents on the 20-level grid (84
+    actions, three mask words, 512-thread CTAs with two observation staging
+    rounds) and 250 agents on the 10-level grid (256-thread CTAs), beside a
+    10-agent class; a 40-step rollout with a period end and an episode end,
+    compared with the oracle environment by environment."""
+    import paper_2410_22165_gb300 as P
+    pops, levels = [500, 250, 500, 10], [20, 10, 20, 5]
+    w = {}
+    for L in sorted(set(levels)):
+        env = P.VecEnv(1, 10, **P.price_grid(L))
+        w[("pop", L)] = torch.from_numpy(synth.net_weights(9 + L, 0, env.D, H, env.nA))
+        w[("gov",)] = torch.from_numpy(synth.net_weights(9, 1, env.G, H, env.p.nb * env.p.tax_levels))
+    T = 40
+    kw = dict(T_ep=30, T_tax=7)
+    br = P.BatchedRollout(pops, levels, T, w, hidden=H, precision="bf16", granularity="exact", **kw)
+    br.reset(seed=8)
+    br.run()
+    torch.cuda.synchronize()
+    for k, c in enumerate(br.classes):
+        b = {n: v.cpu().numpy() for n, v in c["ro"].buf.items()}
+        p = default_params(**kw, **P.price_grid(c["P"]))
+        for j, e in enumerate(c["idx"]):
+            A_e = pops[e]
+            o = OracleEnv(p, A_e)
+            inp = synth.episode_inputs(8 + 7919 * k, [j], A_e, p["R"], p["nb"], o.nA, p["tax_levels"], T, p["T_ep"])
+            o.reset(inp["sg0"][0], inp["sc0"][0])
+            ref = o.run(b["act"][:, j, :A_e], b["gact"][:, j], inp["gather_u"][:, 0], inp["tb"][:, 0],
+                        inp["later_sg"][:, 0], inp["later_sc"][:, 0])
+            g = dict(rew=b["rew"][:, j], grew=b["grew"][:, j], done=b["done"][:, j], obs=b["obs"][1:, j],
+                     gobs=b["gobs"][1:, j], mask=b["mask"][1:, j])
+            compare_env(g, ref, c["env"].params, A_e)
+            assert ref["done"].sum() == 1
+    assert {c["A_max"] for c in br.classes} == {10, 250, 500}

@@ -218,3 +218,19 @@ def test_full_size_sampled_environments():
     # of liquid coin (floor 1 coin) is reported
     print("worst relative errors at full size:", {k: f"{v:.2e}" for k, v in worst.items()})
     assert worst["coin"] < 1e-5 and worst["earnings"] < 1e-5
+
+
+def test_second_device_launches():
+    """Kernel attributes (the shared-memory opt-in) are set per device: with a
+    second GPU present, the same environment steps there too (skipped on
+    one-GPU machines)."""
+    if torch.cuda.device_count() < 2:
+        pytest.skip("one GPU")
+    outs = []
+    for dev in ("cuda:0", "cuda:1"):
+        with torch.cuda.device(dev):
+            env = VecEnv(3, 100, device=dev, T_ep=50, T_tax=10)
+            env.reset(seed=4)
+            outs.append({k: v.cpu() for k, v in env.step(20).items()})
+    for k in outs[0]:
+        assert torch.equal(outs[0][k], outs[1][k]), k
