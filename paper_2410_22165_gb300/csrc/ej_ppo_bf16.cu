@@ -8,13 +8,19 @@
 // persistent over 128-row tiles of the minibatch (one CTA per SM).
 //
 // Per tile, everything stays on chip: forward layers (MMA, then an epilogue
-// that adds the bias, applies ReLU, keeps the ReLU mask bits in registers and
-// writes the BF16 activation back to shared memory as the next operand), the
+// that adds the bias, applies ReLU and writes the BF16 activation back to
+// shared memory as the next operand; the backward masks read it there), the
 // loss gradient per row, the backward-data products, and the weight-gradient
 // products.  The weight gradients of all tiles accumulate in tensor memory
 // (they are sums over rows, i.e. MMAs with K = rows): dW = A^T dZ reads the
 // stored activation tiles as MN-major (transposed) operands, so no transposed
 // copy is ever written.  Bias gradients are MMAs against an all-ones operand.
+// Each backward-data product (dZ2, dZ1) is committed on its own and the
+// weight-gradient products issued behind it, so an epilogue waits only for
+// the product it reads; the weight-gradient products finish under the next
+// epilogue (a commit covers every earlier product, which orders them before
+// the buffers they read are overwritten).  The critic's value head (one
+// output column) is a dot product in the second layer's epilogue.
 // At the end each CTA writes its accumulators once; a reduction kernel sums
 // the CTAs into the gradient vector.
 //
@@ -52,11 +58,13 @@ constexpr int KO = 64;         // logit operand width
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int PC = 352;        // accumulator columns written per TMEM lane
 // Cost of a tile in thousands of SM cycles, measured with clock64 stamps per
-// phase on GB300: about 13.8 for the critic (inputs, three forward products
-// and two epilogues, value loss, backward products and masks) and the same
-// plus the loss epilogue for the actor, about 1.9 per group of 8 logit
-// columns its heads span (24 logits: 5.9; three heads of 21: 18.4).
-constexpr double PPO_TILE = 13.8, PPO_LOSS_GROUP = 1.9;
+// phase on GB300 (population minibatch of E = 2048 x A = 100 x 128 steps):
+// about 11.9 for the critic (inputs, two forward products and epilogues with
+// the value head, value loss, backward products and masks); the actor adds
+// its head product and the loss: 4.5 with at most 32 logits (registers), and
+// for wider heads about 1.9 per group of 8 logit columns they span (three
+// heads of 21: 18.4).
+constexpr double PPO_TILE = 11.9, PPO_LOSS_REG = 4.5, PPO_LOSS_GROUP = 1.9;
 
 // TMEM columns.  Actor: dW1^T [h][in] 0..63, dW2 [h_in][h_out] 64..191,
 // dW3 [h][o] 192..255, db2 (column 256), db3 [o] 272..335 (every lane).
@@ -72,7 +80,7 @@ struct PpoSmem {
 };
 
 // Actor and critic use the same regions under different names:
-//   w1: W1 / V1 [128][KX]        w2: W2 / V2 [128][128]      w3: W3 [KO][128] / V3 [16][128]
+//   w1: W1 / V1 [128][KX]        w2: W2 / V2 [128][128]      w3: W3 [KO][128] (actor)
 //   x:  inputs [128][KX]         h1: H1 / G1 [128][128]      h2: H2 / G2, later dZ1 / dY1
 //   dl: dL [128][KO] (actor)     dz2: dZ2 / dY2 [128][128]   dv: dv [16][128] (critic)
 //   ones: all-ones [128][64]     bias: floats
@@ -89,7 +97,7 @@ __host__ __device__ inline PpoSmem ppo_smem() {
     L.dz2 = b;  b += BM * HID * 2;
     L.ones = b; b += BM * 64 * 2;
     L.dv = b;   b += 16 * BM * 2;
-    L.bias = b; b += (3 * HID + KO + 2 * BM + 8) * 4;
+    L.bias = b; b += (3 * HID + KO + 2 * BM + HID + 2 * BM) * 4;
     L.total = b;
     return L;
 }
@@ -97,6 +105,33 @@ __host__ __device__ inline PpoSmem ppo_smem() {
 __device__ __forceinline__ uint32_t pack2(float a, float b) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// A read-only global load issued where it is written (volatile: the compiler
+// does not move it next to its use), so a prefetch stays a prefetch.
+__device__ __forceinline__ float ld_nc_issue(const float* p) {
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_nc_issue(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.global.nc.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int32_t ld_nc_issue(const int32_t* p) {
+    int32_t v;
+    asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// Hint: bring the line holding p into L2 (no result, nothing waits for it).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+__device__ __forceinline__ void st_shared_u32(uint8_t* p, uint32_t a) {
+    asm volatile("st.shared.b32 [%0], %1;" ::"r"(smem_u32(p)), "r"(a) : "memory");
 }
 
 __device__ __forceinline__ void st_shared_v4(uint8_t* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
@@ -115,20 +150,35 @@ __device__ __forceinline__ uint64_t sw128_desc_ls(uint32_t saddr, uint32_t lbo, 
     return d;
 }
 
-// K-major operand: buffer of `rows` rows, K step kk (16 columns).
-__device__ __forceinline__ uint64_t kmaj(uint32_t base, int rows, int kk) {
-    return sw128_desc(base + (kk >> 2) * (rows / 8) * 1024 + (kk & 3) * 32);
-}
-// MN-major operand: buffer of `rows` rows read with K along the rows, K step kk (16 rows).
-__device__ __forceinline__ uint64_t mnmaj(uint32_t base, int rows, int kk) {
-    return sw128_desc_ls(base + kk * 2048, (rows / 8) * 1024, 1024);
-}
+// Descriptor of a K-major operand (K along the columns of a buffer).
+__device__ __forceinline__ uint64_t kdesc(uint32_t base) { return sw128_desc(base); }
+// Descriptor of an MN-major operand: a buffer of ROWS rows read with K along the rows.
+template <int ROWS>
+__device__ __forceinline__ uint64_t mndesc(uint32_t base) { return sw128_desc_ls(base, (ROWS / 8) * 1024, 1024); }
 
 constexpr uint32_t TA = 1u << 15, TB = 1u << 16;   // MN-major A / B in the instruction descriptor
 
-template <class FA, class FB>
-__device__ __forceinline__ void chain(uint32_t d, int ksteps, uint32_t idesc, bool acc, FA fa, FB fb) {
-    for (int kk = 0; kk < ksteps; ++kk) mma_bf16(d, fa(kk), fb(kk), idesc, (acc || kk > 0) ? 1u : 0u);
+// Walks of an operand over K steps of 16.  The start-address field of a
+// shared-memory descriptor (bits 0-13: address / 16) does not carry out for
+// addresses below 256 KB, so the descriptor of base + off is the base's plus
+// off / 16: one add per step.
+enum : int {
+    K_MAJ = 0,     // K-major buffer of R rows: 64-column panels of R / 8 atoms, 32 bytes per step in a panel
+    MN_MAJ = 1,    // MN-major: the next 16 rows, 2048 bytes on
+    K_ONE = 2,     // K-major, the steps of one 64-column panel repeated (the all-ones operand)
+};
+template <int KIND, int R>
+__device__ __forceinline__ uint32_t kstep(int kk) {
+    return KIND == MN_MAJ ? (uint32_t)kk * 128u
+                          : (KIND == K_ONE ? 0u : (uint32_t)(kk >> 2) * (uint32_t)(R * 8)) + (uint32_t)(kk & 3) * 2u;
+}
+
+// D (+)= A B over KS steps of K = 16, the operands' descriptors walked from a and b.
+template <int KS, int AK, int AR, int BK, int BR>
+__device__ __forceinline__ void chain(uint32_t d, uint32_t idesc, bool acc, uint64_t a, uint64_t b) {
+#pragma unroll
+    for (int kk = 0; kk < KS; ++kk)
+        mma_bf16(d, a + kstep<AK, AR>(kk), b + kstep<BK, BR>(kk), idesc, (acc || kk > 0) ? 1u : 0u);
 }
 
 __device__ __forceinline__ void sync_for_mma() {
@@ -208,9 +258,14 @@ __device__ __forceinline__ __nv_bfloat162 bits_bf2(uint32_t u) { return *reinter
 // 64 accumulator columns [col, col+64) of this thread's row: add the bias,
 // round to BF16 pairs, ReLU on the pairs (max with 0 commutes with the
 // rounding), write to columns [col, col+64) of dst.
-__device__ __forceinline__ void relu_epilogue64(uint32_t taddr, const float* bias, uint8_t* dst, int row, int col) {
+// With dot != nullptr it also returns the sum over these columns of the
+// BF16 activation times dot[k] (the critic's value head: dot holds the
+// BF16-rounded V3 entries, so each product is the one the tensor core forms).
+__device__ __forceinline__ float relu_epilogue64(uint32_t taddr, const float* bias, uint8_t* dst, int row, int col,
+                                                 const float* dot = nullptr) {
     float v[64];
     tmem_ld64(taddr, v);
+    float acc = 0.0f;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         // bias on float32 pairs (add.rn.f32x2: each element rounded once), then
@@ -231,7 +286,18 @@ __device__ __forceinline__ void relu_epilogue64(uint32_t taddr, const float* bia
             asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(w[j]) : "f"(hi), "f"(lo));
         }
         st_shared_v4(dst + sw128_offset(row, col + q * 8, BM), w[0], w[1], w[2], w[3]);
+        if (dot) {
+            const float4 d0 = *reinterpret_cast<const float4*>(dot + q * 8);
+            const float4 d1 = *reinterpret_cast<const float4*>(dot + q * 8 + 4);
+            const float dd[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                acc = fmaf(__uint_as_float(w[j] << 16), dd[2 * j], acc);
+                acc = fmaf(__uint_as_float(w[j] & 0xFFFF0000u), dd[2 * j + 1], acc);
+            }
+        }
     }
+    return acc;
 }
 
 // 64 accumulator columns times the ReLU derivative of the activation stored
@@ -287,16 +353,18 @@ __device__ __forceinline__ RowIn load_row_in(const FbArgs& a, uint32_t row, bool
     q.w1 = 0xFFFFFFFFu;
     if (a.W) {
         const uint32_t* mw = a.mask + (size_t)row * a.W;
-        q.w0 = mw[0];
-        q.w1 = (two_words && a.W > 1) ? mw[1] : 0u;
+        q.w0 = ld_nc_issue(mw);
+        q.w1 = 0u;
+        if (two_words && a.W > 1) q.w1 = ld_nc_issue(mw + 1);
     }
     const int32_t* ac = a.act + (size_t)row * a.n_heads;
-    q.act0 = ac[0];
-    q.act1 = a.n_heads > 1 ? ac[1] : 0;
-    q.act2 = a.n_heads > 2 ? ac[2] : 0;
-    q.act3 = a.n_heads > 3 ? ac[3] : 0;
-    q.lpo = a.logp_old[row];
-    q.adv = a.adv[row];
+    q.act0 = ld_nc_issue(ac);
+    q.act1 = q.act2 = q.act3 = 0;
+    if (a.n_heads > 1) q.act1 = ld_nc_issue(ac + 1);
+    if (a.n_heads > 2) q.act2 = ld_nc_issue(ac + 2);
+    if (a.n_heads > 3) q.act3 = ld_nc_issue(ac + 3);
+    q.lpo = ld_nc_issue(a.logp_old + row);
+    q.adv = ld_nc_issue(a.adv + row);
     return q;
 }
 
@@ -406,6 +474,101 @@ __device__ __forceinline__ ActorRow actor_row_tmem(const FbArgs& a, const RowIn&
     return st;
 }
 
+// The same row for at most 32 logits, in registers: one TMEM load of the 32
+// logit columns, unrolled passes over the 8-column groups that hold logits
+// (a uniform guard skips the others), l - max kept in place per head, and
+// exp as ex2 of the scaled argument (__expf: a few units in the last place,
+// the same value in both passes, so the probabilities are e / S of the e that
+// make up S).
+__device__ __forceinline__ ActorRow actor_row_reg32(const FbArgs& a, const RowIn& in, bool live, uint32_t taddr,
+                                                    const float* b3, uint8_t* dl, int row, float mean, float inv_std,
+                                                    float inv_n) {
+    float l[32];
+    tmem_ld32(taddr, l);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float4 b = *reinterpret_cast<const float4*>(b3 + 4 * q);
+        l[4 * q] += b.x; l[4 * q + 1] += b.y; l[4 * q + 2] += b.z; l[4 * q + 3] += b.w;
+    }
+    const int ng = (a.O + 7) >> 3;                   // groups holding logits
+    Head4 lS, ent_h, rS;
+    float logp = 0.0f, ent = 0.0f;
+#pragma unroll 1
+    for (int h = 0; h < a.n_heads; ++h) {
+        const int lo = h * a.head, hi = lo + a.head, act = lo + in.act(h);
+        const uint32_t win = (hi >= 32 ? 0xFFFFFFFFu : (1u << hi) - 1u) & ~((1u << lo) - 1u);
+        const uint32_t vb = win & in.w0;
+        float m = -FLT_MAX;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (q < ng) {
+#pragma unroll
+                for (int j = 8 * q; j < 8 * q + 8; ++j) m = ((vb >> j) & 1u) ? fmaxf(m, l[j]) : m;
+            }
+        float S = 0.0f, T = 0.0f, la = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (q < ng) {
+#pragma unroll
+                for (int j = 8 * q; j < 8 * q + 8; ++j) {
+                    const float d = l[j] - m;
+                    l[j] = ((win >> j) & 1u) ? d : l[j];
+                    const float e = ((vb >> j) & 1u) ? __expf(d) : 0.0f;
+                    S += e;
+                    T += e * d;
+                    la = j == act ? d : la;
+                }
+            }
+        const float logS = logf(S), inv_S = 1.0f / S;
+        logp += la - logS;
+        const float Hh = logS - T * inv_S;
+        ent += Hh;
+        lS.set(h, logS);
+        ent_h.set(h, Hh);
+        rS.set(h, inv_S);
+    }
+    ActorRow st;
+    const float lpo = in.lpo;
+    const float ratio = expf(logp - lpo);
+    const float an = (in.adv - mean) * inv_std;
+    const float cr = fminf(fmaxf(ratio, 1.0f - a.clip), 1.0f + a.clip);
+    const float s1 = ratio * an, s2 = cr * an;
+    st.pg = -fminf(s1, s2);
+    const bool inside = ratio > 1.0f - a.clip && ratio < 1.0f + a.clip;
+    const float dratio = (s1 <= s2 || inside) ? -an : 0.0f;
+    const float dlogp = live ? dratio * ratio * inv_n : 0.0f;
+    st.clip = fabsf(ratio - 1.0f) > a.clip ? 1.0f : 0.0f;
+    st.kl = lpo - logp;
+    st.ent = ent;
+    const float ec = live ? a.ent_coef * inv_n : 0.0f;
+    // d loss / d logits in place of l - max (0 at masked actions and beyond O)
+#pragma unroll 1
+    for (int h = 0; h < a.n_heads; ++h) {
+        const int lo = h * a.head, hi = lo + a.head, act = lo + in.act(h);
+        const uint32_t win = (hi >= 32 ? 0xFFFFFFFFu : (1u << hi) - 1u) & ~((1u << lo) - 1u);
+        const uint32_t vb = win & in.w0;
+        const float logS = lS.get(h), Hh = ent_h.get(h), inv_S = rS.get(h);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (q < ng) {
+#pragma unroll
+                for (int j = 8 * q; j < 8 * q + 8; ++j) {
+                    const float pk = (((vb >> j) & 1u) ? __expf(l[j]) : 0.0f) * inv_S;
+                    const float gk = dlogp * ((j == act ? 1.0f : 0.0f) - pk) + ec * pk * (l[j] - logS + Hh);
+                    l[j] = ((win >> j) & 1u) ? (((vb >> j) & 1u) ? gk : 0.0f) : l[j];
+                }
+            }
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) l[j] = j < a.O ? l[j] : 0.0f;
+    // gradient row -> BF16 operand
+#pragma unroll
+    for (int c8 = 0; c8 < 32; c8 += 8)
+        st_shared_v4(dl + sw128_offset(row, c8, BM), pack2(l[c8], l[c8 + 1]), pack2(l[c8 + 2], l[c8 + 3]),
+                     pack2(l[c8 + 4], l[c8 + 5]), pack2(l[c8 + 6], l[c8 + 7]));
+    return st;
+}
+
 template <int KT>
 __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
     extern __shared__ uint8_t smem_raw[];
@@ -427,6 +590,8 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
     const float* w = a.weights;
     float* bias = (float*)(smem + L.bias);           // [0,128) b1|c1, [128,256) b2|c2, [256,320) b3|c3, [320,448) V3
     float* dv_s = bias + 448;                        // [BM] critic: d loss / d value per row
+    float* v3r = bias + 576;                         // [HID] critic: V3 rounded to BF16 (the value head's operand)
+    float* vpart = bias + 704;                       // [2][BM] critic: the two halves of each row's value
 
     // weights -> BF16 operands (row n of a B operand = output unit n)
     const size_t oW1 = actor ? off.W1 : off.V1, oW2 = actor ? off.W2 : off.V2;
@@ -435,7 +600,7 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
     if (actor)
         pack_operand(smem + L.w3, KO, HID, [&](int n, int k) { return n < O ? __ldg(w + off.W3 + (size_t)k * O + n) : 0.0f; });
     else
-        pack_operand(smem + L.w3, 16, HID, [&](int n, int k) { return n == 0 ? __ldg(w + off.V3 + k) : 0.0f; });
+        for (int k = tid; k < HID; k += BT) v3r[k] = __bfloat162float(__float2bfloat16_rn(w[off.V3 + k]));
     for (int k = tid; k < 448; k += BT) {
         float v = 0.0f;
         if (k < HID) v = w[(actor ? off.b1 : off.c1) + k];
@@ -477,91 +642,129 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
     uint32_t phase = 0;
     bool ok = true, first = true, pending = false;
     const int n_tiles = (a.mb.count + BM - 1) / BM;
-    // Inputs of the next tile are loaded into registers during the current one
-    // (when a tile's inputs fit two 8-column items per thread).
-    const int xchunks = I / 8 + 1;
-    const bool pf = xchunks * BM <= 2 * BT;
+    // The gathered input rows go in a row per warp instruction (lane k: column
+    // k), so each load touches one or two cache lines.  With inputs and the
+    // ones column in 32 columns, the next tile's are loaded into registers
+    // during the current one: in the actor by every warp (16 rows each), in
+    // the critic by the second warpgroup (32 rows per warp); otherwise every
+    // warp gathers 16 rows at the tile's start.
+    constexpr int RPW = BM / 4, RPW8 = BM / (BT / 32);
+    const bool x_all = actor;                         // loaders: all warps, or the second warpgroup
+    const int x_rows = x_all ? RPW8 : RPW, x_r0 = x_all ? warp * RPW8 : quarter * RPW;
+    const int xcols = (I / 8 + 1) * 8;               // columns written: inputs, the ones column, zeros
+    const bool pf = I + 1 <= 32;
     uint32_t* rows_cur = src_rows[0];
     uint32_t* rows_nxt = src_rows[1];
-    float xv[2][8];
+    float xr[RPW];
     auto load_rows = [&](int t, uint32_t* dst) {
         if (tid < BM) {
             const int j = t * BM + tid;
             dst[tid] = (t < n_tiles && j < a.mb.count) ? (a.rows ? a.rows[j] : mb_row(a.mb, j)) : 0u;
         }
     };
-    auto load_x = [&](int t, const uint32_t* rr) {
+    auto x_at = [&](const uint32_t* rr, int r, int nr, int k) {
+        float v = (r < nr && k == I) ? 1.0f : 0.0f;
+        if (r < nr && k < I) v = ld_nc_issue(a.x + (size_t)rr[r] * I + k);
+        return v;
+    };
+    auto put_x = [&](int r, int k, float v) {   // lanes k, k + 1 -> one BF16 pair
+        const float nx = __shfl_down_sync(0xFFFFFFFFu, v, 1);
+        if ((lane & 1) == 0 && k < xcols) st_shared_u32(smem + L.x + sw128_offset(r, k, BM), pack2(v, nx));
+    };
+    auto load_x = [&](int t, const uint32_t* rr) {   // a loading warp's rows
         const int nr = t < n_tiles ? min(BM, a.mb.count - t * BM) : 0;
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int it = tid + q * BT;
-            const int r = it % BM, c = it / BM;
-            const bool live = it < BM * xchunks && r < nr;
-            const float* src = a.x + (size_t)(live ? rr[r] : 0u) * I;
+        for (int q = 0; q < RPW; ++q)
+            if (q < x_rows) xr[q] = x_at(rr, x_r0 + q, nr, lane);
+    };
+    auto store_x = [&]() {   // the shuffles first, then the stores
+        float nx[RPW];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int k = c * 8 + u;
-                xv[q][u] = !live ? 0.0f : (k < I ? __ldg(src + k) : (k == I ? 1.0f : 0.0f));
-            }
+        for (int q = 0; q < RPW; ++q)
+            if (q < x_rows) nx[q] = __shfl_down_sync(0xFFFFFFFFu, xr[q], 1);
+        if ((lane & 1) == 0 && lane < xcols) {
+#pragma unroll
+            for (int q = 0; q < RPW; ++q)
+                if (q < x_rows) st_shared_u32(smem + L.x + sw128_offset(x_r0 + q, lane, BM), pack2(xr[q], nx[q]));
         }
     };
-    auto store_x = [&]() {
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int it = tid + q * BT;
-            if (it < BM * xchunks) {
-                const int r = it % BM, c = it / BM;
-                st_shared_v4(smem + L.x + sw128_offset(r, c * 8, BM), pack2(xv[q][0], xv[q][1]),
-                             pack2(xv[q][2], xv[q][3]), pack2(xv[q][4], xv[q][5]), pack2(xv[q][6], xv[q][7]));
+    // this thread's row's loss inputs, for the tile whose rows are in rr
+    // (loaded a tile ahead with the inputs; used after the forward pass)
+    RowIn rin_nx{0xFFFFFFFFu, 0xFFFFFFFFu, 0, 0, 0, 0, 0.0f, 0.0f};
+    float vo_nx = 0.0f, ret_nx = 0.0f;
+    auto load_rin = [&](int t, const uint32_t* rr) {   // first warpgroup
+        const int nr = t < n_tiles ? min(BM, a.mb.count - t * BM) : 0;
+        if (half == 0 && row < nr) {
+            const uint32_t src = rr[row];
+            if (actor) rin_nx = load_row_in(a, src, KT > 32);
+            else { vo_nx = ld_nc_issue(a.v_old + src); ret_nx = ld_nc_issue(a.ret + src); }
+        }
+    };
+    // The next tile's inputs and loss inputs (first warpgroup), loaded while
+    // the loading warps would otherwise wait: the actor's during its second
+    // product, the critic's as thread 0 starts issuing the tile's last group
+    // of products.  (The proxy fence ahead of a product waits for loads in
+    // flight; of the placements measured, these gave the shortest update.)
+    // rr: the row table of tile t (loaded and visible to every thread).
+    auto prefetch = [&](int t, const uint32_t* rr) {
+        if (pf) {
+            if (x_all || half) load_x(t, rr);
+            if (half == 0) load_rin(t, rr);
+        }
+        __syncwarp();   // converged again before any warp-collective TMEM access
+    };
+    // Two tiles ahead, the second warpgroup (thread 128 + i: the tile's row i)
+    // reads the row table and asks L2 for the lines of that row's inputs and
+    // loss inputs, so that the loads a tile later hit L2 rather than HBM.
+    auto prefetch_l2_rows = [&](int t) {
+        const int j = t * BM + (tid - BM);
+        if (half == 1 && a.rows && t < n_tiles && j < a.mb.count) {
+            const uint32_t r = a.rows[j];
+            const float* xr0 = a.x + (size_t)r * I;
+            prefetch_l2(xr0);
+            prefetch_l2(xr0 + I - 1);
+            if (actor) {
+                if (a.W) prefetch_l2(a.mask + (size_t)r * a.W);
+                prefetch_l2(a.act + (size_t)r * a.n_heads);
+                prefetch_l2(a.logp_old + r);
+                prefetch_l2(a.adv + r);
+            } else {
+                prefetch_l2(a.v_old + r);
+                prefetch_l2(a.ret + r);
             }
         }
     };
     if (pf && role_cta < n_tiles) {
+        prefetch_l2_rows(role_cta + role_ctas);
         load_rows(role_cta, rows_cur);
         __syncthreads();
-        load_x(role_cta, rows_cur);
+        prefetch(role_cta, rows_cur);
     }
     for (int tile = role_cta; tile < n_tiles; tile += role_ctas) {
         const int j0 = tile * BM;
         const int nrows = min(BM, a.mb.count - j0);
-        // the previous tile's last products read x and h2: wait before overwriting them
+        // the previous tile's last products read x, h1, h2, dL and dZ2: wait before overwriting them
         if (pending) {
             if (!(ok = wait_mma(&bar, phase))) break;
             pending = false;
         }
         if (pf) {
-            store_x();
+            if (x_all || half) store_x();
         } else {
             load_rows(tile, rows_cur);
             __syncthreads();
             // gathered rollout inputs -> x operand: inputs, then 1 (the bias column)
-            for (int it = tid; it < BM * xchunks; it += BT) {
-                const int r = it % BM, c = it / BM;
-                float v[8];
-                const float* src = a.x + (size_t)rows_cur[r] * I;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int k = c * 8 + q;
-                    v[q] = r >= nrows ? 0.0f : (k < I ? __ldg(src + k) : (k == I ? 1.0f : 0.0f));
-                }
-                st_shared_v4(smem + L.x + sw128_offset(r, c * 8, BM), pack2(v[0], v[1]), pack2(v[2], v[3]),
-                             pack2(v[4], v[5]), pack2(v[6], v[7]));
-            }
+            for (int q = 0; q < RPW8; ++q)
+                for (int c0 = 0; c0 < KX; c0 += 32)
+                    put_x(warp * RPW8 + q, c0 + lane, x_at(rows_cur, warp * RPW8 + q, nrows, c0 + lane));
+            load_rin(tile, rows_cur);
         }
-        // this thread's row's loss inputs (used after the forward pass)
-        const uint32_t my_src = rows_cur[row];
-        const bool my_live = half == 0 && row < nrows;
-        RowIn rin{0xFFFFFFFFu, 0xFFFFFFFFu, 0, 0, 0, 0, 0.0f, 0.0f};
-        float v_old = 0.0f, ret = 0.0f;
-        if (my_live) {
-            if (actor) rin = load_row_in(a, my_src, KT > 32);
-            else { v_old = a.v_old[my_src]; ret = a.ret[my_src]; }
-        }
+        const RowIn rin = rin_nx;
+        const float v_old = vo_nx, ret = ret_nx;
         sync_for_mma();
         // layer 1
         if (tid == 0) {
-            chain(tmem + C_SLOT, KX / 16, idesc_bf16(BM, HID), false, [&](int kk) { return kmaj(sx, BM, kk); },
-                  [&](int kk) { return kmaj(sw1, HID, kk); });
+            chain<KX / 16, K_MAJ, BM, K_MAJ, HID>(tmem + C_SLOT, idesc_bf16(BM, HID), false, kdesc(sx), kdesc(sw1));
             mma_commit(&bar);
         }
         if (pf) load_rows(tile + role_ctas, rows_nxt);   // visible after the next barrier
@@ -570,72 +773,76 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
         sync_for_mma();
         // layer 2
         if (tid == 0) {
-            chain(tmem + C_SLOT, HID / 16, idesc_bf16(BM, HID), false, [&](int kk) { return kmaj(sh1, BM, kk); },
-                  [&](int kk) { return kmaj(sw2, HID, kk); });
+            chain<HID / 16, K_MAJ, BM, K_MAJ, HID>(tmem + C_SLOT, idesc_bf16(BM, HID), false, kdesc(sh1), kdesc(sw2));
             mma_commit(&bar);
         }
-        if (pf) load_x(tile + role_ctas, rows_nxt);      // the next tile's inputs, into registers
+        if (actor) prefetch(tile + role_ctas, rows_nxt);
         if (!(ok = wait_mma(&bar, phase))) break;
-        relu_epilogue64(lane_base + C_SLOT + half * 64, bias + HID + half * 64, smem + L.h2, row, half * 64);
-        sync_for_mma();
         if (actor) {
+            relu_epilogue64(lane_base + C_SLOT + half * 64, bias + HID + half * 64, smem + L.h2, row, half * 64);
+            sync_for_mma();
             // head: logits = H2 W3
-            const int N3 = (O + 15) & ~15;
             if (tid == 0) {
-                chain(tmem + C_SLOT, HID / 16, idesc_bf16(BM, N3), false, [&](int kk) { return kmaj(sh2, BM, kk); },
-                      [&](int kk) { return kmaj(sw3, KO, kk); });
+                chain<HID / 16, K_MAJ, BM, K_MAJ, KO>(tmem + C_SLOT, idesc_bf16(BM, (O + 15) & ~15), false, kdesc(sh2),
+                                                       kdesc(sw3));
                 mma_commit(&bar);
             }
             if (!(ok = wait_mma(&bar, phase))) break;
+            if (pf) prefetch_l2_rows(tile + 2 * role_ctas);
             if (half == 0) {
-                // the loss and d loss / d logits of this thread's row; scratch: the dZ2
-                // buffer, free from the last tile's second backward product to this
-                // tile's first mask epilogue
+                // the loss and d loss / d logits of this thread's row
                 const bool live = row < nrows;
-                const ActorRow s = actor_row_tmem(a, rin, live, lane_base + C_SLOT, bias + 2 * HID,
-                                                  reinterpret_cast<float*>(smem + L.dz2) + row, smem + L.dl, row,
-                                                  KT, mean, inv_std, inv_n);
+                ActorRow s;
+                if constexpr (KT == 32)
+                    s = actor_row_reg32(a, rin, live, lane_base + C_SLOT, bias + 2 * HID, smem + L.dl, row, mean,
+                                        inv_std, inv_n);
+                else
+                    // scratch: the dZ2 buffer, free from the last tile's weight-gradient
+                    // products to this tile's first mask epilogue
+                    s = actor_row_tmem(a, rin, live, lane_base + C_SLOT, bias + 2 * HID,
+                                       reinterpret_cast<float*>(smem + L.dz2) + row, smem + L.dl, row, KT, mean,
+                                       inv_std, inv_n);
                 if (live) { acc_st[0] += s.pg; acc_st[2] += s.ent; acc_st[3] += s.clip; acc_st[4] += s.kl; }
             }
             sync_for_mma();
             if (tid == 0) {
-                // dW3 += H2^T dL;  db3 (every lane) += 1^T dL;  dZ2 (before the mask) = dL W3^T
-                chain(tmem + C_W3, BM / 16, idesc_bf16(BM, KO) | TA | TB, !first,
-                      [&](int kk) { return mnmaj(sh2, BM, kk); }, [&](int kk) { return mnmaj(sdl, BM, kk); });
-                chain(tmem + C_B3, BM / 16, idesc_bf16(BM, KO) | TB, !first,
-                      [&](int kk) { return kmaj(sones, BM, kk & 3); }, [&](int kk) { return mnmaj(sdl, BM, kk); });
-                chain(tmem + C_SLOT, KT / 16, idesc_bf16(BM, HID) | TB, false,
-                      [&](int kk) { return kmaj(sdl, BM, kk); }, [&](int kk) { return mnmaj(sw3, KO, kk); });
+                // dZ2 (before the mask) = dL W3^T, committed alone: the mask epilogue waits only for it
+                chain<KT / 16, K_MAJ, BM, MN_MAJ, KO>(tmem + C_SLOT, idesc_bf16(BM, HID) | TB, false, kdesc(sdl),
+                                                       mndesc<KO>(sw3));
                 mma_commit(&bar);
+                // dW3 += H2^T dL;  db3 (every lane) += 1^T dL: done by the next commit
+                chain<BM / 16, MN_MAJ, BM, MN_MAJ, BM>(tmem + C_W3, idesc_bf16(BM, KO) | TA | TB, !first,
+                                                        mndesc<BM>(sh2), mndesc<BM>(sdl));
+                chain<BM / 16, K_ONE, BM, MN_MAJ, BM>(tmem + C_B3, idesc_bf16(BM, KO) | TB, !first, kdesc(sones),
+                                                       mndesc<BM>(sdl));
             }
             if (!(ok = wait_mma(&bar, phase))) break;
             mask_epilogue64(lane_base + C_SLOT + half * 64, smem + L.h2, smem + L.dz2, row, half * 64);
             sync_for_mma();
             if (tid == 0) {
-                // dW2 += H1^T dZ2;  db2 += dZ2^T 1;  dZ1 (before the mask) = dZ2 W2^T
-                chain(tmem + C_W2, BM / 16, idesc_bf16(BM, HID) | TA | TB, !first,
-                      [&](int kk) { return mnmaj(sh1, BM, kk); }, [&](int kk) { return mnmaj(sdz2, BM, kk); });
-                chain(tmem + C_B2, BM / 16, idesc_bf16(BM, 16) | TA, !first,
-                      [&](int kk) { return mnmaj(sdz2, BM, kk); }, [&](int kk) { return kmaj(sones, BM, kk & 3); });
-                chain(tmem + C_SLOT, HID / 16, idesc_bf16(BM, HID) | TB, false,
-                      [&](int kk) { return kmaj(sdz2, BM, kk); }, [&](int kk) { return mnmaj(sw2, HID, kk); });
+                // dZ1 (before the mask) = dZ2 W2^T; this commit also covers dW3 and db3,
+                // which read the h2 buffer the mask epilogue then overwrites
+                chain<HID / 16, K_MAJ, BM, MN_MAJ, HID>(tmem + C_SLOT, idesc_bf16(BM, HID) | TB, false, kdesc(sdz2),
+                                                         mndesc<HID>(sw2));
                 mma_commit(&bar);
+                // dW2 += H1^T dZ2;  db2 += dZ2^T 1: done by the tile's last commit
+                chain<BM / 16, MN_MAJ, BM, MN_MAJ, BM>(tmem + C_W2, idesc_bf16(BM, HID) | TA | TB, !first,
+                                                        mndesc<BM>(sh1), mndesc<BM>(sdz2));
+                chain<BM / 16, MN_MAJ, BM, K_ONE, BM>(tmem + C_B2, idesc_bf16(BM, 16) | TA, !first, mndesc<BM>(sdz2),
+                                                       kdesc(sones));
             }
         } else {
-            // value head: column 0 of G2 V3
-            if (tid == 0) {
-                chain(tmem + C_SLOT, HID / 16, idesc_bf16(BM, 16), false, [&](int kk) { return kmaj(sh2, BM, kk); },
-                      [&](int kk) { return kmaj(sw3, 16, kk); });
-                mma_commit(&bar);
-            }
-            if (!(ok = wait_mma(&bar, phase))) break;
+            // G2, and the value head on the CUDA cores: each thread's half of the
+            // row's products with the BF16 V3 entries, summed over the halves
+            const float vp = relu_epilogue64(lane_base + C_SLOT + half * 64, bias + HID + half * 64, smem + L.h2, row,
+                                             half * 64, v3r + half * 64);
+            vpart[half * BM + row] = vp;
+            sync_for_mma();
             if (half == 0) {
-                float vv[32];
-                tmem_ld32(lane_base + C_SLOT, vv);
                 float dv = 0.0f;
                 if (row < nrows) {
                     // Section 4 clipped value loss, 0.5 max((v - R)^2, (v_clipped - R)^2)
-                    const float v = vv[0] + bias[2 * HID], vo = v_old, R = ret;
+                    const float v = (vpart[row] + vpart[BM + row]) + bias[2 * HID], vo = v_old, R = ret;
                     const float dvv = v - vo;
                     const float vc = vo + fminf(fmaxf(dvv, -a.vclip), a.vclip);
                     const float la = (v - R) * (v - R), lb = (vc - R) * (vc - R);
@@ -665,19 +872,22 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
                 }
             }
             sync_for_mma();
+            prefetch(tile + role_ctas, rows_nxt);
+            if (pf) prefetch_l2_rows(tile + 2 * role_ctas);
             if (tid == 0) {
-                // dV2 += G1^T dY2;  dc2 += dY2^T 1;  dV3 += G2^T dv;  dc3 += 1^T dv;  dY1 (before the mask) = dY2 V2^T
-                chain(tmem + C_W2, BM / 16, idesc_bf16(BM, HID) | TA | TB, !first,
-                      [&](int kk) { return mnmaj(sh1, BM, kk); }, [&](int kk) { return mnmaj(sdz2, BM, kk); });
-                chain(tmem + C_C2, BM / 16, idesc_bf16(BM, 16) | TA, !first,
-                      [&](int kk) { return mnmaj(sdz2, BM, kk); }, [&](int kk) { return kmaj(sones, BM, kk & 3); });
-                chain(tmem + C_V3, BM / 16, idesc_bf16(BM, 16) | TA, !first,
-                      [&](int kk) { return mnmaj(sh2, BM, kk); }, [&](int kk) { return kmaj(sdv, 16, kk); });
-                chain(tmem + C_C3, BM / 16, idesc_bf16(BM, 16), !first,
-                      [&](int kk) { return kmaj(sones, BM, kk & 3); }, [&](int kk) { return kmaj(sdv, 16, kk); });
-                chain(tmem + C_SLOT, HID / 16, idesc_bf16(BM, HID) | TB, false,
-                      [&](int kk) { return kmaj(sdz2, BM, kk); }, [&](int kk) { return mnmaj(sw2, HID, kk); });
+                // dY1 (before the mask) = dY2 V2^T and dV3 += G2^T dv, committed
+                // together: the mask epilogue overwrites G2 in the h2 buffer
+                chain<HID / 16, K_MAJ, BM, MN_MAJ, HID>(tmem + C_SLOT, idesc_bf16(BM, HID) | TB, false, kdesc(sdz2),
+                                                         mndesc<HID>(sw2));
+                chain<BM / 16, MN_MAJ, BM, K_MAJ, 16>(tmem + C_V3, idesc_bf16(BM, 16) | TA, !first, mndesc<BM>(sh2),
+                                                       kdesc(sdv));
                 mma_commit(&bar);
+                // dV2 += G1^T dY2;  dc2 += dY2^T 1;  dc3 += 1^T dv: done by the tile's last commit
+                chain<BM / 16, MN_MAJ, BM, MN_MAJ, BM>(tmem + C_W2, idesc_bf16(BM, HID) | TA | TB, !first,
+                                                        mndesc<BM>(sh1), mndesc<BM>(sdz2));
+                chain<BM / 16, MN_MAJ, BM, K_ONE, BM>(tmem + C_C2, idesc_bf16(BM, 16) | TA, !first, mndesc<BM>(sdz2),
+                                                       kdesc(sones));
+                chain<BM / 16, K_ONE, BM, K_MAJ, 16>(tmem + C_C3, idesc_bf16(BM, 16), !first, kdesc(sones), kdesc(sdv));
             }
         }
         if (!(ok = wait_mma(&bar, phase))) break;
@@ -686,8 +896,8 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
         sync_for_mma();
         if (tid == 0) {
             // dW1^T += dZ1^T X (column I of X is 1: the first-layer bias gradient)
-            chain(tmem + C_W1T, BM / 16, idesc_bf16(BM, KX) | TA | TB, !first,
-                  [&](int kk) { return mnmaj(sh2, BM, kk); }, [&](int kk) { return mnmaj(sx, BM, kk); });
+            chain<BM / 16, MN_MAJ, BM, MN_MAJ, BM>(tmem + C_W1T, idesc_bf16(BM, KX) | TA | TB, !first, mndesc<BM>(sh2),
+                                                    mndesc<BM>(sx));
             mma_commit(&bar);
         }
         pending = true;
@@ -788,7 +998,7 @@ ej_status launch_ppo_bf16(const FbArgs& fa, float* partial, size_t partial_bytes
     const int sms = sm_count();
     int groups = 0;
     for (int h = 0; h < fa.n_heads; ++h) groups += (h * fa.head + fa.head + 7) / 8 - (h * fa.head) / 8;
-    const double c_act = PPO_TILE + PPO_LOSS_GROUP * groups, c_cri = PPO_TILE;
+    const double c_act = PPO_TILE + (fa.O <= 32 ? PPO_LOSS_REG : PPO_LOSS_GROUP * groups), c_cri = PPO_TILE;
     int n_act = 1, n_cri = 1;
     double best = 1e300;
     for (int na = 1; na < sms && na <= n_tiles; ++na) {
