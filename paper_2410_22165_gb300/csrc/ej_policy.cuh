@@ -175,8 +175,9 @@ __device__ __forceinline__ int sample_head(const float* l, int K, const uint32_t
     return act;
 }
 
-__device__ __forceinline__ void sample_row(const PolicyArgs& a, int row, const float* l, float value, float* w) {
-    a.value[row] = value;
+// Outputs of one row's actor: the logits (when asked for) and, when sampling,
+// the actions, log probability and entropy of its heads.
+__device__ __forceinline__ void sample_row_act(const PolicyArgs& a, int row, const float* l, float* w) {
     if (a.logits)
         for (int j = 0; j < a.O; ++j) a.logits[(size_t)row * a.O + j] = l[j];
     if (!a.act) return;
@@ -202,6 +203,11 @@ __device__ __forceinline__ void sample_row(const PolicyArgs& a, int row, const f
     if (none) { logp = 0.0f; ent = 0.0f; }
     a.logp[row] = logp;
     if (a.entropy) a.entropy[row] = ent;
+}
+
+__device__ __forceinline__ void sample_row(const PolicyArgs& a, int row, const float* l, float value, float* w) {
+    a.value[row] = value;
+    sample_row_act(a, row, l, w);
 }
 
 // Row tiles of the SIMT (float32) network kernels.

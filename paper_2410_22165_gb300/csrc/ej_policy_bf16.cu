@@ -1193,8 +1193,297 @@ ej_status launch_policy_bf16_multi(const PolicyArgs* segs, int n, cudaStream_t s
     return EJ_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Hidden 256 (Section 5's networks).  One network's weights in BF16 are
+// 2 x 128 KB for W2 / V2 alone, more than a CTA's shared memory beside the
+// operands, so two CTAs of a thread-block cluster share a tile: both compute
+// layer 1 in full (W1 resident in each), CTA rank r computes output units
+// [128 r, 128 r + 128) of layer 2 (its half of W2 resident) and the head's
+// partial sum over those units (its half of W3, or of V3 as a dot product in
+// the epilogue).  Rank 1 stores its partial logits (or values) into rank 0's
+// shared memory (distributed shared memory) between two cluster barriers;
+// rank 0 adds its own, the bias, and samples.  Clusters are actor or critic
+// clusters of one network (as the pipelined kernel's CTAs), persistent over
+// 128-row tiles; per-agent networks take agent-major tile ranges and pack an
+// agent's weights when the agent changes.
+constexpr int WD_H = 256;           // hidden units of this kernel
+constexpr int WD_HALF = WD_H / 2;   // layer-2 output units per CTA
+constexpr int WD_MAX_O = 63;        // logits (the sampler's staging fits two operand panels)
+constexpr int WD_RECV = 64;         // floats per row of the partial logits received by rank 0
+
+struct WdLayout {
+    uint32_t w1, w2, w3, x, h, bias, total;
+};
+
+// w1 [256][KX], w2 [128][256] (this rank's output units), w3 [64][128] (head
+// rows, this rank's input units), x [BM][KX], h [BM][256]; bias floats: b1 /
+// c1 [256], b2 / c2 half [128], b3 [64], V3 half rounded to BF16 [128], c3.
+__host__ __device__ inline WdLayout wd_layout() {
+    WdLayout L;
+    uint32_t b = 0;
+    L.w1 = b; b += WD_H * KX * 2;
+    L.w2 = b; b += WD_HALF * WD_H * 2;
+    L.w3 = b; b += 64 * WD_HALF * 2;
+    L.x = b;  b += BM * KX * 2;
+    L.h = b;  b += BM * WD_H * 2;
+    L.bias = b; b += (WD_H + WD_HALF + 64 + WD_HALF + 4) * 4;
+    L.total = b;
+    return L;
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Every thread of both CTAs of the cluster; releases this CTA's earlier
+// shared-memory writes (local and remote) to the other's later reads.
+__device__ __forceinline__ void cluster_sync() {
+    __syncwarp();                                    // the .aligned form wants converged warps
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Store v at the same shared-memory offset as `local` in the CTA of rank `rank`.
+__device__ __forceinline__ void st_cluster_f32(const void* local, uint32_t rank, float v) {
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_u32(local)), "r"(rank));
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(remote), "f"(v) : "memory");
+}
+
+// Sum over 32 accumulator columns of relu(acc + bias) rounded to BF16, times
+// dot[k] (the critic's value head on this rank's units; nothing is stored).
+__device__ __forceinline__ float dot32(uint32_t taddr, const float* bias, const float* dot) {
+    float v[32];
+    tmem_ld32(taddr, v);
+    float acc = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+        acc = fmaf(__bfloat162float(__float2bfloat16_rn(fmaxf(v[j] + bias[j], 0.0f))), dot[j], acc);
+    return acc;
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(BT, 1)
+    policy_bf16_wide_kernel(PolicyArgs a, int n_act_pairs) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ float vpart[2][BM];     // critic: this rank's partial values, one per warpgroup
+    __shared__ float vrecv[BM];        // critic rank 0: rank 1's partial values
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const WdLayout L = wd_layout();
+    const uint32_t rank = cluster_rank();
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = quarter * 32 + lane;             // TMEM lane of this thread
+    const int pair = (int)blockIdx.x / 2, n_pairs = (int)gridDim.x / 2;
+    const bool actor = pair < n_act_pairs;
+    const int role_pair = actor ? pair : pair - n_act_pairs;
+    const int role_pairs = actor ? n_act_pairs : n_pairs - n_act_pairs;
+    const int I = a.in_dim, O = a.O, N3 = (O + 15) & ~15, ldo = O | 1;
+    const NetOffsets off = net_offsets(I, WD_H, O);
+    float* b1 = (float*)(smem + L.bias);             // [256] b1 | c1
+    float* b2 = b1 + WD_H;                           // [128] b2 | c2 of this rank's units
+    float* b3 = b2 + WD_HALF;                        // [64]
+    float* v3r = b3 + 64;                            // [128] critic: V3 of this rank's units, BF16-rounded
+    float* c3 = v3r + WD_HALF;
+    const int u0 = (int)rank * WD_HALF;              // this rank's first layer-2 unit
+
+    auto pack_weights = [&](const float* w) {
+        const size_t o1 = actor ? off.W1 : off.V1, o2 = actor ? off.W2 : off.V2;
+        pack_operand(smem + L.w1, WD_H, KX,
+                     [&](int n, int k) { return k < I ? __ldg(w + o1 + (size_t)k * WD_H + n) : 0.0f; });
+        pack_operand(smem + L.w2, WD_HALF, WD_H, [&](int n, int k) { return __ldg(w + o2 + (size_t)k * WD_H + u0 + n); });
+        if (actor)
+            pack_operand(smem + L.w3, 64, WD_HALF, [&](int n, int k) {
+                return n < O ? __ldg(w + off.W3 + (size_t)(u0 + k) * O + n) : 0.0f;
+            });
+        for (int k = tid; k < WD_H; k += BT) b1[k] = w[(actor ? off.b1 : off.c1) + k];
+        for (int k = tid; k < WD_HALF; k += BT) {
+            b2[k] = w[(actor ? off.b2 : off.c2) + u0 + k];
+            v3r[k] = actor ? 0.0f : __bfloat162float(__float2bfloat16_rn(w[off.V3 + u0 + k]));
+        }
+        for (int k = tid; k < 64; k += BT) b3[k] = (actor && k < O) ? w[off.b3 + k] : 0.0f;
+        if (tid == 0) c3[0] = actor ? 0.0f : w[off.c3];
+    };
+    const size_t stride = a.agents ? (actor ? a.actor_stride : a.critic_stride) : 0;
+    pack_weights(a.weights);
+    int packed = 0;                                  // agent whose weights are packed
+    for (int k = tid; k < BM * KX * 2 / 16; k += BT) st_shared_v4(smem + L.x + k * 16, 0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_slot, TMEM_COLS);
+    sync_for_mma();
+    cluster_sync();                                  // both CTAs run before any remote store
+    const uint32_t tmem = tmem_slot;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    const uint32_t sx = smem_u32(smem + L.x), sh = smem_u32(smem + L.h);
+    const uint32_t sw1 = smem_u32(smem + L.w1), sw2 = smem_u32(smem + L.w2), sw3 = smem_u32(smem + L.w3);
+    // rank 0 of an actor cluster, once the head product is read: logits [BM][ldo]
+    // in the first half of the hidden operand, rank 1's partial logits [BM][64]
+    // (then the sampler's scratch) in the second
+    float* lstage = (float*)(smem + L.h);
+    float* recv = (float*)(smem + L.h + BM * WD_HALF * 2);
+    const int n_env = a.rows / a.per_env;
+    const int tpa = (n_env + BM - 1) / BM;
+    const int n_tiles = a.agents ? a.agents * tpa : (a.rows + BM - 1) / BM;
+    const int t_lo = a.agents ? (int)((long long)n_tiles * role_pair / role_pairs) : role_pair;
+    const int t_hi = a.agents ? (int)((long long)n_tiles * (role_pair + 1) / role_pairs) : n_tiles;
+    const int t_step = a.agents ? 1 : role_pairs;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int tile = t_lo; tile < t_hi; tile += t_step) {
+        const int agent = a.agents ? tile / tpa : 0;
+        const int e0 = a.agents ? (tile % tpa) * BM : 0;
+        const int row0 = a.agents ? 0 : tile * BM;
+        const int nrows = a.agents ? min(BM, n_env - e0) : min(BM, a.rows - row0);
+        auto row_of = [&](int r) { return a.agents ? (e0 + r) * a.per_env + agent : row0 + r; };
+        if (stride && agent != packed) {
+            __syncthreads();                         // the previous tile's products are complete (waited)
+            pack_weights(a.weights + (size_t)agent * stride);
+            packed = agent;
+        }
+        // A failed wait skips the rest of the work, never a cluster barrier:
+        // both CTAs pass the same barriers whatever happens.
+        if (ok) {
+            // observations -> BF16 operand [BM][KX] (columns >= I stay zero)
+            if (!a.agents) {
+                const float* src = a.x + (size_t)row0 * I;
+                for (int idx = tid; idx < nrows * I; idx += BT) {
+                    const int r = idx / I, k = idx - r * I;
+                    *reinterpret_cast<__nv_bfloat16*>(smem + L.x + sw128_offset(r, k, BM)) =
+                        __float2bfloat16_rn(__ldg(src + idx));
+                }
+            } else {
+                for (int idx = tid; idx < BM * I; idx += BT) {
+                    const int r = idx / I, k = idx - r * I;
+                    const float f = r < nrows ? __ldg(a.x + (size_t)row_of(r) * I + k) : 0.0f;
+                    *reinterpret_cast<__nv_bfloat16*>(smem + L.x + sw128_offset(r, k, BM)) = __float2bfloat16_rn(f);
+                }
+            }
+            sync_for_mma();
+            if (tid == 0) {                          // layer 1, all 256 units: D[:, 0:256] = X W1
+                mma_chain(tmem, sx, BM, sw1, WD_H, KX, idesc_bf16(BM, WD_H));
+                mma_commit(&bar);
+            }
+            ok = wait_mma(&bar, phase);
+        }
+        if (ok) {
+            for (int c = 0; c < 4; ++c) {            // this warpgroup's 128 units
+                const int col = half * WD_HALF + c * 32;
+                epilogue32(lane_base + col, b1 + col, smem + L.h, row, col);
+            }
+            sync_for_mma();
+            if (tid == 0) {                          // layer 2, this rank's units: D[:, 0:128] = H1 W2[:, u0:u0+128]
+                mma_chain(tmem, sh, BM, sw2, WD_HALF, WD_H, idesc_bf16(BM, WD_HALF));
+                mma_commit(&bar);
+            }
+            ok = wait_mma(&bar, phase);
+        }
+        if (ok) {
+            if (actor) {
+                // H2 (this rank's units) into the first half of the hidden operand (H1 is read)
+                for (int c = 0; c < 2; ++c) {
+                    const int col = half * 64 + c * 32;
+                    epilogue32(lane_base + col, b2 + col, smem + L.h, row, col);
+                }
+                sync_for_mma();
+                if (tid == 0) {                      // partial logits over this rank's units
+                    mma_chain(tmem + 256, sh, BM, sw3, 64, WD_HALF, idesc_bf16(BM, N3));
+                    mma_commit(&bar);
+                }
+                ok = wait_mma(&bar, phase);
+            } else {
+                float vp = 0.0f;
+                for (int c = 0; c < 2; ++c) {
+                    const int col = half * 64 + c * 32;
+                    vp += dot32(lane_base + col, b2 + col, v3r + col);
+                }
+                vpart[half][row] = vp;
+                __syncthreads();
+            }
+        }
+        cluster_sync();                              // H1 is dead in both; rank 0 is done with the last partials
+        if (ok && rank == 1) {
+            if (actor) {
+                if (half * 32 < N3) {                // warp-uniform
+                    float v[32];
+                    tmem_ld32(lane_base + 256 + half * 32, v);
+                    float* dst = recv + row * WD_RECV + half * 32;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (half * 32 + j < O) st_cluster_f32(dst + j, 0, v[j]);
+                }
+            } else if (half == 0) {
+                st_cluster_f32(&vrecv[row], 0, vpart[0][row] + vpart[1][row]);
+            }
+        }
+        cluster_sync();                              // rank 1's partials are in rank 0
+        if (ok && rank == 0) {
+            if (actor) {
+                if (half * 32 < N3) {
+                    float v[32];
+                    tmem_ld32(lane_base + 256 + half * 32, v);
+                    const float* rv = recv + row * WD_RECV + half * 32;
+                    float* lrow = lstage + row * ldo + half * 32;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (half * 32 + j < O) lrow[j] = (v[j] + rv[j]) + b3[half * 32 + j];
+                }
+                tc_fence_before();
+                __syncthreads();
+                tc_fence_after();
+                if (half == 0 && row < nrows) sample_row_act(a, row_of(row), lstage + row * ldo, recv + row * WD_RECV);
+            } else if (half == 0 && row < nrows) {
+                a.value[row_of(row)] = ((vpart[0][row] + vpart[1][row]) + vrecv[row]) + c3[0];
+            }
+        }
+    }
+    if (!ok) mbar_wait(&bar, phase, 200000000LL);   // one more bounded chance before freeing TMEM
+    cluster_sync();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem_slot, TMEM_COLS);
+}
+
+ej_status launch_policy_bf16_wide(const PolicyArgs& a, cudaStream_t stream) {
+    if (a.in_dim > KX) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: input width must be <= %d", KX);
+    if (a.O > WD_MAX_O) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: at most %d logits at hidden %d", WD_MAX_O, WD_H);
+    if (a.n_heads < 1 || a.n_heads > EJ_MAX_NB) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: 1 to %d heads", EJ_MAX_NB);
+    const size_t smem = wd_layout().total + 1024;
+    static SmemOptIn opt_in;
+    ej_status st = opt_in.ensure((const void*)policy_bf16_wide_kernel, smem);
+    if (st != EJ_OK) return st;
+    // clusters of two CTAs, one CTA per SM; actor clusters take the sampler
+    // as well (about 1.5 times a critic cluster's tile)
+    int pairs = device_sms() / 2 >= 2 ? device_sms() / 2 : 2;
+    {
+        // as many clusters as can be resident at once (a GPC may leave an SM unpaired)
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2 * pairs);
+        cfg.blockDim = dim3(BT);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = stream;
+        int resident = 0;
+        if (cudaOccupancyMaxActiveClusters(&resident, (const void*)policy_bf16_wide_kernel, &cfg) == cudaSuccess &&
+            resident >= 2 && resident < pairs)
+            pairs = resident;
+        cudaGetLastError();
+    }
+    int n_act = (int)(pairs * 0.6 + 0.5);
+    n_act = n_act < 1 ? 1 : (n_act > pairs - 1 ? pairs - 1 : n_act);
+    policy_bf16_wide_kernel<<<2 * pairs, BT, smem, stream>>>(a, n_act);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "bf16 policy (hidden 256) launch: %s", cudaGetErrorString(err));
+    return EJ_OK;
+}
+
 ej_status launch_policy_bf16(const PolicyArgs& a, cudaStream_t stream) {
-    if (a.H != 64 && a.H != 128) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: hidden must be 64 or 128");
+    if (a.H == WD_H) return launch_policy_bf16_wide(a, stream);
+    if (a.H != 64 && a.H != 128) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: hidden must be 64, 128 or 256");
     if (a.in_dim > KX) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: input width must be <= %d", KX);
     if (a.O > 128) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: at most 128 logits");
     if ((a.O | 1) > a.H) return fail(EJ_ERR_UNSUPPORTED, "bf16 policy: logits do not fit the staging area");

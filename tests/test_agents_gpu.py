@@ -35,17 +35,17 @@ def _lib():
     build.build()
 
 
-def _agent_weights(seed, A, D, O):
+def _agent_weights(seed, A, D, O, hidden=H):
     """A parameter vectors, agent i's drawn from counter stream 10 + i."""
-    return np.concatenate([synth.net_weights(seed, 10 + i, D, H, O) for i in range(A)])
+    return np.concatenate([synth.net_weights(seed, 10 + i, D, hidden, O) for i in range(A)])
 
 
-def _net_of(vecs, i, layout, D, O):
+def _net_of(vecs, i, layout, D, O, hidden=H):
     """Agent i's actor and the critic it uses, unpacked."""
-    n = synth.net_offsets(D, H, O)[1]
+    n = synth.net_offsets(D, hidden, O)[1]
     j = i if layout == "independent" else 0
-    a = synth.unpack(vecs[i * n:(i + 1) * n], D, H, O)
-    c = synth.unpack(vecs[j * n:(j + 1) * n], D, H, O)
+    a = synth.unpack(vecs[i * n:(i + 1) * n], D, hidden, O)
+    c = synth.unpack(vecs[j * n:(j + 1) * n], D, hidden, O)
     return {**{k: a[k] for k in ACTOR}, **{k: c[k] for k in CRITIC}}
 
 
@@ -171,9 +171,11 @@ def test_update_moves_every_agent(layout):
             assert np.abs(di["V2"]).max() > 0
 
 
+@pytest.mark.parametrize("hidden", [128, 256])
 @pytest.mark.parametrize("layout", ["independent", "ctde"])
-def test_bf16_forward_per_agent(layout):
-    """The tensor-core forward with per-agent weights: 300 environments x 7
+def test_bf16_forward_per_agent(layout, hidden):
+    """The tensor-core forward with per-agent weights (hidden 128: one CTA per
+    tile; hidden 256: the two-CTA cluster kernel): 300 environments x 7
     agents (3 tiles per agent, the last ragged; CTAs crossing agents repack),
     each agent's rows within the BF16 bound of test_policy_gpu, sampled
     actions bit-exact against the oracle's float32 sampler on the kernel's
@@ -185,16 +187,16 @@ def test_bf16_forward_per_agent(layout):
     env = P.VecEnv(E, A)
     env.reset(seed=3)
     out = env.step(29)
-    pw = _agent_weights(3, A, env.D, env.nA)
-    gw = synth.net_weights(3, 1, env.G, H, env.p.nb * env.p.tax_levels)
-    pol = P.Policy(env, torch.from_numpy(pw), torch.from_numpy(gw), hidden=H, precision="bf16", layout=layout)
+    pw = _agent_weights(3, A, env.D, env.nA, hidden)
+    gw = synth.net_weights(3, 1, env.G, hidden, env.p.nb * env.p.tax_levels)
+    pol = P.Policy(env, torch.from_numpy(pw), torch.from_numpy(gw), hidden=hidden, precision="bf16", layout=layout)
     obs, mask = out["obs"][-1].contiguous(), out["mask"][-1].contiguous()
     f = pol.forward(N.NET_POP, obs, mask, logits=True)
     lg, val = f["logits"].cpu().numpy(), f["value"].cpu().numpy()
     x = obs.cpu().numpy().reshape(E * A, env.D)
     for i in range(A):
         rows = np.arange(E) * A + i
-        w = _net_of(pw, i, layout, env.D, env.nA)
+        w = _net_of(pw, i, layout, env.D, env.nA, hidden)
         lg64, v64 = op.mlp64(w, x[rows])
         mlg, mv = magnitude(w, x[rows])
         bound = _bound("bf16", env.D)

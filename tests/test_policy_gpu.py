@@ -251,12 +251,13 @@ def test_split_rollout_equals_one_chain(precision):
         assert torch.equal(out[1][1], out[chains][1])
 
 
-@pytest.mark.parametrize("hidden,levels", [(64, 5), (64, 10), (128, 30)])
+@pytest.mark.parametrize("hidden,levels", [(64, 5), (64, 10), (128, 30), (256, 5), (256, 10)])
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
 def test_forward_outside_the_pipelined_kernel(precision, hidden, levels):
     """Shapes the pipelined BF16 kernel does not take: hidden 64 (24 and 44
-    actions) and 124 actions at hidden 128 (P = 30 levels, 4 mask words);
-    population and government networks against the oracle."""
+    actions), 124 actions at hidden 128 (P = 30 levels, 4 mask words) and
+    hidden 256 (the two-CTA cluster kernel; 300 rows: three tiles, the last
+    ragged); population and government networks against the oracle."""
     P, _ = _mods()
     _forward_vs_oracle(precision, hidden, P.price_grid(levels))
 
@@ -267,6 +268,21 @@ def test_section5_networks_of_256_units_fp32(R, Rd):
     environments (30 and 86 actions), FP32 forward against the oracle."""
     _forward_vs_oracle("fp32", 256, dict(R=R, P=3, price_tick=3.0, price_ticks=[1, 2, 3], Rd=Rd,
                                          gov_enabled=0, skill_gain=0.005, skill_init=1))
+
+
+def test_section5_networks_of_256_units_bf16():
+    """Section 5's 4-resource market (39 inputs, 46 actions) with networks of
+    256 units in BF16 (the cluster kernel) against the oracle; the
+    12-resource market's 95 inputs exceed the kernel's 64-column input operand
+    and are refused before anything is launched."""
+    s5 = dict(P=3, price_tick=3.0, price_ticks=[1, 2, 3], gov_enabled=0, skill_gain=0.005, skill_init=1)
+    _forward_vs_oracle("bf16", 256, dict(R=4, Rd=2, **s5))
+    P, N = _mods()
+    env = P.VecEnv(2, 10, R=12, Rd=3, **s5)
+    pw = torch.from_numpy(synth.net_weights(1, 0, env.D, 256, env.nA))
+    gw = torch.from_numpy(synth.net_weights(1, 1, env.G, 256, env.p.nb * env.p.tax_levels))
+    with pytest.raises(N.EjError, match="UNSUPPORTED"):
+        P.Policy(env, pw, gw, hidden=256, precision="bf16").forward(N.NET_POP, torch.zeros((2, 10, env.D), device="cuda"))
 
 
 def _forward_vs_oracle(precision, hidden, env_kw):
