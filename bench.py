@@ -535,7 +535,8 @@ def run_multi_agent(args, dev, E_m=256, T_m=32, H_m=256, seed=6000):
     networks of 256 units), float32: one training iteration (a T_m-step
     rollout of E_m x A agents, then a PPO update, 4 epochs x 8 minibatches)
     with the population's networks shared, independent (an actor and a critic
-    per agent) and CTDE (an actor per agent, one critic)."""
+    per agent) and CTDE (an actor per agent, one critic); and the rollout
+    again with the BF16 forward (the update at hidden 256 is float32)."""
     import numpy as np
     import torch
 
@@ -570,9 +571,24 @@ def run_multi_agent(args, dev, E_m=256, T_m=32, H_m=256, seed=6000):
         ev[2].record()
         torch.cuda.synchronize(dev)
         ro_ms, up_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        # the same rollout with the BF16 forward (hidden 256: the two-CTA cluster kernel)
+        pol16 = Policy(env, pw, gw, hidden=H_m, precision="bf16", layout=layout)
+        ro16 = Rollout(env, pol16, T_m)
+        ro16.reset(seed=seed)
+        ro16.run()
+        torch.cuda.synchronize(dev)
+        ev[0].record()
+        ro16.carry_over()
+        ro16.run()
+        ev[1].record()
+        torch.cuda.synchronize(dev)
+        ro16_ms = ev[0].elapsed_time(ev[1])
         out[layout] = {"rollout_ms": ro_ms, "update_ms": up_ms, "population_parameters": int(pw.numel()),
-                       "train_agent_steps_per_s": E_m * A * T_m / ((ro_ms + up_ms) / 1e3)}
-        del ppo, ro, pol, env
+                       "train_agent_steps_per_s": E_m * A * T_m / ((ro_ms + up_ms) / 1e3),
+                       "rollout_ms_bf16": ro16_ms,
+                       "rollout_agent_steps_per_s": {"fp32": E_m * A * T_m / (ro_ms / 1e3),
+                                                     "bf16": E_m * A * T_m / (ro16_ms / 1e3)}}
+        del ppo, ro, pol, ro16, pol16, env
         torch.cuda.empty_cache()
     return out
 
@@ -793,6 +809,38 @@ def run_profile_case(args):
             res[prec] = {"launch_ms": ms, "useful_TFLOPs": flops / (statistics.mean(ms) / 1e3) / 1e12}
         print(json.dumps({"profile_case": "policy E=4096 A=100", **res}))
         return
+    if args.profile_case == "policy256":
+        # population forward with Section 5's networks of 256 units: the default
+        # market (24 actions) and the 4-resource market (46 actions), BF16 and FP32
+        import synth
+        from paper_2410_22165_gb300 import Policy
+        from paper_2410_22165_gb300 import _native as N
+        s5 = dict(R=4, Rd=2, P=3, price_tick=3.0, price_ticks=[1, 2, 3], gov_enabled=0, skill_gain=0.005,
+                  skill_init=1)
+        res = {}
+        for label, kw in (("default", {}), ("R4", s5)):
+            env = VecEnv(4096, A, device="cuda", T_ep=T_EP, T_tax=T_TAX, **kw)
+            env.reset(seed=7)
+            o = env.step(3)
+            obs, mask = o["obs"][-1].contiguous(), o["mask"][-1].contiguous()
+            pw = torch.from_numpy(synth.net_weights(7, 0, env.D, 256, env.nA))
+            gw = torch.from_numpy(synth.net_weights(7, 1, env.G, 256, env.p.nb * env.p.tax_levels))
+            flops = 4096 * A * 2 * (env.D * 256 * 2 + 256 * 256 * 2 + 256 * env.nA + 256)
+            for prec in ("bf16", "fp32"):
+                pol = Policy(env, pw, gw, hidden=256, precision=prec)
+                ms = []
+                for k in range(args.warmup + args.steps):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    pol.forward(N.NET_POP, obs, mask)
+                    b.record()
+                    torch.cuda.synchronize()
+                    if k >= args.warmup:
+                        ms.append(a.elapsed_time(b))
+                res[f"{label}_{prec}"] = {"launch_ms": statistics.median(ms),
+                                          "useful_TFLOPs": flops / (statistics.median(ms) / 1e3) / 1e12}
+        print(json.dumps({"profile_case": "policy hidden 256, E=4096 A=100", **res}))
+        return
     if args.profile_case == "ppo":
         import synth
         from paper_2410_22165_gb300 import PPO, Policy, Rollout
@@ -841,7 +889,7 @@ def run_profile_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-case", nargs="?", const="env", default=None, choices=["env", "policy", "ppo"])
+    ap.add_argument("--profile-case", nargs="?", const="env", default=None, choices=["env", "policy", "policy256", "ppo"])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)

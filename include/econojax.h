@@ -289,8 +289,11 @@ ej_status ej_net_floats(const EjParams* p, int32_t net, int32_t hidden, uint64_t
  * logits  (device) float[rows][O] (may be NULL).  Rows with no allowed action
  * get action 0, logp 0, entropy 0.
  * BF16 takes hidden 64 or 128, at most 64 inputs and at most 128 logits with
- * (logits | 1) <= hidden (so <= 63 logits at hidden 64); other shapes return
- * EJ_ERR_UNSUPPORTED (FP32 takes them). */
+ * (logits | 1) <= hidden (so <= 63 logits at hidden 64), and hidden 256 (the
+ * networks of Section 5) with at most 64 inputs and 64 logits (a tile is
+ * shared by the two CTAs of a thread-block cluster, each holding half of the
+ * second layer's weights); other shapes return EJ_ERR_UNSUPPORTED (FP32 takes
+ * them). */
 ej_status policy_forward(const EjParams* p, const void* state, int32_t net, int32_t hidden,
                          int32_t precision, const float* weights, const float* obs,
                          const uint32_t* mask, const float* u, int32_t* act, float* logp,
@@ -330,7 +333,7 @@ ej_status policy_segmented(const EjParams* p, int32_t net, int32_t hidden, int32
  * is vector i's actor part; its critic is vector i's critic part
  * (independent) or vector 0's (CTDE, whose other critic parts are unused and
  * get zero gradients).  The government network stays one shared vector.
- * The forward and the rollout take FP32 or BF16 (BF16: hidden 64 or 128; the
+ * The forward and the rollout take FP32 or BF16 (BF16: hidden 64, 128 or 256; the
  * tensor-core kernel walks agent-major tiles, a contiguous range per CTA, and
  * packs an agent's weights when its tiles begin); the PPO gradient and update
  * of per-agent networks are FP32 (EJ_BF16 returns EJ_ERR_UNSUPPORTED). */

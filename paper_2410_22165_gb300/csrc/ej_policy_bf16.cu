@@ -1202,13 +1202,14 @@ ej_status launch_policy_bf16_multi(const PolicyArgs* segs, int n, cudaStream_t s
 // partial sum over those units (its half of W3, or of V3 as a dot product in
 // the epilogue).  Rank 1 stores its partial logits (or values) into rank 0's
 // shared memory (distributed shared memory) between two cluster barriers;
-// rank 0 adds its own, the bias, and samples.  Clusters are actor or critic
+// rank 0 adds its own and the bias, puts the logits back into TMEM and
+// samples them with the pipelined kernel's sampler.  Clusters are actor or critic
 // clusters of one network (as the pipelined kernel's CTAs), persistent over
 // 128-row tiles; per-agent networks take agent-major tile ranges and pack an
 // agent's weights when the agent changes.
 constexpr int WD_H = 256;           // hidden units of this kernel
 constexpr int WD_HALF = WD_H / 2;   // layer-2 output units per CTA
-constexpr int WD_MAX_O = 63;        // logits (the sampler's staging fits two operand panels)
+constexpr int WD_MAX_O = 64;        // logits: the head's TMEM columns and the sampler's scratch
 constexpr int WD_RECV = 64;         // floats per row of the partial logits received by rank 0
 
 struct WdLayout {
@@ -1244,11 +1245,36 @@ __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// Store v at the same shared-memory offset as `local` in the CTA of rank `rank`.
-__device__ __forceinline__ void st_cluster_f32(const void* local, uint32_t rank, float v) {
+// Address in the CTA of rank `rank` of the same shared-memory offset as `local`.
+__device__ __forceinline__ uint32_t cluster_addr(const void* local, uint32_t rank) {
     uint32_t remote;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_u32(local)), "r"(rank));
-    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(remote), "f"(v) : "memory");
+    return remote;
+}
+__device__ __forceinline__ void st_cluster_f32(const void* local, uint32_t rank, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(cluster_addr(local, rank)), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster_v4(uint32_t remote, float a, float b, float c, float d) {
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(remote), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
+// 32 consecutive 32-bit TMEM columns of this thread's lane <- v.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]),
+        "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15]), "f"(v[16]),
+        "f"(v[17]), "f"(v[18]), "f"(v[19]), "f"(v[20]), "f"(v[21]), "f"(v[22]), "f"(v[23]), "f"(v[24]),
+        "f"(v[25]), "f"(v[26]), "f"(v[27]), "f"(v[28]), "f"(v[29]), "f"(v[30]), "f"(v[31])
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void st_shared_b32(uint8_t* p, uint32_t v) {
+    asm volatile("st.shared.b32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
 }
 
 // Sum over 32 accumulator columns of relu(acc + bias) rounded to BF16, times
@@ -1280,7 +1306,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(BT, 1)
     const bool actor = pair < n_act_pairs;
     const int role_pair = actor ? pair : pair - n_act_pairs;
     const int role_pairs = actor ? n_act_pairs : n_pairs - n_act_pairs;
-    const int I = a.in_dim, O = a.O, N3 = (O + 15) & ~15, ldo = O | 1;
+    const int I = a.in_dim, O = a.O, N3 = (O + 15) & ~15;
     const NetOffsets off = net_offsets(I, WD_H, O);
     float* b1 = (float*)(smem + L.bias);             // [256] b1 | c1
     float* b2 = b1 + WD_H;                           // [128] b2 | c2 of this rank's units
@@ -1321,10 +1347,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(BT, 1)
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
     const uint32_t sx = smem_u32(smem + L.x), sh = smem_u32(smem + L.h);
     const uint32_t sw1 = smem_u32(smem + L.w1), sw2 = smem_u32(smem + L.w2), sw3 = smem_u32(smem + L.w3);
-    // rank 0 of an actor cluster, once the head product is read: logits [BM][ldo]
-    // in the first half of the hidden operand, rank 1's partial logits [BM][64]
-    // (then the sampler's scratch) in the second
-    float* lstage = (float*)(smem + L.h);
+    // rank 0 of an actor cluster, once the head product is read: rank 1's partial
+    // logits [BM][64] in the second half of the hidden operand, the sampler's
+    // scratch in the first
     float* recv = (float*)(smem + L.h + BM * WD_HALF * 2);
     const int n_env = a.rows / a.per_env;
     const int tpa = (n_env + BM - 1) / BM;
@@ -1348,19 +1373,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(BT, 1)
         // A failed wait skips the rest of the work, never a cluster barrier:
         // both CTAs pass the same barriers whatever happens.
         if (ok) {
-            // observations -> BF16 operand [BM][KX] (columns >= I stay zero)
-            if (!a.agents) {
-                const float* src = a.x + (size_t)row0 * I;
-                for (int idx = tid; idx < nrows * I; idx += BT) {
-                    const int r = idx / I, k = idx - r * I;
-                    *reinterpret_cast<__nv_bfloat16*>(smem + L.x + sw128_offset(r, k, BM)) =
-                        __float2bfloat16_rn(__ldg(src + idx));
+            // observations -> BF16 operand [BM][KX]: a row per warp instruction (lane k:
+            // column c0 + k of rows [16 warp, 16 warp + 16)), all of a warp's loads
+            // issued before its stores; rows past the tile's end are zero
+            for (int c0 = 0; c0 < I; c0 += 32) {
+                float v[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int r = warp * 16 + q, k = c0 + lane;
+                    v[q] = (r < nrows && k < I) ? __ldg(a.x + (size_t)row_of(r) * I + k) : 0.0f;
                 }
-            } else {
-                for (int idx = tid; idx < BM * I; idx += BT) {
-                    const int r = idx / I, k = idx - r * I;
-                    const float f = r < nrows ? __ldg(a.x + (size_t)row_of(r) * I + k) : 0.0f;
-                    *reinterpret_cast<__nv_bfloat16*>(smem + L.x + sw128_offset(r, k, BM)) = __float2bfloat16_rn(f);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const float nx = __shfl_down_sync(0xFFFFFFFFu, v[q], 1);
+                    if ((lane & 1) == 0 && c0 + lane < KX)
+                        st_shared_b32(smem + L.x + sw128_offset(warp * 16 + q, c0 + lane, BM), pack2(v[q], nx));
                 }
             }
             sync_for_mma();
@@ -1411,10 +1438,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(BT, 1)
                 if (half * 32 < N3) {                // warp-uniform
                     float v[32];
                     tmem_ld32(lane_base + 256 + half * 32, v);
-                    float* dst = recv + row * WD_RECV + half * 32;
+                    const uint32_t dst = cluster_addr(recv + row * WD_RECV + half * 32, 0);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (half * 32 + j < O) st_cluster_f32(dst + j, 0, v[j]);
+                    for (int j = 0; j < 32; j += 4)
+                        if (half * 32 + j < O) st_cluster_v4(dst + 4 * j, v[j], v[j + 1], v[j + 2], v[j + 3]);
                 }
             } else if (half == 0) {
                 st_cluster_f32(&vrecv[row], 0, vpart[0][row] + vpart[1][row]);
@@ -1423,19 +1450,69 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(BT, 1)
         cluster_sync();                              // rank 1's partials are in rank 0
         if (ok && rank == 0) {
             if (actor) {
+                const bool live = row < nrows;
+                // the logits: this rank's partial + rank 1's + the bias, back into the
+                // head's TMEM columns, from where the sampler reads them
                 if (half * 32 < N3) {
                     float v[32];
                     tmem_ld32(lane_base + 256 + half * 32, v);
-                    const float* rv = recv + row * WD_RECV + half * 32;
-                    float* lrow = lstage + row * ldo + half * 32;
+                    const float4* rv = reinterpret_cast<const float4*>(recv + row * WD_RECV + half * 32);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (half * 32 + j < O) lrow[j] = (v[j] + rv[j]) + b3[half * 32 + j];
+                    for (int j = 0; j < 32; j += 4) {
+                        const float4 r4 = rv[j / 4];
+                        const float4 b4 = *reinterpret_cast<const float4*>(b3 + half * 32 + j);
+                        v[j] = (v[j] + r4.x) + b4.x; v[j + 1] = (v[j + 1] + r4.y) + b4.y;
+                        v[j + 2] = (v[j + 2] + r4.z) + b4.z; v[j + 3] = (v[j + 3] + r4.w) + b4.w;
+                    }
+                    tmem_st32(lane_base + 256 + half * 32, v);
+                    if (live && a.logits)
+                        for (int j = 0; j < 32; ++j)
+                            if (half * 32 + j < O) a.logits[(size_t)row_of(row) * O + half * 32 + j] = v[j];
                 }
                 tc_fence_before();
                 __syncthreads();
                 tc_fence_after();
-                if (half == 0 && row < nrows) sample_row_act(a, row_of(row), lstage + row * ldo, recv + row * WD_RECV);
+                if (half == 0 && a.act) {
+                    // mask words and uniforms of the row, as the pipelined kernel takes them
+                    const int grow = live ? row_of(row) : 0;
+                    uint32_t mw[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+                    float us[EJ_MAX_NB] = {0.0f, 0.0f, 0.0f, 0.0f};
+                    if (live) {
+                        if (a.W) {
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                if (k < a.W) mw[k] = a.mask[(size_t)grow * a.W + k];
+                        }
+                        if (a.u) {
+#pragma unroll
+                            for (int h = 0; h < EJ_MAX_NB; ++h)
+                                if (h < a.n_heads) us[h] = a.u[(size_t)grow * a.n_heads + h];
+                        } else {
+                            const int e = a.env0 + grow / a.per_env, i = grow % a.per_env;
+                            const uint4 x = philox4x32_10(make_uint4(a.stream_id == 0 ? (uint32_t)i : 0u, (uint32_t)e,
+                                                                     a.gstep[e], (uint32_t)a.stream_id),
+                                                          a.key[0], a.key[1]);
+                            if (a.stream_id == 0) us[0] = u01(x.w);
+                            else { us[0] = u01(x.x); us[1] = u01(x.y); us[2] = u01(x.z); us[3] = u01(x.w); }
+                        }
+                    }
+                    // scratch: this thread's column of a [64][128] float array in the
+                    // first half of the hidden operand (H2 is read); bias: zeros (v3r)
+                    float* scr = reinterpret_cast<float*>(smem + L.h) + row;
+                    float logp = 0.0f, ent = 0.0f;
+                    bool none = false;
+                    for (int h = 0; h < a.n_heads; ++h) {
+                        const float uh = h == 0 ? us[0] : h == 1 ? us[1] : h == 2 ? us[2] : us[3];
+                        int act = sample_head_tmem(lane_base + 256, v3r, h * a.head, a.head, mw, uh, scr, logp, ent);
+                        if (act < 0) { act = 0; none = true; }
+                        if (live) a.act[(size_t)grow * a.n_heads + h] = act;
+                    }
+                    if (none) { logp = 0.0f; ent = 0.0f; }
+                    if (live) {
+                        a.logp[grow] = logp;
+                        if (a.entropy) a.entropy[grow] = ent;
+                    }
+                }
             } else if (half == 0 && row < nrows) {
                 a.value[row_of(row)] = ((vpart[0][row] + vpart[1][row]) + vrecv[row]) + c3[0];
             }
@@ -1457,8 +1534,9 @@ ej_status launch_policy_bf16_wide(const PolicyArgs& a, cudaStream_t stream) {
     static SmemOptIn opt_in;
     ej_status st = opt_in.ensure((const void*)policy_bf16_wide_kernel, smem);
     if (st != EJ_OK) return st;
-    // clusters of two CTAs, one CTA per SM; actor clusters take the sampler
-    // as well (about 1.5 times a critic cluster's tile)
+    // clusters of two CTAs, one CTA per SM; the actor's tile costs about 17.7 k
+    // SM cycles against the critic's 10.7 k (clock64 stamps per phase, GB300,
+    // 24 logits): the actor clusters' share balances the two roles
     int pairs = device_sms() / 2 >= 2 ? device_sms() / 2 : 2;
     {
         // as many clusters as can be resident at once (a GPC may leave an SM unpaired)
@@ -1473,7 +1551,7 @@ ej_status launch_policy_bf16_wide(const PolicyArgs& a, cudaStream_t stream) {
             pairs = resident;
         cudaGetLastError();
     }
-    int n_act = (int)(pairs * 0.6 + 0.5);
+    int n_act = (int)(pairs * (17.7 / (17.7 + 10.7)) + 0.5);
     n_act = n_act < 1 ? 1 : (n_act > pairs - 1 ? pairs - 1 : n_act);
     policy_bf16_wide_kernel<<<2 * pairs, BT, smem, stream>>>(a, n_act);
     cudaError_t err = cudaGetLastError();
