@@ -216,6 +216,7 @@ constexpr int NTH = 256;       // threads per CTA
 
 // out[r][c] = act(b[c] + sum_k in[r][k] W[k][c]) for a TILE x N block, N a
 // multiple of 4 (here H = 128); b may be NULL (no bias).  Thread tile: 8 rows x 4 columns.
+// in: 16-byte aligned, ldi a multiple of 4.
 __device__ inline void dense_tile(const float* in, int ldi, int K, const float* __restrict__ W,
                            const float* __restrict__ b, int N, float* out, int ldo, bool relu) {
     const int t = threadIdx.x;
@@ -227,8 +228,28 @@ __device__ inline void dense_tile(const float* in, int ldi, int K, const float* 
         const float4 bb = b ? *reinterpret_cast<const float4*>(b + c0) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int r = 0; r < 8; ++r) { acc[r][0] = bb.x; acc[r][1] = bb.y; acc[r][2] = bb.z; acc[r][3] = bb.w; }
-#pragma unroll 4
-        for (int k = 0; k < K; ++k) {
+        // four k per step: 16-byte loads of the inputs (ldi is a multiple of 4),
+        // four weight rows in flight; each accumulator still takes its k in order
+        int k = 0;
+#pragma unroll 2
+        for (; k + 4 <= K; k += 4) {
+            float4 w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) w[q] = __ldg(reinterpret_cast<const float4*>(W + (size_t)(k + q) * N + c0));
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const float4 x4 = *reinterpret_cast<const float4*>(in + (r0 + r) * ldi + k);
+                const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    acc[r][0] = fmaf(xs[q], w[q].x, acc[r][0]);
+                    acc[r][1] = fmaf(xs[q], w[q].y, acc[r][1]);
+                    acc[r][2] = fmaf(xs[q], w[q].z, acc[r][2]);
+                    acc[r][3] = fmaf(xs[q], w[q].w, acc[r][3]);
+                }
+            }
+        }
+        for (; k < K; ++k) {
             const float4 w = __ldg(reinterpret_cast<const float4*>(W + (size_t)k * N + c0));
 #pragma unroll
             for (int r = 0; r < 8; ++r) {

@@ -375,19 +375,19 @@ def test_government_forward_and_sampling(precision):
     assert np.allclose(out["logp"].cpu().numpy(), lp_tot, atol=1e-5 * (1 + np.abs(lp_tot)).max())
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
-def test_rollout_matches_oracle_step_by_step(precision):
+@pytest.mark.parametrize("precision,hidden", [("fp32", 128), ("bf16", 128), ("bf16", 256)])
+def test_rollout_matches_oracle_step_by_step(precision, hidden):
     """T = 25 steps across an episode end: every sampled action is the oracle's
     decision on the GPU's logits; the environment transitions equal the oracle
     run with the GPU's actions; stored values and log-probabilities are the
-    policy's."""
+    policy's.  Hidden 256 in BF16 is the two-CTA cluster kernel."""
     E, A, T = 3, 20, 25
     kw = dict(T_ep=20, T_tax=5)
     P, N = _mods()
     env = P.VecEnv(E, A, **kw)
-    pw = synth.net_weights(9, 0, env.D, H, env.nA)
-    gw = synth.net_weights(9, 1, env.G, H, env.p.nb * env.p.tax_levels)
-    pol = P.Policy(env, torch.from_numpy(pw), torch.from_numpy(gw), hidden=H, precision=precision)
+    pw = synth.net_weights(9, 0, env.D, hidden, env.nA)
+    gw = synth.net_weights(9, 1, env.G, hidden, env.p.nb * env.p.tax_levels)
+    pol = P.Policy(env, torch.from_numpy(pw), torch.from_numpy(gw), hidden=hidden, precision=precision)
     ro = P.Rollout(env, pol, T)
     ro.reset(seed=9)
     b = {k: v.cpu().numpy() for k, v in ro.run().items()}
@@ -395,8 +395,8 @@ def test_rollout_matches_oracle_step_by_step(precision):
     # a second environment replays the observations through policy_forward
     probe = P.VecEnv(E, A, **kw)
     probe.reset(seed=9)
-    pprobe = P.Policy(probe, torch.from_numpy(pw), torch.from_numpy(gw), hidden=H, precision=precision)
-    wp = synth.unpack(pw, env.D, H, env.nA)
+    pprobe = P.Policy(probe, torch.from_numpy(pw), torch.from_numpy(gw), hidden=hidden, precision=precision)
+    wp = synth.unpack(pw, env.D, hidden, env.nA)
     L = env.p.tax_levels
     for t in range(T + 1):
         obs = torch.from_numpy(b["obs"][t]).cuda()
