@@ -57,11 +57,10 @@ ej_status scratch_for_current_device(unsigned char** out) {
     return EJ_OK;
 }
 
-int half_bits(uint64_t N) {
+int domain_bits(uint64_t N) {
     int b = 2;
     while ((1ull << b) < N) ++b;
-    b += b & 1;
-    return b / 2;
+    return b;
 }
 
 }  // namespace
@@ -131,7 +130,7 @@ extern "C" ej_status ppo_minibatch_grad_static(const EjParams* p, const EjPpoPar
     fa.mb.lo = (int)((N * minibatch) / pp->minibatches);
     fa.mb.count = (int)((N * (minibatch + 1)) / pp->minibatches) - fa.mb.lo;
     fa.mb.N = (uint32_t)N;
-    fa.mb.half = half_bits(N);
+    fa.mb.bits = domain_bits(N);
     fa.mb.k0 = (uint32_t)pp->seed;
     fa.mb.k1 = (uint32_t)(pp->seed >> 32);
     fa.mb.ctr = shuffle_ctr;

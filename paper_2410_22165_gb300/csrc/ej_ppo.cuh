@@ -13,28 +13,38 @@ enum { ST_ADV_SUM = 0, ST_ADV_SQ = 1, ST_PG = 2, ST_VF = 3, ST_ENT = 4, ST_CLIP 
 struct MbDesc {
     int lo, count;
     uint32_t N;
-    int half;
+    int bits;          // the permutation's domain is [0, 2^bits), 2^bits >= N
     uint32_t k0, k1, ctr;
 };
 
-// Feistel permutation of [0, 4^half) restricted to [0, N) by cycle walking
-// (Luby-Rackoff; Black-Rogaway), round function = Philox word x0.
-__device__ __forceinline__ uint32_t feistel(uint32_t x, int half, uint32_t k0, uint32_t k1, uint32_t ctr) {
-    const uint32_t mask = (1u << half) - 1u;
-    uint32_t L = (x >> half) & mask, R = x & mask;
+// Feistel permutation of [0, 2^bits) restricted to [0, N) by cycle walking
+// (Luby-Rackoff; Black-Rogaway).  Alternating (unbalanced) form: the high
+// part has bits / 2 bits, the low part the rest; each round replaces the
+// part that is not the round function's input by its XOR with the round
+// function (Philox word x0 of the other part, masked to the replaced
+// part's width) and swaps the parts, so after the four rounds the widths
+// are back in place.  With bits even this is the balanced network.
+__device__ __forceinline__ uint32_t feistel(uint32_t x, int bits, uint32_t k0, uint32_t k1, uint32_t ctr) {
+    const int wa = bits >> 1, wb = bits - wa;
+    uint32_t A = x >> wb, B = x & ((1u << wb) - 1u);
+    int la = wa, lb = wb;
 #pragma unroll
     for (uint32_t rnd = 0; rnd < 4; ++rnd) {
-        const uint32_t F = philox4x32_10(make_uint4(R, rnd, ctr, 4u), k0, k1).x & mask;
-        const uint32_t nL = R;
-        R = (L ^ F) & mask;
-        L = nL;
+        const uint32_t m = (1u << la) - 1u;
+        const uint32_t F = philox4x32_10(make_uint4(B, rnd, ctr, 4u), k0, k1).x & m;
+        const uint32_t nB = (A ^ F) & m;
+        A = B;
+        B = nB;
+        const int t = la;
+        la = lb;
+        lb = t;
     }
-    return (L << half) | R;
+    return (A << wb) | B;
 }
 
 __device__ __forceinline__ uint32_t mb_row(const MbDesc& d, int j) {
-    uint32_t x = feistel((uint32_t)(d.lo + j), d.half, d.k0, d.k1, d.ctr);
-    while (x >= d.N) x = feistel(x, d.half, d.k0, d.k1, d.ctr);
+    uint32_t x = feistel((uint32_t)(d.lo + j), d.bits, d.k0, d.k1, d.ctr);
+    while (x >= d.N) x = feistel(x, d.bits, d.k0, d.k1, d.ctr);
     return x;
 }
 

@@ -91,11 +91,10 @@ Ws ws_layout(const KParams& kp, const EjPpoParams* pp, int T, int H, int agents 
     return w;
 }
 
-int half_bits(uint64_t N) {
+int domain_bits(uint64_t N) {
     int b = 2;
     while ((1ull << b) < N) ++b;
-    b += b & 1;
-    return b / 2;
+    return b;
 }
 
 ej_status check_common(const EjParams* p, const EjPpoParams* pp, int T, int H, Layout* lay, KParams* kp) {
@@ -157,7 +156,7 @@ MbDesc mb_desc(const KParams& kp, const EjPpoParams* pp, int T, int net, uint32_
     mb.lo = (int)((N * m) / pp->minibatches);
     mb.count = (int)((N * (m + 1)) / pp->minibatches) - mb.lo;
     mb.N = (uint32_t)N;
-    mb.half = half_bits(N);
+    mb.bits = domain_bits(N);
     mb.k0 = (uint32_t)pp->seed;
     mb.k1 = (uint32_t)(pp->seed >> 32);
     mb.ctr = ctr;
@@ -172,7 +171,7 @@ MbDesc mb_desc_positions(const KParams& kp, const EjPpoParams* pp, int T, uint32
     mb.lo = (int)((N * m) / pp->minibatches);
     mb.count = (int)((N * (m + 1)) / pp->minibatches) - mb.lo;
     mb.N = (uint32_t)N;
-    mb.half = half_bits(N);
+    mb.bits = domain_bits(N);
     mb.k0 = (uint32_t)pp->seed;
     mb.k1 = (uint32_t)(pp->seed >> 32);
     mb.ctr = ctr;

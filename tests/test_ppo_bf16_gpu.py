@@ -13,9 +13,11 @@ accumulates in float32.  Two references:
   largest entry.
 * the exact float64 gradient: here the rounding itself counts, including
   ReLU units whose pre-activation sign flips under rounding, which moves a
-  whole term; the stated BF16 error is relative L2 <= 6e-2 per tensor,
-  every entry within 0.2 of the tensor's largest entry (measured values are
-  printed).
+  whole term, so the error depends on the rows (a 32-row government slice
+  reaches 0.1 relative L2 in W2).  The bound is derived per tensor: the
+  kernel's distance from the exact gradient is at most the BF16-operand
+  form's own distance from it plus the first reference's tolerance
+  (measured values are printed).
 """
 import numpy as np
 import pytest
@@ -30,7 +32,6 @@ pytestmark = pytest.mark.gpu
 
 H = 128
 TIGHT = (2e-3, 1e-2)        # against the BF16-operand oracle
-LOOSE = (6e-2, 2e-1)        # against the exact float64 gradient
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -103,6 +104,24 @@ def _compare(env, net, grad, g64, tol, label):
     return worst
 
 
+def _compare_exact(env, net, grad, gbf, g64):
+    """The kernel against the exact gradient, per tensor: relative L2 and
+    relative max error at most those of the BF16-operand form (gbf) plus
+    TIGHT."""
+    in_dim = env.D if net == 0 else env.G
+    O = env.nA if net == 0 else env.p.nb * env.p.tax_levels
+    gg = synth.unpack(grad, in_dim, H, O)
+    errs = {}
+    for k, ref in g64.items():
+        scale_l2, scale_mx = max(np.linalg.norm(ref), 1e-30), max(np.abs(ref).max(), 1e-30)
+        got = gg[k].reshape(ref.shape)
+        l2, mx = np.linalg.norm(got - ref) / scale_l2, np.max(np.abs(got - ref)) / scale_mx
+        f_l2, f_mx = np.linalg.norm(gbf[k] - ref) / scale_l2, np.max(np.abs(gbf[k] - ref)) / scale_mx
+        errs[k] = (float(f"{l2:.2e}"), float(f"{f_l2:.2e}"))
+        assert l2 <= f_l2 + TIGHT[0] and mx <= f_mx + TIGHT[1], (k, l2, f_l2, mx, f_mx)
+    print("bf16 gradient vs float64 oracle (kernel rel L2, BF16-operand form rel L2):", errs)
+
+
 @pytest.mark.parametrize("net", [0, 1])
 def test_bf16_gradient_small_slice(net):
     """One partial tile: 2 (or 8) environments x 4 agents x 16 steps, minibatch 1 of 4."""
@@ -116,7 +135,7 @@ def test_bf16_gradient_small_slice(net):
     loss, g64, st = _oracle(env, b, ppo.pp, net, rows, wv)
     _, gbf, _ = _oracle(env, b, ppo.pp, net, rows, wv, operand=oppo.bf16_round)
     _compare(env, net, grad.cpu().numpy(), gbf, TIGHT, "bf16-operand oracle")
-    _compare(env, net, grad.cpu().numpy(), g64, LOOSE, "float64 oracle")
+    _compare_exact(env, net, grad.cpu().numpy(), gbf, g64)
     s = stats.cpu().numpy()
     assert s[2] / len(rows) == pytest.approx(st["pg"], abs=2e-2 * (1 + abs(st["pg"])))
     assert s[4] / len(rows) == pytest.approx(st["ent"], rel=2e-2)
@@ -138,7 +157,7 @@ def test_bf16_gradient_many_tiles_ragged(net):
     _, g64, _ = _oracle(env, b, ppo.pp, net, rows, wv)
     _, gbf, _ = _oracle(env, b, ppo.pp, net, rows, wv, operand=oppo.bf16_round)
     _compare(env, net, grad.cpu().numpy(), gbf, TIGHT, "bf16-operand oracle")
-    _compare(env, net, grad.cpu().numpy(), g64, LOOSE, "float64 oracle")
+    _compare_exact(env, net, grad.cpu().numpy(), gbf, g64)
 
 
 def test_bf16_update_moves_weights_like_fp32():
