@@ -53,7 +53,7 @@ def magnitude(w, x):
     return lg, v
 
 
-def _setup(E, A, seed=0, steps=37, precision="fp32", **kw):
+def _setup(E, A, seed=0, steps=37, precision="fp32", hidden=None, **kw):
     P, N = _mods()
     env = P.VecEnv(E, A, **kw)
     env.reset(seed=seed)
@@ -63,9 +63,10 @@ def _setup(E, A, seed=0, steps=37, precision="fp32", **kw):
     mask = out["mask"][-1].contiguous()
     D, G = env.D, env.G
     O_pop, O_gov = env.nA, env.p.nb * env.p.tax_levels
-    pw = synth.net_weights(seed, 0, D, H, O_pop)
-    gw = synth.net_weights(seed, 1, G, H, O_gov)
-    pol = P.Policy(env, torch.from_numpy(pw), torch.from_numpy(gw), hidden=H, precision=precision)
+    hid = H if hidden is None else hidden
+    pw = synth.net_weights(seed, 0, D, hid, O_pop)
+    gw = synth.net_weights(seed, 1, G, hid, O_gov)
+    pol = P.Policy(env, torch.from_numpy(pw), torch.from_numpy(gw), hidden=hid, precision=precision)
     return env, pol, obs, gobs, mask, pw, gw
 
 
@@ -464,13 +465,15 @@ def test_rollout_graph_replay_equals_eager():
         assert torch.equal(res[0][k], res[1][k]), k
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
-def test_full_size_forward_sampled_rows(precision):
+@pytest.mark.parametrize("precision,hidden", [("fp32", 128), ("bf16", 128), ("bf16", 256)])
+def test_full_size_forward_sampled_rows(precision, hidden):
     """The rollout workload's size, E = 4096 x A = 100 (409,600 rows, 3,200 tiles: every CTA and both
-    warpgroup pipelines run many tiles): 3,000 sampled rows checked against the float64 forward, and
-    every sampled action against the oracle's float32 sampler on the kernel's logits."""
+    warpgroup pipelines run many tiles; at hidden 256 every cluster): 3,000 sampled rows checked
+    against the float64 forward, and every sampled action against the oracle's float32 sampler on the
+    kernel's logits."""
     E, A = 4096, 100
-    env, pol, obs, gobs, mask, pw, gw = _setup(E, A, seed=8, steps=5, precision=precision, T_ep=1000, T_tax=100)
+    env, pol, obs, gobs, mask, pw, gw = _setup(E, A, seed=8, steps=5, precision=precision, hidden=hidden,
+                                               T_ep=1000, T_tax=100)
     P, N = _mods()
     out = pol.forward(N.NET_POP, obs, mask, logits=True, entropy=True)
     rng = np.random.default_rng(8)
@@ -479,7 +482,7 @@ def test_full_size_forward_sampled_rows(precision):
     lg = out["logits"].cpu().numpy()[rows]
     val = out["value"].cpu().numpy()[rows]
     x = obs.cpu().numpy().reshape(E * A, env.D)[rows]
-    _check_forward(lg, val, synth.unpack(pw, env.D, H, env.nA), x, env.D, precision)
+    _check_forward(lg, val, synth.unpack(pw, env.D, hidden, env.nA), x, env.D, precision)
     valid = op.mask_bits(mask.cpu().numpy().view(np.uint32).reshape(E * A, env.W), env.nA)[rows]
     g = int(env.field("gstep")[0].item())
     u = synth.pop_draws(8, np.arange(E), A, g, 1, env.nA)[3][0].reshape(E * A)[rows]   # key = the reset seed
