@@ -653,8 +653,8 @@ def run_batched(args, dev, E_b=2048, T_b=1000, seed=4000):
     kw = dict(T_ep=T_EP, T_tax=T_TAX)
     from paper_2410_22165_gb300.batch import parse_candidate
     best, rates = autotune(pops, levels, weights, T_probe=8, repeats=5, device=dev,
-                           candidates=("exact", "pow2", "coarse", "exact+merge", "coarse+merge", "exact+chains1",
-                                       "exact+chains2", "pow2+chains2"), **kw)
+                           candidates=("exact", "pow2", "coarse", "exact+merge", "coarse+merge", "exact+merge+chains2",
+                                       "exact+chains1", "exact+chains2", "pow2+chains2"), **kw)
     gran, merged, chains = parse_candidate(best)
     br = BatchedRollout(pops, levels, T_b, weights, granularity=gran, merge=merged, chains=chains, device=dev, **kw)
     br.reset(seed=seed)

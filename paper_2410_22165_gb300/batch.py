@@ -18,7 +18,11 @@ between the networks by rows (policy_forward_segments, one table entry per
 class and network); then each class's env_step runs on its own stream.  Per
 step the graph holds one policy node and one env_step node per class instead
 of three launches per class.  The values, actions and states are those of the
-per-class rollouts, bit for bit.
+per-class rollouts, bit for bit.  With ``chains`` N as well, every class is
+split into N parts and part k of every class forms chain k: each chain's
+merged policy launch and env_steps run on a stream of its own, the chains
+interleaved step by step, so one chain's env_steps run beside another
+chain's policy launch.
 
 The partition is a tuning choice: ``exact`` (one class per distinct
 (P, population)), ``pow2`` (populations rounded up to a power of two: one CTA
@@ -74,8 +78,12 @@ class BatchedRollout:
     def __init__(self, pops, levels, T, weights, hidden=128, precision="bf16", granularity="pow2",
                  device="cuda", merge=False, chains=None, **env_kw):
         """weights: {("pop", P): tensor, ("gov",): tensor} in the library's layout.
-        chains: independent chains of environments per class rollout (1..4;
-        None: the library's choice), for the per-class (unmerged) rollouts."""
+        chains: independent chains of environments (1..4; None: the library's
+        choice): per class rollout for the unmerged rollouts; with merge,
+        every class is split into that many contiguous parts, part k of every
+        class forming chain k, whose merged policy launches and env_steps run
+        on a stream of their own (one chain's env_steps beside another's
+        policy launch)."""
         self.pops, self.levels, self.T = list(pops), list(levels), T
         self.device = torch.device(device)
         self.granularity = granularity
@@ -84,14 +92,23 @@ class BatchedRollout:
         # one device copy per network: classes with the same price grid share it
         weights = {k: v.to(self.device, torch.float32).contiguous() for k, v in weights.items()}
         self.classes = []
-        for P, A_max, idx in plan_classes(self.pops, self.levels, granularity):
-            env = VecEnv(len(idx), A_max, device=self.device, **price_grid(P), **env_kw)
-            pol = Policy(env, weights[("pop", P)], weights[("gov",)], hidden=hidden, precision=precision)
-            ro = Rollout(env, pol, T)
-            ro.chains = None if chains is None else max(1, min(int(chains), len(idx)))
-            pop = torch.tensor([self.pops[e] for e in idx], dtype=torch.int32, device=self.device)
-            self.classes.append(dict(P=P, A_max=A_max, idx=idx, env=env, policy=pol, ro=ro, pop=pop,
-                                     stream=torch.cuda.Stream(device=self.device)))
+        n_split = int(chains) if (merge and chains) else 1
+        for ci, (P, A_max, idx) in enumerate(plan_classes(self.pops, self.levels, granularity)):
+            for q in range(n_split):
+                part = idx[len(idx) * q // n_split: len(idx) * (q + 1) // n_split]
+                if not part:
+                    continue
+                k = (q + ci) % n_split           # rotated per class: small classes spread over the chains
+                env = VecEnv(len(part), A_max, device=self.device, **price_grid(P), **env_kw)
+                pol = Policy(env, weights[("pop", P)], weights[("gov",)], hidden=hidden, precision=precision)
+                ro = Rollout(env, pol, T)
+                ro.chains = None if (chains is None or merge) else max(1, min(int(chains), len(part)))
+                pop = torch.tensor([self.pops[e] for e in part], dtype=torch.int32, device=self.device)
+                self.classes.append(dict(P=P, A_max=A_max, idx=part, env=env, policy=pol, ro=ro, pop=pop, chain=k,
+                                         stream=torch.cuda.Stream(device=self.device)))
+        # one stream per merged chain beyond the first (the first runs on the caller's stream)
+        self.chain_ids = sorted({c["chain"] for c in self.classes})
+        self.chain_streams = {k: torch.cuda.Stream(device=self.device) for k in self.chain_ids[1:]}
         self.graph = None
 
     @property
@@ -103,13 +120,15 @@ class BatchedRollout:
             c["ro"].reset(seed=seed + 7919 * k, pop_sizes=c["pop"])
         torch.cuda.synchronize(self.device)
 
-    def _policies(self, t, stream):
-        """Step t's policy launches of every class (population and government
-        networks) in one policy_forward_segments call (t = T: values only)."""
-        n = 2 * len(self.classes)
+    def _policies(self, t, stream, classes=None):
+        """Step t's policy launches of the given classes (default: all;
+        population and government networks) in one policy_forward_segments
+        call (t = T: values only)."""
+        classes = self.classes if classes is None else classes
+        n = 2 * len(classes)
         last = t == self.T
         V = C.c_void_p * n
-        segs = [(c, net) for c in self.classes for net in (N.NET_POP, N.NET_GOV)]
+        segs = [(c, net) for c in classes for net in (N.NET_POP, N.NET_GOV)]
 
         def buf(c, pop_key, gov_key, net):
             return _ptr(c["ro"].buf[pop_key if net == N.NET_POP else gov_key][t])
@@ -127,24 +146,31 @@ class BatchedRollout:
             "policy_forward_segments")
 
     def _issue_merged(self):
-        """T + 1 steps of {every class's policies in one call on the calling
-        stream, then each class's env_step on its own stream}, then the
-        slot-0 copies."""
+        """T + 1 steps of {a chain's classes' policies in one call on the
+        chain's stream, then each of its classes' env_step on its own
+        stream}, chains interleaved step by step, then the slot-0 copies."""
         main = torch.cuda.current_stream(self.device)
         T = self.T
+        cs = {k: (main if k == self.chain_ids[0] else self.chain_streams[k]) for k in self.chain_ids}
+        members = {k: [c for c in self.classes if c["chain"] == k] for k in self.chain_ids}
+        for k in self.chain_ids[1:]:
+            cs[k].wait_stream(main)
         for t in range(T + 1):
-            self._policies(t, main)
-            if t == T:
-                break
-            for c in self.classes:
-                c["stream"].wait_stream(main)
-                b = c["ro"].buf
-                c["env"].step(1, act=b["act"][t], gov_act=b["gact"][t], stream=c["stream"],
-                              out=dict(rew=b["rew"][t:t + 1], grew=b["grew"][t:t + 1],
-                                       done=b["done"][t:t + 1], obs=b["obs"][t + 1:t + 2],
-                                       gobs=b["gobs"][t + 1:t + 2], mask=b["mask"][t + 1:t + 2]))
-            for c in self.classes:
-                main.wait_stream(c["stream"])
+            for k in self.chain_ids:
+                self._policies(t, cs[k], members[k])
+                if t == T:
+                    continue
+                for c in members[k]:
+                    c["stream"].wait_stream(cs[k])
+                    b = c["ro"].buf
+                    c["env"].step(1, act=b["act"][t], gov_act=b["gact"][t], stream=c["stream"],
+                                  out=dict(rew=b["rew"][t:t + 1], grew=b["grew"][t:t + 1],
+                                           done=b["done"][t:t + 1], obs=b["obs"][t + 1:t + 2],
+                                           gobs=b["gobs"][t + 1:t + 2], mask=b["mask"][t + 1:t + 2]))
+                for c in members[k]:
+                    cs[k].wait_stream(c["stream"])
+        for k in self.chain_ids[1:]:
+            main.wait_stream(cs[k])
         for c in self.classes:
             c["ro"].carry_over()
 
@@ -192,8 +218,6 @@ def parse_candidate(cand: str):
             chains = int(p[6:])
         else:
             raise ValueError(cand)
-    if merge and chains is not None:
-        raise ValueError(f"{cand}: merged launches have no per-class chains")
     return gran, merge, chains
 
 
@@ -203,11 +227,12 @@ def autotune(pops, levels, weights, T_probe=8, hidden=128, precision="bf16", can
     events on the replaying stream, the median of `repeats` replays); returns
     (best candidate, {candidate: agent-steps/s}).  A candidate is a partition
     granularity (the environment CTA size of each class follows from it),
-    with "+merge" for merged policy launches ("exact+merge") or "+chainsN"
-    for N independent environment chains per class rollout (policy and
-    env_step of different chains overlapping)."""
+    with "+merge" for merged policy launches ("exact+merge") and "+chainsN"
+    for N independent chains of environments (per class rollout, or with
+    "+merge" each class split into N parts forming N merged chains), so that
+    policy launches and env_steps of different chains overlap."""
     candidates = candidates or ("exact", "pow2", "coarse", "by_actions", "exact+merge", "coarse+merge",
-                                "exact+chains1", "exact+chains2", "pow2+chains2")
+                                "exact+merge+chains2", "exact+chains1", "exact+chains2", "pow2+chains2")
     rates = {}
     parsed = {cand: parse_candidate(cand) for cand in candidates}    # every name checked before any work
     for cand in candidates:

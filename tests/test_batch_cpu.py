@@ -62,7 +62,8 @@ def test_candidate_names():
     assert parse_candidate("exact") == ("exact", False, None)
     assert parse_candidate("coarse+merge") == ("coarse", True, None)
     assert parse_candidate("pow2+chains3") == ("pow2", False, 3)
-    for bad in ("exact+chains5", "exact+chains0", "exact+merge+chains2", "tiny", "exact+fast"):
+    assert parse_candidate("exact+merge+chains2") == ("exact", True, 2)
+    for bad in ("exact+chains5", "exact+chains0", "tiny", "exact+fast"):
         with pytest.raises(ValueError):
             parse_candidate(bad)
     with pytest.raises(ValueError):              # a bad name later in the list: refused before any work

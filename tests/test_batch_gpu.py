@@ -116,6 +116,37 @@ def test_merged_policy_launches_equal_per_class_rollouts(granularity):
         assert torch.equal(ca["env"].state, cb["env"].state)
 
 
+def test_merged_chains_equal_per_class_rollouts():
+    """Merged policy launches in 2 chains (every class split into two parts,
+    part k of every class in chain k, chains on their own streams, interleaved
+    per step): every part's buffers and state equal a stand-alone rollout of
+    that part (the library's rollout with the same seed), eager and captured."""
+    import paper_2410_22165_gb300 as P
+    T = 6
+    kw = dict(T_ep=5, T_tax=3)
+    w = _weights(8)
+    b = P.BatchedRollout(POPS, LEVELS, T, w, granularity="exact", merge=True, chains=2, **kw)
+    assert {c["chain"] for c in b.classes} == {0, 1} and len(b.chain_streams) == 1
+    b.reset(seed=31)
+    b.capture()                 # one eager run inside, then the graph
+    b.run()
+    torch.cuda.synchronize()
+    for k, c in enumerate(b.classes):
+        env = P.VecEnv(len(c["idx"]), c["A_max"], **P.price_grid(c["P"]), **kw)
+        pol = P.Policy(env, c["policy"].pop_w, c["policy"].gov_w, hidden=128, precision="bf16")
+        ro = P.Rollout(env, pol, T)
+        ro.reset(seed=31 + 7919 * k, pop_sizes=c["pop"])
+        for r in range(2):
+            if r:
+                ro.carry_over()
+            ro.run()
+        ro.carry_over()
+        torch.cuda.synchronize()
+        for n, v in ro.buf.items():
+            assert torch.equal(v, c["ro"].buf[n]), (k, n)
+        assert torch.equal(env.state, c["env"].state), k
+
+
 def test_chains_per_class_equal_one_chain():
     """Class rollouts split into 2 and 3 chains of environments (the
     autotuner's "+chainsN" candidates) give the one-chain buffers and states
