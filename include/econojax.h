@@ -409,9 +409,11 @@ ej_status rollout_split(const EjParams* p, void* state, int32_t T, int32_t hidde
  *   - ent_coef * mean(entropy),       r = exp(logp - logp_old), R = A + v_old.
  * Minibatch m of an epoch holds the rollout rows pi(p), p in
  * [floor(m N / M), floor((m+1) N / M)), N = T * rows per step, where pi is
- * the Feistel permutation of [0, N) (4 rounds on 2h bits, Philox word x0 of
- * counter (R, round, shuffle_ctr, 4) as round function, cycle walking into
- * [0, N)) keyed by `seed`.  ppo_update uses shuffle_ctr = update_index *
+ * the Feistel permutation of [0, N) (4 rounds on b = max(2, ceil(log2 N))
+ * bits: a high part of b / 2 bits and a low part of the rest, each round
+ * XORing the part that is not its input with Philox word x0 of counter
+ * (input part, round, shuffle_ctr, 4) masked to that part's width and
+ * swapping the parts; cycle walking into [0, N)) keyed by `seed`.  ppo_update uses shuffle_ctr = update_index *
  * epochs + epoch for the population, with bit 31 set for the government. */
 typedef struct {
     float gamma;         /* discount (0.99) */
