@@ -14,7 +14,11 @@
 // products.  The weight gradients of all tiles accumulate in tensor memory
 // (they are sums over rows, i.e. MMAs with K = rows): dW = A^T dZ reads the
 // stored activation tiles as MN-major (transposed) operands, so no transposed
-// copy is ever written.  Bias gradients are MMAs against an all-ones operand.
+// copy is ever written.  Bias gradients come with the weight gradients: the
+// second layer's as the transposed product dW2^T | db2 = dZ2^T [H1 | 1] (an
+// all-ones panel follows H1 in shared memory), the first layer's from the
+// inputs' ones column, the head's against an all-ones operand; the value
+// head's bias gradient (a plain sum of dv) on the CUDA cores.
 // Each backward-data product (dZ2, dZ1) is committed on its own and the
 // weight-gradient products issued behind it, so an epilogue waits only for
 // the product it reads; the weight-gradient products finish under the next
@@ -66,12 +70,13 @@ constexpr int PC = 352;        // accumulator columns written per TMEM lane
 // heads of 21: 18.4).
 constexpr double PPO_TILE = 11.9, PPO_LOSS_REG = 4.5, PPO_LOSS_GROUP = 1.9;
 
-// TMEM columns.  Actor: dW1^T [h][in] 0..63, dW2 [h_in][h_out] 64..191,
-// dW3 [h][o] 192..255, db2 (column 256), db3 [o] 272..335 (every lane).
-// Critic: dV1^T 0..63, dV2 64..191, dV3 (192), dc2 (208), dc3 (224).
-// Both: per-tile products in 384..511.
-constexpr uint32_t C_W1T = 0, C_W2 = 64, C_W3 = 192, C_B2 = 256, C_B3 = 272;
-constexpr uint32_t C_V3 = 192, C_C2 = 208, C_C3 = 224;
+// TMEM columns.  Actor: dW1^T [h][in] 0..63, dW2^T [h_out][h_in] 64..191 and
+// db2 (192, from the same product: dZ2^T [H1 | 1]), dW3 [h][o] 208..271, db3
+// [o] 272..335 (every lane).  Critic: dV1^T 0..63, dV2^T 64..191 and dc2 (192),
+// dV3 (208); dc3 is summed on the CUDA cores and stored at column 224 of the
+// CTA's partial row 0.  Both: per-tile products in 384..511.
+constexpr uint32_t C_W1T = 0, C_W2 = 64, C_B2 = 192, C_W3 = 208, C_B3 = 272;
+constexpr uint32_t C_C2 = 192, C_V3 = 208, C_C3 = 224;
 constexpr uint32_t C_SLOT = 384;
 
 // Shared memory (bytes from the 1024-aligned base).
@@ -83,7 +88,7 @@ struct PpoSmem {
 //   w1: W1 / V1 [128][KX]        w2: W2 / V2 [128][128]      w3: W3 [KO][128] (actor)
 //   x:  inputs [128][KX]         h1: H1 / G1 [128][128]      h2: H2 / G2, later dZ1 / dY1
 //   dl: dL [128][KO] (actor)     dz2: dZ2 / dY2 [128][128]   dv: dv [16][128] (critic)
-//   ones: all-ones [128][64]     bias: floats
+//   ones: all-ones [128][64] (follows h1)     bias: floats
 __host__ __device__ inline PpoSmem ppo_smem() {
     PpoSmem L;
     uint32_t b = 0;
@@ -92,10 +97,10 @@ __host__ __device__ inline PpoSmem ppo_smem() {
     L.w3 = b;   b += KO * HID * 2;
     L.x = b;    b += BM * KX * 2;
     L.h1 = b;   b += BM * HID * 2;
+    L.ones = b; b += BM * 64 * 2;      // right after H1: [H1 | 1] is one MN-major operand of 192 columns
     L.h2 = b;   b += BM * HID * 2;
     L.dl = b;   b += BM * KO * 2;
     L.dz2 = b;  b += BM * HID * 2;
-    L.ones = b; b += BM * 64 * 2;
     L.dv = b;   b += 16 * BM * 2;
     L.bias = b; b += (3 * HID + KO + 2 * BM + HID + 2 * BM) * 4;
     L.total = b;
@@ -575,7 +580,7 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
     __shared__ uint64_t bar;
     __shared__ uint32_t tmem_slot;
     __shared__ uint32_t src_rows[2][BM];      // rollout rows of this tile and of the next
-    __shared__ float red[5][BT / 32];
+    __shared__ float red[6][BT / 32];
     const FbArgs& a = P.f;
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const PpoSmem L = ppo_smem();
@@ -639,6 +644,7 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
     const float inv_n = 1.0f / (float)nrows_mb;
 
     float acc_st[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};   // pg, vf, ent, clip, kl of this thread's rows
+    float dc3_part = 0.0f;                               // critic: sum of this thread's rows' BF16 dv
     uint32_t phase = 0;
     bool ok = true, first = true, pending = false;
     const int n_tiles = (a.mb.count + BM - 1) / BM;
@@ -825,11 +831,10 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
                 chain<HID / 16, K_MAJ, BM, MN_MAJ, HID>(tmem + C_SLOT, idesc_bf16(BM, HID) | TB, false, kdesc(sdz2),
                                                          mndesc<HID>(sw2));
                 mma_commit(&bar);
-                // dW2 += H1^T dZ2;  db2 += dZ2^T 1: done by the tile's last commit
-                chain<BM / 16, MN_MAJ, BM, MN_MAJ, BM>(tmem + C_W2, idesc_bf16(BM, HID) | TA | TB, !first,
-                                                        mndesc<BM>(sh1), mndesc<BM>(sdz2));
-                chain<BM / 16, MN_MAJ, BM, K_ONE, BM>(tmem + C_B2, idesc_bf16(BM, 16) | TA, !first, mndesc<BM>(sdz2),
-                                                       kdesc(sones));
+                // dW2^T | db2 += dZ2^T [H1 | 1] (the all-ones panel follows H1): done by the
+                // tile's last commit
+                chain<BM / 16, MN_MAJ, BM, MN_MAJ, BM>(tmem + C_W2, idesc_bf16(BM, HID + 16) | TA | TB, !first,
+                                                        mndesc<BM>(sdz2), mndesc<BM>(sh1));
             }
         } else {
             // G2, and the value head on the CUDA cores: each thread's half of the
@@ -850,7 +855,9 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
                     dv = (la >= lb ? (v - R) : ((vc - R) * (fabsf(dvv) < a.vclip ? 1.0f : 0.0f))) * a.vf_coef * inv_n;
                 }
                 dv_s[row] = dv;
-                *reinterpret_cast<__nv_bfloat16*>(smem + L.dv + sw128_offset(0, row, 16)) = __float2bfloat16_rn(dv);
+                const __nv_bfloat16 dvb = __float2bfloat16_rn(dv);
+                *reinterpret_cast<__nv_bfloat16*>(smem + L.dv + sw128_offset(0, row, 16)) = dvb;
+                dc3_part += __bfloat162float(dvb);       // dc3: the sum of the BF16 operand dv
             }
             __syncthreads();
             // dY2 = dv V3^T, masked by [g2 > 0] (G2 is in the h2 buffer)
@@ -882,12 +889,9 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
                 chain<BM / 16, MN_MAJ, BM, K_MAJ, 16>(tmem + C_V3, idesc_bf16(BM, 16) | TA, !first, mndesc<BM>(sh2),
                                                        kdesc(sdv));
                 mma_commit(&bar);
-                // dV2 += G1^T dY2;  dc2 += dY2^T 1;  dc3 += 1^T dv: done by the tile's last commit
-                chain<BM / 16, MN_MAJ, BM, MN_MAJ, BM>(tmem + C_W2, idesc_bf16(BM, HID) | TA | TB, !first,
-                                                        mndesc<BM>(sh1), mndesc<BM>(sdz2));
-                chain<BM / 16, MN_MAJ, BM, K_ONE, BM>(tmem + C_C2, idesc_bf16(BM, 16) | TA, !first, mndesc<BM>(sdz2),
-                                                       kdesc(sones));
-                chain<BM / 16, K_ONE, BM, K_MAJ, 16>(tmem + C_C3, idesc_bf16(BM, 16), !first, kdesc(sones), kdesc(sdv));
+                // dV2^T | dc2 += dY2^T [G1 | 1]: done by the tile's last commit
+                chain<BM / 16, MN_MAJ, BM, MN_MAJ, BM>(tmem + C_W2, idesc_bf16(BM, HID + 16) | TA | TB, !first,
+                                                        mndesc<BM>(sdz2), mndesc<BM>(sh1));
             }
         }
         if (!(ok = wait_mma(&bar, phase))) break;
@@ -921,10 +925,10 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
         // a wait gave up: give the tensor core one more bounded chance to finish before freeing TMEM
         mbar_wait(&bar, phase, 200000000LL);
     }
-    // loss statistics of this CTA's rows
+    // loss statistics of this CTA's rows, and the critic's dc3
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        float v = acc_st[q];
+    for (int q = 0; q < 6; ++q) {
+        float v = q < 5 ? acc_st[q] : dc3_part;
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
         if (lane == 0) red[q][warp] = v;
     }
@@ -935,6 +939,12 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
         double s = 0.0;
         for (int k = 0; k < BT / 32; ++k) s += red[tid][k];
         if (s != 0.0) atomicAdd(&a.stats[ST_PG + tid], s);
+    }
+    if (tid == 5 && ok && !actor) {
+        // after the accumulator dump above (ordered by the barrier): dc3 of this CTA
+        float s = 0.0f;
+        for (int k = 0; k < BT / 32; ++k) s += red[5][k];
+        P.partial[(size_t)blockIdx.x * BM * PC + C_C3] = s;
     }
     if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
 }
@@ -949,7 +959,7 @@ __global__ void ppo_bf16_reduce_kernel(const float* __restrict__ partial, int n_
         auto in = [&](size_t base, size_t n) { return p >= base && p < base + n; };
         if (in(o.W1, (size_t)I * HID)) { lane = (int)((p - o.W1) % HID); col = C_W1T + (int)((p - o.W1) / HID); }
         else if (in(o.b1, HID)) { lane = (int)(p - o.b1); col = C_W1T + I; }
-        else if (in(o.W2, HID * HID)) { lane = (int)((p - o.W2) / HID); col = C_W2 + (int)((p - o.W2) % HID); }
+        else if (in(o.W2, HID * HID)) { lane = (int)((p - o.W2) % HID); col = C_W2 + (int)((p - o.W2) / HID); }
         else if (in(o.b2, HID)) { lane = (int)(p - o.b2); col = C_B2; }
         else if (in(o.W3, (size_t)HID * O)) { lane = (int)((p - o.W3) / O); col = C_W3 + (int)((p - o.W3) % O); }
         else if (in(o.b3, O)) { lane = 0; col = C_B3 + (int)(p - o.b3); }
@@ -957,7 +967,7 @@ __global__ void ppo_bf16_reduce_kernel(const float* __restrict__ partial, int n_
             act = false;
             if (in(o.V1, (size_t)I * HID)) { lane = (int)((p - o.V1) % HID); col = C_W1T + (int)((p - o.V1) / HID); }
             else if (in(o.c1, HID)) { lane = (int)(p - o.c1); col = C_W1T + I; }
-            else if (in(o.V2, HID * HID)) { lane = (int)((p - o.V2) / HID); col = C_W2 + (int)((p - o.V2) % HID); }
+            else if (in(o.V2, HID * HID)) { lane = (int)((p - o.V2) % HID); col = C_W2 + (int)((p - o.V2) / HID); }
             else if (in(o.c2, HID)) { lane = (int)(p - o.c2); col = C_C2; }
             else if (in(o.V3, HID)) { lane = (int)(p - o.V3); col = C_V3; }
             else if (in(o.c3, 1)) { lane = 0; col = C_C3; }
