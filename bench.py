@@ -632,7 +632,8 @@ def run_batched(args, dev, E_b=2048, T_b=1000, seed=4000):
     """Config 5: E_b environments with populations drawn uniformly from
     {10, 50, 100, 250, 500} and price grids from {5, 10, 20} levels (24, 44,
     84 actions), one network per action-space size; the partition into
-    classes is chosen by the autotuner (8-step probes), then one T_b-step
+    classes is chosen by the autotuner (64-step probes: long enough that the
+    replay's fixed costs, such as the per-class slot-0 copies, do not decide), then one T_b-step
     rollout of all classes is one CUDA-graph replay, timed with events."""
     import numpy as np
     import torch
@@ -652,7 +653,7 @@ def run_batched(args, dev, E_b=2048, T_b=1000, seed=4000):
         del probe
     kw = dict(T_ep=T_EP, T_tax=T_TAX)
     from paper_2410_22165_gb300.batch import parse_candidate
-    best, rates = autotune(pops, levels, weights, T_probe=8, repeats=5, device=dev,
+    best, rates = autotune(pops, levels, weights, T_probe=64, repeats=5, device=dev,
                            candidates=("exact", "pow2", "coarse", "exact+merge", "coarse+merge", "exact+merge+chains2",
                                        "exact+chains1", "exact+chains2", "pow2+chains2"), **kw)
     gran, merged, chains = parse_candidate(best)

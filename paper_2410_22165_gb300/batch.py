@@ -221,10 +221,13 @@ def parse_candidate(cand: str):
     return gran, merge, chains
 
 
-def autotune(pops, levels, weights, T_probe=8, hidden=128, precision="bf16", candidates=None,
+def autotune(pops, levels, weights, T_probe=64, hidden=128, precision="bf16", candidates=None,
              device="cuda", repeats=5, **env_kw):
     """Times a captured T_probe-step batched rollout per candidate (CUDA
-    events on the replaying stream, the median of `repeats` replays); returns
+    events on the replaying stream, the median of `repeats` replays; the probe
+    must be long enough that a replay's fixed costs, such as the per-class
+    copies of the last observation, do not decide between candidates with
+    different class counts); returns
     (best candidate, {candidate: agent-steps/s}).  A candidate is a partition
     granularity (the environment CTA size of each class follows from it),
     with "+merge" for merged policy launches ("exact+merge") and "+chainsN"
