@@ -810,6 +810,26 @@ def run_profile_case(args):
             res[prec] = {"launch_ms": ms, "useful_TFLOPs": flops / (statistics.mean(ms) / 1e3) / 1e12}
         print(json.dumps({"profile_case": "policy E=4096 A=100", **res}))
         return
+    if args.profile_case == "env1":
+        # single-step mode of the headline workload: one launch per step (state
+        # through HBM or L2 every step), E = 1024 x A = 100, every output
+        env = VecEnv(E, A, device="cuda", T_ep=T_EP, T_tax=T_TAX)
+        env.reset(seed=7)
+        n = args.warmup + args.steps
+        d = env.fill_draws(seed=7, g0=0, n_steps=n)
+        out = env.alloc_outputs(n)
+        ms = []
+        for k in range(n):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            env.step(1, act=d["act"][k:k + 1], gov_act=d["gov_act"][k:k + 1], gather_u=d["gather_u"][k:k + 1],
+                     tb=d["tb"][k:k + 1], out={key: v[k:k + 1] for key, v in out.items()})
+            b.record()
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                ms.append(a.elapsed_time(b))
+        print(json.dumps({"profile_case": "env single-step E=1024 A=100", "launch_ms": ms}))
+        return
     if args.profile_case == "policy256":
         # population forward with Section 5's networks of 256 units: the default
         # market (24 actions) and the 4-resource market (46 actions), BF16 and FP32
@@ -890,7 +910,7 @@ def run_profile_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-case", nargs="?", const="env", default=None, choices=["env", "policy", "policy256", "ppo"])
+    ap.add_argument("--profile-case", nargs="?", const="env", default=None, choices=["env", "env1", "policy", "policy256", "ppo"])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
