@@ -746,12 +746,14 @@ def oracle_throughput(target_s: float):
     wall = time.perf_counter() - t0
     value = n_env * A * T_EP / wall
     sample = f"{n_env} environments x A={A} x {T_EP} steps (whole episodes, all outputs), {wall:.1f} s wall"
-    return value, cores, sample
+    single = A * 100 / probe                       # one thread: the probe's 100 steps of one environment
+    return value, cores, sample, single
 
 
 def cpu_baseline(target_s):
-    value, cores, sample = oracle_throughput(target_s)
-    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    value, cores, sample, single = oracle_throughput(target_s)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "single_thread": single}
 
 
 def run_reference(args):
@@ -762,7 +764,7 @@ def run_reference(args):
     for _ in range(args.warmup):
         oracle_throughput(args.ref_seconds)
     for _ in range(args.steps):
-        v, cores, sample = oracle_throughput(args.ref_seconds)
+        v, cores, sample, _ = oracle_throughput(args.ref_seconds)
         per_step.append(v)
     value = statistics.mean(per_step)
     return {
