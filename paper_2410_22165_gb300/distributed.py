@@ -63,7 +63,9 @@ class DistributedPPO:
         self.updates = 0
 
     def _sum(self, t):
-        if dist.is_available() and dist.is_initialized() and dist.get_world_size(self.group) > 1:
+        # over the group whenever one is initialised (with one rank an identity
+        # that still goes through the backend, e.g. NCCL on the device)
+        if dist.is_available() and dist.is_initialized():
             dist.all_reduce(t, op=dist.ReduceOp.SUM, group=self.group)
         return t
 

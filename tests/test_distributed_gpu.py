@@ -99,3 +99,32 @@ def test_distributed_update_without_group_equals_update(precision):
     for a, b in ((ppo1.policy.pop_w, ppo2.policy.pop_w), (ppo1.policy.gov_w, ppo2.policy.gov_w)):
         # the advantage sums are double atomics (order not fixed): equal up to their last bits
         assert torch.allclose(a, b, rtol=0, atol=1e-7)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_nccl_one_rank_update_equals_update(precision):
+    """The update through a real NCCL process group (one rank on this GPU: the
+    all-reduces of the moments and gradients run on the device and sum one
+    part) equals PPO.update."""
+    import socket
+    import torch.distributed as dist
+    from paper_2410_22165_gb300.distributed import DistributedPPO
+    if not dist.is_available() or not dist.is_nccl_available():
+        pytest.skip("no NCCL")
+    import os
+    os.environ.setdefault("NCCL_NVLS_ENABLE", "0")     # no NVLink multicast objects
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1,
+                            device_id=torch.device("cuda", torch.cuda.current_device()))
+    try:
+        _, ro1, ppo1, _, _ = _rank(23, precision)
+        _, ro2, ppo2, _, _ = _rank(23, precision)
+        ppo1.update(ro1)
+        DistributedPPO(ppo2).update(ro2)
+        torch.cuda.synchronize()
+        for a, b in ((ppo1.policy.pop_w, ppo2.policy.pop_w), (ppo1.policy.gov_w, ppo2.policy.gov_w)):
+            assert torch.allclose(a, b, rtol=0, atol=1e-7)
+    finally:
+        dist.destroy_process_group()
