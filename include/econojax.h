@@ -293,7 +293,10 @@ ej_status ej_net_floats(const EjParams* p, int32_t net, int32_t hidden, uint64_t
  * networks of Section 5) with at most 64 inputs and 64 logits (a tile is
  * shared by the two CTAs of a thread-block cluster, each holding half of the
  * second layer's weights); other shapes return EJ_ERR_UNSUPPORTED (FP32 takes
- * them). */
+ * them).  FP32 takes every shape whose 64-row tile (inputs, two hidden-width
+ * buffers, logits twice) fits 227 KB of shared memory (e.g. hidden 256 with
+ * 123 inputs and 114 logits); larger ones return EJ_ERR_UNSUPPORTED before
+ * anything runs. */
 ej_status policy_forward(const EjParams* p, const void* state, int32_t net, int32_t hidden,
                          int32_t precision, const float* weights, const float* obs,
                          const uint32_t* mask, const float* u, int32_t* act, float* logp,
@@ -434,10 +437,11 @@ ej_status ej_ppo_params_default(EjPpoParams* pp);
 /* Bytes of the workspace the PPO calls need (caller-allocated, 256-byte
  * aligned, contents need no initialisation).  hidden: a multiple of 32 in
  * [32, 256] (Section 5's networks have 256 units).  The BF16 gradient takes
- * hidden 128; the FP32 gradient any of these widths whose 64-row tile (inputs,
- * three hidden-width buffers, logits) fits 227 KB of shared memory, e.g. hidden
- * 256 with Section 5's 4-resource market (39 inputs, 30 logits); larger shapes
- * return EJ_ERR_UNSUPPORTED from the gradient calls before anything runs. */
+ * hidden 128 (at most 63 inputs, 64 logits, 4 heads, 2 mask words); the FP32
+ * gradient takes every width, its 32-row tile (inputs, three hidden-width
+ * buffers, logits) fitting shared memory at any shape the calls take (inputs
+ * and logits at most 128).  Other shapes return EJ_ERR_UNSUPPORTED from the
+ * gradient and update calls before anything runs. */
 ej_status ej_ppo_workspace_bytes(const EjParams* p, const EjPpoParams* pp, int32_t T,
                                  int32_t hidden, uint64_t* bytes);
 

@@ -80,6 +80,9 @@ size_t policy_fp32_smem(int in_pad, int H, int O) {
 
 ej_status launch_policy_fp32(const PolicyArgs& a, cudaStream_t stream) {
     const size_t smem = policy_fp32_smem(a.in_pad, a.H, a.O);
+    if (smem > 227u * 1024u)
+        return fail(EJ_ERR_UNSUPPORTED, "float32 policy: %d inputs, hidden %d and %d logits need %zu bytes of shared "
+                    "memory per %d-row tile (at most %u)", a.in_pad, a.H, a.O, smem, TILE, 227u * 1024u);
     static SmemOptIn opt_in;
     ej_status st = opt_in.ensure((const void*)policy_fp32_kernel, smem);
     if (st != EJ_OK) return st;

@@ -214,20 +214,21 @@ __device__ __forceinline__ void sample_row(const PolicyArgs& a, int row, const f
 constexpr int TILE = 64;       // rows per tile
 constexpr int NTH = 256;       // threads per CTA
 
-// out[r][c] = act(b[c] + sum_k in[r][k] W[k][c]) for a TILE x N block, N a
-// multiple of 4 (here H = 128); b may be NULL (no bias).  Thread tile: 8 rows x 4 columns.
+// out[r][c] = act(b[c] + sum_k in[r][k] W[k][c]) for a ROWS x N block, N a
+// multiple of 4 (here H = 128); b may be NULL (no bias).  Thread tile: RT rows x 4 columns.
 // in: 16-byte aligned, ldi a multiple of 4.
+template <int ROWS = TILE, int RT = 8>
 __device__ inline void dense_tile(const float* in, int ldi, int K, const float* __restrict__ W,
                            const float* __restrict__ b, int N, float* out, int ldo, bool relu) {
     const int t = threadIdx.x;
     const int groups = N >> 2;                 // column groups of 4
-    for (int base = t; base < groups * (TILE / 8); base += NTH) {
+    for (int base = t; base < groups * (ROWS / RT); base += NTH) {
         const int cg = base % groups, rg = base / groups;
-        const int c0 = cg * 4, r0 = rg * 8;
-        float acc[8][4];
+        const int c0 = cg * 4, r0 = rg * RT;
+        float acc[RT][4];
         const float4 bb = b ? *reinterpret_cast<const float4*>(b + c0) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int r = 0; r < 8; ++r) { acc[r][0] = bb.x; acc[r][1] = bb.y; acc[r][2] = bb.z; acc[r][3] = bb.w; }
+        for (int r = 0; r < RT; ++r) { acc[r][0] = bb.x; acc[r][1] = bb.y; acc[r][2] = bb.z; acc[r][3] = bb.w; }
         // four k per step: 16-byte loads of the inputs (ldi is a multiple of 4),
         // four weight rows in flight; each accumulator still takes its k in order
         int k = 0;
@@ -237,7 +238,7 @@ __device__ inline void dense_tile(const float* in, int ldi, int K, const float* 
 #pragma unroll
             for (int q = 0; q < 4; ++q) w[q] = __ldg(reinterpret_cast<const float4*>(W + (size_t)(k + q) * N + c0));
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
+            for (int r = 0; r < RT; ++r) {
                 const float4 x4 = *reinterpret_cast<const float4*>(in + (r0 + r) * ldi + k);
                 const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
@@ -252,7 +253,7 @@ __device__ inline void dense_tile(const float* in, int ldi, int K, const float* 
         for (; k < K; ++k) {
             const float4 w = __ldg(reinterpret_cast<const float4*>(W + (size_t)k * N + c0));
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
+            for (int r = 0; r < RT; ++r) {
                 const float x = in[(r0 + r) * ldi + k];
                 acc[r][0] = fmaf(x, w.x, acc[r][0]);
                 acc[r][1] = fmaf(x, w.y, acc[r][1]);
@@ -261,7 +262,7 @@ __device__ inline void dense_tile(const float* in, int ldi, int K, const float* 
             }
         }
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
+        for (int r = 0; r < RT; ++r) {
             float4 v = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
             if (relu) { v.x = fmaxf(v.x, 0.0f); v.y = fmaxf(v.y, 0.0f); v.z = fmaxf(v.z, 0.0f); v.w = fmaxf(v.w, 0.0f); }
             *reinterpret_cast<float4*>(out + (r0 + r) * ldo + c0) = v;
@@ -270,9 +271,10 @@ __device__ inline void dense_tile(const float* in, int ldi, int K, const float* 
 }
 
 // Output head of width O (any): one thread per (row, column).
+template <int ROWS = TILE>
 __device__ inline void head_tile(const float* in, int ldi, int K, const float* __restrict__ W,
                           const float* __restrict__ b, int O, float* out, int ldo) {
-    for (int idx = threadIdx.x; idx < TILE * O; idx += NTH) {
+    for (int idx = threadIdx.x; idx < ROWS * O; idx += NTH) {
         const int r = idx / O, c = idx % O;
         float acc = b[c];
         const float* x = in + r * ldi;
@@ -283,10 +285,11 @@ __device__ inline void head_tile(const float* in, int ldi, int K, const float* _
 }
 
 // Critic output: one warp per row, lanes split the hidden units.
+template <int ROWS = TILE>
 __device__ inline void value_tile(const float* in, int ldi, int K, const float* __restrict__ v,
                            float c, float* out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int r = warp; r < TILE; r += NTH / 32) {
+    for (int r = warp; r < ROWS; r += NTH / 32) {
         float acc = 0.0f;
         for (int k = lane; k < K; k += 32) acc = fmaf(in[r * ldi + k], __ldg(v + k), acc);
 #pragma unroll

@@ -80,34 +80,37 @@ __global__ void zero_kernel(double* p, int n) {
 }
 
 // ---------------------------------- fused forward + loss + backward-data
-// Per tile of 64 minibatch rows: gather the rollout rows, run actor and
+// 32-row tiles (thread tiles of 4 rows x 4 columns): half the shared memory of
+// 64-row tiles, so two CTAs (16 warps) share an SM at hidden 128 and 256.
+constexpr int PTILE = 32;
+// Per tile of PTILE (32) minibatch rows: gather the rollout rows, run actor and
 // critic, form the gradient of the clipped PPO loss with respect to the
 // logits and the value, and back-propagate it through the hidden layers.
 // Every activation and activation gradient the weight gradients need is
 // written to the workspace.
-__global__ void __launch_bounds__(NTH, 1) fwd_bwd_kernel(FbArgs a) {
+__global__ void __launch_bounds__(NTH, 2) fwd_bwd_kernel(FbArgs a) {
     extern __shared__ __align__(16) float sm[];
     const int H = a.H, O = a.O, I = a.in_dim;
     const int ldx = a.in_pad, ldh = H + 4, ldo = ((O + 3) & ~3) + 4;
-    float* xs = sm;                      // [TILE][ldx]
-    float* B0 = xs + TILE * ldx;         // [TILE][ldh]
-    float* B1 = B0 + TILE * ldh;
-    float* B2 = B1 + TILE * ldh;
-    float* LG = B2 + TILE * ldh;         // [TILE][ldo]
-    float* VAL = LG + TILE * ldo;        // [TILE]
-    float* DV = VAL + TILE;              // [TILE]
+    float* xs = sm;                      // [PTILE][ldx]
+    float* B0 = xs + PTILE * ldx;         // [PTILE][ldh]
+    float* B1 = B0 + PTILE * ldh;
+    float* B2 = B1 + PTILE * ldh;
+    float* LG = B2 + PTILE * ldh;         // [PTILE][ldo]
+    float* VAL = LG + PTILE * ldo;        // [PTILE]
+    float* DV = VAL + PTILE;              // [PTILE]
     __shared__ float red[8][NTH / 32];
     const NetOffsets off = net_offsets(I, H, O);
     // advantage moments over the minibatch (or over the union of the ranks'
     // minibatches, when given: count, sum, sum of squares); per agent for
     // per-agent networks
     const double n_mb = a.moments ? a.moments[0] : (double)a.mb.count;
-    const int tpa = (a.mb.count + TILE - 1) / TILE;     // tiles per agent (the minibatch's, shared networks)
+    const int tpa = (a.mb.count + PTILE - 1) / PTILE;     // tiles per agent (the minibatch's, shared networks)
     const int n_tiles = a.agents ? a.agents * tpa : tpa;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int agent = a.agents ? tile / tpa : 0;
-        const int j0 = (a.agents ? tile % tpa : tile) * TILE;   // position in the (agent's) minibatch
-        const int nvalid = min(TILE, a.mb.count - j0);
+        const int j0 = (a.agents ? tile % tpa : tile) * PTILE;   // position in the (agent's) minibatch
+        const int nvalid = min(PTILE, a.mb.count - j0);
         const int base = agent * a.mb.count + j0;               // row of the per-row buffers
         const float* wa = a.weights + (size_t)agent * a.actor_stride;
         const float* wc = a.weights + (size_t)agent * a.critic_stride;
@@ -131,29 +134,29 @@ __global__ void __launch_bounds__(NTH, 1) fwd_bwd_kernel(FbArgs a) {
         // per-agent actors: over every agent's rows)
         const float inv_nc = (a.agents && !a.critic_stride) ? 1.0f / (float)(n * a.agents) : inv_n;
         // gather
-        __shared__ uint32_t src_row[TILE];
-        if (threadIdx.x < TILE) {
+        __shared__ uint32_t src_row[PTILE];
+        if (threadIdx.x < PTILE) {
             const int j = j0 + threadIdx.x;
             src_row[threadIdx.x] = j < a.mb.count ? (a.agents ? mb_row(a.mb, j) * (uint32_t)a.agents + (uint32_t)agent
                                                               : mb_row(a.mb, j)) : 0u;
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < TILE * ldx; idx += NTH) {
+        for (int idx = threadIdx.x; idx < PTILE * ldx; idx += NTH) {
             const int r = idx / ldx, k = idx % ldx;
             const bool in = r < nvalid && k < I;
             xs[idx] = in ? a.x[(size_t)src_row[r] * I + k] : 0.0f;
         }
         __syncthreads();
         // actor forward
-        dense_tile(xs, ldx, I, wa + off.W1, wa + off.b1, H, B0, ldh, true);
+        dense_tile<PTILE, 4>(xs, ldx, I, wa + off.W1, wa + off.b1, H, B0, ldh, true);
         __syncthreads();
-        dense_tile(B0, ldh, H, wa + off.W2, wa + off.b2, H, B1, ldh, true);
+        dense_tile<PTILE, 4>(B0, ldh, H, wa + off.W2, wa + off.b2, H, B1, ldh, true);
         __syncthreads();
-        head_tile(B1, ldh, H, wa + off.W3, wa + off.b3, O, LG, ldo);
+        head_tile<PTILE>(B1, ldh, H, wa + off.W3, wa + off.b3, O, LG, ldo);
         __syncthreads();
-        store_tile(xs, ldx, I, a.ws_x, base, nvalid);
-        store_tile(B0, ldh, H, a.ws_h1, base, nvalid);
-        store_tile(B1, ldh, H, a.ws_h2, base, nvalid);
+        store_tile<PTILE>(xs, ldx, I, a.ws_x, base, nvalid);
+        store_tile<PTILE>(B0, ldh, H, a.ws_h1, base, nvalid);
+        store_tile<PTILE>(B1, ldh, H, a.ws_h2, base, nvalid);
         // loss gradient with respect to the logits, one thread per row
         float pg = 0.0f, ent_sum = 0.0f, clipc = 0.0f, kl = 0.0f;
         if ((int)threadIdx.x < nvalid) {
@@ -217,34 +220,34 @@ __global__ void __launch_bounds__(NTH, 1) fwd_bwd_kernel(FbArgs a) {
             }
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < TILE * O; idx += NTH) {
+        for (int idx = threadIdx.x; idx < PTILE * O; idx += NTH) {
             const int r = idx / O, c = idx % O;
             if (r < nvalid) a.ws_dl[(size_t)(base + r) * O + c] = LG[r * ldo + c];
         }
         // dZ2 = (dL W3^T) * [h2 > 0]
-        dense_tile(LG, ldo, O, w3t, nullptr, H, B2, ldh, false);
+        dense_tile<PTILE, 4>(LG, ldo, O, w3t, nullptr, H, B2, ldh, false);
         __syncthreads();
-        mask_tile(B2, ldh, B1, H);
+        mask_tile<PTILE>(B2, ldh, B1, H);
         __syncthreads();
-        store_tile(B2, ldh, H, a.ws_dz2, base, nvalid);
+        store_tile<PTILE>(B2, ldh, H, a.ws_dz2, base, nvalid);
         // dZ1 = (dZ2 W2^T) * [h1 > 0]
-        dense_tile(B2, ldh, H, w2t, nullptr, H, B1, ldh, false);
+        dense_tile<PTILE, 4>(B2, ldh, H, w2t, nullptr, H, B1, ldh, false);
         __syncthreads();
-        mask_tile(B1, ldh, B0, H);
+        mask_tile<PTILE>(B1, ldh, B0, H);
         __syncthreads();
-        store_tile(B1, ldh, H, a.ws_dz1, base, nvalid);
+        store_tile<PTILE>(B1, ldh, H, a.ws_dz1, base, nvalid);
         // critic forward
-        dense_tile(xs, ldx, I, wc + off.V1, wc + off.c1, H, B0, ldh, true);
+        dense_tile<PTILE, 4>(xs, ldx, I, wc + off.V1, wc + off.c1, H, B0, ldh, true);
         __syncthreads();
-        dense_tile(B0, ldh, H, wc + off.V2, wc + off.c2, H, B1, ldh, true);
+        dense_tile<PTILE, 4>(B0, ldh, H, wc + off.V2, wc + off.c2, H, B1, ldh, true);
         __syncthreads();
-        value_tile(B1, ldh, H, wc + off.V3, wc[off.c3], VAL);
-        store_tile(B0, ldh, H, a.ws_g1, base, nvalid);
-        store_tile(B1, ldh, H, a.ws_g2, base, nvalid);
+        value_tile<PTILE>(B1, ldh, H, wc + off.V3, wc[off.c3], VAL);
+        store_tile<PTILE>(B0, ldh, H, a.ws_g1, base, nvalid);
+        store_tile<PTILE>(B1, ldh, H, a.ws_g2, base, nvalid);
         __syncthreads();
         // value-loss gradient (clipped value loss), one thread per row
         float vf = 0.0f;
-        if (threadIdx.x < TILE) {
+        if (threadIdx.x < PTILE) {
             const int r = threadIdx.x;
             float dv = 0.0f;
             if (r < nvalid) {
@@ -261,17 +264,17 @@ __global__ void __launch_bounds__(NTH, 1) fwd_bwd_kernel(FbArgs a) {
         }
         __syncthreads();
         // dY2 = dv V3^T * [g2 > 0]
-        for (int idx = threadIdx.x; idx < TILE * H; idx += NTH) {
+        for (int idx = threadIdx.x; idx < PTILE * H; idx += NTH) {
             const int r = idx / H, c = idx % H;
             B2[r * ldh + c] = B1[r * ldh + c] > 0.0f ? DV[r] * __ldg(wc + off.V3 + c) : 0.0f;
         }
         __syncthreads();
-        store_tile(B2, ldh, H, a.ws_dy2, base, nvalid);
-        dense_tile(B2, ldh, H, v2t, nullptr, H, B1, ldh, false);
+        store_tile<PTILE>(B2, ldh, H, a.ws_dy2, base, nvalid);
+        dense_tile<PTILE, 4>(B2, ldh, H, v2t, nullptr, H, B1, ldh, false);
         __syncthreads();
-        mask_tile(B1, ldh, B0, H);
+        mask_tile<PTILE>(B1, ldh, B0, H);
         __syncthreads();
-        store_tile(B1, ldh, H, a.ws_dy1, base, nvalid);
+        store_tile<PTILE>(B1, ldh, H, a.ws_dy1, base, nvalid);
         // loss statistics
         float vals[5] = {pg, vf, ent_sum, clipc, kl};
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -435,7 +438,7 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
 
 size_t fwd_bwd_smem(int in_pad, int H, int O) {
     const int ldo = ((O + 3) & ~3) + 4;
-    return sizeof(float) * ((size_t)TILE * in_pad + 3 * (size_t)TILE * (H + 4) + (size_t)TILE * ldo + 2 * TILE);
+    return sizeof(float) * ((size_t)PTILE * in_pad + 3 * (size_t)PTILE * (H + 4) + (size_t)PTILE * ldo + 2 * PTILE);
 }
 
 ej_status launch_gae(const float* rew, const float* value, const uint8_t* done, int T, int rows,
@@ -469,7 +472,7 @@ ej_status launch_minibatch_grad(const FbArgs& fa, const WgJobs& jobs, int n_jobs
                                 float* grad, cudaStream_t s) {
     if (fwd_bwd_smem(fa.in_pad, fa.H, fa.O) > 227u * 1024u)
         return fail(EJ_ERR_UNSUPPORTED, "float32 PPO: %d inputs, hidden %d and %d logits need %zu bytes of shared memory "
-                    "per 64-row tile (at most %u)", fa.in_dim, fa.H, fa.O, fwd_bwd_smem(fa.in_pad, fa.H, fa.O), 227u * 1024u);
+                    "per 32-row tile (at most %u)", fa.in_dim, fa.H, fa.O, fwd_bwd_smem(fa.in_pad, fa.H, fa.O), 227u * 1024u);
     // transposed copies of the weights the backward pass multiplies by (per agent)
     const int na = fa.agents ? fa.agents : 1, nc = fa.agents && fa.critic_stride ? fa.agents : 1;
     transpose_batched_kernel<<<64 * na, 256, 0, s>>>(w3, fa.actor_stride, fa.H, fa.O, na, fa.w3t);
@@ -488,8 +491,8 @@ ej_status launch_minibatch_grad(const FbArgs& fa, const WgJobs& jobs, int n_jobs
     static SmemOptIn opt_in;
     ej_status st = opt_in.ensure((const void*)fwd_bwd_kernel, smem);
     if (st != EJ_OK) return st;
-    const int n_tiles = na * ((fa.mb.count + TILE - 1) / TILE);
-    int g2 = n_tiles < device_sms() ? n_tiles : device_sms();
+    const int n_tiles = na * ((fa.mb.count + PTILE - 1) / PTILE);
+    int g2 = n_tiles < 2 * device_sms() ? n_tiles : 2 * device_sms();   // two CTAs per SM
     fwd_bwd_kernel<<<g2, NTH, smem, s>>>(fa);
     int zt = 1, gmax = 1;
     for (int q = 0; q < n_jobs; ++q) {

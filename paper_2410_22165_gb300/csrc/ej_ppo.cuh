@@ -82,16 +82,18 @@ struct FbArgs {
 };
 
 // Rows [0, nvalid) of a tile buffer to rows [base, base + nvalid) of a per-row buffer.
+template <int ROWS = TILE>
 __device__ inline void store_tile(const float* buf, int ld, int ncols, float* dst, int base, int nvalid) {
-    for (int idx = threadIdx.x; idx < TILE * ncols; idx += NTH) {
+    for (int idx = threadIdx.x; idx < ROWS * ncols; idx += NTH) {
         const int r = idx / ncols, c = idx % ncols;
         if (r < nvalid) dst[(size_t)(base + r) * ncols + c] = buf[r * ld + c];
     }
 }
 
 // out[r][c] = ref[r][c] > 0 ? out[r][c] : 0  (ReLU derivative)
+template <int ROWS = TILE>
 __device__ inline void mask_tile(float* out, int ld, const float* ref, int ncols) {
-    for (int idx = threadIdx.x; idx < TILE * ncols; idx += NTH) {
+    for (int idx = threadIdx.x; idx < ROWS * ncols; idx += NTH) {
         const int r = idx / ncols, c = idx % ncols;
         if (!(ref[r * ld + c] > 0.0f)) out[r * ld + c] = 0.0f;
     }
@@ -144,7 +146,9 @@ ej_status launch_minibatch_loss(double* stats, int count, const double* moments,
 // minibatch-gradient inputs).
 ej_status check_rollout(const EjRollout* b, int net, bool gae, bool grad);
 // EJ_ERR_UNSUPPORTED when the float32 gradient's tile of network net (-1: both) exceeds shared memory.
-ej_status check_fp32_shape(const KParams& kp, int H, int precision, int net);
+// The BF16 gradient's shape limits (hidden, inputs, logits, heads, mask words).
+ej_status bf16_grad_shape(int in_dim, int H, int O, int n_heads, int W);
+ej_status check_grad_shape(const KParams& kp, int H, int precision, int net);
 ej_status launch_adv_stats(const MbDesc& mb, const float* adv, double* stats, cudaStream_t s);
 // Writes the minibatch's rollout rows (the permutation, once) and their advantage sums.
 ej_status launch_mb_rows_stats(const MbDesc& mb, const float* adv, uint32_t* rows, double* stats, cudaStream_t s);

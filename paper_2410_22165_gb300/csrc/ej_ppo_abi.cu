@@ -112,17 +112,23 @@ ej_status check_common(const EjParams* p, const EjPpoParams* pp, int T, int H, L
 
 }  // namespace
 
-// The float32 gradient's 64-row tile of network `net` (-1: both) fits shared memory.
-ej_status check_fp32_shape(const KParams& kp, int H, int precision, int net) {
-    if (precision != EJ_FP32) return EJ_OK;
+// The gradient kernels take network `net` (-1: both) at this precision: the
+// float32 32-row tile fits shared memory; the BF16 kernel's fixed widths hold
+// the shape.  Checked before anything is launched.
+ej_status check_grad_shape(const KParams& kp, int H, int precision, int net) {
     for (int n = 0; n < 2; ++n) {
         if (net >= 0 && n != net) continue;
         const int in = n == EJ_NET_POP ? kp.D : kp.G;
         const int O = n == EJ_NET_POP ? kp.nA : kp.nb * kp.tax_levels;
+        if (precision == EJ_BF16) {
+            const ej_status st = bf16_grad_shape(in, H, O, n == EJ_NET_POP ? 1 : kp.nb, n == EJ_NET_POP ? kp.W : 0);
+            if (st != EJ_OK) return st;
+            continue;
+        }
         const size_t smem = fwd_bwd_smem((in + 3) & ~3, H, O);
         if (smem > 227u * 1024u)
             return fail(EJ_ERR_UNSUPPORTED, "float32 PPO: %d inputs, hidden %d and %d logits need %zu bytes of shared "
-                        "memory per 64-row tile (at most %u)", in, H, O, smem, 227u * 1024u);
+                        "memory per 32-row tile (at most %u)", in, H, O, smem, 227u * 1024u);
     }
     return EJ_OK;
 }
@@ -401,7 +407,7 @@ ej_status ppo_minibatch_grad(const EjParams* p, const EjPpoParams* pp, int32_t T
     if (net != EJ_NET_POP && net != EJ_NET_GOV) return fail(EJ_ERR_ARG, "unknown network %d", net);
     if (!b || !workspace || !weights || !grad) return fail(EJ_ERR_ARG, "NULL argument");
     if ((st = check_rollout(b, net, false, true)) != EJ_OK) return st;
-    if ((st = check_fp32_shape(kp, hidden, precision, net)) != EJ_OK) return st;
+    if ((st = check_grad_shape(kp, hidden, precision, net)) != EJ_OK) return st;
     if ((uintptr_t)workspace % 256 || (uintptr_t)weights % 16) return fail(EJ_ERR_ARG, "misaligned buffer");
     if (minibatch < 0 || minibatch >= pp->minibatches) return fail(EJ_ERR_ARG, "minibatch out of range");
     const Ws W = ws_layout(kp, pp, T, hidden);
@@ -450,7 +456,7 @@ ej_status ppo_minibatch_grad_global(const EjParams* p, const EjPpoParams* pp, in
     if (net != EJ_NET_POP && net != EJ_NET_GOV) return fail(EJ_ERR_ARG, "unknown network %d", net);
     if (!b || !workspace || !weights || !grad || !moments) return fail(EJ_ERR_ARG, "NULL argument");
     if ((st = check_rollout(b, net, false, true)) != EJ_OK) return st;
-    if ((st = check_fp32_shape(kp, hidden, precision, net)) != EJ_OK) return st;
+    if ((st = check_grad_shape(kp, hidden, precision, net)) != EJ_OK) return st;
     if ((uintptr_t)workspace % 256 || (uintptr_t)weights % 16) return fail(EJ_ERR_ARG, "misaligned buffer");
     if (minibatch < 0 || minibatch >= pp->minibatches) return fail(EJ_ERR_ARG, "minibatch out of range");
     const Ws W = ws_layout(kp, pp, T, hidden);
@@ -486,7 +492,7 @@ ej_status ppo_update(const EjParams* p, const EjPpoParams* pp, int32_t T, int32_
     if (!pop_w || !gov_w || !pop_m || !pop_v || !gov_m || !gov_v || !b || !workspace)
         return fail(EJ_ERR_ARG, "NULL argument");
     if ((st = check_rollout(b, -1, true, true)) != EJ_OK) return st;
-    if ((st = check_fp32_shape(kp, hidden, precision, -1)) != EJ_OK) return st;
+    if ((st = check_grad_shape(kp, hidden, precision, -1)) != EJ_OK) return st;
     if ((uintptr_t)workspace % 256 || (uintptr_t)pop_w % 16 || (uintptr_t)gov_w % 16)
         return fail(EJ_ERR_ARG, "misaligned buffer");
     const Ws W = ws_layout(kp, pp, T, hidden);
@@ -552,7 +558,7 @@ ej_status ppo_minibatch_grad_agents(const EjParams* p, const EjPpoParams* pp, in
     if ((st = check_agents(layout, precision)) != EJ_OK) return st;
     if (!b || !workspace || !weights || !grad) return fail(EJ_ERR_ARG, "NULL argument");
     if ((st = check_rollout(b, EJ_NET_POP, false, true)) != EJ_OK) return st;
-    if ((st = check_fp32_shape(kp, hidden, precision, EJ_NET_POP)) != EJ_OK) return st;
+    if ((st = check_grad_shape(kp, hidden, precision, EJ_NET_POP)) != EJ_OK) return st;
     if ((uintptr_t)workspace % 256 || (uintptr_t)weights % 16) return fail(EJ_ERR_ARG, "misaligned buffer");
     if (minibatch < 0 || minibatch >= pp->minibatches) return fail(EJ_ERR_ARG, "minibatch out of range");
     const Ws W = ws_layout(kp, pp, T, hidden, kp.A);
@@ -582,7 +588,7 @@ ej_status ppo_update_agents(const EjParams* p, const EjPpoParams* pp, int32_t T,
     if (!pop_w || !gov_w || !pop_m || !pop_v || !gov_m || !gov_v || !b || !workspace)
         return fail(EJ_ERR_ARG, "NULL argument");
     if ((st = check_rollout(b, -1, true, true)) != EJ_OK) return st;
-    if ((st = check_fp32_shape(kp, hidden, precision, -1)) != EJ_OK) return st;
+    if ((st = check_grad_shape(kp, hidden, precision, -1)) != EJ_OK) return st;
     if ((uintptr_t)workspace % 256 || (uintptr_t)pop_w % 16 || (uintptr_t)gov_w % 16)
         return fail(EJ_ERR_ARG, "misaligned buffer");
     const Ws W = ws_layout(kp, pp, T, hidden, kp.A);

@@ -988,13 +988,18 @@ int sm_count() {
 
 }  // namespace
 
+ej_status bf16_grad_shape(int in_dim, int H, int O, int n_heads, int W) {
+    if (H != HID) return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: hidden must be %d", HID);
+    if (in_dim + 1 > KX) return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: input width must be <= %d", KX - 1);
+    if (O > KO) return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: at most %d logits", KO);
+    if (n_heads < 1 || n_heads > 4) return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: 1 to 4 action heads");
+    if (W > 2) return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: at most 2 mask words");
+    return EJ_OK;
+}
+
 ej_status launch_ppo_bf16(const FbArgs& fa, float* partial, size_t partial_bytes, float* grad, cudaStream_t s) {
-    if (fa.H != HID) return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: hidden must be %d", HID);
-    if (fa.in_dim + 1 > KX) return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: input width must be <= %d", KX - 1);
-    if (fa.O > KO) return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: at most %d logits", KO);
-    if (fa.n_heads < 1 || fa.n_heads > 4) return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: 1 to 4 action heads");
-    if (fa.W > 2) return fail(EJ_ERR_UNSUPPORTED, "bf16 PPO: at most 2 mask words");
-    ej_status st = EJ_OK;
+    ej_status st = bf16_grad_shape(fa.in_dim, fa.H, fa.O, fa.n_heads, fa.W);
+    if (st != EJ_OK) return st;
     if (!fa.rows && (st = launch_adv_stats(fa.mb, fa.adv, fa.stats, s)) != EJ_OK) return st;
     const NetOffsets off = net_offsets(fa.in_dim, HID, fa.O);
     const int n_tiles = (fa.mb.count + BM - 1) / BM;

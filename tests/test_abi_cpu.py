@@ -235,9 +235,8 @@ def test_step_host_argument_checks(lib):
 
 
 def test_ppo_hidden_limits(lib):
-    """Hidden widths: multiples of 32 up to 256 size a workspace; the
-    12-resource market at hidden 256 exceeds the float32 tile and BF16 takes
-    hidden 128 only: both refused on the host (EJ_ERR_UNSUPPORTED)."""
+    """Hidden widths: multiples of 32 up to 256 size a workspace; the BF16
+    gradient takes hidden 128 only: refused on the host (EJ_ERR_UNSUPPORTED)."""
     pp = N.EjPpoParams()
     lib.ej_ppo_params_default(C.byref(pp))
     p4 = N.make_params(E=2, A=4, R=4, P=3, price_ticks=[1, 2, 3], price_tick=3.0, Rd=2, gov_enabled=0)
@@ -249,9 +248,19 @@ def test_ppo_hidden_limits(lib):
     assert lib.ej_ppo_workspace_bytes(C.byref(p4), C.byref(pp), 8, 100, C.byref(nb)) == 3
     fake = C.c_void_p(4096)
     b = N.EjRollout(**{f: 4096 for f, _ in N.EjRollout._fields_})
-    for prec in (N.FP32, N.BF16):
-        st = lib.ppo_minibatch_grad(C.byref(p12), C.byref(pp), 8, 256, prec, 0, fake, C.byref(b), fake,
-                                    0, 0, fake, None, None)
-        assert st == 3, prec
-    assert lib.ppo_update(C.byref(p12), C.byref(pp), 8, 256, N.FP32, fake, fake, fake, fake, fake, fake, 0, 0,
+    st = lib.ppo_minibatch_grad(C.byref(p12), C.byref(pp), 8, 256, N.BF16, 0, fake, C.byref(b), fake,
+                                0, 0, fake, None, None)
+    assert st == 3
+    assert lib.ppo_update(C.byref(p12), C.byref(pp), 8, 256, N.BF16, fake, fake, fake, fake, fake, fake, 0, 0,
                           C.byref(b), fake, None, None) == 3
+
+
+def test_fp32_policy_tile_limit(lib):
+    """The float32 policy's 64-row tile of the 16-resource, 7-level market
+    (124 padded inputs, 242 logits) at hidden 256 exceeds shared memory:
+    refused on the host before anything runs."""
+    p = N.make_params(E=2, A=4, R=16, P=7, price_ticks=list(range(1, 8)), price_tick=3.0, Rd=3, gov_enabled=0)
+    fake = C.c_void_p(4096)
+    assert lib.policy_forward(C.byref(p), fake, 0, 256, N.FP32, fake, fake, None, None, None, None, fake,
+                              None, None, None) == 3
+    assert b"shared memory" in lib.ej_last_error()

@@ -153,18 +153,28 @@ def test_update_is_one_adam_step_per_minibatch():
         assert stats[net, 0] == pytest.approx(st["pg"], abs=1e-3 * (1 + abs(st["pg"])))
 
 
-@pytest.mark.parametrize("net", [0, 1])
-def test_section5_hidden256_gradient_matches_float64(net):
-    """Section 5's networks of 256 units on its 4-resource market (prices 3,
-    6, 9, no taxes, skills growing around 1): the float32 minibatch gradient
+# Section 5's 4-resource market (prices 3, 6, 9, no taxes, skills growing
+# around 1), and the largest market the PPO calls take (inputs and logits at
+# most 128): 16 resources at 3 price levels, 123 inputs, 114 logits
+MARKETS = {
+    "r4": dict(R=4, P=3, price_ticks=[1, 2, 3], price_tick=3.0, Rd=2, gov_enabled=0, skill_gain=0.005,
+               skill_init=1, T_ep=12, T_tax=4),
+    "r16": dict(R=16, P=3, price_ticks=[1, 2, 3], price_tick=3.0, Rd=3, gov_enabled=0, skill_gain=0.005,
+                skill_init=1, T_ep=12, T_tax=4),
+}
+
+
+@pytest.mark.parametrize("net,market", [(0, "r4"), (1, "r4"), (0, "r16")])
+def test_section5_hidden256_gradient_matches_float64(net, market):
+    """Section 5's networks of 256 units: the float32 minibatch gradient
     against the float64 oracle, every parameter tensor, within 1e-3 of the
-    tensor's largest entry (the weight-gradient kernel then spans 2 x 2
+    tensor's largest entry, on minibatches of 60 to 80 rows (two or three
+    32-row tiles, the last one ragged; the weight-gradient kernel spans 2 x 2
     output tiles of 128)."""
     import paper_2410_22165_gb300 as P
     H2 = 256
-    kw = dict(R=4, P=3, price_ticks=[1, 2, 3], price_tick=3.0, Rd=2, gov_enabled=0, skill_gain=0.005,
-              skill_init=1, T_ep=12, T_tax=4)
-    E, A, T = (2, 4, 16) if net == 0 else (8, 4, 16)
+    kw = MARKETS[market]
+    E, A, T = (3, 5, 16) if net == 0 else (15, 4, 16)
     env = P.VecEnv(E, A, **kw)
     O_gov = env.p.nb * env.p.tax_levels
     pw = synth.net_weights(4, 0, env.D, H2, env.nA)
@@ -201,13 +211,12 @@ def test_section5_hidden256_gradient_matches_float64(net):
     for k, ref in g64.items():
         tol = 1e-3 * np.abs(ref).max() + 1e-7
         assert np.max(np.abs(gg[k].reshape(ref.shape) - ref)) <= tol, k
-    assert env.nA == 30 and (net == 1 or env.D == 39)
+    assert (env.D, env.nA) == ((39, 30) if market == "r4" else (123, 114))
 
 
-def test_hidden256_shapes_beyond_shared_memory_are_refused():
-    """The 12-resource market (95 inputs, 86 logits) at hidden 256 does not
-    fit the float32 tile: refused on the host before anything runs; the BF16
-    gradient takes hidden 128 only."""
+def test_bf16_gradient_refuses_hidden_256():
+    """The BF16 gradient takes hidden 128 only: hidden 256 is refused on the
+    host before anything runs (EJ_ERR_UNSUPPORTED)."""
     import ctypes as C
     import paper_2410_22165_gb300 as P
     from paper_2410_22165_gb300 import _native as N
@@ -216,7 +225,6 @@ def test_hidden256_shapes_beyond_shared_memory_are_refused():
     N.load().ej_ppo_params_default(C.byref(pp))
     fake = C.c_void_p(4096)
     b = N.EjRollout(**{f: 4096 for f, _ in N.EjRollout._fields_})
-    for prec in (N.FP32, N.BF16):
-        st = N.load().ppo_minibatch_grad(C.byref(env.p), C.byref(pp), 8, 256, prec, 0, fake, C.byref(b), fake,
-                                         0, 0, fake, None, None)
-        assert st == 3, prec
+    st = N.load().ppo_minibatch_grad(C.byref(env.p), C.byref(pp), 8, 256, N.BF16, 0, fake, C.byref(b), fake,
+                                     0, 0, fake, None, None)
+    assert st == 3
