@@ -215,20 +215,28 @@ constexpr int TILE = 64;       // rows per tile
 constexpr int NTH = 256;       // threads per CTA
 
 // out[r][c] = act(b[c] + sum_k in[r][k] W[k][c]) for a ROWS x N block, N a
-// multiple of 4 (here H = 128); b may be NULL (no bias).  Thread tile: RT rows x 4 columns.
-// in: 16-byte aligned, ldi a multiple of 4.
+// multiple of 32 (the hidden width); b may be NULL (no bias).  Thread tile: RT
+// rows x 4 columns, the rows strided by ROWS / RT.  in: 16-byte aligned, ldi a
+// multiple of 4.  A warp covers 8 column groups x 4 row groups: per k it reads
+// 128 contiguous weight bytes (one L1 wavefront, where 32 column groups would
+// take four) and 4 consecutive input rows, on distinct banks for row pitches
+// of 4 to 28 floats mod 32.  Each output still sums its k in order.
 template <int ROWS = TILE, int RT = 8>
 __device__ inline void dense_tile(const float* in, int ldi, int K, const float* __restrict__ W,
                            const float* __restrict__ b, int N, float* out, int ldo, bool relu) {
-    const int t = threadIdx.x;
-    const int groups = N >> 2;                 // column groups of 4
-    for (int base = t; base < groups * (ROWS / RT); base += NTH) {
-        const int cg = base % groups, rg = base / groups;
-        const int c0 = cg * 4, r0 = rg * RT;
+    constexpr int RG = ROWS / RT;              // row groups
+    static_assert(RG % 4 == 0, "a warp covers 4 row groups");
+    const int cb = N >> 5;                     // warp tiles across the columns
+    for (int base = threadIdx.x; base < (N >> 2) * RG; base += NTH) {
+        const int lane = base & 31, blk = base >> 5;
+        const int bc = blk % cb;
+        const int c0 = (bc * 8 + (lane & 7)) * 4;
+        const int rg = (blk - bc) / cb * 4 + (lane >> 3);
         float acc[RT][4];
         const float4 bb = b ? *reinterpret_cast<const float4*>(b + c0) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int r = 0; r < RT; ++r) { acc[r][0] = bb.x; acc[r][1] = bb.y; acc[r][2] = bb.z; acc[r][3] = bb.w; }
+        const float* x0 = in + rg * ldi;
         // four k per step: 16-byte loads of the inputs (ldi is a multiple of 4),
         // four weight rows in flight; each accumulator still takes its k in order
         int k = 0;
@@ -239,7 +247,7 @@ __device__ inline void dense_tile(const float* in, int ldi, int K, const float* 
             for (int q = 0; q < 4; ++q) w[q] = __ldg(reinterpret_cast<const float4*>(W + (size_t)(k + q) * N + c0));
 #pragma unroll
             for (int r = 0; r < RT; ++r) {
-                const float4 x4 = *reinterpret_cast<const float4*>(in + (r0 + r) * ldi + k);
+                const float4 x4 = *reinterpret_cast<const float4*>(x0 + r * RG * ldi + k);
                 const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -254,7 +262,7 @@ __device__ inline void dense_tile(const float* in, int ldi, int K, const float* 
             const float4 w = __ldg(reinterpret_cast<const float4*>(W + (size_t)k * N + c0));
 #pragma unroll
             for (int r = 0; r < RT; ++r) {
-                const float x = in[(r0 + r) * ldi + k];
+                const float x = x0[r * RG * ldi + k];
                 acc[r][0] = fmaf(x, w.x, acc[r][0]);
                 acc[r][1] = fmaf(x, w.y, acc[r][1]);
                 acc[r][2] = fmaf(x, w.z, acc[r][2]);
@@ -265,7 +273,7 @@ __device__ inline void dense_tile(const float* in, int ldi, int K, const float* 
         for (int r = 0; r < RT; ++r) {
             float4 v = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
             if (relu) { v.x = fmaxf(v.x, 0.0f); v.y = fmaxf(v.y, 0.0f); v.z = fmaxf(v.z, 0.0f); v.w = fmaxf(v.w, 0.0f); }
-            *reinterpret_cast<float4*>(out + (r0 + r) * ldo + c0) = v;
+            *reinterpret_cast<float4*>(out + (rg + r * RG) * ldo + c0) = v;
         }
     }
 }
