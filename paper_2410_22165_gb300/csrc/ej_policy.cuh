@@ -278,17 +278,45 @@ __device__ inline void dense_tile(const float* in, int ldi, int K, const float* 
     }
 }
 
-// Output head of width O (any): one thread per (row, column).
-template <int ROWS = TILE>
+// Output head of width O (any): one thread per (row, column), IPT of them
+// in flight per thread (independent chains; each sums its k in order).
+template <int ROWS = TILE, int IPT = 1>
 __device__ inline void head_tile(const float* in, int ldi, int K, const float* __restrict__ W,
                           const float* __restrict__ b, int O, float* out, int ldo) {
-    for (int idx = threadIdx.x; idx < ROWS * O; idx += NTH) {
-        const int r = idx / O, c = idx % O;
-        float acc = b[c];
-        const float* x = in + r * ldi;
+    const int n = ROWS * O;
+    if constexpr (IPT == 1) {
+        for (int idx = threadIdx.x; idx < n; idx += NTH) {
+            const int r = idx / O, c = idx % O;
+            float acc = b[c];
+            const float* x = in + r * ldi;
 #pragma unroll 8
-        for (int k = 0; k < K; ++k) acc = fmaf(x[k], __ldg(W + (size_t)k * O + c), acc);
-        out[r * ldo + c] = acc;
+            for (int k = 0; k < K; ++k) acc = fmaf(x[k], __ldg(W + (size_t)k * O + c), acc);
+            out[r * ldo + c] = acc;
+        }
+        return;
+    }
+    for (int base = threadIdx.x; base < n; base += NTH * IPT) {
+        float acc[IPT];
+        const float* x[IPT];
+        int c[IPT];
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            const int idx = min(base + j * NTH, n - 1);     // past the end: recompute the last, not stored
+            c[j] = idx % O;
+            x[j] = in + (idx / O) * ldi;
+            acc[j] = b[c[j]];
+        }
+#pragma unroll 4
+        for (int k = 0; k < K; ++k) {
+            const float* wk = W + (size_t)k * O;
+#pragma unroll
+            for (int j = 0; j < IPT; ++j) acc[j] = fmaf(x[j][k], __ldg(wk + c[j]), acc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            const int idx = base + j * NTH;
+            if (idx < n) out[(idx / O) * ldo + idx % O] = acc[j];
+        }
     }
 }
 

@@ -79,6 +79,19 @@ __global__ void zero_kernel(double* p, int n) {
     for (int k = threadIdx.x; k < n; k += blockDim.x) p[k] = 0.0;
 }
 
+// Maximum and sum over an aligned group of eight lanes (mask `gm`); the
+// butterfly leaves the same value in every lane of the group.
+__device__ __forceinline__ float group8_max(float v, unsigned gm) {
+    v = fmaxf(v, __shfl_xor_sync(gm, v, 4, 8));
+    v = fmaxf(v, __shfl_xor_sync(gm, v, 2, 8));
+    return fmaxf(v, __shfl_xor_sync(gm, v, 1, 8));
+}
+__device__ __forceinline__ float group8_sum(float v, unsigned gm) {
+    v += __shfl_xor_sync(gm, v, 4, 8);
+    v += __shfl_xor_sync(gm, v, 2, 8);
+    return v + __shfl_xor_sync(gm, v, 1, 8);
+}
+
 // ---------------------------------- fused forward + loss + backward-data
 // 32-row tiles (thread tiles of 4 rows x 4 columns): half the shared memory of
 // 64-row tiles, so two CTAs (16 warps) share an SM at hidden 128 and 256.
@@ -152,15 +165,19 @@ __global__ void __launch_bounds__(NTH, 2) fwd_bwd_kernel(FbArgs a) {
         __syncthreads();
         dense_tile<PTILE, 4>(B0, ldh, H, wa + off.W2, wa + off.b2, H, B1, ldh, true);
         __syncthreads();
-        head_tile<PTILE>(B1, ldh, H, wa + off.W3, wa + off.b3, O, LG, ldo);
+        head_tile<PTILE, 4>(B1, ldh, H, wa + off.W3, wa + off.b3, O, LG, ldo);
         __syncthreads();
         store_tile<PTILE>(xs, ldx, I, a.ws_x, base, nvalid);
         store_tile<PTILE>(B0, ldh, H, a.ws_h1, base, nvalid);
         store_tile<PTILE>(B1, ldh, H, a.ws_h2, base, nvalid);
-        // loss gradient with respect to the logits, one thread per row
+        // loss gradient with respect to the logits: eight lanes per row, each
+        // taking every eighth logit of a head; maxima and sums over the eight
+        // lanes by butterflies (every lane ends with the same value)
         float pg = 0.0f, ent_sum = 0.0f, clipc = 0.0f, kl = 0.0f;
-        if ((int)threadIdx.x < nvalid) {
-            const int r = threadIdx.x;
+        static_assert(NTH == PTILE * 8, "eight lanes per row");
+        if ((int)(threadIdx.x >> 3) < nvalid) {
+            const int r = threadIdx.x >> 3, sub = threadIdx.x & 7;
+            const unsigned gm = 0xFFu << (threadIdx.x & 24);
             const uint32_t row = src_row[r];
             float* l = LG + r * ldo;
             const uint32_t* mw = a.W ? a.mask + (size_t)row * a.W : nullptr;
@@ -169,29 +186,32 @@ __global__ void __launch_bounds__(NTH, 2) fwd_bwd_kernel(FbArgs a) {
             for (int h = 0; h < a.n_heads; ++h) {
                 float* lh = l + h * a.head;
                 float m = -FLT_MAX;
-                for (int k = 0; k < a.head; ++k) {
+                for (int k = sub; k < a.head; k += 8) {
                     const int bit = h * a.head + k;
                     if (!mw || ((mw[bit >> 5] >> (bit & 31)) & 1u)) m = fmaxf(m, lh[k]);
                 }
+                m = group8_max(m, gm);
                 float S = 0.0f;
-                for (int k = 0; k < a.head; ++k) {
+                for (int k = sub; k < a.head; k += 8) {
                     const int bit = h * a.head + k;
                     if (!mw || ((mw[bit >> 5] >> (bit & 31)) & 1u)) S += expf(lh[k] - m);
                 }
-                const float logS = logf(S);
+                const float logS = logf(group8_sum(S, gm));
                 const int act = a.act[(size_t)row * a.n_heads + h];
                 logp += lh[act] - m - logS;
+                __syncwarp(gm);     // lh[act] read by every lane before it is overwritten
                 // keep log p in place (masked entries: +inf marker)
                 float Hh = 0.0f;
-                for (int k = 0; k < a.head; ++k) {
+                for (int k = sub; k < a.head; k += 8) {
                     const int bit = h * a.head + k;
                     const bool ok = !mw || ((mw[bit >> 5] >> (bit & 31)) & 1u);
                     const float lp = lh[k] - m - logS;
                     if (ok) Hh -= expf(lp) * lp;
                     lh[k] = ok ? lp : FLT_MAX;
                 }
+                Hh = group8_sum(Hh, gm);
                 ent_sum += Hh;
-                LG[r * ldo + O + (h & 3)] = Hh;   // per-head entropy (O is padded by at least 4)
+                if (sub == 0) LG[r * ldo + O + (h & 3)] = Hh;   // per-head entropy (O is padded by at least 4)
             }
             const float lpo = a.logp_old[row];
             const float ratio = expf(logp - lpo);
@@ -204,11 +224,12 @@ __global__ void __launch_bounds__(NTH, 2) fwd_bwd_kernel(FbArgs a) {
             const float dlogp = dratio * ratio * inv_n;
             clipc = fabsf(ratio - 1.0f) > a.clip ? 1.0f : 0.0f;
             kl = lpo - logp;
+            __syncwarp(gm);         // the entropies and every log p stored
             for (int h = 0; h < a.n_heads; ++h) {
                 float* lh = l + h * a.head;
                 const int act = a.act[(size_t)row * a.n_heads + h];
                 const float Hh = LG[r * ldo + O + (h & 3)];
-                for (int k = 0; k < a.head; ++k) {
+                for (int k = sub; k < a.head; k += 8) {
                     const float lp = lh[k];
                     float g = 0.0f;
                     if (lp != FLT_MAX) {
@@ -218,6 +239,7 @@ __global__ void __launch_bounds__(NTH, 2) fwd_bwd_kernel(FbArgs a) {
                     lh[k] = g;
                 }
             }
+            if (sub != 0) pg = ent_sum = clipc = kl = 0.0f;   // each row counted once in the statistics
         }
         __syncthreads();
         for (int idx = threadIdx.x; idx < PTILE * O; idx += NTH) {
@@ -298,10 +320,68 @@ __global__ void __launch_bounds__(NTH, 2) fwd_bwd_kernel(FbArgs a) {
 // Job q: G[m][n] = sum over minibatch rows of A[row][i] B[row][j], and the
 // bias gradient sum of B[row][j]; rows split in chunks over blockIdx.x, the
 // output in 128 x 128 tiles over blockIdx.z (hidden widths above 128).
+//
+// A block stages 32 rows of its A and B columns at a time in shared memory
+// (cp.async, two stages: the next rows land while these are multiplied).  A
+// thread owns an 8 x 8 block of G: rows {4 ti .. 4 ti + 3} and the same four
+// rows a half-tile further, columns likewise (16-byte shared loads of
+// consecutive threads are contiguous: no bank conflicts).  A tile narrower
+// than 128 x 128 needs fewer threads; the block then runs S row slices
+// (slice s takes rows s, s + S, ...) whose sums are added in slice order at
+// the end.
 constexpr int WG_ROWS = 32;
+constexpr int WG_PITCH = WG_TILE + 4;
+constexpr int WG_STAGE = 2 * WG_ROWS * WG_PITCH;        // floats of one stage (A and B)
 
-__global__ void __launch_bounds__(NTH) wgrad_kernel(WgJobs jobs, int rows, int chunks, size_t stride, int gmax,
+struct WgShape {
+    int tm, tn;      // 8 x 8 thread blocks over the tile's rows and columns
+    int tp;          // threads of one slice (power of two >= tm * tn)
+    int slices;      // NTH / tp
+};
+
+__host__ __device__ inline WgShape wg_shape(int m, int n) {
+    WgShape w;
+    const int mt = m < WG_TILE ? m : WG_TILE, nt = n < WG_TILE ? n : WG_TILE;
+    w.tm = (mt + 7) / 8;
+    w.tn = (nt + 7) / 8;
+    w.tp = 1;
+    while (w.tp < w.tm * w.tn) w.tp *= 2;
+    w.slices = NTH / w.tp;
+    return w;
+}
+
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// Copies rows [base, base + nr) of columns [c0, c0 + cols) of X (row pitch
+// ld) into S[WG_ROWS][WG_PITCH].  The rest of S is left as it is: rows past nr
+// are never read, and columns past cols only feed sums that are not stored.
+__device__ __forceinline__ void wg_stage_copy(float* S, const float* __restrict__ X, int ld, int c0, int cols,
+                                              int base, int nr, bool vec) {
+    if (vec) {      // ld, c0 and cols multiples of 4, X 16-byte aligned
+        const int cw = cols >> 2;
+        for (int k = threadIdx.x; k < nr * cw; k += NTH) {
+            const int r = k / cw, col = (k - r * cw) * 4;
+            cp_async16(S + r * WG_PITCH + col, X + (size_t)(base + r) * ld + c0 + col);
+        }
+    } else {
+        for (int k = threadIdx.x; k < nr * cols; k += NTH) {
+            const int r = k / cols, col = k - r * cols;
+            cp_async4(S + r * WG_PITCH + col, X + (size_t)(base + r) * ld + c0 + col);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(NTH, 2) wgrad_kernel(WgJobs jobs, int rows, int chunks, size_t stride, int gmax,
                                                     float* __restrict__ partial) {
+    extern __shared__ __align__(16) float wsm[];
     const WgJob jb = jobs.job[blockIdx.y];
     const int groups = jb.groups > 0 ? jb.groups : 1;
     const int grows = jb.groups > 0 ? jb.group_rows : rows;
@@ -310,53 +390,109 @@ __global__ void __launch_bounds__(NTH) wgrad_kernel(WgJobs jobs, int rows, int c
     if ((int)blockIdx.z >= groups * tiles) return;
     const int g = (int)blockIdx.z / tiles, tz = (int)blockIdx.z % tiles;
     const int m0 = (tz / tiles_n) * WG_TILE, n0 = (tz % tiles_n) * WG_TILE;
-    __shared__ __align__(16) float As[WG_ROWS][WG_TILE + 4];
-    __shared__ __align__(16) float Bs[WG_ROWS][WG_TILE + 4];
+    const int mt = min(WG_TILE, jb.m - m0), nt = min(WG_TILE, jb.n - n0);
+    const WgShape sh = wg_shape(jb.m, jb.n);
     const int c = blockIdx.x;
     const int r0 = g * grows + (int)(((long long)grows * c) / chunks);
     const int r1 = g * grows + (int)(((long long)grows * (c + 1)) / chunks);
-    const int ib = threadIdx.x / 16, jbk = threadIdx.x % 16;    // 16 x 16 blocks of 8 x 8
-    const int i0 = ib * 8, j0 = jbk * 8;
-    const bool active = m0 + i0 < jb.m && n0 + j0 < jb.n;
+    const int slice = threadIdx.x / sh.tp, t = threadIdx.x % sh.tp;
+    const bool active = t < sh.tm * sh.tn;
+    const int ti = active ? t / sh.tn : 0, tj = active ? t % sh.tn : 0;
+    const int hm = 4 * sh.tm, hn = 4 * sh.tn;        // the second four rows / columns
+    const bool vec_a = (jb.lda & 3) == 0 && (m0 & 3) == 0 && (mt & 3) == 0 && ((uintptr_t)jb.A & 15) == 0;
+    const bool vec_b = (jb.ldb & 3) == 0 && (n0 & 3) == 0 && (nt & 3) == 0 && ((uintptr_t)jb.B & 15) == 0;
     float acc[8][8];
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
     float bsum = 0.0f;
-    for (int base = r0; base < r1; base += WG_ROWS) {
+    const bool bias_col = m0 == 0 && (int)threadIdx.x < nt;
+    auto issue = [&](int stage, int base) {
+        float* As = wsm + stage * WG_STAGE;
         const int nr = min(WG_ROWS, r1 - base);
-        for (int k = threadIdx.x; k < WG_ROWS * WG_TILE; k += NTH) {
-            const int r = k / WG_TILE, col = k % WG_TILE;
-            As[r][col] = (r < nr && m0 + col < jb.m) ? jb.A[(size_t)(base + r) * jb.lda + m0 + col] : 0.0f;
-            Bs[r][col] = (r < nr && n0 + col < jb.n) ? jb.B[(size_t)(base + r) * jb.ldb + n0 + col] : 0.0f;
-        }
+        wg_stage_copy(As, jb.A, jb.lda, m0, mt, base, nr, vec_a);
+        wg_stage_copy(As + WG_ROWS * WG_PITCH, jb.B, jb.ldb, n0, nt, base, nr, vec_b);
+    };
+    if (r0 < r1) issue(0, r0);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    int it = 0;
+    for (int base = r0; base < r1; base += WG_ROWS, ++it) {
+        if (base + WG_ROWS < r1) issue((it + 1) & 1, base + WG_ROWS);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         __syncthreads();
+        const float* As = wsm + (it & 1) * WG_STAGE;
+        const float* Bs = As + WG_ROWS * WG_PITCH;
+        const int nr = min(WG_ROWS, r1 - base);
         if (active) {
-            for (int r = 0; r < nr; ++r) {
-                float av[8], bv[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) { av[q] = As[r][i0 + q]; bv[q] = Bs[r][j0 + q]; }
+            for (int r = slice; r < nr; r += sh.slices) {
+                const float4 a0 = *reinterpret_cast<const float4*>(As + r * WG_PITCH + 4 * ti);
+                const float4 a1 = *reinterpret_cast<const float4*>(As + r * WG_PITCH + hm + 4 * ti);
+                const float4 b0 = *reinterpret_cast<const float4*>(Bs + r * WG_PITCH + 4 * tj);
+                const float4 b1 = *reinterpret_cast<const float4*>(Bs + r * WG_PITCH + hn + 4 * tj);
+                const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
                 for (int x = 0; x < 8; ++x)
 #pragma unroll
                     for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
             }
         }
-        if (m0 == 0 && threadIdx.x < WG_TILE && n0 + (int)threadIdx.x < jb.n)
-            for (int r = 0; r < nr; ++r) bsum += Bs[r][threadIdx.x];
+        if (bias_col) {
+#pragma unroll
+            for (int r8 = 0; r8 < WG_ROWS; r8 += 8) {
+                float bt[8];        // loads issued together, then summed in row order
+#pragma unroll
+                for (int r = 0; r < 8; ++r) bt[r] = Bs[(r8 + r) * WG_PITCH + threadIdx.x];
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+                    if (r8 + r < nr) bsum += bt[r];
+            }
+        }
         __syncthreads();
     }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     float* out = partial + (((size_t)blockIdx.y * gmax + g) * chunks + c) * stride;
-    if (active) {
+    if (sh.slices > 1) {
+        // slice sums through shared memory (the staging buffers are free),
+        // added in slice order by slice 0
+        float* red = wsm;
+        if (active && slice > 0) {
 #pragma unroll
-        for (int x = 0; x < 8; ++x)
+            for (int x = 0; x < 8; ++x)
 #pragma unroll
-            for (int y = 0; y < 8; ++y)
-                if (m0 + i0 + x < jb.m && n0 + j0 + y < jb.n) out[(size_t)(m0 + i0 + x) * jb.n + (n0 + j0 + y)] = acc[x][y];
+                for (int y = 0; y < 8; ++y) red[((slice - 1) * sh.tp + t) * 64 + x * 8 + y] = acc[x][y];
+        }
+        __syncthreads();
+        if (active && slice == 0) {
+            for (int q = 1; q < sh.slices; ++q)
+#pragma unroll
+                for (int x = 0; x < 8; ++x)
+#pragma unroll
+                    for (int y = 0; y < 8; ++y) acc[x][y] += red[((q - 1) * sh.tp + t) * 64 + x * 8 + y];
+        }
     }
-    if (m0 == 0 && threadIdx.x < WG_TILE && n0 + (int)threadIdx.x < jb.n)
-        out[(size_t)jb.m * jb.n + n0 + threadIdx.x] = bsum;
+    if (active && slice == 0) {
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            const int i = x < 4 ? 4 * ti + x : hm + 4 * ti + x - 4;
+            if (i >= mt) continue;
+#pragma unroll
+            for (int y = 0; y < 8; ++y) {
+                const int j = y < 4 ? 4 * tj + y : hn + 4 * tj + y - 4;
+                if (j < nt) out[(size_t)(m0 + i) * jb.n + (n0 + j)] = acc[x][y];
+            }
+        }
+    }
+    if (bias_col) out[(size_t)jb.m * jb.n + n0 + threadIdx.x] = bsum;
+}
+
+size_t wgrad_smem() {
+    // two stages; the slice sums (at most (NTH - 1) / 2 ... NTH threads x 64) fit in them
+    const size_t stages = sizeof(float) * 2 * WG_STAGE;
+    const size_t red = sizeof(float) * (size_t)NTH * 64;
+    return stages > red ? stages : red;
 }
 
 __global__ void wgrad_reduce_kernel(WgJobs jobs, int n_jobs, int chunks, size_t stride, int gmax,
@@ -501,7 +637,10 @@ ej_status launch_minibatch_grad(const FbArgs& fa, const WgJobs& jobs, int n_jobs
         zt = t > zt ? t : zt;
         gmax = g > gmax ? g : gmax;
     }
-    wgrad_kernel<<<dim3(chunks, n_jobs, zt), NTH, 0, s>>>(jobs, na * fa.mb.count, chunks, stride, gmax, partial);
+    static SmemOptIn wg_opt_in;
+    if ((st = wg_opt_in.ensure((const void*)wgrad_kernel, wgrad_smem())) != EJ_OK) return st;
+    wgrad_kernel<<<dim3(chunks, n_jobs, zt), NTH, wgrad_smem(), s>>>(jobs, na * fa.mb.count, chunks, stride, gmax,
+                                                                     partial);
     wgrad_reduce_kernel<<<device_sms() * 4, 256, 0, s>>>(jobs, n_jobs, chunks, stride, gmax, partial, grad);
     return cudaGetLastError() == cudaSuccess ? EJ_OK : fail(EJ_ERR_CUDA, "minibatch gradient launch failed");
 }
