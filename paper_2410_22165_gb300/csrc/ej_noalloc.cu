@@ -146,16 +146,17 @@ extern "C" ej_status ppo_minibatch_grad_static(const EjParams* p, const EjPpoPar
     fa.stats = (double*)(sc + o_stats);      // cleared by the gradient launch itself
     const uint64_t R = (uint64_t)fa.mb.count;
     float* rb = (float*)(sc + o_rows);
-    fa.ws_x = rb; rb += R * in;
+    // hidden-width arrays first: each starts on a 16-byte boundary (H is a multiple of 32)
     fa.ws_h1 = rb; rb += R * H;
     fa.ws_h2 = rb; rb += R * H;
     fa.ws_g1 = rb; rb += R * H;
     fa.ws_g2 = rb; rb += R * H;
-    fa.ws_dl = rb; rb += R * O;
     fa.ws_dz2 = rb; rb += R * H;
     fa.ws_dz1 = rb; rb += R * H;
     fa.ws_dy2 = rb; rb += R * H;
     fa.ws_dy1 = rb; rb += R * H;
+    fa.ws_x = rb; rb += R * in;
+    fa.ws_dl = rb; rb += R * O;
     fa.ws_dv = rb;
     WgJobs jobs;
     memset(&jobs, 0, sizeof jobs);

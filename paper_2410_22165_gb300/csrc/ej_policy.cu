@@ -43,11 +43,10 @@ __global__ void __launch_bounds__(NTH, 2) policy_fp32_kernel(PolicyArgs a) {
         const float* wa = a.weights + (size_t)agent * a.actor_stride;
         const float* wc = a.weights + (size_t)agent * a.critic_stride;
         // observations of the tile (zero rows past the end, zero padding columns)
-        for (int idx = threadIdx.x; idx < TILE * ldx; idx += NTH) {
-            const int r = idx / ldx, k = idx % ldx;
+        tile_for<TILE>(ldx, [&](int r, int k) {
             const int row = row_of(r);
-            xs[idx] = (row >= 0 && k < in_dim) ? a.x[(size_t)row * in_dim + k] : 0.0f;
-        }
+            xs[r * ldx + k] = (row >= 0 && k < in_dim) ? a.x[(size_t)row * in_dim + k] : 0.0f;
+        });
         __syncthreads();
         // actor: two hidden layers and the logits
         dense_tile(xs, ldx, in_dim, wa + off.W1, wa + off.b1, H, hA, ldh, true);

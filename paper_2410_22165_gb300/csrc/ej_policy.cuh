@@ -214,6 +214,17 @@ __device__ __forceinline__ void sample_row(const PolicyArgs& a, int row, const f
 constexpr int TILE = 64;       // rows per tile
 constexpr int NTH = 256;       // threads per CTA
 
+// Visits (r, c) for r < ROWS, c < ncols (ncols <= NTH): thread t takes
+// column t % ncols of rows t / ncols, t / ncols + NTH / ncols, ... (one
+// division per call rather than per element).
+template <int ROWS, class F>
+__device__ __forceinline__ void tile_for(int ncols, F&& f) {
+    const int per = NTH / ncols, r0 = (int)threadIdx.x / ncols;
+    if (r0 >= per) return;
+    const int c = (int)threadIdx.x - r0 * ncols;
+    for (int r = r0; r < ROWS; r += per) f(r, c);
+}
+
 // out[r][c] = act(b[c] + sum_k in[r][k] W[k][c]) for a ROWS x N block, N a
 // multiple of 32 (the hidden width); b may be NULL (no bias).  Thread tile: RT
 // rows x 4 columns, the rows strided by ROWS / RT.  in: 16-byte aligned, ldi a

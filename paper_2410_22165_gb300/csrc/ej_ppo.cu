@@ -154,11 +154,10 @@ __global__ void __launch_bounds__(NTH, 2) fwd_bwd_kernel(FbArgs a) {
                                                               : mb_row(a.mb, j)) : 0u;
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < PTILE * ldx; idx += NTH) {
-            const int r = idx / ldx, k = idx % ldx;
+        tile_for<PTILE>(ldx, [&](int r, int k) {
             const bool in = r < nvalid && k < I;
-            xs[idx] = in ? a.x[(size_t)src_row[r] * I + k] : 0.0f;
-        }
+            xs[r * ldx + k] = in ? a.x[(size_t)src_row[r] * I + k] : 0.0f;
+        });
         __syncthreads();
         // actor forward
         dense_tile<PTILE, 4>(xs, ldx, I, wa + off.W1, wa + off.b1, H, B0, ldh, true);
@@ -242,10 +241,7 @@ __global__ void __launch_bounds__(NTH, 2) fwd_bwd_kernel(FbArgs a) {
             if (sub != 0) pg = ent_sum = clipc = kl = 0.0f;   // each row counted once in the statistics
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < PTILE * O; idx += NTH) {
-            const int r = idx / O, c = idx % O;
-            if (r < nvalid) a.ws_dl[(size_t)(base + r) * O + c] = LG[r * ldo + c];
-        }
+        store_tile<PTILE>(LG, ldo, O, a.ws_dl, base, nvalid);
         // dZ2 = (dL W3^T) * [h2 > 0]
         dense_tile<PTILE, 4>(LG, ldo, O, w3t, nullptr, H, B2, ldh, false);
         __syncthreads();
@@ -286,10 +282,17 @@ __global__ void __launch_bounds__(NTH, 2) fwd_bwd_kernel(FbArgs a) {
         }
         __syncthreads();
         // dY2 = dv V3^T * [g2 > 0]
-        for (int idx = threadIdx.x; idx < PTILE * H; idx += NTH) {
-            const int r = idx / H, c = idx % H;
-            B2[r * ldh + c] = B1[r * ldh + c] > 0.0f ? DV[r] * __ldg(wc + off.V3 + c) : 0.0f;
-        }
+        tile_for<PTILE>(H >> 2, [&](int r, int c4) {
+            const float4 g = *reinterpret_cast<const float4*>(B1 + r * ldh + 4 * c4);
+            const float4 v3 = __ldg(reinterpret_cast<const float4*>(wc + off.V3 + 4 * c4));
+            const float d = DV[r];
+            float4 o;
+            o.x = g.x > 0.0f ? d * v3.x : 0.0f;
+            o.y = g.y > 0.0f ? d * v3.y : 0.0f;
+            o.z = g.z > 0.0f ? d * v3.z : 0.0f;
+            o.w = g.w > 0.0f ? d * v3.w : 0.0f;
+            *reinterpret_cast<float4*>(B2 + r * ldh + 4 * c4) = o;
+        });
         __syncthreads();
         store_tile<PTILE>(B2, ldh, H, a.ws_dy2, base, nvalid);
         dense_tile<PTILE, 4>(B2, ldh, H, v2t, nullptr, H, B1, ldh, false);

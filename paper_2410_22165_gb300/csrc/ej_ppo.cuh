@@ -82,21 +82,38 @@ struct FbArgs {
 };
 
 // Rows [0, nvalid) of a tile buffer to rows [base, base + nvalid) of a per-row buffer.
+// dst[base + r][c] = buf[r][c] for the tile's first nvalid rows (dst row
+// pitch ncols); 16-byte copies when ncols is a multiple of 4 and dst is
+// 16-byte aligned (ld is a multiple of 4 at every call).
 template <int ROWS = TILE>
 __device__ inline void store_tile(const float* buf, int ld, int ncols, float* dst, int base, int nvalid) {
-    for (int idx = threadIdx.x; idx < ROWS * ncols; idx += NTH) {
-        const int r = idx / ncols, c = idx % ncols;
-        if (r < nvalid) dst[(size_t)(base + r) * ncols + c] = buf[r * ld + c];
+    if ((ncols & 3) == 0 && ((uintptr_t)dst & 15) == 0) {
+        tile_for<ROWS>(ncols >> 2, [&](int r, int c4) {
+            if (r < nvalid)
+                *reinterpret_cast<float4*>(dst + (size_t)(base + r) * ncols + 4 * c4) =
+                    *reinterpret_cast<const float4*>(buf + r * ld + 4 * c4);
+        });
+    } else {
+        tile_for<ROWS>(ncols, [&](int r, int c) {
+            if (r < nvalid) dst[(size_t)(base + r) * ncols + c] = buf[r * ld + c];
+        });
     }
 }
 
-// out[r][c] = ref[r][c] > 0 ? out[r][c] : 0  (ReLU derivative)
+// out[r][c] = ref[r][c] > 0 ? out[r][c] : 0  (ReLU derivative); ncols and ld
+// multiples of 4, out and ref 16-byte aligned.
 template <int ROWS = TILE>
 __device__ inline void mask_tile(float* out, int ld, const float* ref, int ncols) {
-    for (int idx = threadIdx.x; idx < ROWS * ncols; idx += NTH) {
-        const int r = idx / ncols, c = idx % ncols;
-        if (!(ref[r * ld + c] > 0.0f)) out[r * ld + c] = 0.0f;
-    }
+    tile_for<ROWS>(ncols >> 2, [&](int r, int c4) {
+        float4* o = reinterpret_cast<float4*>(out + r * ld + 4 * c4);
+        const float4 g = *reinterpret_cast<const float4*>(ref + r * ld + 4 * c4);
+        float4 v = *o;
+        if (!(g.x > 0.0f)) v.x = 0.0f;
+        if (!(g.y > 0.0f)) v.y = 0.0f;
+        if (!(g.z > 0.0f)) v.z = 0.0f;
+        if (!(g.w > 0.0f)) v.w = 0.0f;
+        *o = v;
+    });
 }
 
 constexpr int WG_STRIDE = 128 * 128 + 128;   // floats of one job's partial up to hidden 128

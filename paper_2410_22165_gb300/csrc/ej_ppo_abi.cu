@@ -223,16 +223,17 @@ ej_status minibatch_grad(const KParams& kp, const EjPpoParams* pp, int T, int H,
     }
     const uint64_t R = (uint64_t)fa.mb.count;
     float* rb = (float*)(ws + W.rows);
-    fa.ws_x = rb; rb += R * d.in;
+    // hidden-width arrays first: each starts on a 16-byte boundary (H is a multiple of 32)
     fa.ws_h1 = rb; rb += R * H;
     fa.ws_h2 = rb; rb += R * H;
     fa.ws_g1 = rb; rb += R * H;
     fa.ws_g2 = rb; rb += R * H;
-    fa.ws_dl = rb; rb += R * d.O;
     fa.ws_dz2 = rb; rb += R * H;
     fa.ws_dz1 = rb; rb += R * H;
     fa.ws_dy2 = rb; rb += R * H;
     fa.ws_dy1 = rb; rb += R * H;
+    fa.ws_x = rb; rb += R * d.in;
+    fa.ws_dl = rb; rb += R * d.O;
     fa.ws_dv = rb;
     WgJobs jobs;
     memset(&jobs, 0, sizeof jobs);
@@ -281,16 +282,17 @@ ej_status minibatch_grad_agents(const KParams& kp, const EjPpoParams* pp, int T,
     fa.agent_moments = (const double*)(ws + W.amom);
     const uint64_t cnt = (uint64_t)fa.mb.count, R = (uint64_t)Ag * cnt;
     float* rb = (float*)(ws + W.rows);
-    fa.ws_x = rb; rb += R * d.in;
+    // hidden-width arrays first: each starts on a 16-byte boundary (H is a multiple of 32)
     fa.ws_h1 = rb; rb += R * H;
     fa.ws_h2 = rb; rb += R * H;
     fa.ws_g1 = rb; rb += R * H;
     fa.ws_g2 = rb; rb += R * H;
-    fa.ws_dl = rb; rb += R * d.O;
     fa.ws_dz2 = rb; rb += R * H;
     fa.ws_dz1 = rb; rb += R * H;
     fa.ws_dy2 = rb; rb += R * H;
     fa.ws_dy1 = rb; rb += R * H;
+    fa.ws_x = rb; rb += R * d.in;
+    fa.ws_dl = rb; rb += R * d.O;
     fa.ws_dv = rb;
     WgJobs jobs;
     memset(&jobs, 0, sizeof jobs);
