@@ -93,15 +93,15 @@ __device__ __forceinline__ float group8_sum(float v, unsigned gm) {
 }
 
 // ---------------------------------- fused forward + loss + backward-data
-// 32-row tiles (thread tiles of 4 rows x 4 columns): half the shared memory of
-// 64-row tiles, so two CTAs (16 warps) share an SM at hidden 128 and 256.
+// 32-row tiles (thread tiles of 4 rows x 4 columns) and at most 80 registers
+// a thread: three CTAs (24 warps) share an SM at hidden 128, two at 256.
 constexpr int PTILE = 32;
 // Per tile of PTILE (32) minibatch rows: gather the rollout rows, run actor and
 // critic, form the gradient of the clipped PPO loss with respect to the
 // logits and the value, and back-propagate it through the hidden layers.
 // Every activation and activation gradient the weight gradients need is
 // written to the workspace.
-__global__ void __launch_bounds__(NTH, 2) fwd_bwd_kernel(FbArgs a) {
+__global__ void __launch_bounds__(NTH, 3) fwd_bwd_kernel(FbArgs a) {
     extern __shared__ __align__(16) float sm[];
     const int H = a.H, O = a.O, I = a.in_dim;
     const int ldx = a.in_pad, ldh = H + 4, ldo = ((O + 3) & ~3) + 4;
@@ -631,7 +631,11 @@ ej_status launch_minibatch_grad(const FbArgs& fa, const WgJobs& jobs, int n_jobs
     ej_status st = opt_in.ensure((const void*)fwd_bwd_kernel, smem);
     if (st != EJ_OK) return st;
     const int n_tiles = na * ((fa.mb.count + PTILE - 1) / PTILE);
-    int g2 = n_tiles < 2 * device_sms() ? n_tiles : 2 * device_sms();   // two CTAs per SM
+    // as many CTAs as fit an SM (three at hidden 128, two at 256)
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_bwd_kernel, NTH, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    int g2 = n_tiles < per_sm * device_sms() ? n_tiles : per_sm * device_sms();
     fwd_bwd_kernel<<<g2, NTH, smem, s>>>(fa);
     int zt = 1, gmax = 1;
     for (int q = 0; q < n_jobs; ++q) {
