@@ -38,11 +38,11 @@ __global__ void gae_kernel(const float* __restrict__ rew, const float* __restric
 // ------------------------------------- minibatch advantage statistics
 __global__ void adv_stats_kernel(MbDesc d, const float* __restrict__ adv, double* stats) {
     double s = 0.0, q = 0.0;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.count; j += gridDim.x * blockDim.x) {
-        const double a = adv[mb_row(d, j)];
+    mb_rows_strided(d, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, [&](int, uint32_t r) {
+        const double a = adv[r];
         s += a;
         q += a * a;
-    }
+    });
     for (int o = 16; o > 0; o >>= 1) {
         s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
         q += __shfl_xor_sync(0xFFFFFFFFu, q, o);
@@ -58,13 +58,12 @@ __global__ void adv_stats_kernel(MbDesc d, const float* __restrict__ adv, double
 __global__ void mb_rows_stats_kernel(MbDesc d, const float* __restrict__ adv, uint32_t* __restrict__ rows,
                                      double* stats) {
     double s = 0.0, q = 0.0;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.count; j += gridDim.x * blockDim.x) {
-        const uint32_t r = mb_row(d, j);
+    mb_rows_strided(d, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, [&](int j, uint32_t r) {
         rows[j] = r;
         const double a = adv[r];
         s += a;
         q += a * a;
-    }
+    });
     for (int o = 16; o > 0; o >>= 1) {
         s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
         q += __shfl_xor_sync(0xFFFFFFFFu, q, o);
@@ -537,11 +536,11 @@ __global__ void agent_moments_kernel(MbDesc d, int agents, const float* __restri
     __shared__ double ss[2][NTH];
     const int agent = blockIdx.x;
     double s = 0.0, q = 0.0;
-    for (int j = threadIdx.x; j < d.count; j += NTH) {
-        const double v = adv[(size_t)mb_row(d, j) * agents + agent];
+    mb_rows_strided(d, threadIdx.x, NTH, [&](int, uint32_t r) {
+        const double v = adv[(size_t)r * agents + agent];
         s += v;
         q += v * v;
-    }
+    });
     ss[0][threadIdx.x] = s;
     ss[1][threadIdx.x] = q;
     __syncthreads();

@@ -48,6 +48,24 @@ __device__ __forceinline__ uint32_t mb_row(const MbDesc& d, int j) {
     return x;
 }
 
+// f(j, mb_row(d, j)) for j = j0, j0 + stride, ... < d.count, in that order.
+// Each iteration applies the Feistel network once; a lane whose cycle walk
+// has landed in [0, N) moves on to its next position, so the lanes of a warp
+// stay busy while their walks differ in length.
+template <class F>
+__device__ __forceinline__ void mb_rows_strided(const MbDesc& d, int j0, int stride, F&& f) {
+    int j = j0;
+    uint32_t x = (uint32_t)(d.lo + j);
+    while (j < d.count) {
+        x = feistel(x, d.bits, d.k0, d.k1, d.ctr);
+        if (x < d.N) {
+            f(j, x);
+            j += stride;
+            x = (uint32_t)(d.lo + j);
+        }
+    }
+}
+
 struct FbArgs {
     MbDesc mb;
     int in_dim, in_pad, H, O, n_heads, head, W;
