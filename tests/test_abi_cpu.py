@@ -253,14 +253,3 @@ def test_ppo_hidden_limits(lib):
     assert st == 3
     assert lib.ppo_update(C.byref(p12), C.byref(pp), 8, 256, N.BF16, fake, fake, fake, fake, fake, fake, 0, 0,
                           C.byref(b), fake, None, None) == 3
-
-
-def test_fp32_policy_tile_limit(lib):
-    """The float32 policy's 64-row tile of the 16-resource, 7-level market
-    (124 padded inputs, 242 logits) at hidden 256 exceeds shared memory:
-    refused on the host before anything runs."""
-    p = N.make_params(E=2, A=4, R=16, P=7, price_ticks=list(range(1, 8)), price_tick=3.0, Rd=3, gov_enabled=0)
-    fake = C.c_void_p(4096)
-    assert lib.policy_forward(C.byref(p), fake, 0, 256, N.FP32, fake, fake, None, None, None, None, fake,
-                              None, None, None) == 3
-    assert b"shared memory" in lib.ej_last_error()

@@ -271,6 +271,14 @@ def test_section5_networks_of_256_units_fp32(R, Rd):
                                          gov_enabled=0, skill_gain=0.005, skill_init=1))
 
 
+def test_largest_market_fp32_hidden_256():
+    """The largest market under 256 actions (16 resources at 7 price levels:
+    123 inputs, 242 logits, 8 mask words) at hidden 256: the FP32 forward's
+    largest tile of shared memory, against the oracle."""
+    _forward_vs_oracle("fp32", 256, dict(R=16, P=7, price_tick=3.0, price_ticks=list(range(1, 8)), Rd=3,
+                                         gov_enabled=0))
+
+
 def test_section5_networks_of_256_units_bf16():
     """Section 5's 4-resource market (39 inputs, 46 actions) with networks of
     256 units in BF16 (the cluster kernel) against the oracle; the
