@@ -952,32 +952,41 @@ __global__ void __launch_bounds__(BT, 1) ppo_bf16_kernel(BfPpoArgs P) {
 // Sums the CTAs' accumulators into the gradient vector (padding = 0).
 __global__ void ppo_bf16_reduce_kernel(const float* __restrict__ partial, int n_actor, int n_critic, int I, int O,
                                        float* __restrict__ grad) {
+    // Items [0, 2 BM PC): one (role, lane, column) of the CTAs' partial rows,
+    // consecutive items on consecutive columns (coalesced reads), summed over
+    // the role's CTAs in CTA order into the parameter that column holds.
+    // Items past that: the parameter vector's padding, written 0.
     const NetOffsets o = net_offsets(I, HID, O);
-    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < o.total; p += (size_t)gridDim.x * blockDim.x) {
-        int lane = -1, col = 0;
-        bool act = true;
-        auto in = [&](size_t base, size_t n) { return p >= base && p < base + n; };
-        if (in(o.W1, (size_t)I * HID)) { lane = (int)((p - o.W1) % HID); col = C_W1T + (int)((p - o.W1) / HID); }
-        else if (in(o.b1, HID)) { lane = (int)(p - o.b1); col = C_W1T + I; }
-        else if (in(o.W2, HID * HID)) { lane = (int)((p - o.W2) % HID); col = C_W2 + (int)((p - o.W2) / HID); }
-        else if (in(o.b2, HID)) { lane = (int)(p - o.b2); col = C_B2; }
-        else if (in(o.W3, (size_t)HID * O)) { lane = (int)((p - o.W3) / O); col = C_W3 + (int)((p - o.W3) % O); }
-        else if (in(o.b3, O)) { lane = 0; col = C_B3 + (int)(p - o.b3); }
-        else {
-            act = false;
-            if (in(o.V1, (size_t)I * HID)) { lane = (int)((p - o.V1) % HID); col = C_W1T + (int)((p - o.V1) / HID); }
-            else if (in(o.c1, HID)) { lane = (int)(p - o.c1); col = C_W1T + I; }
-            else if (in(o.V2, HID * HID)) { lane = (int)((p - o.V2) % HID); col = C_W2 + (int)((p - o.V2) / HID); }
-            else if (in(o.c2, HID)) { lane = (int)(p - o.c2); col = C_C2; }
-            else if (in(o.V3, HID)) { lane = (int)(p - o.V3); col = C_V3; }
-            else if (in(o.c3, 1)) { lane = 0; col = C_C3; }
+    constexpr int per_role = BM * PC;
+    const size_t n_items = 2 * (size_t)per_role + o.total;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_items; e += (size_t)gridDim.x * blockDim.x) {
+        if (e >= 2 * (size_t)per_role) {
+            const size_t p = e - 2 * (size_t)per_role;
+            auto in = [&](size_t base, size_t n) { return p >= base && p < base + n; };
+            const bool used = in(o.W1, (size_t)I * HID) || in(o.b1, HID) || in(o.W2, HID * HID) || in(o.b2, HID) ||
+                              in(o.W3, (size_t)HID * O) || in(o.b3, O) || in(o.V1, (size_t)I * HID) ||
+                              in(o.c1, HID) || in(o.V2, HID * HID) || in(o.c2, HID) || in(o.V3, HID) || in(o.c3, 1);
+            if (!used) grad[p] = 0.0f;
+            continue;
         }
-        float s = 0.0f;
-        if (lane >= 0) {
-            const int c0 = act ? 0 : n_actor, c1 = act ? n_actor : n_actor + n_critic;
-            for (int c = c0; c < c1; ++c) s += partial[((size_t)c * BM + lane) * PC + col];
-        }
-        grad[p] = s;
+        const bool act = e < (size_t)per_role;
+        const int le = (int)(act ? e : e - per_role);
+        const int lane = le / PC, col = le % PC;
+        long long p = -1;
+        if (col < I) p = (long long)(act ? o.W1 : o.V1) + (long long)col * HID + lane;
+        else if (col == I) p = (long long)(act ? o.b1 : o.c1) + lane;
+        else if (col >= (int)C_W2 && col < (int)C_W2 + HID) p = (long long)(act ? o.W2 : o.V2) + (long long)(col - C_W2) * HID + lane;
+        else if (col == (int)(act ? C_B2 : C_C2)) p = (long long)(act ? o.b2 : o.c2) + lane;
+        else if (act && col >= (int)C_W3 && col < (int)C_W3 + O) p = (long long)o.W3 + (long long)lane * O + (col - C_W3);
+        else if (act && col >= (int)C_B3 && col < (int)C_B3 + O && lane == 0) p = (long long)o.b3 + (col - C_B3);
+        else if (!act && col == (int)C_V3) p = (long long)o.V3 + lane;
+        else if (!act && col == (int)C_C3 && lane == 0) p = (long long)o.c3;
+        if (p < 0) continue;
+        const int c0 = act ? 0 : n_actor, c1 = act ? n_actor : n_actor + n_critic;
+        float sum = 0.0f;
+#pragma unroll 8
+        for (int c = c0; c < c1; ++c) sum += partial[(size_t)c * per_role + le];
+        grad[p] = sum;
     }
 }
 
@@ -1040,7 +1049,7 @@ ej_status launch_ppo_bf16(const FbArgs& fa, float* partial, size_t partial_bytes
     else ppo_bf16_kernel<64><<<n_act + n_cri, BT, smem, s>>>(P);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "bf16 PPO launch: %s", cudaGetErrorString(err));
-    ppo_bf16_reduce_kernel<<<128, 256, 0, s>>>(partial, n_act, n_cri, fa.in_dim, fa.O, grad);
+    ppo_bf16_reduce_kernel<<<sm_count() * 4, 256, 0, s>>>(partial, n_act, n_cri, fa.in_dim, fa.O, grad);
     err = cudaGetLastError();
     if (err != cudaSuccess) return fail(EJ_ERR_CUDA, "bf16 PPO reduce launch: %s", cudaGetErrorString(err));
     return EJ_OK;
