@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(BT, 1) policy_bf16_fast_kernel(PolicyArgs a) {
 // Each CTA serves one network in one role (actor or critic): it packs that
 // network's weights once and then takes that network's tiles PP_NWG at a time.
 
-constexpr int PP_NWG = 3;       // tile pipelines per CTA
+constexpr int PP_NWG = 4;       // tile pipelines per CTA
 constexpr int PP_MAX_O = 96;    // logits: the head operand [N3][H] fits beside three pipelines
 constexpr int PP_SCR = 64;      // exp weights a thread keeps in shared memory per head
 // Cost of a tile in thousands of SM cycles, measured with clock64 stamps per
@@ -605,7 +605,7 @@ constexpr int PP_SCR = 64;      // exp weights a thread keeps in shared memory p
 constexpr double PP_CRITIC_TILE = 12.0, PP_ACTOR_TILE = 13.0, PP_ACTOR_GROUP = 2.2;
 
 struct PpLayout {
-    uint32_t w1, w2, w3, x[PP_NWG], h[PP_NWG], bias, total;
+    uint32_t w1, w2, w3, h[PP_NWG], bias, total;
 };
 
 __host__ __device__ inline PpLayout pp_layout(int H, int n3_max) {
@@ -614,7 +614,9 @@ __host__ __device__ inline PpLayout pp_layout(int H, int n3_max) {
     L.w1 = b; b += (uint32_t)H * KX * 2;                        // [H][KX]
     L.w2 = b; b += (uint32_t)H * H * 2;                         // [H][H]
     L.w3 = b; b += (uint32_t)(n3_max > 16 ? n3_max : 16) * H * 2;   // [N3][H] (actor) or [16][H] (critic)
-    for (int w = 0; w < PP_NWG; ++w) { L.x[w] = b; b += BM * KX * 2; }
+    // a pipeline's observation operand [BM][K1 <= 32] is the second 64-column
+    // panel of its hidden operand: free from the tile's start until the
+    // layer-1 product has read it (the first panel stages the floats)
     for (int w = 0; w < PP_NWG; ++w) { L.h[w] = b; b += (uint32_t)BM * H * 2; }
     L.bias = b; b += ((2u * H + (uint32_t)n3_max + 4) * 4 + 1023) & ~1023u;   // layer 1 | layer 2 | head (to N3)
     L.total = b;
@@ -858,7 +860,6 @@ __global__ void __launch_bounds__(128 * PP_NWG, 1) policy_bf16_pp_kernel(const _
         else v = k == 2 * H ? w[off.c3] : 0.0f;
         bias[k] = v;
     }
-    for (int k = tid; k < NWG * BM * KX * 2 / 16; k += NTH) st_shared_v4(smem + L.x[0] + k * 16, 0u, 0u, 0u, 0u);
     if (tid == 0) {
         for (int q = 0; q < NWG; ++q) mbar_init(&bars[q], 1);
         fence_mbar_init();
@@ -867,8 +868,9 @@ __global__ void __launch_bounds__(128 * PP_NWG, 1) policy_bf16_pp_kernel(const _
     sync_for_mma();
     const uint32_t tcol = tmem_slot + (uint32_t)wg * 128u;                   // this pipeline's columns
     const uint32_t lane_base = tcol + ((uint32_t)(quarter * 32) << 16);
-    uint8_t* xb = smem + L.x[wg];
     uint8_t* hb = smem + L.h[wg];
+    uint8_t* xb = hb + BM * 64 * 2;                     // the hidden operand's second panel
+    const int K1 = (I + 15) & ~15;                      // layer-1 K: the inputs rounded up to an MMA step
     float* scr = reinterpret_cast<float*>(hb) + wtid;   // sampler scratch: the hidden operand is free after layer 3
     const uint32_t sx = smem_u32(xb), sh = smem_u32(hb);
     const uint32_t sw1 = smem_u32(smem + L.w1), sw2 = smem_u32(smem + L.w2), sw3 = smem_u32(smem + L.w3);
@@ -908,9 +910,9 @@ __global__ void __launch_bounds__(128 * PP_NWG, 1) policy_bf16_pp_kernel(const _
         }
     };
     // observations -> BF16 operand: the prefetched floats go row-major into the
-    // hidden operand's buffer (free at the start of a tile), then each thread
-    // converts its own row in 16-byte chunks (columns I.. of the last chunk
-    // are zero; the chunks after it stay zero from the start)
+    // hidden operand's first panel (free at the start of a tile), then each
+    // thread converts its own row in 16-byte chunks up to K1 (columns I.. are
+    // zero) into the second panel
     auto store_obs = [&]() {
         float* stage = reinterpret_cast<float*>(hb);
         wg_bar(bar_id);                        // every warp is done with the last tile's sampler scratch
@@ -929,7 +931,7 @@ __global__ void __launch_bounds__(128 * PP_NWG, 1) policy_bf16_pp_kernel(const _
         wg_bar(bar_id);
         const float* srow = stage + row_in_tile * I;
 #pragma unroll 1
-        for (int c8 = 0; c8 < I; c8 += 8) {
+        for (int c8 = 0; c8 < K1; c8 += 8) {
             float f8[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) f8[j] = c8 + j < I ? srow[c8 + j] : 0.0f;
@@ -969,7 +971,7 @@ __global__ void __launch_bounds__(128 * PP_NWG, 1) policy_bf16_pp_kernel(const _
         const bool live = row_in_tile < nrows;
         wg_sync_for_mma(bar_id);
         if (wtid == 0) {
-            mma_chain(tcol, sx, BM, sw1, H, KX, idesc_bf16(BM, H));
+            mma_chain(tcol, sx, BM, sw1, H, K1, idesc_bf16(BM, H));
             mma_commit(bar);
         }
         // the sampler's mask words and uniforms: their loads overlap the products
