@@ -293,9 +293,10 @@ ej_status ej_net_floats(const EjParams* p, int32_t net, int32_t hidden, uint64_t
  * networks of Section 5) with at most 64 inputs and 64 logits (a tile is
  * shared by the two CTAs of a thread-block cluster, each holding half of the
  * second layer's weights); other shapes return EJ_ERR_UNSUPPORTED (FP32 takes
- * them).  FP32 takes every shape: its 32-row tile (inputs, two hidden-width
- * buffers, logits twice) fits shared memory up to hidden 256 with the largest
- * market (123 inputs, 242 logits). */
+ * them).  FP32 takes every shape: 64-row tiles (inputs, two hidden-width
+ * buffers, logits twice) where they fit shared memory, 32-row tiles otherwise
+ * (which fit up to hidden 256 with the largest market: 123 inputs, 242
+ * logits). */
 ej_status policy_forward(const EjParams* p, const void* state, int32_t net, int32_t hidden,
                          int32_t precision, const float* weights, const float* obs,
                          const uint32_t* mask, const float* u, int32_t* act, float* logp,
