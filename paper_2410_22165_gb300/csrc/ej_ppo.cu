@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(NTH, 2) wgrad_kernel(WgJobs jobs, int rows, in
 }
 
 size_t wgrad_smem() {
-    // two stages; the slice sums (at most (NTH - 1) / 2 ... NTH threads x 64) fit in them
+    // two staging buffers; the slice sums reuse them (slices 1.. of at most NTH threads, 64 floats each)
     const size_t stages = sizeof(float) * 2 * WG_STAGE;
     const size_t red = sizeof(float) * (size_t)NTH * 64;
     return stages > red ? stages : red;
