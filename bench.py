@@ -889,6 +889,30 @@ def run_profile_case(args):
             res[prec] = {"update_ms": ms}
         print(json.dumps({"profile_case": "ppo E=256 A=100 T=32", **res}))
         return
+    if args.profile_case == "ppo4":
+        # the PPO configuration's BF16 update: a 128-step rollout of 2048
+        # environments, then timed updates (4 epochs x 8 minibatches)
+        import synth
+        from paper_2410_22165_gb300 import PPO, Policy, Rollout
+        env = VecEnv(2048, A, device="cuda", T_ep=T_EP, T_tax=T_TAX)
+        pw = torch.from_numpy(synth.net_weights(7, 0, env.D, 128, env.nA))
+        gw = torch.from_numpy(synth.net_weights(7, 1, env.G, 128, env.p.nb * env.p.tax_levels))
+        pol = Policy(env, pw, gw, hidden=128, precision="bf16")
+        ro = Rollout(env, pol, 128)
+        ro.reset(seed=7)
+        ro.run()
+        ppo = PPO(pol, 128, precision="bf16")
+        ms = []
+        for k in range(args.warmup + args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ppo.update(ro)
+            b.record()
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                ms.append(a.elapsed_time(b))
+        print(json.dumps({"profile_case": "ppo E=2048 A=100 T=128 bf16", "update_ms": ms}))
+        return
 
     n = 100
     env = VecEnv(E, A, device="cuda", T_ep=T_EP, T_tax=T_TAX)
@@ -912,7 +936,7 @@ def run_profile_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-case", nargs="?", const="env", default=None, choices=["env", "env1", "policy", "policy256", "ppo"])
+    ap.add_argument("--profile-case", nargs="?", const="env", default=None, choices=["env", "env1", "policy", "policy256", "ppo", "ppo4"])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
