@@ -148,9 +148,10 @@ def test_ragged_populations_and_tight_limits():
         _check_state(env, o, e, A_e)
 
 
-@pytest.mark.parametrize("A", [33, 64, 200, 700])
+@pytest.mark.parametrize("A", [33, 64, 200, 700, 1024])
 def test_other_cta_sizes(A):
-    """Every CTA size the library instantiates (64 .. 1024 threads)."""
+    """Every CTA size the library instantiates (64 .. 1024 threads), up to
+    the largest population (1024 agents)."""
     kw = dict(T_ep=50, T_tax=10)
     env = VecEnv(2, A, **kw)
     T = 60
@@ -174,6 +175,10 @@ def test_other_cta_sizes(A):
     dict(R=4, P=3, price_ticks=[1, 2, 3], price_tick=3.0, Rd=2, gov_enabled=0, skill_gain=0.005, skill_init=1),
     dict(R=12, P=3, price_ticks=[1, 2, 3], price_tick=3.0, Rd=3, gov_enabled=0, skill_gain=0.005, skill_init=1),
     dict(skill_gain=0.2, skill_max=1.5, skill_init=1),         # fast growth: skills reach the cap
+    # the largest action spaces: 16 resources at 7 levels (242 actions, 8 mask
+    # words, 224 book levels) and the most price levels (32: 132 actions)
+    dict(R=16, P=7, price_ticks=[1, 2, 3, 4, 5, 6, 7], price_tick=3.0, Rd=3),
+    dict(P=32, price_ticks=list(range(1, 33)), price_tick=0.5),
 ])
 def test_parameter_variants(variant):
     kw = dict(T_ep=45, T_tax=8, **variant)
