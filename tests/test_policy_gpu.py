@@ -271,6 +271,14 @@ def test_section5_networks_of_256_units_fp32(R, Rd):
                                          gov_enabled=0, skill_gain=0.005, skill_init=1))
 
 
+@pytest.mark.parametrize("hidden", [32, 96])
+def test_fp32_forward_small_and_odd_widths(hidden):
+    """The smallest hidden width (32) and one that is not a power of two
+    (96: three warp tiles across the columns), FP32 forward and sampling
+    against the oracle."""
+    _forward_vs_oracle("fp32", hidden, {})
+
+
 def test_largest_market_fp32_hidden_256():
     """The largest market under 256 actions (16 resources at 7 price levels:
     123 inputs, 242 logits, 8 mask words) at hidden 256: the FP32 forward's

@@ -164,15 +164,16 @@ MARKETS = {
 }
 
 
-@pytest.mark.parametrize("net,market", [(0, "r4"), (1, "r4"), (0, "r16")])
-def test_section5_hidden256_gradient_matches_float64(net, market):
-    """Section 5's networks of 256 units: the float32 minibatch gradient
-    against the float64 oracle, every parameter tensor, within 1e-3 of the
-    tensor's largest entry, on minibatches of 60 to 80 rows (two or three
-    32-row tiles, the last one ragged; the weight-gradient kernel spans 2 x 2
+@pytest.mark.parametrize("net,market,H2", [(0, "r4", 256), (1, "r4", 256), (0, "r16", 256),
+                                           (0, "r4", 32), (1, "r4", 96), (0, "r16", 96)])
+def test_fp32_gradient_widths_match_float64(net, market, H2):
+    """Section 5's networks of 256 units, the smallest width (32) and one
+    that is not a power of two (96): the float32 minibatch gradient against
+    the float64 oracle, every parameter tensor, within 1e-3 of the tensor's
+    largest entry, on minibatches of 60 to 80 rows (two or three 32-row
+    tiles, the last one ragged; at 256 the weight-gradient kernel spans 2 x 2
     output tiles of 128)."""
     import paper_2410_22165_gb300 as P
-    H2 = 256
     kw = MARKETS[market]
     E, A, T = (3, 5, 16) if net == 0 else (15, 4, 16)
     env = P.VecEnv(E, A, **kw)
