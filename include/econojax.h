@@ -428,7 +428,8 @@ typedef struct {
     float lr;            /* Adam learning rate (5e-4; the caller anneals it) */
     float beta1, beta2, eps;   /* Adam (0.9, 0.999, 1e-5) */
     int32_t epochs;      /* 4 */
-    int32_t minibatches; /* 8 */
+    int32_t minibatches; /* 8; at most T x E, so that every minibatch of the
+                          * government network holds a row (EJ_ERR_ARG otherwise) */
     uint64_t seed;       /* key of the minibatch shuffles */
 } EjPpoParams;
 

@@ -94,6 +94,8 @@ extern "C" ej_status ppo_minibatch_grad_static(const EjParams* p, const EjPpoPar
     if (in > 128 || O > 128) return fail(EJ_ERR_UNSUPPORTED, "inputs and logits must be <= 128");
     const int rows_per_step = pop ? kp.E * kp.A : kp.E;
     const uint64_t N = (uint64_t)T * rows_per_step;
+    if ((uint64_t)pp->minibatches > N)
+        return fail(EJ_ERR_ARG, "%d minibatches exceed the network's %llu rows", pp->minibatches, (unsigned long long)N);
     const uint64_t count_max = (N + pp->minibatches - 1) / pp->minibatches;
     const uint64_t row_floats = in + 8ull * H + O + 1;
     // scratch layout: adv, ret, stats, transposed weights, per-row buffers, partials

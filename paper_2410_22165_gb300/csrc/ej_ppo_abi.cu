@@ -103,6 +103,11 @@ ej_status check_common(const EjParams* p, const EjPpoParams* pp, int T, int H, L
     if (!pp) return fail(EJ_ERR_ARG, "ppo params is NULL");
     if (T < 1) return fail(EJ_ERR_ARG, "T must be >= 1");
     if (pp->minibatches < 1 || pp->epochs < 1) return fail(EJ_ERR_ARG, "epochs and minibatches must be >= 1");
+    // every minibatch of every network holds at least one row (the government
+    // network has the fewest: T x E)
+    if ((uint64_t)pp->minibatches > (uint64_t)T * (uint64_t)kp->E)
+        return fail(EJ_ERR_ARG, "%d minibatches exceed the government network's %llu rows (T x E)", pp->minibatches,
+                    (unsigned long long)T * (unsigned long long)kp->E);
     if (H < 32 || H > 256 || H % 32) return fail(EJ_ERR_UNSUPPORTED, "PPO update supports hidden 32 .. 256 in steps of 32");
     if (kp->nb * p->tax_levels > 128 || kp->nA > 128 || kp->D > 128 || kp->G > 128)
         return fail(EJ_ERR_UNSUPPORTED, "PPO update needs inputs and logits <= 128");

@@ -234,6 +234,20 @@ def test_step_host_argument_checks(lib):
     assert lib.env_step_host(*args(fake, 1 << 40, gu=fake)) == 1
 
 
+def test_ppo_minibatches_need_rows(lib):
+    """More minibatches than the government network's T x E rows would leave
+    some empty: refused on the host (EJ_ERR_ARG) by every PPO entry point,
+    starting with the workspace query."""
+    pp = N.EjPpoParams()
+    lib.ej_ppo_params_default(C.byref(pp))
+    p = N.make_params(E=2, A=4)
+    nb = C.c_uint64()
+    pp.minibatches = 8
+    assert lib.ej_ppo_workspace_bytes(C.byref(p), C.byref(pp), 4, 128, C.byref(nb)) == 0       # 8 rows
+    assert lib.ej_ppo_workspace_bytes(C.byref(p), C.byref(pp), 3, 128, C.byref(nb)) == 1       # 6 rows
+    assert b"minibatches" in lib.ej_last_error()
+
+
 def test_ppo_hidden_limits(lib):
     """Hidden widths: multiples of 32 up to 256 size a workspace; the BF16
     gradient takes hidden 128 only: refused on the host (EJ_ERR_UNSUPPORTED)."""
