@@ -595,7 +595,7 @@ __global__ void __launch_bounds__(BT, 1) policy_bf16_fast_kernel(PolicyArgs a) {
 // network's weights once and then takes that network's tiles PP_NWG at a time.
 
 constexpr int PP_NWG = 4;       // tile pipelines per CTA
-constexpr int PP_MAX_O = 96;    // logits: the head operand [N3][H] fits beside three pipelines
+constexpr int PP_MAX_O = 96;    // logits: the head operand [N3][H] fits beside four pipelines
 constexpr int PP_SCR = 64;      // exp weights a thread keeps in shared memory per head
 // Cost of a tile in thousands of SM cycles, measured with clock64 stamps per
 // phase on GB300 (hidden 128, three pipelines per CTA): the critic's tile
