@@ -216,7 +216,9 @@ constexpr int NTH = 256;       // threads per CTA
 
 // Visits (r, c) for r < ROWS, c < ncols (ncols <= NTH): thread t takes
 // column t % ncols of rows t / ncols, t / ncols + NTH / ncols, ... (one
-// division per call rather than per element).
+// division per call rather than per element).  Every caller passes at most
+// NTH columns: padded inputs (at most 124: 16 resources), hidden widths (at
+// most 256) or a quarter of them, logits (at most 128 in the PPO kernels).
 template <int ROWS, class F>
 __device__ __forceinline__ void tile_for(int ncols, F&& f) {
     const int per = NTH / ncols, r0 = (int)threadIdx.x / ncols;
